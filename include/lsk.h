@@ -1,0 +1,205 @@
+/*
+ * lsk.h -- C ABI of the GB300 sketching library (liblsk.so).
+ *
+ * Randomised sketching kernels for tall-and-skinny matrices after
+ * Sobczyk & Gallopoulos, "pylspack: Parallel algorithms and data structures
+ * for sketching, column subset selection, regression and leverage scores"
+ * (arXiv 2203.02798).  Section, definition and algorithm numbers below refer
+ * to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns LSK_OK (0) or a negative LSK_ERR_* code; on error
+ *    lsk_error_string(ctx) holds a one-line description.  Argument errors are
+ *    detected on the host before anything is launched.
+ *  - Calls are asynchronous on the context's CUDA stream (lsk_set_stream).
+ *    Errors found on the device (a rank-deficient sketch, an out-of-range
+ *    CSR index, a wait that timed out) set a device flag; lsk_sync()
+ *    synchronises the stream and returns that error (and clears the flag).
+ *    lsk_sketch_precondition_lsq is the exception: it synchronises itself.
+ *  - All matrix and vector pointers are DEVICE pointers owned by the caller.
+ *    The library never frees them and keeps no reference after the call
+ *    returns.  Inputs are const; outputs have the documented sizes.
+ *  - Scratch memory comes from a workspace owned by the context, grown on
+ *    demand (stream-ordered cudaMallocAsync) and freed by lsk_destroy.
+ *  - Dense matrices are row-major (C_CONTIGUOUS, Sec. 2.1 and Sec. 5) with a
+ *    row stride ld >= d (in elements).  CSR matrices (Sec. 1.3: V, J, I) are
+ *    0-based with int64 row pointers and int32 column indices; column
+ *    indices must lie in [0, d).  Values are float32.
+ *  - Random draws are a pure function of (seed, index) through
+ *    Philox-4x32-10 (Salmon et al., SC'11), so results do not depend on the
+ *    launch configuration:
+ *      CountSketch (Def. 3): w = Philox(ctr=(i_lo, i_hi, 0, 0), key=seed),
+ *        h(i) = (w0 * r) >> 32,  sigma_i = (w1 >> 31) ? -1 : +1.
+ *      Gaussian G (Alg. 3, csrcgs scaling 1/sqrt(k)): column c, row j:
+ *        w = Philox(ctr=(c_lo, c_hi, 1, j >> 2), key=seed), the pair
+ *        (w_{2p}, w_{2p+1}) with p = (j >> 1) & 1 feeds Box-Muller,
+ *        u1 = (a + 1) 2^-32, u2 = b 2^-32, z = sqrt(-2 ln u1) cos(2 pi u2)
+ *        for even j, sin(...) for odd j;  G[j, c] = z / sqrt(k)
+ *        (rounded to bfloat16, nearest-even, in LSK_PREC_BF16).
+ */
+#ifndef LSK_H
+#define LSK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LSK_OK                   0
+#define LSK_ERR_INVALID_ARG     -1  /* bad size, null pointer, bad enum      */
+#define LSK_ERR_BAD_CSR         -2  /* rowptr not monotone / colidx >= d     */
+#define LSK_ERR_UNSUPPORTED     -3  /* dtype or size this build does not run */
+#define LSK_ERR_RANK_DEFICIENT  -4  /* sketch R has a (near-)zero pivot      */
+#define LSK_ERR_NOT_CONVERGED   -5  /* least squares did not reach its tol   */
+#define LSK_ERR_OOM             -6  /* workspace allocation failed           */
+#define LSK_ERR_TIMEOUT         -7  /* a bounded device-side wait gave up    */
+#define LSK_ERR_CUDA            -8  /* a CUDA runtime call failed            */
+
+/* ---- matrix descriptor ------------------------------------------------- */
+#define LSK_DENSE 0
+#define LSK_CSR   1
+#define LSK_F32   0
+
+typedef struct lsk_mat {
+    int32_t kind;           /* LSK_DENSE or LSK_CSR                         */
+    int32_t dtype;          /* LSK_F32 (the only value type of this build)  */
+    int64_t n;              /* rows    (tall dimension)                     */
+    int64_t d;              /* columns (skinny dimension)                   */
+    int64_t ld;             /* dense: row stride in elements, >= d          */
+    const void* values;     /* dense: n*ld floats; CSR: nnz floats (V)      */
+    const int64_t* rowptr;  /* CSR: n+1 entries (I), rowptr[0] == 0         */
+    const int32_t* colidx;  /* CSR: nnz entries (J), each in [0, d)         */
+    int64_t nnz;            /* CSR: number of stored entries                */
+} lsk_mat;
+
+/* precision of the contractions (Gaussian stage, row-norm GEMM) */
+#define LSK_PREC_FP32 0     /* plain FP32 on CUDA cores                     */
+#define LSK_PREC_TF32 1     /* reserved (accepted, runs as LSK_PREC_FP32)    */
+#define LSK_PREC_BF16 2     /* tensor cores: BF16 G, split-BF16 operands,   */
+                            /* FP32 accumulation                            */
+
+typedef struct lsk_ctx lsk_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+/* Create a context on CUDA device `device`, launching on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle, owned by the caller until lsk_destroy. */
+int lsk_create(lsk_ctx** ctx, int device, void* stream);
+/* Free the context and its workspace (synchronises its stream first). */
+int lsk_destroy(lsk_ctx* ctx);
+/* Change the stream later calls launch on. */
+int lsk_set_stream(lsk_ctx* ctx, void* stream);
+/* Synchronise the stream; return (and clear) any deferred device error. */
+int lsk_sync(lsk_ctx* ctx);
+/* Detail of the last error on this context (never NULL). */
+const char* lsk_error_string(const lsk_ctx* ctx);
+/* Bytes currently held by the context's workspace. */
+size_t lsk_workspace_bytes(const lsk_ctx* ctx);
+/* Grow the workspace to at least `bytes` now (so later calls allocate
+ * nothing, e.g. before stream capture). */
+int lsk_reserve(lsk_ctx* ctx, size_t bytes);
+
+/* ---- the sketching path ------------------------------------------------ */
+
+/* CountSketch S*A (Def. 3, Alg. 2; the library call csrcgs / rmcgs with
+ * m = 0, Sec. 5).  S is r x n with one +-1 per column (hash and signs from
+ * `seed`, see the header comment).  A: dense or CSR, n x d.  SA: device,
+ * r*d floats, row-major, fully overwritten (rows no row of A hashes to are
+ * zero).  Requires 1 <= r < 2^31, n < 2^31. */
+int lsk_cs_sketch(lsk_ctx* ctx, const lsk_mat* A, int64_t r, uint64_t seed,
+                  float* SA);
+
+/* Gaussian stage of CountGauss (Alg. 3; csrcgs / rmcgs with m = k, Sec. 5):
+ * GSA = G * SA with G k x r, N(0,1) entries scaled by 1/sqrt(k) (header
+ * comment).  SA: device r*d floats row-major; GSA: device k*d floats
+ * row-major, overwritten.  prec: LSK_PREC_FP32 or LSK_PREC_BF16 (G exact in
+ * bfloat16, SA split into two bfloat16 terms, FP32 accumulation). */
+int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
+                     int64_t k, uint64_t seed, int32_t prec, float* GSA);
+
+/* Gram matrix C <- alpha * A^T A + beta * C (csrrk, Sec. 5; Alg. 5 and
+ * Alg. 7 for CSR A; the same operation for dense A).  C: device d*d floats
+ * row-major, read when beta != 0 and overwritten.  Products are FP32,
+ * partial sums are folded into FP64 before the final FP32 store. */
+int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
+             float* C);
+
+/* Squared row norms x <- alpha * diag(A B B^T A^T) + beta * x (csrsqn /
+ * rmsqn, Sec. 5; Alg. 8 for CSR A).  B: device d*c floats row-major.
+ * x: device n floats, read when beta != 0.  A*B is never stored.
+ * `upper_triangular` != 0 promises B[i][j] == 0 for i > j (c == d), which
+ * lets the dense kernel skip the zero blocks. */
+int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B,
+                      int64_t c, double alpha, double beta,
+                      int32_t upper_triangular, float* x);
+
+/* R of the sketch (Alg. 12 step 2 / Alg. 15 step 3 with a QR in place of
+ * the SVD): B = GSA (k x d floats, device, row-major, k >= d) -> R (d x d,
+ * upper triangular, R_jj > 0) and R^-1, both FP64 row-major on the device.
+ * Computed in FP64 as the Cholesky factor of B^T B (identical to the
+ * sign-normalised Householder R in exact arithmetic).  Rank deficiency
+ * (a pivot <= 0 or min R_jj <= 16 eps64 d max R_jj) sets the deferred
+ * LSK_ERR_RANK_DEFICIENT.  Either output may be NULL. */
+int lsk_sketch_qr(lsk_ctx* ctx, const float* B, int64_t k, int64_t d,
+                  double* R, double* Rinv);
+
+/* Leverage-score estimates (Alg. 15 without the right Gaussian Pi):
+ * sketch A to k x d with r CountSketch rows and k Gaussian rows (k == 0:
+ * the r x d CountSketch alone, as m = 0 in csrcgs), R from the sketch as in
+ * lsk_sketch_qr, then ell_i = ||A_i R^-1||^2 (Alg. 8).  ell: device n
+ * floats.  R_out: NULL or device d*d doubles receiving R.  Requires the
+ * sketch to have at least d rows. */
+int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                        uint64_t seed, int32_t prec, float* ell,
+                        double* R_out);
+
+/* ---- sketch-and-precondition least squares (Alg. 12) ------------------- */
+typedef struct lsk_lsq_opts {
+    int64_t r;              /* CountSketch rows (e.g. d*d)                  */
+    int64_t k;              /* Gaussian rows (e.g. 2d; 0 = CountSketch only) */
+    uint64_t seed;
+    int32_t prec;           /* precision of the sketch (LSK_PREC_*)          */
+    int32_t max_iter;       /* LSQR iterations per refinement step           */
+    int32_t max_refine;     /* FP64 refinement steps                         */
+    double tol;             /* target eta = ||A^T(b-Ax)|| / ||A^T b||         */
+    double inner_tol;       /* LSQR stopping tolerance of each inner solve   */
+} lsk_lsq_opts;
+
+typedef struct lsk_lsq_info {
+    int32_t iters;          /* LSQR iterations in total                      */
+    int32_t refinements;    /* FP64 refinement steps taken                   */
+    double eta;             /* final normal-equation residual (FP64)         */
+    int32_t status;         /* LSK_OK or LSK_ERR_NOT_CONVERGED               */
+} lsk_lsq_info;
+
+/* Fill `opts` with defaults for a d-column problem (r = max(d*d, 4d),
+ * k = 2d, BF16 sketch, tol 1e-10). */
+void lsk_lsq_default_opts(lsk_lsq_opts* opts, int64_t d);
+
+/* Alg. 12: R from the sketch of A, N = R^-1, then LSQR (Paige & Saunders
+ * 1982) on min ||A N y - r_t|| with FP32 products, wrapped in FP64
+ * iterative refinement r_t = b - A x_t, x_{t+1} = x_t + N y, until
+ * eta <= opts->tol.  b: device n doubles; x: device d doubles (output).
+ * info may be NULL.  Synchronises the stream (it reads scalars back). */
+int lsk_sketch_precondition_lsq(lsk_ctx* ctx, const lsk_mat* A,
+                                const double* b, double* x,
+                                const lsk_lsq_opts* opts, lsk_lsq_info* info);
+
+/* ---- debug / test entry points ----------------------------------------- */
+/* The CountSketch hash of rows 0..n-1: bucket[i] = h(i), sign[i] = sigma_i
+ * (Def. 3, spec in the header comment).  Device outputs. */
+int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed,
+                   int32_t* bucket, int8_t* sign);
+/* The Gaussian matrix G (k x r floats, device, row-major) as used by
+ * lsk_gauss_sketch with the same precision mode. */
+int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed,
+                    int32_t prec, float* G);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSK_H */

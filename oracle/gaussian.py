@@ -1,0 +1,82 @@
+"""Gaussian sketch G and the product G*(S*A) (oracle; test infrastructure).
+
+Alg. 3 (Sec. 2.2.2) multiplies S*A by an m x r matrix G of i.i.d. N(0,1)
+entries; the library call csrcgs / rmcgs (Sec. 5) scales G by 1/sqrt(m).
+The reading used here keeps that scaling (m is called k below) and makes
+every entry a deterministic function of (seed, j, c) through Philox-4x32-10
+and the Box-Muller transform (Box & Muller 1958):
+
+    (w0, w1, w2, w3) = Philox4x32_10(ctr = (c mod 2^32, c >> 32, 1, j >> 2),
+                                     key = (seed mod 2^32, seed >> 32))
+    p = (j >> 1) & 1;  (a, b) = (w_{2p}, w_{2p+1})
+    u1 = (a + 1) / 2^32 in (0, 1],   u2 = b / 2^32 in [0, 1)
+    z  = sqrt(-2 ln u1) * cos(2 pi u2)   if j is even
+         sqrt(-2 ln u1) * sin(2 pi u2)   if j is odd
+    G[j, c] = z / sqrt(k)
+
+so one Philox call yields the four entries j = 4q..4q+3 of column c.
+In the BF16 precision mode G is *defined* as the bfloat16 value nearest
+(ties to even) to the float32 rounding of z / sqrt(k); that rounding is the
+one decision both the oracle and the GPU take in float32.
+"""
+import numpy as np
+
+from .philox import philox4x32_10, split_seed
+
+STREAM_G = 1
+
+PREC_FP32 = 0
+PREC_TF32 = 1
+PREC_BF16 = 2
+
+
+def float32_to_bf16_rne(x32):
+    """Round float32 values to bfloat16 (nearest, ties to even); returns float64."""
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    u = x32.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    rounded = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (rounded & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    return out.astype(np.float64)
+
+
+def gaussian_matrix(k, r, seed, prec=PREC_FP32):
+    """G (k x r, float64): z / sqrt(k), bfloat16-rounded in the BF16 mode."""
+    return gaussian_columns(k, 0, r, seed, prec)
+
+
+def gaussian_columns(k, c0, c1, seed, prec=PREC_FP32):
+    """Columns c0..c1-1 of G (k x (c1-c0), float64)."""
+    j = np.arange(k, dtype=np.uint64)[:, None]
+    c = np.arange(c0, c1, dtype=np.uint64)[None, :]
+    k0, k1 = split_seed(seed)
+    w = philox4x32_10(c & np.uint64(0xFFFFFFFF), c >> np.uint64(32), STREAM_G,
+                      j >> np.uint64(2), k0, k1)
+    p = ((j >> np.uint64(1)) & np.uint64(1)).astype(bool)
+    a = np.where(p, w[2], w[0]).astype(np.float64)
+    b = np.where(p, w[3], w[1]).astype(np.float64)
+    u1 = (a + 1.0) * 2.0**-32
+    u2 = b * 2.0**-32
+    rho = np.sqrt(-2.0 * np.log(u1))
+    even = (np.arange(k)[:, None] % 2) == 0
+    z = np.where(even, rho * np.cos(2.0 * np.pi * u2), rho * np.sin(2.0 * np.pi * u2))
+    g = z / np.sqrt(float(k))
+    if prec == PREC_BF16:
+        return float32_to_bf16_rne(g.astype(np.float32))
+    return g
+
+
+def gauss_sketch(SA, k, seed, prec=PREC_FP32, batch=4096):
+    """G * SA in float64 (Alg. 3).
+
+    As in Alg. 3, the r columns of G are taken in batches of ``batch``: each
+    batch of G is generated and C <- C + G_i B_i is accumulated, so G is never
+    held whole.  Batching changes only the float64 summation order.
+    """
+    SA = np.asarray(SA, dtype=np.float64)
+    r = SA.shape[0]
+    C = np.zeros((k, SA.shape[1]), dtype=np.float64)
+    for c0 in range(0, r, batch):
+        c1 = min(r, c0 + batch)
+        C += gaussian_columns(k, c0, c1, seed, prec) @ SA[c0:c1]
+    return C
