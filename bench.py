@@ -1,0 +1,310 @@
+"""Benchmark: leverage scores of a dense tall-skinny matrix on GB300.
+
+Workload (one "step" = one pass of the whole sketching hot path):
+  A: 4,000,000 x 256 float32 (4.1 GB), A_ij = z_ij * 10^u_j, z ~ N(0,1),
+     u_j ~ U(-3, 3);  CountSketch r = 65,536;  Gaussian k = 512 (BF16 tensor
+     stage, FP32 accumulation);  FP64 R of the 512 x 256 sketch;  row norms
+     ell_i = ||A_i R^-1||^2.
+  metric: A-bytes per second through lsk_leverage_scores ("A GB/s sketched
+  and scored"); the input (4.1 GB) is larger than L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded row sample of the same workload instead (no GPU work).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_ROWS, D, R_SKETCH, K_GAUSS, SEED, DATA_SEED = 4_000_000, 256, 65_536, 512, 2, 2
+METRIC = "A GB/s sketched+scored (leverage scores, dense 4M x 256 FP32)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[6:10]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15]
+        use = inside if inside else rows[-3:]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+
+# ------------------------------------------------------------------ oracle --
+def oracle_sample(n_sample):
+    """Time the FP64 oracle's leverage pipeline on the first n_sample rows."""
+    from oracle import gaussian as oga
+    from oracle import leverage as olev
+    A = workloads.dense_colscaled(n=n_sample, d=D, seed=DATA_SEED)
+    t = time.perf_counter()
+    olev.leverage_scores_dense(A, R_SKETCH, K_GAUSS, SEED, oga.PREC_BF16)
+    dt = time.perf_counter() - t
+    return A.nbytes, dt
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_s = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_sample(n_s)
+    times, nbytes = [], 0
+    for _ in range(args.steps):
+        nbytes, dt = oracle_sample(n_s)
+        times.append(dt)
+    tot = sum(times)
+    value = nbytes * len(times) / tot / 1e9
+    sample = (f"first {n_s} rows of the {N_ROWS} x {D} workload per step (r={R_SKETCH}, k={K_GAUSS}); "
+              f"FP64 numpy oracle, BLAS steps multithreaded, scatter single-threaded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def workload_config(args):
+    return {"workload": "dense_colscaled_leverage", "n": N_ROWS, "d": D, "r": R_SKETCH, "k": K_GAUSS,
+            "prec": args.prec, "input_bytes": N_ROWS * D * 4, "l2_policy": "input 4.1 GB > L2 (no flush)",
+            "parallelism": f"replicas{args.gpus}"}
+
+
+# ---------------------------------------------------------------- GPU path --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--ref-rows", type=int, default=65_536)
+    ap.add_argument("--cpu-rows", type=int, default=262_144)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2203_02798_gb300 import build as lskbuild
+    lskbuild.build()
+    import paper_2203_02798_gb300 as lsk
+
+    hbm, bf16_peak, sm_max, peak_kind = peaks()
+    # inputs: pinned host copy (for e2e) and the device copy
+    A_host = torch.empty((N_ROWS, D), dtype=torch.float32, pin_memory=True)
+    workloads.dense_colscaled(n=N_ROWS, d=D, seed=DATA_SEED, out=A_host.numpy())
+    A = A_host.cuda()
+    ell = torch.empty(N_ROWS, dtype=torch.float32, device="cuda")
+    ctx = lsk.context()
+    st = torch.cuda.current_stream()
+
+    def step(prec):
+        lsk.leverage_scores(A, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, t0, t1
+
+    for _ in range(max(3, args.warmup)):
+        step(args.prec)
+    ctx.sync()
+
+    # main timed region (per-kernel events on, clocks sampled)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile(True)
+    ctx.profile_reset()
+    ms, t0, t1 = timed(lambda: step(args.prec), args.steps)
+    ctx.profile(False)
+    clk = clocks.stop(t0, t1)
+    ctx.sync()
+    kern = ctx.profile_totals()
+    ms_step = ms / args.steps
+    a_bytes = N_ROWS * D * 4
+    value = world * a_bytes / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel
+    top = max(kern.items(), key=lambda kv: kv[1][1]) if kern else ("none", (1, 0.0))
+    name, (launches, tot_ms) = top
+    per_launch_ms = tot_ms / max(launches, 1)
+    algo = algorithmic_work(name)
+    if algo["bound"] == "hbm":
+        achieved = algo["bytes"] / (per_launch_ms * 1e-3) / 1e9
+        peak, unit = hbm, "GB/s"
+    elif algo["bound"] == "tensor":
+        achieved = algo["flops"] / (per_launch_ms * 1e-3) / 1e12
+        peak, unit = bf16_peak, "TFLOP/s"
+    else:
+        achieved = algo["flops"] / (per_launch_ms * 1e-3) / 1e12
+        peak, unit = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s"
+    roofline = {"kernel": name, "bound": algo["bound"], "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind if algo["bound"] != "alu"
+                else "152 SMs x 128 FP32 lanes x 2 x max SM clock", "per_launch_ms": per_launch_ms,
+                "algorithmic": algo["bytes"] if algo["bound"] == "hbm" else algo["flops"]}
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                   "share": v[1] / max(sum(x[1] for x in kern.values()), 1e-9)} for k, v in kern.items()}
+    gpu_launches = int(sum(v[0] for v in kern.values()))
+
+    # the plain FP32 single-problem path on the same GPU
+    plain = None
+    if not args.no_plain and args.prec != "fp32":
+        for _ in range(2):
+            step("fp32")
+        pms, _, _ = timed(lambda: step("fp32"), max(3, args.steps // 5))
+        pms /= max(3, args.steps // 5)
+        plain = {"value": world * a_bytes / (pms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": pms}
+
+    # end to end through the public API with host buffers
+    ell_host = torch.empty(N_ROWS, dtype=torch.float32, pin_memory=True)
+
+    def e2e_step():
+        A.copy_(A_host, non_blocking=True)
+        step(args.prec)
+        ell_host.copy_(ell, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_step()
+    ems, _, _ = timed(e2e_step, e2e_steps)
+    ems /= e2e_steps
+    e2e = {"value": world * a_bytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+           "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": N_ROWS * 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nb, dt = oracle_sample(args.cpu_rows)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": cores(), "kind": "oracle",
+               "sample": f"first {args.cpu_rows} rows of the workload (r={R_SKETCH}, k={K_GAUSS}), "
+                         f"one run, {dt:.1f} s; FP64 numpy, BLAS multithreaded"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+fp32+f64" if args.prec == "bf16" else "f32+f64",
+            "data": "synthetic", "config": workload_config(args),
+            "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
+            "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
+            "plain_fp32": plain, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def algorithmic_work(kernel):
+    """Algorithmic bytes / flops of one launch of `kernel` on this workload."""
+    n, d, r, k = N_ROWS, D, R_SKETCH, K_GAUSS
+    a_bytes = n * d * 4
+    table = {
+        "cs_dense_gather": {"bound": "hbm", "bytes": a_bytes + 4 * r * d},
+        "rownorm_dense_simt": {"bound": "alu", "flops": n * d * (d + 1)},
+        "rownorm_dense_tc": {"bound": "hbm", "bytes": a_bytes + 4 * n},
+        "gauss_simt": {"bound": "alu", "flops": 2 * k * r * d},
+        "gauss_tc": {"bound": "tensor", "flops": 2 * 2 * k * r * d},
+    }
+    return table.get(kernel, {"bound": "hbm", "bytes": a_bytes})
+
+
+if __name__ == "__main__":
+    main()

@@ -33,8 +33,9 @@
  *        h(i) = (w0 * r) >> 32,  sigma_i = (w1 >> 31) ? -1 : +1.
  *      Gaussian G (Alg. 3, csrcgs scaling 1/sqrt(k)): column c, row j:
  *        w = Philox(ctr=(c_lo, c_hi, 1, j >> 2), key=seed), the pair
- *        (w_{2p}, w_{2p+1}) with p = (j >> 1) & 1 feeds Box-Muller,
- *        u1 = (a + 1) 2^-32, u2 = b 2^-32, z = sqrt(-2 ln u1) cos(2 pi u2)
+ *        (a, b) = (w_{2p} >> 8, w_{2p+1} >> 8) with p = (j >> 1) & 1 feeds
+ *        Box-Muller, u1 = (a + 1) 2^-24, u2 = b 2^-24 (exact in float32),
+ *        z = sqrt(-2 ln u1) cos(2 pi u2)
  *        for even j, sin(...) for odd j;  G[j, c] = z / sqrt(k)
  *        (rounded to bfloat16, nearest-even, in LSK_PREC_BF16).
  */
@@ -198,6 +199,20 @@ int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed,
  * lsk_gauss_sketch with the same precision mode. */
 int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed,
                     int32_t prec, float* G);
+
+/* ---- tracing ------------------------------------------------------------ */
+/* Per-kernel CUDA-event timing on the context's stream (off by default).
+ * While on, every kernel launch of a call is bracketed by two events; the
+ * totals are resolved (synchronising on the events) by the query calls. */
+int lsk_profile_enable(lsk_ctx* ctx, int on);
+/* Drop the accumulated totals. */
+int lsk_profile_reset(lsk_ctx* ctx);
+/* Number of distinct kernel names with recorded launches. */
+int lsk_profile_count(lsk_ctx* ctx);
+/* Entry idx: kernel name (NUL-terminated, truncated to name_len), number of
+ * launches and their summed duration in milliseconds. */
+int lsk_profile_get(lsk_ctx* ctx, int idx, char* name, size_t name_len,
+                    long long* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -63,11 +63,19 @@ def from_vector_representation(v):
     return np.abs(v) - 1, np.sign(v).astype(np.int8)
 
 
-def countsketch_apply_dense(A, bucket, sign, r):
-    """S*A for a dense row-major A (Alg. 2): SA[h(i), :] += sigma_i * A[i, :]."""
-    A = np.asarray(A, dtype=np.float64)
+def countsketch_apply_dense(A, bucket, sign, r, chunk=1 << 16):
+    """S*A for a dense row-major A (Alg. 2): SA[h(i), :] += sigma_i * A[i, :].
+
+    The rows are visited in chunks only to bound the float64 temporaries
+    (the order of the additions is the row order either way).
+    """
+    A = np.asarray(A)
+    bucket = np.asarray(bucket)
+    sign = np.asarray(sign, dtype=np.float64)
     SA = np.zeros((r, A.shape[1]), dtype=np.float64)
-    np.add.at(SA, np.asarray(bucket), np.asarray(sign, dtype=np.float64)[:, None] * A)
+    for i0 in range(0, A.shape[0], chunk):
+        i1 = min(A.shape[0], i0 + chunk)
+        np.add.at(SA, bucket[i0:i1], sign[i0:i1, None] * A[i0:i1].astype(np.float64))
     return SA
 
 

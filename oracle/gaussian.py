@@ -8,13 +8,17 @@ and the Box-Muller transform (Box & Muller 1958):
 
     (w0, w1, w2, w3) = Philox4x32_10(ctr = (c mod 2^32, c >> 32, 1, j >> 2),
                                      key = (seed mod 2^32, seed >> 32))
-    p = (j >> 1) & 1;  (a, b) = (w_{2p}, w_{2p+1})
-    u1 = (a + 1) / 2^32 in (0, 1],   u2 = b / 2^32 in [0, 1)
+    p = (j >> 1) & 1;  (a, b) = (w_{2p} >> 8, w_{2p+1} >> 8)   (24-bit words)
+    u1 = (a + 1) / 2^24 in (0, 1],   u2 = b / 2^24 in [0, 1)
     z  = sqrt(-2 ln u1) * cos(2 pi u2)   if j is even
          sqrt(-2 ln u1) * sin(2 pi u2)   if j is odd
     G[j, c] = z / sqrt(k)
 
-so one Philox call yields the four entries j = 4q..4q+3 of column c.
+so one Philox call yields the four entries j = 4q..4q+3 of column c.  The
+24-bit uniforms are exact in float32, so a float32 evaluation of the same
+formula sees exactly the arguments the float64 oracle sees (the paper only
+asks for i.i.d. N(0,1) entries; the uniform resolution is part of this
+reading, and it caps |z| at sqrt(48 ln 2) = 5.77).
 In the BF16 precision mode G is *defined* as the bfloat16 value nearest
 (ties to even) to the float32 rounding of z / sqrt(k); that rounding is the
 one decision both the oracle and the GPU take in float32.
@@ -53,10 +57,10 @@ def gaussian_columns(k, c0, c1, seed, prec=PREC_FP32):
     w = philox4x32_10(c & np.uint64(0xFFFFFFFF), c >> np.uint64(32), STREAM_G,
                       j >> np.uint64(2), k0, k1)
     p = ((j >> np.uint64(1)) & np.uint64(1)).astype(bool)
-    a = np.where(p, w[2], w[0]).astype(np.float64)
-    b = np.where(p, w[3], w[1]).astype(np.float64)
-    u1 = (a + 1.0) * 2.0**-32
-    u2 = b * 2.0**-32
+    a = (np.where(p, w[2], w[0]) >> np.uint32(8)).astype(np.float64)
+    b = (np.where(p, w[3], w[1]) >> np.uint32(8)).astype(np.float64)
+    u1 = (a + 1.0) * 2.0**-24
+    u2 = b * 2.0**-24
     rho = np.sqrt(-2.0 * np.log(u1))
     even = (np.arange(k)[:, None] % 2) == 0
     z = np.where(even, rho * np.cos(2.0 * np.pi * u2), rho * np.sin(2.0 * np.pi * u2))

@@ -45,7 +45,7 @@ def leverage_scores_dense(A, r, k, seed, prec=gaussian.PREC_FP32):
 def leverage_scores_csr(V, J, I, n, d, r, k, seed, prec=gaussian.PREC_FP32):
     R = sketch_R(sketch_csr(V, J, I, n, d, r, k, seed, prec))
     Rinv = qr.upper_triangular_inverse(R)
-    return rownorms.rownorms_prod_csr_direct(V, J, I, n, d, Rinv), R
+    return rownorms.rownorms_prod_csr_alg8(V, J, I, n, Rinv), R
 
 
 def leverage_scores_exact_qr(A):

@@ -1,0 +1,328 @@
+"""Python binding of liblsk.so -- GB300 sketching for tall-and-skinny matrices.
+
+Thin ctypes marshalling over the C ABI in ``include/lsk.h`` (same names,
+without the ``lsk_`` prefix).  Every step of every call runs in the CUDA
+kernels of liblsk.so; PyTorch only provides device memory and the stream.
+There is no CPU fallback: if the library or a CUDA device is missing, the
+calls raise.
+
+Matrices are either a 2-D ``torch.float32`` CUDA tensor (dense, row-major,
+unit column stride) or a :class:`CSR` of CUDA tensors (V float32, J int32,
+I int64, 0-based, sorted/unique column indices per row).
+
+The operations follow Sobczyk & Gallopoulos, "pylspack" (arXiv 2203.02798):
+``cs_sketch`` = S*A (Def. 3, Alg. 2); ``gauss_sketch`` = G*(S*A) (Alg. 3);
+``gram`` = alpha A^T A + beta C (Alg. 5/7, csrrk); ``rownorms_prod`` =
+alpha diag(A B B^T A^T) + beta x (Alg. 8, csrsqn/rmsqn); ``leverage_scores``
+(Alg. 15 without Pi); ``sketch_precondition_lsq`` (Alg. 12).
+"""
+import ctypes
+import os
+from collections import namedtuple
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblsk.so")
+
+PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2
+_PRECS = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16}
+
+ERRORS = {
+    -1: "INVALID_ARG", -2: "BAD_CSR", -3: "UNSUPPORTED", -4: "RANK_DEFICIENT",
+    -5: "NOT_CONVERGED", -6: "OOM", -7: "TIMEOUT", -8: "CUDA",
+}
+
+CSR = namedtuple("CSR", ["V", "J", "I", "n", "d"])
+
+
+class LskError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class _Mat(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int64), ("ld", ctypes.c_int64), ("values", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("nnz", ctypes.c_int64)]
+
+
+class LsqOpts(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int64), ("k", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+
+
+class LsqInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("status", ctypes.c_int32)]
+
+
+_lib = None
+_P, _I32, _I64, _U64, _D = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                            ctypes.c_double)
+_SIGS = {
+    "lsk_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _P]),
+    "lsk_destroy": (ctypes.c_int, [_P]),
+    "lsk_set_stream": (ctypes.c_int, [_P, _P]),
+    "lsk_sync": (ctypes.c_int, [_P]),
+    "lsk_error_string": (ctypes.c_char_p, [_P]),
+    "lsk_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "lsk_reserve": (ctypes.c_int, [_P, ctypes.c_size_t]),
+    "lsk_cs_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _P]),
+    "lsk_gauss_sketch": (ctypes.c_int, [_P, _P, _I64, _I64, _I64, _U64, _I32, _P]),
+    "lsk_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _P]),
+    "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _P]),
+    "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
+    "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
+    "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
+    "lsk_sketch_precondition_lsq": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _P,
+                                                   ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
+    "lsk_debug_hash": (ctypes.c_int, [_P, _I64, _I64, _U64, _P, _P]),
+    "lsk_debug_gauss": (ctypes.c_int, [_P, _I64, _I64, _U64, _I32, _P]),
+    "lsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lsk_profile_reset": (ctypes.c_int, [_P]),
+    "lsk_profile_count": (ctypes.c_int, [_P]),
+    "lsk_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load liblsk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2203_02798_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _prec(p):
+    return _PRECS[p] if isinstance(p, str) else int(p)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("liblsk works on CUDA tensors (use .cuda())")
+
+
+class Context:
+    """An lsk_ctx bound to one CUDA device; launches on torch's current stream."""
+
+    def __init__(self, device=None):
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblsk needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib.lsk_create(ctypes.byref(h), self.device.index,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            raise LskError(rc, "lsk_create failed")
+        self.h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lsk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        self._lib.lsk_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        rc = getattr(self._lib, name)(self.h, *args)
+        if rc != 0:
+            raise LskError(rc, self._lib.lsk_error_string(self.h).decode())
+        return rc
+
+    def sync(self):
+        """Synchronise the stream and raise any deferred device error."""
+        self._call("lsk_sync")
+
+    def reserve(self, nbytes):
+        self._call("lsk_reserve", ctypes.c_size_t(int(nbytes)))
+
+    def workspace_bytes(self):
+        return int(self._lib.lsk_workspace_bytes(self.h))
+
+    def profile(self, on=True):
+        """Turn per-kernel CUDA-event timing on or off (lsk_profile_enable)."""
+        self._lib.lsk_profile_enable(self.h, int(bool(on)))
+
+    def profile_reset(self):
+        self._lib.lsk_profile_reset(self.h)
+
+    def profile_totals(self):
+        """{kernel name: (launches, total ms)} recorded since the last reset."""
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        for i in range(self._lib.lsk_profile_count(self.h)):
+            n, ms = ctypes.c_longlong(), ctypes.c_double()
+            self._lib.lsk_profile_get(self.h, i, buf, 128, ctypes.byref(n), ctypes.byref(ms))
+            out[buf.value.decode()] = (int(n.value), float(ms.value))
+        return out
+
+
+_ctx = {}
+
+
+def context(device=None):
+    """The per-device default :class:`Context`."""
+    idx = torch.cuda.current_device() if device is None else int(device)
+    if idx not in _ctx:
+        _ctx[idx] = Context(idx)
+    return _ctx[idx]
+
+
+def _mat(A):
+    m = _Mat()
+    if isinstance(A, CSR):
+        _check_cuda(A.V, A.J, A.I)
+        assert A.V.dtype == torch.float32 and A.J.dtype == torch.int32 and A.I.dtype == torch.int64
+        m.kind, m.dtype, m.n, m.d, m.ld = 1, 0, int(A.n), int(A.d), 0
+        m.values, m.rowptr, m.colidx, m.nnz = A.V.data_ptr(), A.I.data_ptr(), A.J.data_ptr(), A.V.numel()
+        return m, int(A.n), int(A.d)
+    _check_cuda(A)
+    if A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("dense A must be a 2-D float32 tensor with unit column stride")
+    m.kind, m.dtype, m.n, m.d, m.ld = 0, 0, A.shape[0], A.shape[1], max(A.stride(0), A.shape[1])
+    m.values, m.rowptr, m.colidx, m.nnz = A.data_ptr(), None, None, 0
+    return m, A.shape[0], A.shape[1]
+
+
+def _dev(A):
+    return A.V.device if isinstance(A, CSR) else A.device
+
+
+def cs_sketch(A, r, seed, out=None, ctx=None):
+    """lsk_cs_sketch: S*A (r x d, float32)."""
+    m, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    SA = out if out is not None else torch.empty((r, d), dtype=torch.float32, device=_dev(A))
+    ctx._call("lsk_cs_sketch", ctypes.byref(m), int(r), int(seed), _ptr(SA))
+    return SA
+
+
+def gauss_sketch(SA, k, seed, prec="fp32", out=None, ctx=None):
+    """lsk_gauss_sketch: G*SA (k x d, float32), G scaled by 1/sqrt(k)."""
+    _check_cuda(SA)
+    r, d = SA.shape
+    ctx = ctx or context(SA.device.index)
+    GSA = out if out is not None else torch.empty((k, d), dtype=torch.float32, device=SA.device)
+    ctx._call("lsk_gauss_sketch", _ptr(SA.contiguous()), int(r), int(d), int(k), int(seed), _prec(prec),
+              _ptr(GSA))
+    return GSA
+
+
+def gram(A, alpha=1.0, beta=0.0, C=None, ctx=None):
+    """lsk_gram: alpha A^T A + beta C (d x d float32, C updated in place if given)."""
+    m, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    if C is None:
+        C = torch.empty((d, d), dtype=torch.float32, device=_dev(A))
+        beta = 0.0
+    ctx._call("lsk_gram", ctypes.byref(m), float(alpha), float(beta), _ptr(C))
+    return C
+
+
+def rownorms_prod(A, B, alpha=1.0, beta=0.0, x=None, upper_triangular=False, ctx=None):
+    """lsk_rownorms_prod: alpha ||A_i B||^2 + beta x_i (n float32)."""
+    m, n, d = _mat(A)
+    _check_cuda(B)
+    B = B.contiguous()
+    ctx = ctx or context(_dev(A).index)
+    if x is None:
+        x = torch.empty(n, dtype=torch.float32, device=_dev(A))
+        beta = 0.0
+    ctx._call("lsk_rownorms_prod", ctypes.byref(m), _ptr(B), int(B.shape[1]), float(alpha), float(beta),
+              int(bool(upper_triangular)), _ptr(x))
+    return x
+
+
+def sketch_qr(B, ctx=None):
+    """lsk_sketch_qr: (R, R^-1) of the sketch B (float64, d x d)."""
+    _check_cuda(B)
+    k, d = B.shape
+    ctx = ctx or context(B.device.index)
+    R = torch.empty((d, d), dtype=torch.float64, device=B.device)
+    Ri = torch.empty((d, d), dtype=torch.float64, device=B.device)
+    ctx._call("lsk_sketch_qr", _ptr(B.contiguous()), int(k), int(d), _ptr(R), _ptr(Ri))
+    return R, Ri
+
+
+def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=None):
+    """lsk_leverage_scores: ell_i = ||A_i R^-1||^2 (n float32); optionally R."""
+    m, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    ell = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
+    ctx._call("lsk_leverage_scores", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), _ptr(ell),
+              _ptr(R))
+    return (ell, R) if return_R else ell
+
+
+def lsq_default_opts(d):
+    o = LsqOpts()
+    load_library().lsk_lsq_default_opts(ctypes.byref(o), int(d))
+    return o
+
+
+def sketch_precondition_lsq(A, b, opts=None, ctx=None, **kw):
+    """lsk_sketch_precondition_lsq: x (d float64) and an info dict."""
+    m, n, d = _mat(A)
+    _check_cuda(b)
+    ctx = ctx or context(_dev(A).index)
+    o = opts if opts is not None else lsq_default_opts(d)
+    for key, val in kw.items():
+        setattr(o, key, _prec(val) if key == "prec" else val)
+    x = torch.empty(d, dtype=torch.float64, device=_dev(A))
+    info = LsqInfo()
+    ctx._call("lsk_sketch_precondition_lsq", ctypes.byref(m), _ptr(b.contiguous()), _ptr(x),
+              ctypes.byref(o), ctypes.byref(info))
+    return x, dict(iters=info.iters, refinements=info.refinements, eta=info.eta, status=info.status)
+
+
+def debug_hash(n, r, seed, device=None, ctx=None):
+    """lsk_debug_hash: (bucket int32[n], sign int8[n]) of the CountSketch."""
+    ctx = ctx or context(device)
+    b = torch.empty(n, dtype=torch.int32, device=ctx.device)
+    s = torch.empty(n, dtype=torch.int8, device=ctx.device)
+    ctx._call("lsk_debug_hash", int(n), int(r), int(seed), _ptr(b), _ptr(s))
+    return b, s
+
+
+def debug_gauss(k, r, seed, prec="fp32", device=None, ctx=None):
+    """lsk_debug_gauss: G (k x r float32) as used by gauss_sketch."""
+    ctx = ctx or context(device)
+    G = torch.empty((k, r), dtype=torch.float32, device=ctx.device)
+    ctx._call("lsk_debug_gauss", int(k), int(r), int(seed), _prec(prec), _ptr(G))
+    return G
+
+
+def csr_from_numpy(V, J, I, d, device="cuda"):
+    """Copy numpy CSR arrays to the device as a :class:`CSR`."""
+    import numpy as np
+    return CSR(torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).to(device),
+               torch.from_numpy(np.ascontiguousarray(J, dtype=np.int32)).to(device),
+               torch.from_numpy(np.ascontiguousarray(I, dtype=np.int64)).to(device),
+               len(I) - 1, int(d))

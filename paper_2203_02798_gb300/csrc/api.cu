@@ -1,0 +1,391 @@
+// api.cu -- the extern "C" entry points declared in include/lsk.h.
+//
+// Host-side argument validation, the context's workspace, and the order in
+// which the kernels of each call are launched.  No compute happens here.
+#include "lsk_internal.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+namespace {
+
+int fail(lsk_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(lsk_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, LSK_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Grow the workspace to `bytes` (stream-ordered: safe for work still queued).
+int ws_ensure(lsk_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return LSK_OK;
+    size_t want = bytes + bytes / 8;
+    if (ctx->ws) {
+        cudaError_t e = cudaFreeAsync(ctx->ws, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFreeAsync(workspace)");
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, want, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LSK_ERR_OOM, "workspace allocation of %zu bytes failed: %s", want,
+                    cudaGetErrorString(e));
+    }
+    ctx->ws = p;
+    ctx->ws_bytes = want;
+    return LSK_OK;
+}
+
+int check_mat(lsk_ctx* ctx, const lsk_mat* A) {
+    if (!A) return fail(ctx, LSK_ERR_INVALID_ARG, "A is NULL");
+    if (A->dtype != LSK_F32) return fail(ctx, LSK_ERR_UNSUPPORTED, "only LSK_F32 values are supported");
+    if (A->n < 0 || A->d < 1) return fail(ctx, LSK_ERR_INVALID_ARG, "bad shape n=%lld d=%lld",
+                                          (long long)A->n, (long long)A->d);
+    if (A->n >= (int64_t)1 << 31) return fail(ctx, LSK_ERR_UNSUPPORTED, "n must be < 2^31");
+    if (A->kind == LSK_DENSE) {
+        if (A->ld < A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "ld < d");
+        if (A->n > 0 && !A->values) return fail(ctx, LSK_ERR_INVALID_ARG, "A->values is NULL");
+    } else if (A->kind == LSK_CSR) {
+        if (!A->rowptr) return fail(ctx, LSK_ERR_INVALID_ARG, "A->rowptr is NULL");
+        if (A->nnz < 0) return fail(ctx, LSK_ERR_INVALID_ARG, "nnz < 0");
+        if (A->nnz > 0 && (!A->colidx || !A->values))
+            return fail(ctx, LSK_ERR_INVALID_ARG, "A->colidx / A->values is NULL");
+        if (A->d > INT32_MAX) return fail(ctx, LSK_ERR_UNSUPPORTED, "d too large for int32 column indices");
+    } else {
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown matrix kind %d", (int)A->kind);
+    }
+    return LSK_OK;
+}
+
+int finish(lsk_ctx* ctx, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    return LSK_OK;
+}
+
+int flag_to_status(lsk_ctx* ctx, int f) {
+    if (f & LSK_FLAG_BAD_CSR) return fail(ctx, LSK_ERR_BAD_CSR, "CSR row pointer or column index out of range");
+    if (f & LSK_FLAG_RANK_DEFICIENT)
+        return fail(ctx, LSK_ERR_RANK_DEFICIENT, "sketch is numerically rank deficient");
+    if (f & LSK_FLAG_TIMEOUT) return fail(ctx, LSK_ERR_TIMEOUT, "a bounded device wait timed out");
+    return LSK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsk_create(lsk_ctx** out, int device, void* stream) {
+    if (!out) return LSK_ERR_INVALID_ARG;
+    *out = nullptr;
+    lsk_ctx* ctx = (lsk_ctx*)calloc(1, sizeof(lsk_ctx));
+    if (!ctx) return LSK_ERR_OOM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->flag, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free(ctx);
+        return LSK_ERR_CUDA;
+    }
+    ctx->stream = (cudaStream_t)stream;
+    *out = ctx;
+    return LSK_OK;
+}
+
+int lsk_destroy(lsk_ctx* ctx) {
+    if (!ctx) return LSK_OK;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->flag) cudaFree(ctx->flag);
+    if (ctx->prof) lsk_prof_delete(ctx->prof);
+    free(ctx);
+    return LSK_OK;
+}
+
+int lsk_set_stream(lsk_ctx* ctx, void* stream) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return LSK_OK;
+}
+
+int lsk_sync(lsk_ctx* ctx) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    int f = 0;
+    e = cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the device flag");
+    if (f) {
+        cudaMemset(ctx->flag, 0, sizeof(int));
+        return flag_to_status(ctx, f);
+    }
+    return LSK_OK;
+}
+
+const char* lsk_error_string(const lsk_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+size_t lsk_workspace_bytes(const lsk_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int lsk_reserve(lsk_ctx* ctx, size_t bytes) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    return ws_ensure(ctx, bytes);
+}
+
+int lsk_cs_sketch(lsk_ctx* ctx, const lsk_mat* A, int64_t r, uint64_t seed, float* SA) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (r < 1 || r >= ((int64_t)1 << 31)) return fail(ctx, LSK_ERR_INVALID_ARG, "r must be in [1, 2^31)");
+    if (!SA) return fail(ctx, LSK_ERR_INVALID_ARG, "SA is NULL");
+    if (A->kind == LSK_CSR && A->d > 51200) return fail(ctx, LSK_ERR_UNSUPPORTED, "CSR sketch needs d <= 51200");
+    rc = ws_ensure(ctx, cs_workspace_bytes(A->n, r));
+    if (rc) return rc;
+    cudaError_t e = cs_launch(A, r, seed, SA, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_cs_sketch");
+    return finish(ctx, "lsk_cs_sketch");
+}
+
+int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
+                     int32_t prec, float* GSA) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    if (!SA || !GSA) return fail(ctx, LSK_ERR_INVALID_ARG, "SA / GSA is NULL");
+    if (r < 1 || d < 1 || k < 1) return fail(ctx, LSK_ERR_INVALID_ARG, "r, d, k must be >= 1");
+    if (k >= ((int64_t)1 << 32)) return fail(ctx, LSK_ERR_INVALID_ARG, "k too large");
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    int rc = ws_ensure(ctx, gauss_workspace_bytes(r, d, k, prec, ctx->sm_count));
+    if (rc) return rc;
+    cudaError_t e = gauss_launch(SA, r, d, k, seed, prec, GSA, ctx->ws, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_gauss_sketch");
+    return finish(ctx, "lsk_gauss_sketch");
+}
+
+int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (!C) return fail(ctx, LSK_ERR_INVALID_ARG, "C is NULL");
+    rc = ws_ensure(ctx, gram_workspace_bytes(A, ctx->sm_count));
+    if (rc) return rc;
+    cudaError_t e = gram_launch(A, alpha, beta, C, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_gram");
+    return finish(ctx, "lsk_gram");
+}
+
+int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B, int64_t c, double alpha,
+                      double beta, int32_t upper_triangular, float* x) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (!B || !x) return fail(ctx, LSK_ERR_INVALID_ARG, "B / x is NULL");
+    if (c < 1) return fail(ctx, LSK_ERR_INVALID_ARG, "c must be >= 1");
+    if (upper_triangular && c != A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "upper_triangular needs c == d");
+    rc = ws_ensure(ctx, rownorms_workspace_bytes(A, c));
+    if (rc) return rc;
+    cudaError_t e = rownorms_launch(A, B, c, alpha, beta, upper_triangular, x, ctx->ws, ctx->flag,
+                                    ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_rownorms_prod");
+    return finish(ctx, "lsk_rownorms_prod");
+}
+
+int lsk_sketch_qr(lsk_ctx* ctx, const float* B, int64_t k, int64_t d, double* R, double* Rinv) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    if (!B) return fail(ctx, LSK_ERR_INVALID_ARG, "B is NULL");
+    if (d < 1 || k < d) return fail(ctx, LSK_ERR_INVALID_ARG, "need k >= d >= 1");
+    if (d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "sketch QR supports d <= 1024");
+    int rc = ws_ensure(ctx, qr_workspace_bytes(k, d));
+    if (rc) return rc;
+    cudaError_t e = qr_launch(B, k, d, R, Rinv, nullptr, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_qr");
+    return finish(ctx, "lsk_sketch_qr");
+}
+
+// Workspace layout shared by leverage_scores and the LSQ driver:
+//   [SA r*d f32][GSA k*d f32][Rinv64 d*d][Rinv32 d*d][R64 d*d][stage scratch]
+namespace {
+struct SketchBufs {
+    float* SA;
+    float* GSA;
+    double* Rinv64;
+    float* Rinv32;
+    double* R64;
+    void* scratch;
+};
+
+size_t stage_scratch(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int sm) {
+    size_t s = cs_workspace_bytes(A->n, r);
+    if (k > 0) {
+        const size_t g = gauss_workspace_bytes(r, A->d, k, prec, sm);
+        if (g > s) s = g;
+    }
+    const size_t q = qr_workspace_bytes(k > 0 ? k : r, A->d);
+    if (q > s) s = q;
+    const size_t rn = rownorms_workspace_bytes(A, A->d);
+    if (rn > s) s = rn;
+    return s;
+}
+
+size_t sketch_bytes(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int sm, size_t extra) {
+    const int64_t d = A->d;
+    return ws_round((size_t)r * d * 4) + ws_round((size_t)(k > 0 ? k : 1) * d * 4) +
+           ws_round((size_t)d * d * 8) * 2 + ws_round((size_t)d * d * 4) +
+           (stage_scratch(A, r, k, prec, sm) > extra ? stage_scratch(A, r, k, prec, sm) : extra) + 4096;
+}
+
+SketchBufs carve(void* ws, const lsk_mat* A, int64_t r, int64_t k) {
+    const int64_t d = A->d;
+    WsCarver wc{(char*)ws, 0};
+    SketchBufs b;
+    b.SA = wc.take<float>((size_t)r * d);
+    b.GSA = wc.take<float>((size_t)(k > 0 ? k : 1) * d);
+    b.Rinv64 = wc.take<double>((size_t)d * d);
+    b.R64 = wc.take<double>((size_t)d * d);
+    b.Rinv32 = wc.take<float>((size_t)d * d);
+    b.scratch = wc.take<char>(1);
+    return b;
+}
+
+// SA -> (GSA) -> R, R^-1 on the device, all asynchronous.
+cudaError_t sketch_and_factor(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed,
+                              int32_t prec, const SketchBufs& b, double* R_out) {
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, ctx->flag, ctx->sm_count, st);
+    if (e != cudaSuccess) return e;
+    const float* sk = b.SA;
+    int64_t rows = r;
+    if (k > 0) {
+        e = gauss_launch(b.SA, r, A->d, k, seed, prec, b.GSA, b.scratch, ctx->sm_count, st);
+        if (e != cudaSuccess) return e;
+        sk = b.GSA;
+        rows = k;
+    }
+    return qr_launch(sk, rows, A->d, R_out ? R_out : b.R64, b.Rinv64, b.Rinv32, b.scratch, ctx->flag,
+                     ctx->sm_count, st);
+}
+
+int check_sketch_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec) {
+    if (r < 1 || r >= ((int64_t)1 << 31)) return fail(ctx, LSK_ERR_INVALID_ARG, "r must be in [1, 2^31)");
+    if (k < 0) return fail(ctx, LSK_ERR_INVALID_ARG, "k must be >= 0");
+    const int64_t rows = k > 0 ? k : r;
+    if (rows < A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "the sketch needs at least d rows");
+    if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "d <= 1024 is supported");
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    return LSK_OK;
+}
+}  // namespace
+
+int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                        float* ell, double* R_out) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    rc = check_sketch_args(ctx, A, r, k, prec);
+    if (rc) return rc;
+    if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, 0));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    cudaError_t e = sketch_and_factor(ctx, A, r, k, seed, prec, b, R_out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (sketch)");
+    e = rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, ell, b.scratch, ctx->flag, ctx->sm_count,
+                        ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (row norms)");
+    return finish(ctx, "lsk_leverage_scores");
+}
+
+void lsk_lsq_default_opts(lsk_lsq_opts* o, int64_t d) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->r = d * d > 4 * d ? d * d : 4 * d;
+    o->k = 2 * d;
+    o->seed = 0;
+    o->prec = LSK_PREC_BF16;
+    o->max_iter = 100;
+    o->max_refine = 8;
+    o->tol = 1e-10;
+    o->inner_tol = 1e-6;
+}
+
+int lsk_sketch_precondition_lsq(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x,
+                                const lsk_lsq_opts* opts, lsk_lsq_info* info) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (!opts) return fail(ctx, LSK_ERR_INVALID_ARG, "opts is NULL");
+    if (!x || (!b && A->n > 0)) return fail(ctx, LSK_ERR_INVALID_ARG, "b / x is NULL");
+    int32_t prec = opts->prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : opts->prec;
+    rc = check_sketch_args(ctx, A, opts->r, opts->k, prec);
+    if (rc) return rc;
+    if (opts->max_iter < 1 || opts->max_refine < 0 || !(opts->tol > 0.0))
+        return fail(ctx, LSK_ERR_INVALID_ARG, "bad LSQ options");
+    rc = ws_ensure(ctx, sketch_bytes(A, opts->r, opts->k, prec, ctx->sm_count, lsq_workspace_bytes(A)));
+    if (rc) return rc;
+    const SketchBufs bufs = carve(ctx->ws, A, opts->r, opts->k);
+    cudaError_t e = sketch_and_factor(ctx, A, opts->r, opts->k, opts->seed, prec, bufs, nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_precondition_lsq (sketch)");
+    // the factor must be valid before iterating: read the flag now
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_precondition_lsq (sync)");
+    int f = 0;
+    cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (f) {
+        cudaMemset(ctx->flag, 0, sizeof(int));
+        return flag_to_status(ctx, f);
+    }
+    lsk_lsq_info tmp;
+    rc = lsq_run(ctx, A, b, x, opts, bufs.Rinv64, bufs.Rinv32, bufs.scratch, info ? info : &tmp);
+    if (rc == LSK_ERR_CUDA) return fail(ctx, rc, "lsk_sketch_precondition_lsq: CUDA error %s",
+                                        cudaGetErrorString(cudaGetLastError()));
+    if (rc == LSK_ERR_NOT_CONVERGED) return fail(ctx, rc, "least squares did not reach tol");
+    cudaMemcpy(&f, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (f) {
+        cudaMemset(ctx->flag, 0, sizeof(int));
+        return flag_to_status(ctx, f);
+    }
+    return rc;
+}
+
+int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    if (n < 0 || r < 1 || r >= ((int64_t)1 << 32)) return fail(ctx, LSK_ERR_INVALID_ARG, "bad n / r");
+    if (n > 0 && (!bucket || !sign)) return fail(ctx, LSK_ERR_INVALID_ARG, "NULL output");
+    cudaError_t e = cs_hash_launch(n, r, seed, bucket, sign, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_debug_hash");
+    return finish(ctx, "lsk_debug_hash");
+}
+
+int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed, int32_t prec, float* G) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    if (k < 1 || r < 1 || !G) return fail(ctx, LSK_ERR_INVALID_ARG, "bad k / r / G");
+    cudaError_t e = gauss_debug_launch(k, r, seed, prec == LSK_PREC_BF16 ? LSK_PREC_BF16 : LSK_PREC_FP32, G,
+                                       ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_debug_gauss");
+    return finish(ctx, "lsk_debug_gauss");
+}
+
+}  // extern "C"

@@ -1,0 +1,368 @@
+// countsketch.cu -- CountSketch S*A for dense and CSR A (Def. 3, Alg. 2).
+//
+// The paper stores S as a Block (Column) CountSketch and lets each thread
+// own whole rows of SA (Alg. 2, the b_r = r case of Sec. 2.3), so that no two
+// threads write the same output row.  Here S is never stored: (h(i), sigma_i)
+// is recomputed from Philox whenever it is needed, and row ownership is kept
+// at the finest grain -- one warp owns one bucket (one row of SA):
+//
+//   1. rank:  cnt[h(i)]++ for every row, remembering each row's arrival rank
+//   2. scan:  off = exclusive prefix sum of cnt        (bucket -> first slot)
+//   3. place: perm[off[h(i)] + rank[i]] = i | sigma_bit << 31
+//   4. gather (dense): the warp owning bucket b streams the rows listed in
+//      perm[off[b] .. off[b+1]) with 16-byte coalesced loads, accumulates them
+//      (with their signs) in registers and writes row b of SA exactly once.
+//      gather (CSR): same ownership, the row of SA is accumulated in shared
+//      memory because CSR columns are scattered.
+//
+// Every byte of A is read once and every row of SA written once, with no
+// global atomics on floating-point data; the only extra traffic is the
+// 8 bytes per row of rank/perm.  The per-bucket loads are the Y of Lemma 1:
+// expected n/r rows per warp, concentrated as in Lemma 2-3.
+#include "lsk_internal.cuh"
+
+namespace {
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__global__ void cs_rank_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
+                               uint32_t* __restrict__ cnt, uint32_t* __restrict__ rank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t b, neg;
+        cs_hash((uint64_t)i, r, k0, k1, b, neg);
+        rank[i] = atomicAdd(&cnt[b], 1u);
+    }
+}
+
+__global__ void cs_place_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
+                                const uint32_t* __restrict__ off,
+                                const uint32_t* __restrict__ rank, uint32_t* __restrict__ perm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t b, neg;
+        cs_hash((uint64_t)i, r, k0, k1, b, neg);
+        perm[off[b] + rank[i]] = (uint32_t)i | (neg << 31);
+    }
+}
+
+// Block-local exclusive scan of kScanTile entries; writes the tile total.
+__global__ void scan_tiles_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                  uint32_t* __restrict__ tile_sums, int64_t len) {
+    __shared__ uint32_t warp_tot[kScanBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t run = 0;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t i = base + t;
+        v[t] = (i < len) ? in[i] : 0u;
+        const uint32_t x = v[t];
+        v[t] = run;
+        run += x;
+    }
+    // exclusive scan of the per-thread totals across the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = (lane < kScanBlock / 32) ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kScanBlock / 32) warp_tot[lane] = wi - w;
+        if (lane == kScanBlock / 32 - 1) tile_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    const uint32_t excl = warp_tot[wid] + incl - run;
+#pragma unroll
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t i = base + t;
+        if (i < len) out[i] = v[t] + excl;
+    }
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ out, const uint32_t* __restrict__ tile_off,
+                                int64_t len) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] += tile_off[i / kScanTile];
+}
+
+// Exclusive scan of `len` uint32 into `out` (may alias nothing); `tmp` must
+// hold scan_tmp_words(len) words.
+size_t scan_tmp_words(int64_t len) {
+    size_t words = 0;
+    int64_t l = len;
+    while (true) {
+        const int64_t tiles = (l + kScanTile - 1) / kScanTile;
+        words += 2 * (size_t)tiles + 64;
+        if (tiles <= 1) break;
+        l = tiles;
+    }
+    return words;
+}
+
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint32_t* tmp,
+                           cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    const int64_t tiles = (len + kScanTile - 1) / kScanTile;
+    uint32_t* sums = tmp;
+    scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, out, sums, len);
+    if (tiles > 1) {
+        uint32_t* sums_off = tmp + tiles + 32;
+        cudaError_t e = exclusive_scan(sums, sums_off, tiles, sums_off + tiles + 32, st);
+        if (e != cudaSuccess) return e;
+        scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(out, sums_off, len);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void write_total_kernel(uint32_t* off, int64_t r, uint32_t n) { off[r] = n; }
+
+// ---- dense gather ---------------------------------------------------------
+// One warp per bucket.  Lanes own VEC consecutive columns in each of U
+// column groups of 32*VEC; the bucket's rows are fetched four at a time so
+// that each warp keeps 4 rows of loads in flight.
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<4> {
+    using T = float4;
+};
+template <>
+struct VecT<1> {
+    using T = float;
+};
+
+__device__ __forceinline__ void vadd(float4& a, const float4& b, float s) {
+    a.x = fmaf(s, b.x, a.x);
+    a.y = fmaf(s, b.y, a.y);
+    a.z = fmaf(s, b.z, a.z);
+    a.w = fmaf(s, b.w, a.w);
+}
+__device__ __forceinline__ void vadd(float& a, const float& b, float s) { a = fmaf(s, b, a); }
+__device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vzero(float& a) { a = 0.f; }
+
+template <int VEC>
+__device__ __forceinline__ typename VecT<VEC>::T ldg_stream(const float* p) {
+    if constexpr (VEC == 4) {
+        float4 v;
+        asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(p));
+        return v;
+    } else {
+        float v;
+        asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
+}
+
+template <int VEC, int U>
+__global__ void __launch_bounds__(256) cs_dense_gather_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t d, uint32_t r,
+    const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA) {
+    using V = typename VecT<VEC>::T;
+    constexpr int kCols = 32 * VEC * U;  // columns per pass
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < r; b += nwarps) {
+        const uint32_t s = off[b], e = off[b + 1];
+        for (int64_t c0 = 0; c0 < d; c0 += kCols) {
+            V acc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) vzero(acc[u]);
+            bool colok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) colok[u] = (c0 + (int64_t)(u * 32 + lane) * VEC) < d;
+            for (uint32_t t0 = s; t0 < e; t0 += 32) {
+                const uint32_t m = min(32u, e - t0);
+                const uint32_t mine = (lane < (int)m) ? perm[t0 + lane] : 0u;
+                uint32_t j = 0;
+                for (; j + 4 <= m; j += 4) {
+                    V v[4][U];
+                    float sg[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t p = __shfl_sync(0xffffffffu, mine, j + q);
+                        sg[q] = (p >> 31) ? -1.0f : 1.0f;
+                        const float* row = A + (int64_t)(p & 0x7fffffffu) * lda + c0;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (colok[u]) v[q][u] = ldg_stream<VEC>(row + (u * 32 + lane) * VEC);
+                            else vzero(v[q][u]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int u = 0; u < U; ++u) vadd(acc[u], v[q][u], sg[q]);
+                }
+                for (; j < m; ++j) {
+                    const uint32_t p = __shfl_sync(0xffffffffu, mine, j);
+                    const float sg = (p >> 31) ? -1.0f : 1.0f;
+                    const float* row = A + (int64_t)(p & 0x7fffffffu) * lda + c0;
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (colok[u]) vadd(acc[u], ldg_stream<VEC>(row + (u * 32 + lane) * VEC), sg);
+                }
+            }
+            float* out = SA + (int64_t)b * d + c0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (colok[u]) *reinterpret_cast<V*>(out + (u * 32 + lane) * VEC) = acc[u];
+        }
+    }
+}
+
+// ---- CSR gather -----------------------------------------------------------
+// One warp per bucket; the bucket's row of SA lives in shared memory (d
+// floats per warp).  Lane t handles the t-th row of the bucket's list and
+// adds its nonzeros with shared-memory atomics (columns of different rows
+// may collide).  Out-of-range row pointers or column indices are skipped
+// and reported through the BAD_CSR flag.
+__global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
+                                     const int64_t* __restrict__ I, int64_t nnz, int64_t d,
+                                     uint32_t r, const uint32_t* __restrict__ off,
+                                     const uint32_t* __restrict__ perm, float* __restrict__ SA,
+                                     int* flag) {
+    extern __shared__ float srow[];
+    const int lane = threadIdx.x & 31;
+    float* acc = srow + (int64_t)(threadIdx.x >> 5) * d;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < r; b += nwarps) {
+        for (int64_t c = lane; c < d; c += 32) acc[c] = 0.0f;
+        __syncwarp();
+        const uint32_t s = off[b], e = off[b + 1];
+        bool bad = false;
+        for (uint32_t t = s + lane; t < e; t += 32) {
+            const uint32_t p = perm[t];
+            const float sg = (p >> 31) ? -1.0f : 1.0f;
+            const int64_t row = p & 0x7fffffffu;
+            const int64_t k0 = I[row], k1 = I[row + 1];
+            if (k0 < 0 || k1 < k0 || k1 > nnz) {
+                bad = true;
+                continue;
+            }
+            for (int64_t kk = k0; kk < k1; ++kk) {
+                const int32_t col = __ldg(J + kk);
+                if (col < 0 || col >= d) {
+                    bad = true;
+                    continue;
+                }
+                atomicAdd(&acc[col], sg * __ldg(V + kk));
+            }
+        }
+        if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
+        __syncwarp();
+        float* out = SA + (int64_t)b * d;
+        for (int64_t c = lane; c < d; c += 32) out[c] = acc[c];
+        __syncwarp();
+    }
+}
+
+__global__ void cs_hash_debug_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
+                                     int32_t* bucket, int8_t* sign) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t b, neg;
+        cs_hash((uint64_t)i, r, k0, k1, b, neg);
+        bucket[i] = (int32_t)b;
+        sign[i] = neg ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 8) {
+    int64_t g = (items + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+size_t cs_workspace_bytes(int64_t n, int64_t r) {
+    return ws_round((size_t)(r + 1) * 4) * 2 + ws_round((size_t)n * 4) * 2 +
+           ws_round(scan_tmp_words(r) * 4) + 4096;
+}
+
+cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cs_hash_debug_kernel<<<grid_for(n, 256, 152, 16), 256, 0, st>>>(
+        n, (uint32_t)r, (uint32_t)seed, (uint32_t)(seed >> 32), bucket, sign);
+    return cudaGetLastError();
+}
+
+cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
+                      int sm_count, cudaStream_t st) {
+    const int64_t n = A->n, d = A->d;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    WsCarver wc{(char*)ws, 0};
+    uint32_t* cnt = wc.take<uint32_t>(r + 1);
+    uint32_t* off = wc.take<uint32_t>(r + 1);
+    uint32_t* rank = wc.take<uint32_t>(n > 0 ? n : 1);
+    uint32_t* perm = wc.take<uint32_t>(n > 0 ? n : 1);
+    uint32_t* tmp = wc.take<uint32_t>(scan_tmp_words(r));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)r * 4, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) LSK_PROF("cs_rank", st) cs_rank_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cnt, rank);
+    LSK_PROF("cs_scan", st) e = exclusive_scan(cnt, off, r, tmp, st);
+    if (e != cudaSuccess) return e;
+    write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
+    if (n > 0)
+        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, off, rank, perm);
+
+    const int64_t warps_needed = r;
+    if (A->kind == LSK_DENSE) {
+        const float* Av = (const float*)A->values;
+        const bool vec4 = (d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)Av & 15) == 0) &&
+                          (((uintptr_t)SA & 15) == 0);
+        const unsigned grid = grid_for(warps_needed * 32, 256, sm_count, 8);
+        if (vec4) {
+            if (d <= 128)
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+            else
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+        } else {
+            if (d <= 32)
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+            else
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+        }
+    } else {
+        // shared-memory row per warp: pick warps per block to fit 200 KB
+        int warps = 8;
+        while (warps > 1 && (size_t)warps * d * 4 > 200 * 1024) warps >>= 1;
+        const size_t smem = (size_t)warps * d * 4;
+        if (smem > 200 * 1024) return cudaErrorInvalidValue;
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(cs_csr_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const int threads = warps * 32;
+        int64_t g = (warps_needed + warps - 1) / warps;
+        const int64_t cap = (int64_t)sm_count * 32 / warps * 2;
+        if (g > cap) g = cap;
+        if (g < 1) g = 1;
+        LSK_PROF("cs_csr_gather", st) cs_csr_gather_kernel<<<(unsigned)g, threads, smem, st>>>(
+            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,252 @@
+// gram.cu -- C <- alpha A^T A + beta C (csrrk semantics; Alg. 5 and Alg. 7).
+//
+// Both forms follow Alg. 7's structure -- row blocks of A produce private
+// partial Gram matrices which are then summed -- with GPU-sized grains:
+//
+//  dense: a block owns one 64x64 tile of the upper triangle of C and one
+//         chunk of rows; FP32 products are accumulated in registers and
+//         folded into FP64 every kFold rows (bounding FP32 chain length), the
+//         FP64 partials of the chunks are added in a fixed order.
+//  CSR:   a block owns a slice of rows of C held in shared memory (the
+//         "private d x d" of Alg. 7, sliced so it fits) and a range of rows
+//         of A; each thread runs Alg. 5 on its rows (outer products of the
+//         row's nonzeros, shared-memory atomics), the FP32 slices of all
+//         blocks are then summed in FP64 in a fixed order.
+#include "lsk_internal.cuh"
+
+namespace {
+
+constexpr int GT = 64;       // tile edge of C
+constexpr int GK = 16;       // rows of A per step
+constexpr int kFold = 64;    // steps (of GK rows) between FP32 -> FP64 folds
+
+__device__ __forceinline__ void tile_of(int t, int nt, int& ta, int& tb) {
+    // enumerate the upper-triangular tile pairs (ta <= tb) row by row
+    ta = 0;
+    while (t >= nt - ta) {
+        t -= nt - ta;
+        ++ta;
+    }
+    tb = ta + t;
+}
+
+__global__ void __launch_bounds__(256) gram_dense_kernel(const float* __restrict__ A, int64_t lda,
+                                                         int64_t n, int64_t d, int64_t rows_per,
+                                                         double* __restrict__ part) {
+    __shared__ __align__(16) float As[GK][GT];
+    __shared__ __align__(16) float Bs[GK][GT];
+    const int nt = (int)((d + GT - 1) / GT);
+    int ta, tb;
+    tile_of(blockIdx.x, nt, ta, tb);
+    const int64_t a0 = (int64_t)ta * GT, b0 = (int64_t)tb * GT;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int64_t i_begin = (int64_t)blockIdx.y * rows_per;
+    const int64_t i_end = min(n, i_begin + rows_per);
+    float acc[4][4];
+    double acc64[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            acc[a][b] = 0.f;
+            acc64[a][b] = 0.0;
+        }
+    int steps = 0;
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += GK) {
+#pragma unroll
+        for (int t = 0; t < (GK * GT) / 256; ++t) {
+            const int idx = tid + 256 * t;
+            const int kr = idx / GT, cc = idx % GT;
+            const int64_t i = i0 + kr;
+            const bool rok = i < i_end;
+            As[kr][cc] = (rok && a0 + cc < d) ? __ldg(A + i * lda + a0 + cc) : 0.f;
+            Bs[kr][cc] = (rok && b0 + cc < d) ? __ldg(A + i * lda + b0 + cc) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            const float4 x = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+            const float4 y = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+            const float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+        }
+        __syncthreads();
+        if (++steps == kFold) {
+            steps = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc64[a][b] += (double)acc[a][b];
+                    acc[a][b] = 0.f;
+                }
+        }
+    }
+    const int ntiles = nt * (nt + 1) / 2;
+    double* P = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * GT * GT;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) P[(4 * ty + a) * GT + 4 * tx + b] = acc64[a][b] + (double)acc[a][b];
+}
+
+__global__ void gram_dense_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
+                                         int64_t d, double alpha, double beta,
+                                         float* __restrict__ C) {
+    const int nt = (int)((d + GT - 1) / GT);
+    const int ntiles = nt * (nt + 1) / 2;
+    const int64_t len = d * d;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+        int64_t a = e / d, b = e % d;
+        if (a > b) {
+            const int64_t t = a;
+            a = b;
+            b = t;
+        }
+        const int ta = (int)(a / GT), tb = (int)(b / GT);
+        const int tile = ta * nt - ta * (ta - 1) / 2 + (tb - ta);
+        const int64_t w = (a % GT) * GT + (b % GT);
+        double s = 0.0;
+        for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * GT * GT + w];
+        double v = alpha * s;
+        if (beta != 0.0) v += beta * (double)C[e];
+        C[e] = (float)v;
+    }
+}
+
+// ---- CSR ------------------------------------------------------------------
+__global__ void gram_csr_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
+                                const int64_t* __restrict__ I, int64_t n, int64_t nnz, int64_t d,
+                                int64_t slice_rows, int64_t rows_per, float* __restrict__ part,
+                                int* flag) {
+    extern __shared__ float S[];
+    const int64_t j0 = (int64_t)blockIdx.y * slice_rows;
+    const int64_t j1 = min(d, j0 + slice_rows);
+    const int64_t sl = j1 - j0;
+    for (int64_t e = threadIdx.x; e < sl * d; e += blockDim.x) S[e] = 0.f;
+    __syncthreads();
+    const int64_t i_begin = (int64_t)blockIdx.x * rows_per;
+    const int64_t i_end = min(n, i_begin + rows_per);
+    bool bad = false;
+    for (int64_t i = i_begin + threadIdx.x; i < i_end; i += blockDim.x) {
+        const int64_t k0 = I[i], k1 = I[i + 1];
+        if (k0 < 0 || k1 < k0 || k1 > nnz) {
+            bad = true;
+            continue;
+        }
+        for (int64_t p = k0; p < k1; ++p) {
+            const int32_t jp = __ldg(J + p);
+            if (jp < 0 || jp >= d) {
+                bad = true;
+                continue;
+            }
+            if (jp < j0 || jp >= j1) continue;
+            const float vp = __ldg(V + p);
+            float* Srow = S + (jp - j0) * d;
+            for (int64_t q = k0; q < k1; ++q) {
+                const int32_t jq = __ldg(J + q);
+                if (jq < 0 || jq >= d) continue;
+                atomicAdd(&Srow[jq], vp * __ldg(V + q));
+            }
+        }
+    }
+    if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
+    __syncthreads();
+    float* P = part + (int64_t)blockIdx.x * d * d + j0 * d;
+    for (int64_t e = threadIdx.x; e < sl * d; e += blockDim.x) P[e] = S[e];
+}
+
+__global__ void gram_csr_reduce_kernel(const float* __restrict__ part, int64_t nblocks, int64_t d,
+                                       double alpha, double beta, float* __restrict__ C) {
+    const int64_t len = d * d;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+        double s = 0.0;
+        for (int64_t z = 0; z < nblocks; ++z) s += (double)part[z * len + e];
+        double v = alpha * s;
+        if (beta != 0.0) v += beta * (double)C[e];
+        C[e] = (float)v;
+    }
+}
+
+struct DensePlan {
+    int ntiles;
+    int64_t nchunks, rows_per;
+};
+DensePlan dense_plan(int64_t n, int64_t d, int sm_count) {
+    DensePlan p;
+    const int nt = (int)((d + GT - 1) / GT);
+    p.ntiles = nt * (nt + 1) / 2;
+    int64_t want = (4 * (int64_t)sm_count + p.ntiles - 1) / p.ntiles;
+    int64_t rows = (n + want - 1) / want;
+    rows = ((rows + GK - 1) / GK) * GK;
+    if (rows < GK) rows = GK;
+    p.rows_per = rows;
+    p.nchunks = (n + rows - 1) / rows;
+    if (p.nchunks < 1) p.nchunks = 1;
+    return p;
+}
+
+struct CsrPlan {
+    int64_t slice_rows, nslices, nblocks, rows_per;
+    size_t smem;
+};
+CsrPlan csr_plan(int64_t n, int64_t d, int sm_count) {
+    CsrPlan p;
+    const int64_t max_floats = 48 * 1024;  // 192 KB of shared memory
+    p.slice_rows = max_floats / d;
+    if (p.slice_rows > d) p.slice_rows = d;
+    if (p.slice_rows < 1) p.slice_rows = 1;
+    p.nslices = (d + p.slice_rows - 1) / p.slice_rows;
+    int64_t nb = (2 * (int64_t)sm_count + p.nslices - 1) / p.nslices;
+    if (nb < 1) nb = 1;
+    p.rows_per = (n + nb - 1) / nb;
+    if (p.rows_per < 1) p.rows_per = 1;
+    p.nblocks = (n + p.rows_per - 1) / p.rows_per;
+    if (p.nblocks < 1) p.nblocks = 1;
+    p.smem = (size_t)p.slice_rows * d * 4;
+    return p;
+}
+
+}  // namespace
+
+size_t gram_workspace_bytes(const lsk_mat* A, int sm_count) {
+    if (A->kind == LSK_DENSE) {
+        const DensePlan p = dense_plan(A->n, A->d, sm_count);
+        return ws_round((size_t)p.nchunks * p.ntiles * GT * GT * 8);
+    }
+    const CsrPlan p = csr_plan(A->n, A->d, sm_count);
+    return ws_round((size_t)p.nblocks * A->d * A->d * 4);
+}
+
+cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag,
+                        int sm_count, cudaStream_t st) {
+    const int64_t n = A->n, d = A->d;
+    const int64_t len = d * d;
+    int64_t rg = (len + 255) / 256;
+    if (rg > 8 * (int64_t)sm_count) rg = 8 * (int64_t)sm_count;
+    if (A->kind == LSK_DENSE) {
+        const DensePlan p = dense_plan(n, d, sm_count);
+        double* part = (double*)ws;
+        dim3 grid((unsigned)p.ntiles, (unsigned)p.nchunks);
+        LSK_PROF("gram_dense", st) gram_dense_kernel<<<grid, 256, 0, st>>>((const float*)A->values, A->ld, n, d, p.rows_per, part);
+        LSK_PROF("gram_reduce", st) gram_dense_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(part, p.nchunks, d, alpha, beta, C);
+    } else {
+        const CsrPlan p = csr_plan(n, d, sm_count);
+        if (p.smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(gram_csr_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+            if (e != cudaSuccess) return e;
+        }
+        float* part = (float*)ws;
+        dim3 grid((unsigned)p.nblocks, (unsigned)p.nslices);
+        LSK_PROF("gram_csr", st) gram_csr_kernel<<<grid, 256, p.smem, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
+                                                   A->nnz, d, p.slice_rows, p.rows_per, part, flag);
+        LSK_PROF("gram_reduce", st) gram_csr_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(part, p.nblocks, d, alpha, beta, C);
+    }
+    return cudaGetLastError();
+}

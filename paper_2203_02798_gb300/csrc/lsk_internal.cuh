@@ -1,0 +1,162 @@
+// lsk_internal.cuh -- shared declarations of the CUDA library behind lsk.h.
+//
+// Device helpers (counter-based random draws, warp reductions) and the
+// internal launchers each .cu file provides to the C-ABI layer (api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/lsk.h"
+#include "prof.cuh"
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+// Device-side error flag bits (OR-ed by kernels, read by lsk_sync).
+enum : int {
+    LSK_FLAG_BAD_CSR = 1,
+    LSK_FLAG_RANK_DEFICIENT = 2,
+    LSK_FLAG_TIMEOUT = 4,
+};
+
+struct lsk_ctx {
+    int device;
+    int sm_count;
+    cudaStream_t stream;
+    void* ws;             // workspace (device), stream-ordered allocation
+    size_t ws_bytes;
+    int* flag;            // device int, OR of LSK_FLAG_*
+    LskProf* prof;        // per-kernel event timings (NULL until enabled)
+    int prof_on;
+    char err[512];
+};
+
+LskProf* lsk_prof_new();
+void lsk_prof_delete(LskProf* p);
+
+// Points lsk_prof_current at the context's profiler while a call runs.
+struct ProfGuard {
+    ProfGuard(lsk_ctx* ctx) { lsk_prof_current = (ctx && ctx->prof_on) ? ctx->prof : nullptr; }
+    ~ProfGuard() { lsk_prof_current = nullptr; }
+};
+
+// Bump allocator over the context workspace (256-byte aligned pieces).
+struct WsCarver {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon et al., SC'11).  Round: multiply words 0 and 2 by
+// the two Philox multipliers, recombine high/low halves with words 1, 3 and
+// the key; the key advances by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        if (rnd) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// CountSketch column i (Def. 3): bucket h(i) in [0, r) by multiply-shift of
+// the first word, sign from the top bit of the second word.
+__device__ __forceinline__ void cs_hash(uint64_t i, uint32_t r, uint32_t k0, uint32_t k1,
+                                        uint32_t& bucket, uint32_t& negative) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u), k0, k1);
+    bucket = __umulhi(w.x, r);
+    negative = w.y >> 31;
+}
+
+// Box-Muller pair from two 32-bit words: 24-bit uniforms u1 = (a+1) 2^-24,
+// u2 = b 2^-24 (both exact in float32), z0 = rho cos(2 pi u2), z1 = rho sin.
+__device__ __forceinline__ float2 box_muller24(uint32_t wa, uint32_t wb) {
+    const float u1 = (float)((wa >> 8) + 1u) * 5.9604644775390625e-08f;   // 2^-24, exact
+    const float rho = sqrtf(-2.0f * logf(u1));
+    float s, co;
+    sincospif((float)(wb >> 8) * 1.1920928955078125e-07f, &s, &co);      // 2 u2 = b 2^-23, exact
+    return make_float2(rho * co, rho * s);
+}
+
+// Four Gaussian entries G[4q + t, c], t = 0..3, unscaled (pairs (w0, w1) and
+// (w2, w3); even rows take the cosine branch).
+__device__ __forceinline__ float4 gauss4(uint64_t c, uint32_t q, uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 1u, q), k0, k1);
+    const float2 z01 = box_muller24(w.x, w.y);
+    const float2 z23 = box_muller24(w.z, w.w);
+    return make_float4(z01.x, z01.y, z23.x, z23.y);
+}
+
+__device__ __forceinline__ float bf16_round(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_flag(int* flag, int bit) {
+    if (flag) atomicOr(flag, bit);
+}
+
+// ---------------------------------------------------------------------------
+// internal launchers (all asynchronous on `st`)
+// ---------------------------------------------------------------------------
+// countsketch.cu
+size_t cs_workspace_bytes(int64_t n, int64_t r);
+cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws,
+                      int* flag, int sm_count, cudaStream_t st);
+cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
+                           cudaStream_t st);
+
+// gauss.cu
+size_t gauss_workspace_bytes(int64_t r, int64_t d, int64_t k, int32_t prec, int sm_count);
+cudaError_t gauss_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
+                         int32_t prec, float* GSA, void* ws, int sm_count, cudaStream_t st);
+cudaError_t gauss_debug_launch(int64_t k, int64_t r, uint64_t seed, int32_t prec, float* G,
+                               cudaStream_t st);
+
+// gram.cu
+size_t gram_workspace_bytes(const lsk_mat* A, int sm_count);
+cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws,
+                        int* flag, int sm_count, cudaStream_t st);
+
+// rownorms.cu
+size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c);
+cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha,
+                            double beta, int upper_tri, float* x, void* ws, int* flag,
+                            int sm_count, cudaStream_t st);
+
+// qr.cu
+size_t qr_workspace_bytes(int64_t k, int64_t d);
+cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv,
+                      float* Rinv32, void* ws, int* flag, int sm_count, cudaStream_t st);
+
+// lsq.cu
+size_t lsq_workspace_bytes(const lsk_mat* A);
+int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
+            const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info);

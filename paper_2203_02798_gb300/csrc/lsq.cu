@@ -1,0 +1,487 @@
+// lsq.cu -- sketch-and-precondition least squares (Alg. 12).
+//
+// Alg. 12 leaves the "parallel preconditioned iterative method" open; the
+// reading used here is LSQR (Paige & Saunders, ACM TOMS 1982) on
+// min_y ||A N y - r_t|| with N = R^-1 from the sketch, wrapped in FP64
+// iterative refinement:
+//     r_t = b - A x_t   (FP64, A's FP32 values taken exactly)
+//     eta_t = ||A^T r_t|| / ||A^T b||          stop when eta_t <= tol
+//     y = LSQR(A N, r_t) in FP32;  x_{t+1} = x_t + N y   (FP64)
+// Each LSQR iteration makes ONE pass over A: the block that forms
+// u_i = A_i p - (alpha/beta) u_i immediately adds u_i A_i^T into its partial
+// of A^T u while the row is still in registers.  The FP64 residual pass
+// likewise forms r_i and accumulates r_i A_i^T (giving A^T r for eta and
+// the first LSQR vector) in the same read.  Scalars live on the device; the
+// host reads them back once per iteration for the stopping test.
+#include "lsk_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+namespace {
+
+struct LsqrState {
+    double alpha, beta, rhobar, phibar, anorm2, atb_norm, eta, bnorm;
+    double arnorm, rnorm;
+    int done, it;
+};
+
+constexpr int kPassThreads = 256;
+
+// ---- FP64 residual + A^T r, dense: warp per row ---------------------------
+__global__ void __launch_bounds__(kPassThreads) resid64_dense_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t n, int64_t d, const double* __restrict__ b,
+    const double* __restrict__ x, float* __restrict__ u32, double* __restrict__ qpart,
+    double* __restrict__ sspart) {
+    extern __shared__ double sh[];   // x (d) then per-warp q (8 * d)
+    double* xs = sh;
+    double* qs = sh + d;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) xs[j] = x[j];
+    for (int64_t j = threadIdx.x; j < 8 * d; j += blockDim.x) qs[j] = 0.0;
+    __syncthreads();
+    double* qw = qs + w * d;
+    double ss = 0.0;
+    const int64_t wid = (int64_t)blockIdx.x * 8 + w, nw = (int64_t)gridDim.x * 8;
+    for (int64_t i = wid; i < n; i += nw) {
+        const float* row = A + i * lda;
+        double dot = 0.0;
+        for (int64_t j = lane; j < d; j += 32) dot = fma((double)row[j], xs[j], dot);
+        dot = warp_sum(dot);
+        const double ri = b[i] - dot;
+        if (lane == 0) u32[i] = (float)ri;
+        ss = fma(ri, ri, ss);
+        for (int64_t j = lane; j < d; j += 32) qw[j] = fma((double)row[j], ri, qw[j]);
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < 8; ++t) s += qs[t * d + j];
+        qpart[(int64_t)blockIdx.x * d + j] = s;
+    }
+    // each warp's ss is replicated across lanes (ri is uniform): lane 0 adds
+    __shared__ double ssw[8];
+    if (lane == 0) ssw[w] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < 8; ++t) s += ssw[t];
+        sspart[blockIdx.x] = s;
+    }
+}
+
+// ---- FP64 residual + A^T r, CSR: thread per row ----------------------------
+__global__ void __launch_bounds__(kPassThreads) resid64_csr_kernel(
+    const float* __restrict__ V, const int32_t* __restrict__ J, const int64_t* __restrict__ I,
+    int64_t n, int64_t nnz, int64_t d, const double* __restrict__ b, const double* __restrict__ x,
+    float* __restrict__ u32, double* __restrict__ qpart, double* __restrict__ sspart, int* flag) {
+    extern __shared__ double sh[];
+    double* xs = sh;
+    double* qs = sh + d;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        xs[j] = x[j];
+        qs[j] = 0.0;
+    }
+    __syncthreads();
+    double ss = 0.0;
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t k0 = I[i], k1 = I[i + 1];
+        double dot = 0.0;
+        const bool ok = !(k0 < 0 || k1 < k0 || k1 > nnz);
+        if (!ok) bad = true;
+        if (ok)
+            for (int64_t p = k0; p < k1; ++p) {
+                const int32_t j = J[p];
+                if (j >= 0 && j < d) dot = fma((double)V[p], xs[j], dot);
+                else bad = true;
+            }
+        const double ri = b[i] - dot;
+        u32[i] = (float)ri;
+        ss = fma(ri, ri, ss);
+        if (ok)
+            for (int64_t p = k0; p < k1; ++p) {
+                const int32_t j = J[p];
+                if (j >= 0 && j < d) atomicAdd(&qs[j], (double)V[p] * ri);
+            }
+    }
+    if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
+    ss = warp_sum(ss);
+    __shared__ double ssw[kPassThreads / 32];
+    if ((threadIdx.x & 31) == 0) ssw[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) qpart[(int64_t)blockIdx.x * d + j] = qs[j];
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < kPassThreads / 32; ++t) s += ssw[t];
+        sspart[blockIdx.x] = s;
+    }
+}
+
+// Reduce the residual pass: A^T r, eta, beta_1; then the LSQR start vectors
+// v_1 = N^T A^T r / (beta_1 alpha_1), w_1 = v_1, y = 0.  One block.
+__global__ void resid_finish_kernel(const double* __restrict__ qpart, const double* __restrict__ sspart,
+                                    int nblocks, int64_t d, const double* __restrict__ N64,
+                                    int first, LsqrState* st, float* __restrict__ v,
+                                    float* __restrict__ w, double* __restrict__ y,
+                                    double* __restrict__ atr) {
+    __shared__ double red[32];
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < nblocks; ++z) s += qpart[(int64_t)z * d + j];
+        atr[j] = s;
+    }
+    __syncthreads();
+    // ||A^T r|| and ||r||^2
+    double a2 = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) a2 = fma(atr[j], atr[j], a2);
+    double s2 = 0.0;
+    for (int z = threadIdx.x; z < nblocks; z += blockDim.x) s2 += sspart[z];
+    a2 = warp_sum(a2);
+    s2 = warp_sum(s2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[wid] = a2;
+        red[16 + wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A2 = 0.0, S2 = 0.0;
+        for (int t = 0; t < nw; ++t) {
+            A2 += red[t];
+            S2 += red[16 + t];
+        }
+        const double atrn = sqrt(A2);
+        if (first) st->atb_norm = atrn;
+        st->eta = (st->atb_norm > 0.0) ? atrn / st->atb_norm : 0.0;
+        st->beta = sqrt(S2);
+        st->bnorm = st->beta;
+    }
+    __syncthreads();
+    const double beta = st->beta;
+    // v_raw = N^T (A^T r) / beta   (N upper triangular: N^T v uses column j)
+    double vv = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t i = 0; i <= j; ++i) s = fma(N64[i * d + j], atr[i], s);
+        s = (beta > 0.0) ? s / beta : 0.0;
+        y[j] = s;   // temporary
+        vv = fma(s, s, vv);
+    }
+    vv = warp_sum(vv);
+    __syncthreads();
+    if (lane == 0) red[wid] = vv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double V2 = 0.0;
+        for (int t = 0; t < nw; ++t) V2 += red[t];
+        const double alpha = sqrt(V2);
+        st->alpha = alpha;
+        st->rhobar = alpha;
+        st->phibar = beta;
+        st->anorm2 = 0.0;
+        st->done = (alpha == 0.0 || beta == 0.0) ? 1 : 0;
+        st->it = 0;
+        st->arnorm = alpha * beta;
+        st->rnorm = beta;
+    }
+    __syncthreads();
+    const double alpha = st->alpha;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        const double vj = (alpha > 0.0) ? y[j] / alpha : 0.0;
+        v[j] = (float)vj;
+        w[j] = (float)vj;
+        y[j] = 0.0;
+    }
+}
+
+// p = N v (FP32, N upper triangular).  One block.
+__global__ void pv_kernel(const float* __restrict__ N32, int64_t d, const float* __restrict__ v,
+                          const LsqrState* __restrict__ st, float* __restrict__ p) {
+    if (st->done) return;
+    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+        float s = 0.f;
+        for (int64_t j = i; j < d; ++j) s = fmaf(N32[i * d + j], v[j], s);
+        p[i] = s;
+    }
+}
+
+// u <- A p - (alpha/beta) u; partial sums of u^2 and of A^T u.  Dense, warp per row.
+__global__ void __launch_bounds__(kPassThreads) lsqr_pass_dense_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t n, int64_t d, const float* __restrict__ p,
+    const LsqrState* __restrict__ st, float* __restrict__ u, float* __restrict__ qpart,
+    double* __restrict__ sspart) {
+    extern __shared__ float shf[];   // p (d) then per-warp q (8 * d)
+    if (st->done) return;
+    float* ps = shf;
+    float* qs = shf + d;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) ps[j] = p[j];
+    for (int64_t j = threadIdx.x; j < 8 * d; j += blockDim.x) qs[j] = 0.f;
+    __syncthreads();
+    const float ab = (st->beta > 0.0) ? (float)(st->alpha / st->beta) : 0.f;
+    float* qw = qs + w * d;
+    double ss = 0.0;
+    const int64_t wid = (int64_t)blockIdx.x * 8 + w, nw = (int64_t)gridDim.x * 8;
+    for (int64_t i = wid; i < n; i += nw) {
+        const float* row = A + i * lda;
+        float dot = 0.f;
+        for (int64_t j = lane; j < d; j += 32) dot = fmaf(row[j], ps[j], dot);
+        dot = warp_sum(dot);
+        const float ui = dot - ab * u[i];
+        __syncwarp();
+        if (lane == 0) u[i] = ui;
+        ss = fma((double)ui, (double)ui, ss);
+        for (int64_t j = lane; j < d; j += 32) qw[j] = fmaf(row[j], ui, qw[j]);
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        float s = 0.f;
+        for (int t = 0; t < 8; ++t) s += qs[t * d + j];
+        qpart[(int64_t)blockIdx.x * d + j] = s;
+    }
+    __shared__ double ssw[8];
+    if (lane == 0) ssw[w] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < 8; ++t) s += ssw[t];
+        sspart[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kPassThreads) lsqr_pass_csr_kernel(
+    const float* __restrict__ V, const int32_t* __restrict__ J, const int64_t* __restrict__ I,
+    int64_t n, int64_t nnz, int64_t d, const float* __restrict__ p, const LsqrState* __restrict__ st,
+    float* __restrict__ u, float* __restrict__ qpart, double* __restrict__ sspart) {
+    extern __shared__ float shf[];
+    if (st->done) return;
+    float* ps = shf;
+    float* qs = shf + d;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        ps[j] = p[j];
+        qs[j] = 0.f;
+    }
+    __syncthreads();
+    const float ab = (st->beta > 0.0) ? (float)(st->alpha / st->beta) : 0.f;
+    double ss = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t k0 = I[i], k1 = I[i + 1];
+        const bool ok = !(k0 < 0 || k1 < k0 || k1 > nnz);
+        float dot = 0.f;
+        if (ok)
+            for (int64_t q = k0; q < k1; ++q) {
+                const int32_t j = J[q];
+                if (j >= 0 && j < d) dot = fmaf(V[q], ps[j], dot);
+            }
+        const float ui = dot - ab * u[i];
+        u[i] = ui;
+        ss = fma((double)ui, (double)ui, ss);
+        if (ok)
+            for (int64_t q = k0; q < k1; ++q) {
+                const int32_t j = J[q];
+                if (j >= 0 && j < d) atomicAdd(&qs[j], V[q] * ui);
+            }
+    }
+    ss = warp_sum(ss);
+    __shared__ double ssw[kPassThreads / 32];
+    if ((threadIdx.x & 31) == 0) ssw[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) qpart[(int64_t)blockIdx.x * d + j] = qs[j];
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < kPassThreads / 32; ++t) s += ssw[t];
+        sspart[blockIdx.x] = s;
+    }
+}
+
+// One LSQR step after the pass (Paige & Saunders 1982, Sec. 4.1): beta,
+// v = (N^T A^T u)/beta... , the plane rotation and the y, w updates.  One block.
+__global__ void lsqr_step_kernel(const float* __restrict__ qpart, const double* __restrict__ sspart,
+                                 int nblocks, int64_t d, const float* __restrict__ N32,
+                                 LsqrState* st, float* __restrict__ v, float* __restrict__ w,
+                                 double* __restrict__ y, float* __restrict__ qtmp, double inner_tol) {
+    __shared__ double red[32];
+    __shared__ double sc[8];
+    if (st->done) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double s2 = 0.0;
+    for (int z = threadIdx.x; z < nblocks; z += blockDim.x) s2 += sspart[z];
+    s2 = warp_sum(s2);
+    if (lane == 0) red[wid] = s2;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < nblocks; ++z) s += qpart[(int64_t)z * d + j];
+        qtmp[j] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S2 = 0.0;
+        for (int t = 0; t < nw; ++t) S2 += red[t];
+        sc[0] = sqrt(S2);   // beta_{i+1}
+    }
+    __syncthreads();
+    const double beta = sc[0];
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+    // v_raw = N^T q / beta - beta v
+    double vv = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        float s = 0.f;
+        for (int64_t i = 0; i <= j; ++i) s = fmaf(N32[i * d + j], qtmp[i], s);
+        const double vr = (double)s * ib - beta * (double)v[j];
+        qtmp[d + j] = (float)vr;
+        vv = fma(vr, vr, vv);
+    }
+    vv = warp_sum(vv);
+    __syncthreads();
+    if (lane == 0) red[wid] = vv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double V2 = 0.0;
+        for (int t = 0; t < nw; ++t) V2 += red[t];
+        const double alpha_new = sqrt(V2);
+        const double alpha_old = st->alpha;
+        st->anorm2 += alpha_old * alpha_old + beta * beta;
+        const double rho = hypot(st->rhobar, beta);
+        const double c = st->rhobar / rho, s = beta / rho;
+        const double theta = s * alpha_new;
+        st->rhobar = -c * alpha_new;
+        const double phi = c * st->phibar;
+        st->phibar = s * st->phibar;
+        sc[1] = phi / rho;         // y step
+        sc[2] = theta / rho;       // w step
+        sc[3] = alpha_new > 0.0 ? 1.0 / alpha_new : 0.0;
+        st->alpha = alpha_new;
+        st->beta = beta;
+        st->rnorm = st->phibar;
+        st->arnorm = st->phibar * alpha_new * fabs(c);
+        st->it += 1;
+        if (st->arnorm <= inner_tol * sqrt(st->anorm2) * st->rnorm || alpha_new == 0.0 || beta == 0.0)
+            st->done = 1;
+    }
+    __syncthreads();
+    const double ys = sc[1], ws = sc[2], ia = sc[3];
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        const double wj = (double)w[j];
+        y[j] = fma(ys, wj, y[j]);
+        const double vj = (double)qtmp[d + j] * ia;
+        v[j] = (float)vj;
+        w[j] = (float)(vj - ws * wj);
+    }
+}
+
+// x <- x + N y (FP64).  One block.
+__global__ void update_x_kernel(const double* __restrict__ N64, int64_t d, const double* __restrict__ y,
+                                double* __restrict__ x) {
+    __shared__ double ys[1024];
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+        double s = 0.0;
+        for (int64_t j = i; j < d; ++j) s = fma(N64[i * d + j], ys[j], s);
+        x[i] += s;
+    }
+}
+
+int pass_blocks(int sm_count) { return 2 * sm_count; }
+
+}  // namespace
+
+size_t lsq_workspace_bytes(const lsk_mat* A) {
+    const int64_t n = A->n, d = A->d;
+    const int nb = pass_blocks(152 * 2);
+    return ws_round(sizeof(LsqrState)) + ws_round((size_t)n * 4) + 4 * ws_round((size_t)d * 8) +
+           ws_round((size_t)nb * d * 8) + ws_round((size_t)nb * 8) + 3 * ws_round((size_t)d * 4) +
+           ws_round((size_t)2 * d * 4) + 4096;
+}
+
+int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
+            const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = A->n, d = A->d;
+    const int nb = pass_blocks(ctx->sm_count);
+    WsCarver wc{(char*)ws, 0};
+    LsqrState* S = wc.take<LsqrState>(1);
+    float* u = wc.take<float>(n > 0 ? n : 1);
+    double* y = wc.take<double>(d);
+    double* atr = wc.take<double>(d);
+    double* qpart64 = wc.take<double>((size_t)nb * d);
+    double* sspart = wc.take<double>(nb);
+    float* v = wc.take<float>(d);
+    float* w = wc.take<float>(d);
+    float* p = wc.take<float>(d);
+    float* qtmp = wc.take<float>(2 * d);
+    float* qpart32 = reinterpret_cast<float*>(qpart64);   // reused by the FP32 pass
+
+    LsqrState h{};
+    cudaError_t e = cudaMemsetAsync(x, 0, (size_t)d * 8, st);
+    if (e != cudaSuccess) return LSK_ERR_CUDA;
+    const bool dense = A->kind == LSK_DENSE;
+    const size_t sh64 = dense ? (size_t)9 * d * 8 : (size_t)2 * d * 8;
+    const size_t sh32 = dense ? (size_t)9 * d * 4 : (size_t)2 * d * 4;
+    if (sh64 > 48 * 1024) {
+        cudaFuncSetAttribute(resid64_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64);
+        cudaFuncSetAttribute(resid64_csr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64);
+    }
+    if (sh32 > 48 * 1024) {
+        cudaFuncSetAttribute(lsqr_pass_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32);
+        cudaFuncSetAttribute(lsqr_pass_csr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32);
+    }
+    int total_it = 0, refinements = 0, status = LSK_ERR_NOT_CONVERGED;
+    double eta = INFINITY;
+    for (int t = 0; t <= o->max_refine; ++t) {
+        if (dense)
+            LSK_PROF("lsq_resid64", st) resid64_dense_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->ld, n, d, b, x, u,
+                                                                 qpart64, sspart);
+        else
+            LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
+                                                               A->nnz, d, b, x, u, qpart64, sspart, ctx->flag);
+        resid_finish_kernel<<<1, 256, 0, st>>>(qpart64, sspart, nb, d, Rinv64, t == 0 ? 1 : 0, S, v, w, y,
+                                               atr);
+        e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return LSK_ERR_CUDA;
+        eta = h.eta;
+        refinements = t;
+        if (!(eta > o->tol)) {
+            status = LSK_OK;
+            break;
+        }
+        if (t == o->max_refine) break;
+        int it = 0;
+        while (!h.done && it < o->max_iter) {
+            pv_kernel<<<1, 256, 0, st>>>(Rinv32, d, v, S, p);
+            if (dense)
+                LSK_PROF("lsq_pass", st) lsqr_pass_dense_kernel<<<nb, kPassThreads, sh32, st>>>((const float*)A->values, A->ld, n, d, p,
+                                                                       S, u, qpart32, sspart);
+            else
+                LSK_PROF("lsq_pass", st) lsqr_pass_csr_kernel<<<nb, kPassThreads, sh32, st>>>((const float*)A->values, A->colidx,
+                                                                     A->rowptr, n, A->nnz, d, p, S, u,
+                                                                     qpart32, sspart);
+            lsqr_step_kernel<<<1, 256, 0, st>>>(qpart32, sspart, nb, d, Rinv32, S, v, w, y, qtmp,
+                                                o->inner_tol);
+            ++it;
+            if ((it & 3) == 0 || it >= o->max_iter) {   // stopping test every 4 iterations
+                e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) return LSK_ERR_CUDA;
+            }
+        }
+        e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return LSK_ERR_CUDA;
+        total_it += h.it;
+        update_x_kernel<<<1, 256, 0, st>>>(Rinv64, d, y, x);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return LSK_ERR_CUDA;
+    if (info) {
+        info->iters = total_it;
+        info->refinements = refinements;
+        info->eta = eta;
+        info->status = status;
+    }
+    return status;
+}

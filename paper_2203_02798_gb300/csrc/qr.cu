@@ -1,0 +1,326 @@
+// qr.cu -- R of the sketch and R^-1 in FP64 (Alg. 12 step 2, Alg. 15 step 3).
+//
+// The paper factors the small sketch B (k x d) with an SVD; the reading used
+// here takes the QR factor R with a positive diagonal, computed as the
+// Cholesky factor of B^T B:
+//   1. C = B^T B in FP64 (products of FP32 values are exact in FP64), split
+//      over row chunks of B and tiles of C, partials added in fixed order;
+//   2. C = L L^T by right-looking blocked Cholesky, 16x16 blocks, two
+//      launches per block column (panel, trailing update), so the FP64 work
+//      is spread over the whole GPU (FP64 is scarce on this part);
+//   3. R = L^T; rank check min R_jj <= 16 eps d max R_jj (flag);
+//   4. R^-1 column by column (one warp per column, back substitution).
+// In exact arithmetic this R equals the sign-normalised Householder R of B.
+#include "lsk_internal.cuh"
+
+namespace {
+
+constexpr int QT = 32;   // tile edge of the sketch Gram
+constexpr int NB = 16;   // Cholesky block
+
+__device__ __forceinline__ void utile_of(int t, int nt, int& ta, int& tb) {
+    ta = 0;
+    while (t >= nt - ta) {
+        t -= nt - ta;
+        ++ta;
+    }
+    tb = ta + t;
+}
+
+__global__ void __launch_bounds__(256) sketch_gram64_kernel(const float* __restrict__ B, int64_t k,
+                                                            int64_t d, int64_t rows_per,
+                                                            double* __restrict__ part) {
+    __shared__ float Xa[QT][QT + 1];
+    __shared__ float Xb[QT][QT + 1];
+    const int nt = (int)((d + QT - 1) / QT);
+    int ta, tb;
+    utile_of(blockIdx.x, nt, ta, tb);
+    const int64_t a0 = (int64_t)ta * QT, b0 = (int64_t)tb * QT;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;   // outputs (2ty+u, 2tx+v)
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+    const int64_t r1 = min(k, r0 + rows_per);
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int64_t i0 = r0; i0 < r1; i0 += QT) {
+#pragma unroll
+        for (int t = 0; t < (QT * QT) / 256; ++t) {
+            const int idx = tid + 256 * t;
+            const int rr = idx / QT, cc = idx % QT;
+            const int64_t i = i0 + rr;
+            Xa[rr][cc] = (i < r1 && a0 + cc < d) ? B[i * d + a0 + cc] : 0.f;
+            Xb[rr][cc] = (i < r1 && b0 + cc < d) ? B[i * d + b0 + cc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < QT; ++rr) {
+            const double x0 = Xa[rr][2 * ty], x1 = Xa[rr][2 * ty + 1];
+            const double y0 = Xb[rr][2 * tx], y1 = Xb[rr][2 * tx + 1];
+            acc[0][0] = fma(x0, y0, acc[0][0]);
+            acc[0][1] = fma(x0, y1, acc[0][1]);
+            acc[1][0] = fma(x1, y0, acc[1][0]);
+            acc[1][1] = fma(x1, y1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+    const int ntiles = nt * (nt + 1) / 2;
+    double* P = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * QT * QT;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) P[(2 * ty + u) * QT + 2 * tx + v] = acc[u][v];
+}
+
+__global__ void sketch_gram64_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
+                                            int64_t d, double* __restrict__ C) {
+    const int nt = (int)((d + QT - 1) / QT);
+    const int ntiles = nt * (nt + 1) / 2;
+    const int64_t len = d * d;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+        int64_t a = e / d, b = e % d;
+        if (a > b) {
+            const int64_t t = a;
+            a = b;
+            b = t;
+        }
+        const int ta = (int)(a / QT), tb = (int)(b / QT);
+        const int tile = ta * nt - ta * (ta - 1) / 2 + (tb - ta);
+        const int64_t w = (a % QT) * QT + (b % QT);
+        double s = 0.0;
+        for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * QT * QT + w];
+        C[e] = s;
+    }
+}
+
+// Factor the diagonal block K of C (lower part) in shared memory.  Every
+// block of the panel launch does this redundantly (it is 16x16).  A pivot
+// that is not positive and finite flags rank deficiency and is replaced by 1.
+__device__ void factor_diag_block(double* C, int64_t d, int64_t kb, double (*L)[NB + 1], int m,
+                                  int* flag) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        L[i][j] = (i < m && j < m && j <= i) ? C[(kb + i) * d + kb + j] : 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int i = tid;
+        for (int j = 0; j < m; ++j) {
+            double piv = L[j][j];
+            if (!(piv > 0.0) || !isfinite(piv)) {
+                if (i == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+                piv = 1.0;
+            }
+            const double ljj = sqrt(piv);
+            __syncwarp();
+            if (i == j) L[j][j] = ljj;
+            if (i > j && i < m) L[i][j] /= ljj;
+            __syncwarp();
+            if (i > j && i < m)
+                for (int l = j + 1; l <= i; ++l) L[i][l] -= L[i][j] * L[l][j];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// Block 0 stores L_KK in `Ldiag` (not in C: the other blocks of this launch
+// are still reading A_KK from C); copy_diag_kernel moves it into C at the end.
+__global__ void chol_panel_kernel(double* __restrict__ C, int64_t d, int64_t K,
+                                  double* __restrict__ Ldiag, int* flag) {
+    __shared__ double L[NB][NB + 1];
+    const int64_t kb = K * NB;
+    const int m = (int)min((int64_t)NB, d - kb);
+    factor_diag_block(C, d, kb, L, m, flag);
+    if (blockIdx.x == 0) {
+        double* D = Ldiag + K * NB * NB;
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            const int i = e / NB, j = e % NB;
+            D[e] = (j <= i && i < m) ? L[i][j] : 0.0;
+        }
+        return;
+    }
+    // row block I = K + blockIdx.x: L_IK = A_IK L_KK^-T (forward substitution per row)
+    const int64_t ib = kb + (int64_t)blockIdx.x * NB;
+    if (ib >= d) return;
+    const int mi = (int)min((int64_t)NB, d - ib);
+    const int t = threadIdx.x;
+    if (t < mi) {
+        double x[NB];
+        double* row = C + (ib + t) * d + kb;
+        for (int j = 0; j < m; ++j) {
+            double s = row[j];
+            for (int l = 0; l < j; ++l) s -= x[l] * L[j][l];
+            x[j] = s / L[j][j];
+        }
+        for (int j = 0; j < m; ++j) row[j] = x[j];
+    }
+}
+
+// Trailing update of the lower triangle: A_IJ -= L_IK L_JK^T for I >= J > K.
+__global__ void chol_update_kernel(double* __restrict__ C, int64_t d, int64_t K) {
+    const int64_t nbk = (d + NB - 1) / NB;
+    const int T = (int)(nbk - K - 1);
+    int t = blockIdx.x, I = 0;
+    // lower-triangular tile pairs (J <= I) over the trailing T blocks
+    while (t > I) {
+        t -= I + 1;
+        ++I;
+    }
+    const int J = t;
+    const int64_t ib = (K + 1 + I) * NB, jb = (K + 1 + J) * NB, kb = K * NB;
+    __shared__ double Li[NB][NB + 1], Lj[NB][NB + 1];
+    const int mk = (int)min((int64_t)NB, d - kb);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int a = e / NB, b = e % NB;
+        Li[a][b] = (ib + a < d && b < mk) ? C[(ib + a) * d + kb + b] : 0.0;
+        Lj[a][b] = (jb + a < d && b < mk) ? C[(jb + a) * d + kb + b] : 0.0;
+    }
+    __syncthreads();
+    (void)T;
+    const int a = threadIdx.x / NB, b = threadIdx.x % NB;
+    if (ib + a < d && jb + b < d && (I != J || b <= a)) {
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < NB; ++l) s = fma(Li[a][l], Lj[b][l], s);
+        C[(ib + a) * d + jb + b] -= s;
+    }
+}
+
+__global__ void copy_diag_kernel(double* __restrict__ C, int64_t d,
+                                 const double* __restrict__ Ldiag) {
+    const int64_t kb = (int64_t)blockIdx.x * NB;
+    const double* D = Ldiag + (int64_t)blockIdx.x * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        if (kb + i < d && kb + j < d) C[(kb + i) * d + kb + j] = D[e];
+    }
+}
+
+__global__ void rank_check_kernel(const double* __restrict__ Lm, int64_t d, int* flag) {
+    double mn = INFINITY, mx = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        const double v = fabs(Lm[j * d + j]);
+        mn = fmin(mn, v);
+        mx = fmax(mx, v);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ double smn[32], smx[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        smn[w] = mn;
+        smx[w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mn = fmin(mn, smn[i]);
+            mx = fmax(mx, smx[i]);
+        }
+        mn = fmin(mn, smn[0]);
+        mx = fmax(mx, smx[0]);
+        const double eps = 2.220446049250313e-16;
+        if (!(mn > 16.0 * eps * (double)d * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+    }
+}
+
+// X = R^-1 with R = L^T: warp per column j, lane owns rows i = lane + 32 s.
+template <int S>
+__global__ void trinv_kernel(const double* __restrict__ Lm, int64_t d, double* __restrict__ X64,
+                             float* __restrict__ X32, double* __restrict__ Rout) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= d) return;
+    double xr[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) xr[s] = ((int64_t)(lane + 32 * s) == j) ? 1.0 : 0.0;
+    for (int64_t l = j; l >= 0; --l) {
+        const int owner = (int)(l & 31), slot = (int)(l >> 5);
+        double v = 0.0;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (s == slot) v = xr[s];
+        v = __shfl_sync(0xffffffffu, v, owner);
+        const double xl = v / Lm[l * d + l];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (s == slot && lane == owner) xr[s] = xl;
+        const double* Lrow = Lm + l * d;   // R[i][l] = L[l][i]
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t i = lane + 32 * s;
+            if (i < l) xr[s] = fma(-Lrow[i], xl, xr[s]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t i = lane + 32 * s;
+        if (i < d) {
+            const double v = (i <= j) ? xr[s] : 0.0;
+            if (X64) X64[i * d + j] = v;
+            if (X32) X32[i * d + j] = (float)v;
+            if (Rout) Rout[i * d + j] = (i <= j) ? Lm[j * d + i] : 0.0;
+        }
+    }
+}
+
+struct QrPlan {
+    int ntiles;
+    int64_t nchunks, rows_per;
+};
+QrPlan qr_plan(int64_t k, int64_t d) {
+    QrPlan p;
+    const int nt = (int)((d + QT - 1) / QT);
+    p.ntiles = nt * (nt + 1) / 2;
+    int64_t want = (600 + p.ntiles - 1) / p.ntiles;
+    int64_t rows = (k + want - 1) / want;
+    rows = ((rows + QT - 1) / QT) * QT;
+    if (rows < QT) rows = QT;
+    p.rows_per = rows;
+    p.nchunks = (k + rows - 1) / rows;
+    if (p.nchunks < 1) p.nchunks = 1;
+    return p;
+}
+
+}  // namespace
+
+size_t qr_workspace_bytes(int64_t k, int64_t d) {
+    const QrPlan p = qr_plan(k, d);
+    const int64_t nbk = (d + NB - 1) / NB;
+    return ws_round((size_t)d * d * 8) + ws_round((size_t)p.nchunks * p.ntiles * QT * QT * 8) +
+           ws_round((size_t)nbk * NB * NB * 8);
+}
+
+cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv, float* Rinv32,
+                      void* ws, int* flag, int sm_count, cudaStream_t st) {
+    if (d > 1024) return cudaErrorInvalidValue;
+    const QrPlan p = qr_plan(k, d);
+    WsCarver wc{(char*)ws, 0};
+    double* C = wc.take<double>((size_t)d * d);
+    double* part = wc.take<double>((size_t)p.nchunks * p.ntiles * QT * QT);
+    const int64_t nbk = (d + NB - 1) / NB;
+    double* Ldiag = wc.take<double>((size_t)nbk * NB * NB);
+    LSK_PROF("qr_gram64", st) sketch_gram64_kernel<<<dim3((unsigned)p.ntiles, (unsigned)p.nchunks), 256, 0, st>>>(B, k, d, p.rows_per,
+                                                                                      part);
+    int64_t g = (d * d + 255) / 256;
+    if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
+    LSK_PROF("qr_gram64", st) sketch_gram64_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, p.nchunks, d, C);
+    for (int64_t K = 0; K < nbk; ++K) {
+        const unsigned panel_blocks = (unsigned)(nbk - K);   // diag + blocks below
+        LSK_PROF("qr_cholesky", st) chol_panel_kernel<<<panel_blocks, 64, 0, st>>>(C, d, K, Ldiag, flag);
+        const int64_t T = nbk - K - 1;
+        if (T > 0) LSK_PROF("qr_cholesky", st) chol_update_kernel<<<(unsigned)(T * (T + 1) / 2), NB * NB, 0, st>>>(C, d, K);
+    }
+    LSK_PROF("qr_cholesky", st) copy_diag_kernel<<<(unsigned)nbk, NB * NB, 0, st>>>(C, d, Ldiag);
+    rank_check_kernel<<<1, 256, 0, st>>>(C, d, flag);
+    const unsigned tg = (unsigned)((d * 32 + 127) / 128);
+    if (d <= 256)
+        LSK_PROF("qr_trinv", st) trinv_kernel<8><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
+    else
+        LSK_PROF("qr_trinv", st) trinv_kernel<32><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
+    return cudaGetLastError();
+}

@@ -1,0 +1,313 @@
+"""GPU parity: every C-ABI call against the FP64 oracle, element by element.
+
+Sizes span several tiles / warps / buckets and a ragged tail.  Tolerances:
+  - hash and signs: bit-exact;
+  - integer-valued inputs (every FP32 partial sum exact): bit-exact;
+  - FP32 paths: the benchmark spec's bound of 1e-5 relative Frobenius error on SA
+    and A^T A, plus element-wise bounds from the summation length;
+  - leverage scores: max relative error <= 1e-3 against the oracle's estimate
+    on the same seeds;
+  - least squares: eta = ||A^T(b - Ax)|| / ||A^T b|| <= 1e-10, computed by the
+    oracle in FP64 on the GPU's x.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import countsketch as ocs
+from oracle import gaussian as oga
+from oracle import gram as ogr
+from oracle import leverage as olev
+from oracle import lsq as olsq
+from oracle import qr as oqr
+from oracle import rownorms as orn
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def lsk():
+    from paper_2203_02798_gb300 import build
+    build.build()
+    import paper_2203_02798_gb300 as p
+    return p
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_fro(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def csr_dev(lsk, V, J, I, d):
+    return lsk.csr_from_numpy(V, J, I, d)
+
+
+# ---------------------------------------------------------------- hash / G --
+@pytest.mark.parametrize("n,r,seed", [(100_003, 2500, 0), (70_001, 1, 5), (5000, 2**31 - 1, 2**63 + 17),
+                                      (1, 7, 3), (0, 3, 1)])
+def test_hash_bit_exact(lsk, n, r, seed):
+    b, s = lsk.debug_hash(n, r, seed)
+    ob, os_ = ocs.countsketch_hash(n, r, seed)
+    assert np.array_equal(host(b).astype(np.int64), ob)
+    assert np.array_equal(host(s).astype(np.int8), os_)
+
+
+@pytest.mark.parametrize("k,r,seed", [(100, 2500, 0), (13, 777, 2**40 + 3)])
+def test_gaussian_fp32_matches(lsk, k, r, seed):
+    G = host(lsk.debug_gauss(k, r, seed, "fp32")).astype(np.float64)
+    Go = oga.gaussian_matrix(k, r, seed, oga.PREC_FP32)
+    # the same float32-exact uniforms on both sides: only the float32
+    # evaluation of log / sqrt / sincospi and the scaling differ (a few ulp)
+    assert np.all(np.abs(G - Go) <= 16 * U32 * np.abs(Go) + 4 * U32 / np.sqrt(k))
+
+
+def test_gaussian_bf16_rounding_agrees(lsk):
+    k, r, seed = 64, 20000, 9
+    G = host(lsk.debug_gauss(k, r, seed, "bf16")).astype(np.float64)
+    Go = oga.gaussian_matrix(k, r, seed, oga.PREC_BF16)
+    diff = G != Go
+    # both sides round the float32 value; only few-ulp float32 evaluation
+    # differences that straddle a bfloat16 rounding midpoint disagree, by one
+    # bf16 ulp (expected rate ~ ulps * 2^-16)
+    assert diff.mean() < 2e-4
+    if diff.any():
+        assert np.all(np.abs(G[diff] - Go[diff]) <= 2.0**-7 * np.abs(Go[diff]) * 1.01)
+
+
+# ---------------------------------------------------------------- S * A ----
+@pytest.mark.parametrize("n,d,r", [(20_011, 50, 2500), (9_000, 256, 700), (4_099, 130, 5000),
+                                   (3_000, 3, 1), (1_000, 1, 7), (2_500, 64, 40_000)])
+def test_cs_sketch_dense_integer_bit_exact(lsk, n, d, r):
+    A = workloads.integer_dense(n, d, seed=n + d)
+    SA = host(lsk.cs_sketch(dev(A), r, seed=11))
+    ref = ocs.cs_sketch_dense(A, r, 11)
+    assert np.array_equal(SA.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("n,d,r,seed", [(20_000, 50, 2500, 0), (60_000, 256, 1024, 3),
+                                        (7_777, 200, 333, 2**50)])
+def test_cs_sketch_dense_float(lsk, n, d, r, seed):
+    A = workloads.dense_normal(n, d, seed=seed + 1)
+    SA = host(lsk.cs_sketch(dev(A), r, seed)).astype(np.float64)
+    bucket, sign = ocs.countsketch_hash(n, r, seed)
+    ref = ocs.countsketch_apply_dense(A, bucket, sign, r)
+    absref = ocs.countsketch_apply_dense(np.abs(A), bucket, np.ones_like(sign), r)
+    m = np.bincount(bucket, minlength=r).max()
+    assert rel_fro(SA, ref) <= 1e-5
+    assert np.all(np.abs(SA - ref) <= 2 * m * U32 * absref + 1e-30)
+
+
+def test_cs_sketch_dense_strided_and_empty(lsk):
+    A = workloads.dense_normal(3000, 40, seed=4)
+    big = torch.zeros((3000, 48), dtype=torch.float32, device="cuda")
+    big[:, :40] = dev(A)
+    SA = host(lsk.cs_sketch(big[:, :40], 97, 5)).astype(np.float64)
+    assert rel_fro(SA, ocs.cs_sketch_dense(A, 97, 5)) <= 1e-6
+    empty = torch.zeros((0, 16), dtype=torch.float32, device="cuda")
+    SA0 = lsk.cs_sketch(empty, 10, 1)
+    assert torch.count_nonzero(SA0).item() == 0
+
+
+@pytest.mark.parametrize("n,d,p,r", [(50_000, 200, 0.01, 4000), (20_000, 64, 0.2, 300), (1000, 33, 0.0, 17)])
+def test_cs_sketch_csr_integer_bit_exact(lsk, n, d, p, r):
+    V, J, I = workloads.integer_csr(n, d, p, seed=n)
+    SA = host(lsk.cs_sketch(csr_dev(lsk, V, J, I, d), r, 7))
+    ref = ocs.cs_sketch_csr(V, J, I, n, d, r, 7)
+    assert np.array_equal(SA.astype(np.float64), ref)
+
+
+def test_cs_sketch_csr_float(lsk):
+    n, d, r = 200_000, 200, 8000
+    V, J, I = workloads.csr_bernoulli(n, d, 0.01, seed=1)
+    SA = host(lsk.cs_sketch(csr_dev(lsk, V, J, I, d), r, 1)).astype(np.float64)
+    ref = ocs.cs_sketch_csr(V, J, I, n, d, r, 1)
+    assert rel_fro(SA, ref) <= 1e-6
+
+
+def test_cs_sketch_bad_csr_reported(lsk):
+    n, d = 500, 16
+    V, J, I = workloads.integer_csr(n, d, 0.3, seed=3)
+    J = J.copy()
+    J[len(J) // 2] = d          # out of range: skipped by the kernel, flagged
+    ctx = lsk.context()
+    lsk.cs_sketch(csr_dev(lsk, V, J, I, d), 10, 1)
+    with pytest.raises(lsk.LskError) as ei:
+        ctx.sync()
+    assert ei.value.name == "BAD_CSR"
+    ctx.sync()                   # the flag is cleared
+
+
+# ---------------------------------------------------------------- G * SA ---
+@pytest.mark.parametrize("r,d,k,prec", [(2500, 50, 100, "fp32"), (40_000, 200, 400, "fp32"),
+                                        (3000, 256, 512, "bf16"), (777, 3, 5, "fp32"), (1000, 129, 70, "bf16")])
+def test_gauss_sketch(lsk, r, d, k, prec):
+    SA = workloads.dense_normal(r, d, seed=r + d)
+    got = host(lsk.gauss_sketch(dev(SA), k, 21, prec)).astype(np.float64)
+    ref = oga.gauss_sketch(SA.astype(np.float64), k, 21, oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32)
+    # FP32: 1e-5.  BF16: G is exact in bf16 on both sides except the rare
+    # rounding disagreements above (each one bf16 ulp of one entry)
+    assert rel_fro(got, ref) <= (1e-5 if prec == "fp32" else 1e-4)
+    G = oga.gaussian_matrix(k, r, 21, oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32)
+    bound = np.abs(G) @ np.abs(SA.astype(np.float64))
+    slack = (2.0**-7 if prec == "bf16" else 0.0) * bound   # rare bf16 rounding disagreements of G
+    assert np.all(np.abs(got - ref) <= 2 * (r + 16) * U32 * bound + slack + 1e-30)
+
+
+# ---------------------------------------------------------------- A^T A ----
+@pytest.mark.parametrize("n,d", [(20_000, 50), (33_000, 256), (1000, 3), (5000, 130)])
+def test_gram_dense(lsk, n, d):
+    A = workloads.dense_normal(n, d, seed=d)
+    C = host(lsk.gram(dev(A))).astype(np.float64)
+    ref = ogr.gram_dense(A)
+    assert rel_fro(C, ref) <= 1e-5
+    assert np.array_equal(C, C.T)
+
+
+def test_gram_dense_integer_exact_and_alpha_beta(lsk):
+    A = workloads.integer_dense(4000, 70, seed=2, lo=-3, hi=3)
+    C = host(lsk.gram(dev(A))).astype(np.float64)
+    assert np.array_equal(C, ogr.gram_dense(A))
+    C0 = workloads.dense_normal(70, 70, seed=3)
+    Ct = dev(C0.copy())
+    lsk.gram(dev(A), alpha=0.5, beta=-2.0, C=Ct)
+    ref = ogr.gram_dense(A, 0.5, -2.0, C0)
+    assert rel_fro(host(Ct).astype(np.float64), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("n,d,p", [(200_000, 200, 0.01), (30_000, 256, 0.05), (4000, 20, 0.5)])
+def test_gram_csr(lsk, n, d, p):
+    V, J, I = workloads.csr_bernoulli(n, d, p, seed=d)
+    C = host(lsk.gram(csr_dev(lsk, V, J, I, d))).astype(np.float64)
+    ref = ogr.gram_csr(V, J, I, d)
+    assert rel_fro(C, ref) <= 1e-5
+
+
+# ----------------------------------------------------- row norms of A * B ---
+@pytest.mark.parametrize("n,d,c,tri", [(20_011, 50, 50, True), (10_000, 256, 256, True),
+                                       (3_333, 130, 17, False), (500, 1, 1, False)])
+def test_rownorms_dense(lsk, n, d, c, tri):
+    A = workloads.dense_normal(n, d, seed=c)
+    B = workloads.dense_normal(d, c, seed=d + 1)
+    if tri:
+        B = np.triu(B)
+    x = host(lsk.rownorms_prod(dev(A), dev(B), upper_triangular=tri)).astype(np.float64)
+    ref = orn.rownorms_prod_dense(A, B)
+    assert np.max(np.abs(x - ref) / ref) <= 1e-5
+
+
+def test_rownorms_alpha_beta(lsk):
+    A = workloads.dense_normal(1000, 20, seed=1)
+    B = workloads.dense_normal(20, 7, seed=2)
+    x0 = workloads.dense_normal(1000, 1, seed=3)[:, 0]
+    xt = dev(x0.copy())
+    lsk.rownorms_prod(dev(A), dev(B), alpha=2.0, beta=-0.5, x=xt)
+    ref = orn.rownorms_prod_dense(A, B, 2.0, -0.5, x0)
+    assert np.max(np.abs(host(xt) - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,d,p,c", [(100_000, 200, 0.01, 200), (20_000, 256, 0.05, 256), (3000, 40, 0.3, 9)])
+def test_rownorms_csr(lsk, n, d, p, c):
+    V, J, I = workloads.csr_bernoulli(n, d, p, seed=c)
+    B = workloads.dense_normal(d, c, seed=5)
+    x = host(lsk.rownorms_prod(csr_dev(lsk, V, J, I, d), dev(B))).astype(np.float64)
+    ref = orn.rownorms_prod_csr_alg8(V, J, I, n, B)
+    nz = ref > 0
+    assert np.all(x[~nz] == 0)
+    assert np.max(np.abs(x[nz] - ref[nz]) / ref[nz]) <= 1e-5
+
+
+# ---------------------------------------------------------------- R, R^-1 --
+@pytest.mark.parametrize("k,d", [(100, 50), (512, 256), (40, 37), (300, 1)])
+def test_sketch_qr(lsk, k, d):
+    B = workloads.dense_normal(k, d, seed=k) * (10.0 ** np.linspace(-3, 3, d)).astype(np.float32)
+    R, Ri = lsk.sketch_qr(dev(B))
+    R, Ri = host(R), host(Ri)
+    Ro = oqr.qr_r(B.astype(np.float64))
+    colnorm = np.linalg.norm(B.astype(np.float64), axis=0)
+    assert np.all(np.abs(R - Ro) <= 1e-9 * colnorm[None, :])
+    assert np.array_equal(R, np.triu(R)) and np.all(np.diag(R) > 0)
+    Rio = oqr.upper_triangular_inverse(Ro)
+    assert np.all(np.abs(Ri - Rio) <= 1e-8 * np.abs(Rio).max(axis=0)[None, :] + 1e-300)
+
+
+def test_sketch_qr_rank_deficient(lsk):
+    B = workloads.dense_normal(64, 8, seed=1)
+    B[:, 5] = B[:, 2]
+    ctx = lsk.context()
+    lsk.sketch_qr(dev(B))
+    with pytest.raises(lsk.LskError) as ei:
+        ctx.sync()
+    assert ei.value.name == "RANK_DEFICIENT"
+
+
+# ---------------------------------------------------------- leverage scores -
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_leverage_config1_dense_outliers(lsk, prec):
+    A = workloads.dense_outliers().astype(np.float32)          # the FP32 path casts once
+    ell, R = lsk.leverage_scores(dev(A), 2500, 100, 0, prec, return_R=True)
+    lsk.context().sync()
+    ell = host(ell).astype(np.float64)
+    ref, Ro = olev.leverage_scores_dense(A.astype(np.float64), 2500, 100, 0,
+                                         oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32)
+    assert np.max(np.abs(ell - ref) / ref) <= 1e-3
+    assert set(np.argsort(-ell)[:5]) == set(range(5))
+    colnorm = np.linalg.norm(Ro, axis=0)
+    assert np.all(np.abs(host(R) - Ro) <= 1e-4 * colnorm[None, :])
+
+
+def test_leverage_countsketch_only_k0(lsk):
+    A = workloads.dense_normal(30_000, 20, seed=7)
+    ell = lsk.leverage_scores(dev(A), 2000, 0, 3)
+    lsk.context().sync()
+    ell = host(ell).astype(np.float64)
+    ref, _ = olev.leverage_scores_dense(A.astype(np.float64), 2000, 0, 3)
+    assert np.max(np.abs(ell - ref) / ref) <= 1e-3
+
+
+def test_leverage_csr(lsk):
+    n, d = 200_000, 100
+    V, J, I = workloads.csr_bernoulli(n, d, 0.02, seed=2)
+    ell = lsk.leverage_scores(csr_dev(lsk, V, J, I, d), 10_000, 200, 1, "fp32")
+    lsk.context().sync()
+    ell = host(ell).astype(np.float64)
+    ref, _ = olev.leverage_scores_csr(V, J, I, n, d, 10_000, 200, 1)
+    nz = ref > 0
+    assert np.all(ell[~nz] == 0)          # empty rows score zero
+    assert np.max(np.abs(ell[nz] - ref[nz]) / ref[nz]) <= 1e-3
+
+
+# ------------------------------------------------------------ least squares -
+@pytest.mark.parametrize("kind", ["dense", "csr"])
+def test_sketch_precondition_lsq(lsk, kind):
+    n, d = 50_000, 32
+    if kind == "dense":
+        A = workloads.dense_normal(n, d, seed=9) * (10.0 ** np.linspace(-2, 2, d)).astype(np.float32)
+        A64 = A.astype(np.float64)
+        mv, rmv = (lambda v: A64 @ v), (lambda u: A64.T @ u)
+        Ad = dev(A)
+    else:
+        V, J, I = workloads.csr_bernoulli(n, d, 0.2, seed=9)
+        rows = np.repeat(np.arange(n), np.diff(I))
+        def mv(v):
+            return np.bincount(rows, weights=V.astype(np.float64) * v[J], minlength=n)
+        def rmv(u):
+            return np.bincount(J, weights=V.astype(np.float64) * u[rows], minlength=d)
+        Ad = csr_dev(lsk, V, J, I, d)
+    xs, b = workloads.lsq_rhs(n, d, mv, seed=4)
+    x, info = lsk.sketch_precondition_lsq(Ad, dev(b), r=d * d, k=2 * d, seed=5)
+    x = host(x)
+    eta = olsq.normal_equation_residual(mv, rmv, b, x)
+    assert eta <= 1e-10, (eta, info)
+    assert info["status"] == 0 and info["eta"] <= 1e-10
+    assert np.linalg.norm(x - xs) <= 1e-3 * np.linalg.norm(xs)
