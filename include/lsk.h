@@ -200,6 +200,34 @@ int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed,
 int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed,
                     int32_t prec, float* G);
 
+/* ---- fixed-capacity CountSketch (no device allocation) ------------------ */
+/* The paper has no counterpart to this call: it is an interface for callers
+ * that cannot let a library allocate device memory -- applications whose
+ * pool allocator owns all of HBM, or latency-critical loops where
+ * cudaMalloc / cudaFree may synchronise the device.
+ *
+ * Same result as lsk_cs_sketch (S*A, same hash, same layouts), but it takes
+ * no context and allocates nothing: its scratch is one 12 MiB array in device
+ * global memory reserved by the library on every GPU that loads it (held
+ * until the process exits).  The caller passes A and the output SA (device
+ * pointers) and the cudaStream_t to launch on (NULL = legacy default).
+ *  - Limits: n <= LSK_NOALLOC_MAX_ROWS, 1 <= r <= LSK_NOALLOC_MAX_BUCKETS;
+ *    larger sizes return LSK_ERR_UNSUPPORTED before anything is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents (the
+ *    bucket counts are cleared at the start of each call), so calls whose
+ *    GPU work overlaps -- on two streams or from two threads -- race and
+ *    must be serialised by the caller.
+ *  - Asynchronous on `stream`.  Out-of-range CSR entries are skipped and not
+ *    reported (there is no context to hold an error flag).
+ * Returns LSK_OK, LSK_ERR_INVALID_ARG, LSK_ERR_UNSUPPORTED or LSK_ERR_CUDA. */
+#define LSK_NOALLOC_MAX_ROWS    (1 << 20)
+#define LSK_NOALLOC_MAX_BUCKETS (1 << 18)
+int lsk_cs_sketch_noalloc(const lsk_mat* A, int64_t r, uint64_t seed,
+                          float* SA, void* stream);
+
 /* ---- tracing ------------------------------------------------------------ */
 /* Per-kernel CUDA-event timing on the context's stream (off by default).
  * While on, every kernel launch of a call is bracketed by two events; the
