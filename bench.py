@@ -153,7 +153,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=262_144)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller for profiling)")
     args = ap.parse_args()
+    global N_ROWS
+    N_ROWS = args.rows
     if args.impl == "reference":
         return run_reference(args)
 
@@ -299,7 +302,8 @@ def algorithmic_work(kernel):
     table = {
         "cs_dense_gather": {"bound": "hbm", "bytes": a_bytes + 4 * r * d},
         "rownorm_dense_simt": {"bound": "alu", "flops": n * d * (d + 1)},
-        "rownorm_dense_tc": {"bound": "hbm", "bytes": a_bytes + 4 * n},
+        "rownorm_dense_tc": {"bound": "hbm", "bytes": a_bytes + 4 * n,
+                             "flops": 3 * n * d * (d + 1)},
         "gauss_simt": {"bound": "alu", "flops": 2 * k * r * d},
         "gauss_tc": {"bound": "tensor", "flops": 2 * 2 * k * r * d},
     }

@@ -133,10 +133,14 @@ int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
  * rmsqn, Sec. 5; Alg. 8 for CSR A).  B: device d*c floats row-major.
  * x: device n floats, read when beta != 0.  A*B is never stored.
  * `upper_triangular` != 0 promises B[i][j] == 0 for i > j (c == d), which
- * lets the dense kernel skip the zero blocks. */
+ * lets the dense kernels skip the zero blocks.  prec (dense A):
+ * LSK_PREC_FP32 = CUDA-core FP32; LSK_PREC_BF16 = tensor cores with A and B
+ * split into bf16 hi + lo, A B ~ AhBh + AhBl + AlBh, FP32 accumulation, for
+ * d, c <= 256 (other shapes run the FP32 kernel).  CSR A always runs Alg. 8
+ * in FP32. */
 int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B,
                       int64_t c, double alpha, double beta,
-                      int32_t upper_triangular, float* x);
+                      int32_t upper_triangular, int32_t prec, float* x);
 
 /* R of the sketch (Alg. 12 step 2 / Alg. 15 step 3 with a QR in place of
  * the SVD): B = GSA (k x d floats, device, row-major, k >= d) -> R (d x d,

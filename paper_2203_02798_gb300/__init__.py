@@ -74,7 +74,7 @@ _SIGS = {
     "lsk_cs_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _P]),
     "lsk_gauss_sketch": (ctypes.c_int, [_P, _P, _I64, _I64, _I64, _U64, _I32, _P]),
     "lsk_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _P]),
-    "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _P]),
+    "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _I32, _P]),
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
@@ -245,7 +245,7 @@ def gram(A, alpha=1.0, beta=0.0, C=None, ctx=None):
     return C
 
 
-def rownorms_prod(A, B, alpha=1.0, beta=0.0, x=None, upper_triangular=False, ctx=None):
+def rownorms_prod(A, B, alpha=1.0, beta=0.0, x=None, upper_triangular=False, prec="fp32", ctx=None):
     """lsk_rownorms_prod: alpha ||A_i B||^2 + beta x_i (n float32)."""
     m, n, d = _mat(A)
     _check_cuda(B)
@@ -255,7 +255,7 @@ def rownorms_prod(A, B, alpha=1.0, beta=0.0, x=None, upper_triangular=False, ctx
         x = torch.empty(n, dtype=torch.float32, device=_dev(A))
         beta = 0.0
     ctx._call("lsk_rownorms_prod", ctypes.byref(m), _ptr(B), int(B.shape[1]), float(alpha), float(beta),
-              int(bool(upper_triangular)), _ptr(x))
+              int(bool(upper_triangular)), _prec(prec), _ptr(x))
     return x
 
 

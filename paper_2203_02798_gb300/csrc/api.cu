@@ -192,7 +192,7 @@ int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C
 }
 
 int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B, int64_t c, double alpha,
-                      double beta, int32_t upper_triangular, float* x) {
+                      double beta, int32_t upper_triangular, int32_t prec, float* x) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     ProfGuard pg(ctx);
     int rc = check_mat(ctx, A);
@@ -200,9 +200,11 @@ int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B, int64_t c,
     if (!B || !x) return fail(ctx, LSK_ERR_INVALID_ARG, "B / x is NULL");
     if (c < 1) return fail(ctx, LSK_ERR_INVALID_ARG, "c must be >= 1");
     if (upper_triangular && c != A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "upper_triangular needs c == d");
-    rc = ws_ensure(ctx, rownorms_workspace_bytes(A, c));
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    rc = ws_ensure(ctx, rownorms_workspace_bytes(A, c, upper_triangular, prec));
     if (rc) return rc;
-    cudaError_t e = rownorms_launch(A, B, c, alpha, beta, upper_triangular, x, ctx->ws, ctx->flag,
+    cudaError_t e = rownorms_launch(A, B, c, alpha, beta, upper_triangular, prec, x, ctx->ws, ctx->flag,
                                     ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_rownorms_prod");
     return finish(ctx, "lsk_rownorms_prod");
@@ -241,7 +243,7 @@ size_t stage_scratch(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int s
     }
     const size_t q = qr_workspace_bytes(k > 0 ? k : r, A->d);
     if (q > s) s = q;
-    const size_t rn = rownorms_workspace_bytes(A, A->d);
+    const size_t rn = rownorms_workspace_bytes(A, A->d, 1, prec);
     if (rn > s) s = rn;
     return s;
 }
@@ -311,7 +313,7 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, ui
     const SketchBufs b = carve(ctx->ws, A, r, k);
     cudaError_t e = sketch_and_factor(ctx, A, r, k, seed, prec, b, R_out);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (sketch)");
-    e = rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, ell, b.scratch, ctx->flag, ctx->sm_count,
+    e = rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, prec, ell, b.scratch, ctx->flag, ctx->sm_count,
                         ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (row norms)");
     return finish(ctx, "lsk_leverage_scores");

@@ -146,10 +146,15 @@ cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, v
                         int* flag, int sm_count, cudaStream_t st);
 
 // rownorms.cu
-size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c);
+size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec);
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha,
-                            double beta, int upper_tri, float* x, void* ws, int* flag,
+                            double beta, int upper_tri, int32_t prec, float* x, void* ws, int* flag,
                             int sm_count, cudaStream_t st);
+// rownorms_tc.cu
+bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri);
+size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri);
+cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta,
+                               int upper_tri, float* x, void* ws, int* flag, int sm_count, cudaStream_t st);
 
 // qr.cu
 size_t qr_workspace_bytes(int64_t k, int64_t d);

@@ -194,16 +194,31 @@ def test_gram_csr(lsk, n, d, p):
 
 
 # ----------------------------------------------------- row norms of A * B ---
-@pytest.mark.parametrize("n,d,c,tri", [(20_011, 50, 50, True), (10_000, 256, 256, True),
-                                       (3_333, 130, 17, False), (500, 1, 1, False)])
-def test_rownorms_dense(lsk, n, d, c, tri):
-    A = workloads.dense_normal(n, d, seed=c)
+RN_CASES = [(20_011, 50, 50, True), (10_000, 256, 256, True), (3_333, 130, 17, False), (500, 1, 1, False),
+            (70_000, 64, 64, True), (1_000, 256, 160, False), (2_000, 256, 256, False), (129, 200, 200, True)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("n,d,c,tri", RN_CASES)
+def test_rownorms_dense(lsk, n, d, c, tri, prec):
+    A = workloads.dense_normal(n, d, seed=c) * (10.0 ** np.linspace(-2, 2, d)).astype(np.float32)
     B = workloads.dense_normal(d, c, seed=d + 1)
     if tri:
         B = np.triu(B)
-    x = host(lsk.rownorms_prod(dev(A), dev(B), upper_triangular=tri)).astype(np.float64)
-    ref = orn.rownorms_prod_dense(A, B)
-    assert np.max(np.abs(x - ref) / ref) <= 1e-5
+    x = host(lsk.rownorms_prod(dev(A), dev(B), upper_triangular=tri, prec=prec)).astype(np.float64)
+    lsk.context().sync()
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = orn.rownorms_prod_dense(A64, B64)
+    y = A64 @ B64
+    absy = np.abs(A64) @ np.abs(B64)
+    if prec == "fp32":
+        E = (d + 2) * U32 * absy                       # FP32 dot products of length d
+    else:
+        # split-bf16 operands (~2^-17 each, dropped lo*lo ~2^-18) + FP32 sums of 3d terms
+        E = (2.0**-15 + 3 * (d + 2) * U32) * absy
+    bound = np.sum(2 * np.abs(y) * E + E * E, axis=1) + 2 * U32 * ref * c
+    assert np.all(np.abs(x - ref) <= bound)
+    assert np.max(np.abs(x - ref) / ref) <= (1e-5 if prec == "fp32" else 1e-3)
 
 
 def test_rownorms_alpha_beta(lsk):
