@@ -143,6 +143,7 @@ def workload_config(args):
 
 # ---------------------------------------------------------------- GPU path --
 def main():
+    global N_ROWS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -155,7 +156,6 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller for profiling)")
     args = ap.parse_args()
-    global N_ROWS
     N_ROWS = args.rows
     if args.impl == "reference":
         return run_reference(args)
