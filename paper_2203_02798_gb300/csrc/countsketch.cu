@@ -132,8 +132,8 @@ __global__ void write_total_kernel(uint32_t* off, int64_t r, uint32_t n) { off[r
 
 // ---- dense gather ---------------------------------------------------------
 // One warp per bucket.  Lanes own VEC consecutive columns in each of U
-// column groups of 32*VEC; the bucket's rows are fetched four at a time so
-// that each warp keeps 4 rows of loads in flight.
+// column groups of 32*VEC; the bucket's rows are fetched kBatch at a time so
+// that each warp keeps kBatch rows of loads in flight.
 template <int VEC>
 struct VecT;
 template <>
@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
     const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA) {
     using V = typename VecT<VEC>::T;
     constexpr int kCols = 32 * VEC * U;  // columns per pass
+    constexpr int kBatch = (VEC * U >= 8) ? 8 : 4;   // rows of loads in flight per warp
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -192,11 +193,11 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
                 const uint32_t m = min(32u, e - t0);
                 const uint32_t mine = (lane < (int)m) ? perm[t0 + lane] : 0u;
                 uint32_t j = 0;
-                for (; j + 4 <= m; j += 4) {
-                    V v[4][U];
-                    float sg[4];
+                for (; j + kBatch <= m; j += kBatch) {
+                    V v[kBatch][U];
+                    float sg[kBatch];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < kBatch; ++q) {
                         const uint32_t p = __shfl_sync(0xffffffffu, mine, j + q);
                         sg[q] = (p >> 31) ? -1.0f : 1.0f;
                         const float* row = A + (int64_t)(p & 0x7fffffffu) * lda + c0;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
+                    for (int q = 0; q < kBatch; ++q)
 #pragma unroll
                         for (int u = 0; u < U; ++u) vadd(acc[u], v[q][u], sg[q]);
                 }

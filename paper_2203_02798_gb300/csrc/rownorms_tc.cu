@@ -7,33 +7,47 @@
 //     A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi     (FP32 accumulation),
 // the dropped A_lo B_lo term being ~2^-18 relative.
 //
-// Persistent kernel, one CTA per SM (416 threads):
+// Persistent kernel, one CTA per SM (672 threads):
 //   warps 0-3   epilogue: tcgen05.ld the accumulator rows, square, sum, store
 //   warp  4     TMEM allocation; lane 0 issues every MMA and commit
-//   warps 5-12  converters: stream A from HBM (two K-chunks of loads in
-//               flight per thread), split into bf16 hi/lo and write the
-//               128-byte-swizzled K-major operand tiles of the current stage
-// B (hi and lo) stays resident in shared memory for the whole kernel; when
-// B is upper triangular (B = R^-1) only the blocks on or above the diagonal
-// are stored and multiplied: K-chunk q (rows 64q..64q+63 of B) only touches
-// columns >= 64q.  TMEM holds two 128 x 256 FP32 accumulators so the
-// epilogue of one tile overlaps the MMAs of the next.
+//   warps 5-20  converters: each owns every 16th half-chunk (64 rows x 32 K)
+//               of the operand stream: it loads its piece from HBM (fully
+//               coalesced 16-byte loads), splits it into bf16 hi/lo and
+//               writes the 64-byte-swizzled K-major tile into the stage
+//               ring.  A warp arrives on the stage barrier only after its own
+//               loads have landed (the arrive has release semantics and would
+//               otherwise wait for loads still in flight), while the other 15
+//               warps keep 8 chunks (128 KB) of loads in flight per SM.  The
+//               uses of each stage are handed out in order (a per-stage count
+//               of stored halves), so no warp waits on a stage barrier more
+//               than one phase ahead of it.
+// B (hi and lo) stays resident in shared memory for the whole kernel.  K is
+// cut into chunks of 32; when B is upper triangular (B = R^-1) K-chunk q
+// (rows 32q..32q+31 of B) only touches columns >= 32q, so only those blocks
+// are stored and multiplied.  TMEM holds two 128 x 256 FP32 accumulators so
+// the epilogue of one tile overlaps the MMAs of the next.
 #include "tc_common.cuh"
 
 namespace {
 
 constexpr int kRows = 128;
-constexpr int kStages = 2;
-constexpr int kConvWarps = 8;
+constexpr int kKC = 32;                              // K per chunk (one 64-byte swizzle row)
+constexpr int kMaxQ = 8;                             // d <= 256
+constexpr int kConvWarps = 16;
+constexpr int kPieceRows = 64;                       // rows of one converter piece (half a chunk)
+constexpr int kPieces = kRows / kPieceRows;          // pieces per chunk (2)
+constexpr int kF4 = kPieceRows * kKC / 4 / 32;       // float4 loads per lane per piece (16)
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kConvWarp0 = 5;
 constexpr int kThreads = (kEpiWarps + 1 + kConvWarps) * 32;
-constexpr uint32_t kHalfStage = kRows * 128;        // one bf16 tile, 64 K-columns
-constexpr uint32_t kStageBytes = 2 * kHalfStage;    // hi + lo
+constexpr uint32_t kHalfStage = kRows * kKC * 2;     // one bf16 tile: 8 KB
+constexpr uint32_t kStageBytes = 2 * kHalfStage;     // hi + lo
+constexpr int kMaxStages = 8;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;
 constexpr size_t kSmemLimit = 232448;
+constexpr size_t kSmemExtra = 1024 + 256;            // alignment slack + barriers
 
 struct RnParams {
     const float* A;
@@ -41,79 +55,76 @@ struct RnParams {
     int64_t n;
     float* x;
     float alpha, beta;
-    int d, c, nq, npad, ntiles;
-    uint32_t n0[4], nn[4], boff[4];
+    int d, c, nq, npad, ntiles, stages;
+    uint32_t n0[kMaxQ], nn[kMaxQ], boff[kMaxQ];
     uint32_t b_bytes;
     int* flag;
 };
 
 // B (d x c, row-major) -> the shared-memory image of its bf16 hi / lo parts:
-// per K-chunk q, an (nn[q] x 64) K-major tile whose row r is column n0[q]+r.
+// per K-chunk q, an (nn[q] x 32) K-major tile whose row r is column n0[q]+r.
 __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnParams p, uint8_t* __restrict__ img) {
     uint32_t total = 0;
-    for (int q = 0; q < p.nq; ++q) total += p.nn[q] * 32;
+    for (int q = 0; q < p.nq; ++q) total += p.nn[q] * (kKC / 2);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         int q = 0;
         uint32_t el = e;
-        while (el >= p.nn[q] * 32) {
-            el -= p.nn[q] * 32;
+        while (el >= p.nn[q] * (kKC / 2)) {
+            el -= p.nn[q] * (kKC / 2);
             ++q;
         }
-        const uint32_t r = el >> 5, kl = (el & 31) * 2;
-        const int j = (int)(p.n0[q] + r), k = 64 * q + (int)kl;
+        const uint32_t r = el / (kKC / 2), kl = (el % (kKC / 2)) * 2;
+        const int j = (int)(p.n0[q] + r), k = kKC * q + (int)kl;
         const float b0 = (k < p.d && j < p.c) ? B[(int64_t)k * p.c + j] : 0.f;
         const float b1 = (k + 1 < p.d && j < p.c) ? B[(int64_t)(k + 1) * p.c + j] : 0.f;
         uint32_t hi, lo;
         tc::split_bf16x2(b0, b1, hi, lo);
-        const uint32_t off = p.boff[q] + tc::sw128_offset(r, kl);
+        const uint32_t off = p.boff[q] + tc::sw64_offset(r, kl);
         *reinterpret_cast<uint32_t*>(img + off) = hi;
         *reinterpret_cast<uint32_t*>(img + p.b_bytes + off) = lo;
     }
 }
 
+// Lane l loads float4 number f = l + 32 i of the piece (row f / 8 of the
+// piece, columns 4 (f % 8) .. +3): consecutive lanes read consecutive
+// 16-byte pieces, four 128-byte row segments per warp instruction.
 template <bool VEC>
-__device__ __forceinline__ void load_chunk(const RnParams& p, int tile, int q, int ct, float4 (&v)[4][2]) {
+__device__ __forceinline__ void load_piece(const RnParams& p, int tile, int q, int half, int lane, float4 (&v)[kF4]) {
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
-        const int idx = ct + 256 * it;
-        const int m = idx >> 3, cc = idx & 7;
+    for (int i = 0; i < kF4; ++i) {
+        const int f = lane + 32 * i;
+        const int m = half * kPieceRows + (f >> 3), c4 = f & 7;
         const int64_t row = (int64_t)tile * kRows + m;
-        const int k = 64 * q + 8 * cc;
-        v[it][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        v[it][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k = kKC * q + 4 * c4;
+        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < p.n && k < p.d) {
             const float* src = p.A + row * p.lda + k;
             if constexpr (VEC) {
-                asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                    : "=f"(v[it][0].x), "=f"(v[it][0].y), "=f"(v[it][0].z), "=f"(v[it][0].w)
-                    : "l"(src));
-                asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                    : "=f"(v[it][1].x), "=f"(v[it][1].y), "=f"(v[it][1].z), "=f"(v[it][1].w)
-                    : "l"(src + 4));
+                // volatile: a prefetch kAhead chunks before its use, issued here
+                asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                             : "=f"(v[i].x), "=f"(v[i].y), "=f"(v[i].z), "=f"(v[i].w)
+                             : "l"(src));
             } else {
-                float t[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) t[e] = (k + e < p.d) ? __ldg(src + e) : 0.f;
-                v[it][0] = make_float4(t[0], t[1], t[2], t[3]);
-                v[it][1] = make_float4(t[4], t[5], t[6], t[7]);
+                v[i].x = __ldg(src);
+                v[i].y = (k + 1 < p.d) ? __ldg(src + 1) : 0.f;
+                v[i].z = (k + 2 < p.d) ? __ldg(src + 2) : 0.f;
+                v[i].w = (k + 3 < p.d) ? __ldg(src + 3) : 0.f;
             }
         }
     }
 }
 
-__device__ __forceinline__ void store_chunk(uint8_t* stage, int ct, const float4 (&v)[4][2]) {
+__device__ __forceinline__ void store_piece(uint8_t* stage, int half, int lane, const float4 (&v)[kF4]) {
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
-        const int idx = ct + 256 * it;
-        const uint32_t m = idx >> 3, cc = idx & 7;
-        uint4 hi, lo;
-        tc::split_bf16x2(v[it][0].x, v[it][0].y, hi.x, lo.x);
-        tc::split_bf16x2(v[it][0].z, v[it][0].w, hi.y, lo.y);
-        tc::split_bf16x2(v[it][1].x, v[it][1].y, hi.z, lo.z);
-        tc::split_bf16x2(v[it][1].z, v[it][1].w, hi.w, lo.w);
-        const uint32_t off = tc::sw128_offset(m, 8 * cc);
-        *reinterpret_cast<uint4*>(stage + off) = hi;
-        *reinterpret_cast<uint4*>(stage + kHalfStage + off) = lo;
+    for (int i = 0; i < kF4; ++i) {
+        const int f = lane + 32 * i;
+        const uint32_t m = half * kPieceRows + (f >> 3), c4 = f & 7;
+        uint2 hi, lo;
+        tc::split_bf16x2(v[i].x, v[i].y, hi.x, lo.x);
+        tc::split_bf16x2(v[i].z, v[i].w, hi.y, lo.y);
+        const uint32_t off = tc::sw64_offset(m, 4 * c4);
+        *reinterpret_cast<uint2*>(stage + off) = hi;
+        *reinterpret_cast<uint2*>(stage + kHalfStage + off) = lo;
     }
 }
 
@@ -128,27 +139,32 @@ template <bool VEC>
 __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams p, const uint8_t* __restrict__ img) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + kStages * kStageBytes;            // hi image, then lo image
+    const int S = p.stages;
+    uint8_t* sA = smem;                                  // S stages of (hi, lo)
+    uint8_t* sB = smem + S * kStageBytes;                // B hi image, then lo image
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * p.b_bytes);
-    uint64_t* full = bars;        // [2] stage filled     (kConvWarps arrivals)
-    uint64_t* empty = bars + 2;   // [2] stage consumed   (MMA commit)
-    uint64_t* tfull = bars + 4;   // [2] accumulator done (MMA commit)
-    uint64_t* tempty = bars + 6;  // [2] accumulator read (kEpiWarps arrivals)
-    uint64_t* fin = bars + 8;     // all MMAs complete    (MMA commit)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+    uint64_t* full = bars;                       // [S] stage filled     (kPieces arrivals)
+    uint64_t* empty = bars + kMaxStages;         // [S] stage consumed   (MMA commit)
+    uint64_t* tfull = bars + 2 * kMaxStages;     // [2] accumulator done (MMA commit)
+    uint64_t* tempty = tfull + 2;                // [2] accumulator read (kEpiWarps arrivals)
+    uint64_t* fin = tfull + 4;                   // all MMAs complete    (MMA commit)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* stored = const_cast<int*>(abort) + 1;   // [S] halves stored per stage (in use order)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(full + s, kConvWarps);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full + s, kPieces);
             tc::mbar_init(empty + s, 1);
-            tc::mbar_init(tfull + s, 1);
-            tc::mbar_init(tempty + s, kEpiWarps);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tfull + a, 1);
+            tc::mbar_init(tempty + a, kEpiWarps);
         }
         tc::mbar_init(fin, 1);
         *abort = 0;
+        for (int s = 0; s < kMaxStages; ++s) stored[s] = 0;
         tc::fence_mbar_init();
     }
     if (warp == kMmaWarp) {
@@ -176,11 +192,18 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
             tc::fence_after_sync();
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * kAccCols;
             float sum = 0.f;
-            for (int col = 0; col < p.npad; col += 32) {
-                float v[32];
-                tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col, v);
+            for (int col = 0; col < p.npad; col += 64) {   // two loads in flight per wait
+                uint32_t v0[32], v1[32];
+                tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col, v0);
+                const bool two = col + 32 < p.npad;
+                if (two) tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col + 32u, v1);
+                tc::tmem_ld_wait();
 #pragma unroll
-                for (int e = 0; e < 32; ++e) sum = fmaf(v[e], v[e], sum);
+                for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v0[e]), __uint_as_float(v0[e]), sum);
+                if (two) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v1[e]), __uint_as_float(v1[e]), sum);
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -193,15 +216,15 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
         if (lane == 0) {
             const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
             bool ok = true;
+            int g = 0;
             for (int i = 0; i < my_tiles && ok; ++i) {
                 const int acc = i & 1;
                 if (!tc::mbar_wait(tempty + acc, ((uint32_t)(i >> 1) & 1u) ^ 1u, abort)) break;
                 tc::fence_after_sync();
                 const uint32_t d_base = tmem + (uint32_t)acc * kAccCols;
-                for (int q = 0; q < p.nq; ++q) {
-                    const int g = i * p.nq + q;
-                    const int s = g & 1;
-                    if (!tc::mbar_wait(full + s, (uint32_t)(g >> 1) & 1u, abort)) {
+                for (int q = 0; q < p.nq; ++q, ++g) {
+                    const int s = g % S;
+                    if (!tc::mbar_wait(full + s, (uint32_t)(g / S) & 1u, abort)) {
                         ok = false;
                         break;
                     }
@@ -211,12 +234,12 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
                     const uint32_t idesc = tc::idesc_bf16_f32(128, p.nn[q]);
                     const uint32_t d_tmem = d_base + p.n0[q];
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t ko = 32u * kk;
-                        tc::mma_bf16(d_tmem, tc::desc_sw128_kmajor(a_hi + ko), tc::desc_sw128_kmajor(b_hi + ko), idesc,
+                    for (int kk = 0; kk < kKC / 16; ++kk) {
+                        const uint32_t ko = 32u * kk;   // 16 bf16 = 32 bytes along the swizzled row
+                        tc::mma_bf16(d_tmem, tc::desc_sw64_kmajor(a_hi + ko), tc::desc_sw64_kmajor(b_hi + ko), idesc,
                                      (q | kk) != 0);
-                        tc::mma_bf16(d_tmem, tc::desc_sw128_kmajor(a_hi + ko), tc::desc_sw128_kmajor(b_lo + ko), idesc, 1);
-                        tc::mma_bf16(d_tmem, tc::desc_sw128_kmajor(a_lo + ko), tc::desc_sw128_kmajor(b_hi + ko), idesc, 1);
+                        tc::mma_bf16(d_tmem, tc::desc_sw64_kmajor(a_hi + ko), tc::desc_sw64_kmajor(b_lo + ko), idesc, 1);
+                        tc::mma_bf16(d_tmem, tc::desc_sw64_kmajor(a_lo + ko), tc::desc_sw64_kmajor(b_hi + ko), idesc, 1);
                     }
                     tc::mma_commit(empty + s);
                 }
@@ -230,26 +253,30 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
         __syncwarp();
     } else {
         // ------------------------------------------------------------ converters
-        const int ct = threadIdx.x - kConvWarp0 * 32;   // 0 .. 255
+        // piece number pc = kPieces * g + half goes to converter warp pc % kConvWarps
+        const int cw = warp - kConvWarp0;
+        const int half = cw % kPieces;
         const int G = my_tiles * p.nq;
-        float4 b0[4][2], b1[4][2];
-        auto tile_of = [&](int g) { return (int)blockIdx.x + (g / p.nq) * (int)gridDim.x; };
-        if (G > 0) load_chunk<VEC>(p, tile_of(0), 0 % p.nq, ct, b0);
-        if (G > 1) load_chunk<VEC>(p, tile_of(1), 1 % p.nq, ct, b1);
-        for (int g = 0; g < G; g += 2) {
-            if (!warp_wait(empty + 0, ((uint32_t)(g >> 1) & 1u) ^ 1u, abort)) break;
-            store_chunk(sA, ct, b0);
+        const int gstep = kConvWarps / kPieces;
+        float4 buf[kF4];
+        for (int g = cw / kPieces; g < G; g += gstep) {
+            load_piece<VEC>(p, (int)blockIdx.x + (g / p.nq) * (int)gridDim.x, g % p.nq, half, lane, buf);
+            const int s = g % S, u = g / S;
+            int ok = 1;
+            if (lane == 0) {
+                // both halves of this stage's previous use are stored: the stage
+                // barriers are now at most one phase behind this use
+                ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + s), kPieces * u, abort) &&
+                     tc::mbar_wait(empty + s, ((uint32_t)u & 1u) ^ 1u, abort);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            store_piece(sA + s * kStageBytes, half, lane, buf);
             tc::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(full + 0);
-            if (g + 2 < G) load_chunk<VEC>(p, tile_of(g + 2), (g + 2) % p.nq, ct, b0);
-            if (g + 1 >= G) break;
-            if (!warp_wait(empty + 1, ((uint32_t)((g + 1) >> 1) & 1u) ^ 1u, abort)) break;
-            store_chunk(sA + kStageBytes, ct, b1);
-            tc::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(full + 1);
-            if (g + 3 < G) load_chunk<VEC>(p, tile_of(g + 3), (g + 3) % p.nq, ct, b1);
+            if (lane == 0) {
+                tc::mbar_arrive(full + s);
+                atomicAdd(stored + s, 1);
+            }
         }
     }
 
@@ -262,32 +289,38 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }
 
+size_t smem_bytes(const RnParams& p) {
+    return (size_t)p.stages * kStageBytes + 2 * (size_t)p.b_bytes + kSmemExtra;
+}
+
 bool make_plan(const lsk_mat* A, int64_t c, int upper_tri, RnParams& p) {
     const int64_t d = A->d;
     if (A->kind != LSK_DENSE || d < 1 || d > 256 || c < 1 || c > 256) return false;
     if (upper_tri && c != d) return false;
     p.d = (int)d;
     p.c = (int)c;
-    p.nq = (int)((d + 63) / 64);
+    p.nq = (int)((d + kKC - 1) / kKC);
     p.npad = (int)((c + 31) / 32) * 32;
     uint32_t off = 0;
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kMaxQ; ++q) {
         p.n0[q] = 0;
         p.nn[q] = 0;
         p.boff[q] = off;
         if (q < p.nq) {
-            p.n0[q] = upper_tri ? (uint32_t)(64 * q) : 0u;
+            p.n0[q] = upper_tri ? (uint32_t)(kKC * q) : 0u;
             if ((int)p.n0[q] >= p.npad) return false;
             p.nn[q] = (uint32_t)p.npad - p.n0[q];
-            off += p.nn[q] * 128u;
+            off += p.nn[q] * (kKC * 2);
         }
     }
-    p.b_bytes = off;
-    const size_t smem = (size_t)kStages * kStageBytes + 2 * (size_t)p.b_bytes + 1024 + 128;
-    return smem <= kSmemLimit;
+    p.b_bytes = off;   // multiple of 2048 (nn multiple of 32, 64-byte rows)
+    // the deepest ring that fits next to B (at least 2 stages)
+    for (int s = kMaxStages; s >= 2; --s) {
+        p.stages = s;
+        if (smem_bytes(p) <= kSmemLimit) return true;
+    }
+    return false;
 }
-
-size_t smem_bytes(const RnParams& p) { return (size_t)kStages * kStageBytes + 2 * (size_t)p.b_bytes + 1024 + 128; }
 
 }  // namespace
 
@@ -318,7 +351,7 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     uint8_t* img = (uint8_t*)ws;
     LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
     const size_t smem = smem_bytes(p);
-    const bool vec = (p.d % 8 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
+    const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
     const int grid = p.ntiles < sm_count ? p.ntiles : sm_count;
     cudaError_t e;
     if (vec) {

@@ -58,6 +58,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
 }
 
+// Wait until the shared-memory counter *ctr reaches `target` (bounded like
+// mbar_wait).  Used to hand out the uses of a pipeline stage in order.
+__device__ __forceinline__ bool counter_wait(volatile int* ctr, int target, volatile int* abort) {
+    if (*ctr >= target) return true;
+    const uint64_t t0 = globaltimer();
+    while (*ctr < target) {
+        if (*abort) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -96,6 +111,18 @@ __device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t smem_addr) {
     return d;
 }
 
+// Same, 64-byte swizzle: rows of 64 B (32 bf16 along K), 8-row atoms of 512 B
+// (SBO = 512); the atom base must be 512-byte aligned.
+__device__ __forceinline__ uint64_t desc_sw64_kmajor(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;                              // 64-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
     return (1u << 4)            // D format F32
@@ -122,9 +149,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // 32 lanes x 32 columns of FP32 from TMEM: thread t of the warp gets row
-// (lane base + t), columns [col, col + 32).
-__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// (lane base + t), columns [col, col + 32).  Asynchronous: the registers are
+// valid after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -135,16 +162,21 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
           "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
           "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte offset of element (row, k) inside a K-major, 128-byte-swizzled bf16
 // tile whose rows hold 64 elements: 16-byte chunk (k / 8) of row r is stored
 // at chunk position (k / 8) XOR (r mod 8).
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {
     return (row >> 3) * 1024u + (row & 7u) * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + (k & 7u) * 2u;
+}
+
+// Byte offset of element (row, k) inside a K-major, 64-byte-swizzled bf16
+// tile whose rows hold 32 elements: 16-byte chunk (k / 8) of row r is stored
+// at chunk position (k / 8) XOR ((r / 2) mod 4).
+__host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t row, uint32_t k) {
+    return (row >> 3) * 512u + (row & 7u) * 64u + ((((k >> 3) ^ (row >> 1)) & 3u) << 4) + (k & 7u) * 2u;
 }
 
 // hi = bf16(x), lo = bf16(x - hi): x = hi + lo to ~16 significant bits.
