@@ -282,8 +282,7 @@ cudaError_t sketch_and_factor(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t
         sk = b.GSA;
         rows = k;
     }
-    return qr_launch(sk, rows, A->d, R_out ? R_out : b.R64, b.Rinv64, b.Rinv32, b.scratch, ctx->flag,
-                     ctx->sm_count, st);
+    return qr_launch(sk, rows, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, ctx->flag, ctx->sm_count, st);
 }
 
 int check_sketch_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec) {

@@ -1,9 +1,322 @@
-// gauss_tc.cu -- tensor-core (tcgen05) path of the Gaussian stage (BF16).
-#include "lsk_internal.cuh"
+// gauss_tc.cu -- Gaussian stage GSA = G * SA on tcgen05 tensor cores (BF16).
+//
+// G (k x r) is exactly representable in bfloat16 by definition of the BF16
+// mode (the bf16 rounding of z / sqrt(k)); SA is split into bf16 hi + lo.
+//     GSA = G SA_hi + G SA_lo       (FP32 accumulation in tensor memory)
+// A block owns one 128-row tile of G and one slice of the r dimension; the
+// k x d partials of the slices are added in FP64 in a fixed order afterwards
+// (deterministic).  Per 32-column chunk of the slice:
+//   - the 8 worker warps draw their part of the G chunk (Philox + Box-Muller,
+//     4 rows per draw) straight into the bf16 K-major operand tile, and load
+//     the 32 rows of SA (row-major, N contiguous) into a padded FP32 staging
+//     buffer, then transpose it into the K-major bf16 hi / lo tiles;
+//   - lane 0 of warp 8 issues the 4 MMAs (2 K-steps x {hi, lo}).
+// The draws of the next chunk overlap the loads of SA; the loads are always
+// consumed before the stage barrier is arrived on.  All workers move through
+// the chunks in lockstep (one thread waits on a stage and broadcasts the
+// verdict through a named barrier), so a timeout exits every worker alike.
+#include "tc_common.cuh"
 
-bool gauss_tc_supported(int64_t, int64_t, int64_t) { return false; }
-size_t gauss_tc_workspace_bytes(int64_t, int64_t, int64_t, int) { return 0; }
-cudaError_t gauss_tc_launch(const float*, int64_t, int64_t, int64_t, uint64_t, float*, void*, int,
-                            cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int kM = 128;            // rows of G per block
+constexpr int kKC = 32;            // r-columns per chunk (64-byte swizzle rows)
+constexpr int kWorkers = 8;        // worker warps (also the epilogue, warps 0-3)
+constexpr int kMmaWarp = kWorkers;
+constexpr int kThreads = (kWorkers + 1) * 32;
+constexpr int kWorkerThreads = kWorkers * 32;
+constexpr int kMaxN = 256;
+constexpr int kStagePad = 4;       // FP32 staging row padding (floats)
+constexpr int kStages = 3;
+constexpr size_t kSmemLimit = 232448;
+
+struct GtParams {
+    const float* SA;
+    float* part;       // [slices][k][d]
+    int64_t r, k;
+    int d, npad;
+    int64_t kslice;    // r-columns per slice (multiple of kKC)
+    int tiles_m, slices;
+    uint32_t k0, k1;
+    float scale;
+    int* flag;
+};
+
+__host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 8 KB
+__host__ __device__ inline uint32_t b_bytes(int npad) { return (uint32_t)npad * kKC * 2; }  // per hi / lo
+__host__ __device__ inline uint32_t stage_bytes(int npad) { return a_bytes() + 2 * b_bytes(npad); }
+
+__device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkerThreads) : "memory"); }
+
+__global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t sbytes = stage_bytes(p.npad);
+    uint8_t* stages = smem;
+    float* stagef = reinterpret_cast<float*>(smem + kStages * sbytes);        // kKC x (npad + pad)
+    const int ldf = p.npad + kStagePad;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stagef + kKC * ldf);
+    uint64_t* full = bars;              // [kStages] (kWorkers arrivals)
+    uint64_t* empty = bars + kStages;   // [kStages] (MMA commit)
+    uint64_t* done = bars + 2 * kStages;  // accumulator complete   (MMA commit)
+    uint64_t* fin = done + 1;             // every MMA complete     (MMA commit)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* verdict = abort + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x % p.tiles_m, slice = blockIdx.x / p.tiles_m;
+    const int64_t j0 = (int64_t)mt * kM;
+    const int64_t c_begin = (int64_t)slice * p.kslice;
+    const int64_t c_end = min(p.r, c_begin + p.kslice);
+    const int nchunks = (int)((c_end - c_begin + kKC - 1) / kKC);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(full + s, kWorkers);
+            tc::mbar_init(empty + s, 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_init(fin, 1);
+        *abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc(tmem_slot, 256);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < kWorkers) {
+        const int wt = threadIdx.x;   // 0 .. 255
+        bool ok = true;
+        for (int g = 0; g < nchunks; ++g) {
+            const int s = g % kStages;
+            const int64_t c0 = c_begin + (int64_t)g * kKC;
+            // (1) SA rows c0 .. c0+31 into registers: float4 f = wt + 256 i,
+            //     row f / (npad/4), columns 4 (f % (npad/4))
+            const int q4 = p.npad / 4;
+            const int nf = kKC * q4 / kWorkerThreads;   // float4 per thread (npad / 32)
+            float4 sa[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                sa[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < nf) {
+                    const int f = wt + kWorkerThreads * i;
+                    const int rr = f / q4, n = 4 * (f % q4);
+                    const int64_t c = c0 + rr;
+                    if (c < c_end) {
+                        const float* src = p.SA + c * p.d + n;
+                        if (n + 3 < p.d) {
+                            sa[i] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+                        } else {
+                            sa[i].x = n < p.d ? __ldg(src) : 0.f;
+                            sa[i].y = n + 1 < p.d ? __ldg(src + 1) : 0.f;
+                            sa[i].z = n + 2 < p.d ? __ldg(src + 2) : 0.f;
+                        }
+                    }
+                }
+            }
+            // (2) G chunk: item = wt + 256 i -> (row quad gq = item / 16, column pair cp = item % 16)
+            uint32_t gw[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int item = wt + kWorkerThreads * i;
+                const int gq = item >> 4, cp = item & 15;
+                const int64_t jq = j0 + 4 * gq;
+                const int64_t c = c0 + 2 * cp;
+                float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
+                if (jq < p.k) {
+                    if (c < c_end) z0 = gauss4((uint64_t)c, (uint32_t)(jq >> 2), p.k0, p.k1);
+                    if (c + 1 < c_end) z1 = gauss4((uint64_t)(c + 1), (uint32_t)(jq >> 2), p.k0, p.k1);
+                }
+                const float a0[4] = {z0.x, z0.y, z0.z, z0.w}, a1[4] = {z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const bool rowok = jq + t < p.k;
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(rowok ? a0[t] * p.scale : 0.f,
+                                                                   rowok ? a1[t] * p.scale : 0.f);
+                    gw[i][t] = *reinterpret_cast<const uint32_t*>(&h);
+                }
+            }
+            // (3) wait for the stage (one thread decides for all workers)
+            if (wt == 0) *verdict = tc::mbar_wait(empty + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
+            named_sync();
+            if (!*verdict) {
+                ok = false;
+                break;
+            }
+            uint8_t* st = stages + s * sbytes;
+            // (4) G words: row 4 gq + t, columns 2cp, 2cp+1
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int item = wt + kWorkerThreads * i;
+                const int gq = item >> 4, cp = item & 15;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    *reinterpret_cast<uint32_t*>(st + tc::sw64_offset(4 * gq + t, 2 * cp)) = gw[i][t];
+            }
+            // (5) SA into the FP32 staging buffer
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i < nf) {
+                    const int f = wt + kWorkerThreads * i;
+                    const int rr = f / q4, n = 4 * (f % q4);
+                    *reinterpret_cast<float4*>(stagef + rr * ldf + n) = sa[i];
+                }
+            }
+            named_sync();
+            // (6) transpose + split: item (n, c8) -> 8 consecutive c of column n
+            uint8_t* bh = st + a_bytes();
+            uint8_t* bl = bh + b_bytes(p.npad);
+            for (int item = wt; item < p.npad * (kKC / 8); item += kWorkerThreads) {
+                const int n = item % p.npad, c8 = item / p.npad;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = stagef[(8 * c8 + e) * ldf + n];
+                uint4 hi, lo;
+                tc::split_bf16x2(v[0], v[1], hi.x, lo.x);
+                tc::split_bf16x2(v[2], v[3], hi.y, lo.y);
+                tc::split_bf16x2(v[4], v[5], hi.z, lo.z);
+                tc::split_bf16x2(v[6], v[7], hi.w, lo.w);
+                const uint32_t off = tc::sw64_offset(n, 8 * c8);
+                *reinterpret_cast<uint4*>(bh + off) = hi;
+                *reinterpret_cast<uint4*>(bl + off) = lo;
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(full + s);
+        }
+        // epilogue: warps 0-3 read the 128 x npad accumulator
+        if (warp < 4) {
+            int okw = 0;
+            if (lane == 0) okw = (ok && tc::mbar_wait(done, 0, abort)) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (okw) {
+                tc::fence_after_sync();
+                const int64_t j = j0 + warp * 32 + lane;
+                float* dst = p.part + ((int64_t)slice * p.k + j) * p.d;
+                for (int col = 0; col < p.npad; col += 32) {
+                    uint32_t v[32];
+                    tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+                    tc::tmem_ld_wait();
+                    if (j < p.k) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (col + e < p.d) dst[col + e] = __uint_as_float(v[e]);
+                    }
+                }
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            const uint32_t base = tc::smem_u32(stages);
+            const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)p.npad);
+            bool okm = true;
+            for (int g = 0; g < nchunks; ++g) {
+                const int s = g % kStages;
+                if (!tc::mbar_wait(full + s, (uint32_t)(g / kStages) & 1u, abort)) {
+                    okm = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t a = base + s * sbytes, bh = a + a_bytes(), bl = bh + b_bytes(p.npad);
+#pragma unroll
+                for (int kk = 0; kk < kKC / 16; ++kk) {
+                    const uint32_t ko = 32u * kk;
+                    tc::mma_bf16(tmem, tc::desc_sw64_kmajor(a + ko), tc::desc_sw64_kmajor(bh + ko), idesc, (g | kk) != 0);
+                    tc::mma_bf16(tmem, tc::desc_sw64_kmajor(a + ko), tc::desc_sw64_kmajor(bl + ko), idesc, 1);
+                }
+                tc::mma_commit(empty + s);
+            }
+            if (okm && nchunks > 0) tc::mma_commit(done);
+            tc::mma_commit(fin);
+            volatile int never = 0;
+            tc::mbar_wait(fin, 0, &never);
+        }
+        __syncwarp();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 256);
+    }
+    if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
+}
+
+struct Plan {
+    int npad, tiles_m, slices;
+    int64_t kslice;
+    size_t smem;
+};
+
+bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
+    if (d < 1 || d > kMaxN || k < 1 || r < 1) return false;
+    P.npad = (int)((d + 31) / 32) * 32;
+    P.tiles_m = (int)((k + kM - 1) / kM);
+    int64_t want = (2 * (int64_t)sm_count + P.tiles_m - 1) / P.tiles_m;
+    const int64_t max_slices = (r + kKC - 1) / kKC;
+    if (want > max_slices) want = max_slices;
+    if (want < 1) want = 1;
+    int64_t ks = (r + want - 1) / want;
+    ks = ((ks + kKC - 1) / kKC) * kKC;
+    P.kslice = ks;
+    P.slices = (int)((r + ks - 1) / ks);
+    P.smem = (size_t)kStages * stage_bytes(P.npad) + (size_t)kKC * (P.npad + kStagePad) * 4 + 1024 + 128;
+    return P.smem <= kSmemLimit;
+}
+
+__global__ void gauss_tc_reduce_kernel(const float* __restrict__ part, int slices, int64_t len,
+                                       float* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+        double s = 0.0;
+        for (int z = 0; z < slices; ++z) s += (double)part[(int64_t)z * len + e];
+        out[e] = (float)s;
+    }
+}
+
+}  // namespace
+
+bool gauss_tc_supported(int64_t r, int64_t d, int64_t k) {
+    Plan P;
+    return make_plan(r, d, k, 152, P);
+}
+
+size_t gauss_tc_workspace_bytes(int64_t r, int64_t d, int64_t k, int sm_count) {
+    Plan P;
+    if (!make_plan(r, d, k, sm_count, P)) return 0;
+    return ws_round((size_t)P.slices * k * d * 4);
+}
+
+cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed, float* GSA, void* ws,
+                            int sm_count, cudaStream_t st) {
+    Plan P;
+    if (!make_plan(r, d, k, sm_count, P)) return cudaErrorNotSupported;
+    GtParams p;
+    p.SA = SA;
+    p.part = (float*)ws;
+    p.r = r;
+    p.k = k;
+    p.d = (int)d;
+    p.npad = P.npad;
+    p.kslice = P.kslice;
+    p.tiles_m = P.tiles_m;
+    p.slices = P.slices;
+    p.k0 = (uint32_t)seed;
+    p.k1 = (uint32_t)(seed >> 32);
+    p.scale = (float)(1.0 / sqrt((double)k));
+    p.flag = nullptr;
+    cudaError_t e = cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    if (e != cudaSuccess) return e;
+    LSK_PROF("gauss_tc", st) gauss_tc_kernel<<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
+    const int64_t len = k * d;
+    int64_t g = (len + 255) / 256;
+    if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
+    LSK_PROF("gauss_reduce", st) gauss_tc_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(p.part, P.slices, len, GSA);
+    return cudaGetLastError();
 }

@@ -11,7 +11,15 @@
 //   3. R = L^T; rank check min R_jj <= 16 eps d max R_jj (flag);
 //   4. R^-1 column by column (one warp per column, back substitution).
 // In exact arithmetic this R equals the sign-normalised Householder R of B.
+// For d <= 256 steps 2-4 are replaced by the mixed-precision factorisation of
+// qr_mixed.cu (FP32 Cholesky + one FP64 correction made of parallel
+// triangular products), which avoids FP64 dependency chains; the all-FP64
+// blocked path below serves larger d.
 #include "lsk_internal.cuh"
+
+size_t qr_mixed_workspace_bytes(int64_t d);
+cudaError_t qr_mixed_launch(const double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws,
+                            int* flag, cudaStream_t st);
 
 namespace {
 
@@ -291,8 +299,9 @@ QrPlan qr_plan(int64_t k, int64_t d) {
 size_t qr_workspace_bytes(int64_t k, int64_t d) {
     const QrPlan p = qr_plan(k, d);
     const int64_t nbk = (d + NB - 1) / NB;
-    return ws_round((size_t)d * d * 8) + ws_round((size_t)p.nchunks * p.ntiles * QT * QT * 8) +
-           ws_round((size_t)nbk * NB * NB * 8);
+    size_t rest = ws_round((size_t)nbk * NB * NB * 8);
+    if (d <= 256 && qr_mixed_workspace_bytes(d) > rest) rest = qr_mixed_workspace_bytes(d);
+    return ws_round((size_t)d * d * 8) + ws_round((size_t)p.nchunks * p.ntiles * QT * QT * 8) + rest;
 }
 
 cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv, float* Rinv32,
@@ -309,6 +318,7 @@ cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* R
     int64_t g = (d * d + 255) / 256;
     if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
     LSK_PROF("qr_gram64", st) sketch_gram64_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, p.nchunks, d, C);
+    if (d <= 256) return qr_mixed_launch(C, d, R, Rinv, Rinv32, Ldiag, flag, st);
     for (int64_t K = 0; K < nbk; ++K) {
         const unsigned panel_blocks = (unsigned)(nbk - K);   // diag + blocks below
         LSK_PROF("qr_cholesky", st) chol_panel_kernel<<<panel_blocks, 64, 0, st>>>(C, d, K, Ldiag, flag);

@@ -1,0 +1,397 @@
+// qr_mixed.cu -- R of the sketch with FP32 factorisation and one FP64 correction.
+//
+// FP64 on this part is slow and, worse, has long dependent-operation
+// latency, so the serial chain of a Cholesky factorisation is run in FP32
+// and FP64 is used only in parallel matrix products:
+//   1. C = B^T B in FP64 (qr.cu), equilibrated by powers of two:
+//      Ct = D^-1 C D^-1, D_j = 2^round(log2 sqrt(C_jj))            (exact)
+//   2. Ct ~ Rt^T Rt by FP32 Cholesky (one CTA, packed lower triangle in
+//      shared memory), X = Rt^-1 by FP32 back substitution
+//   3. one correction step in FP64, all products of triangular matrices:
+//        M = X^T Ct X = I + E,  U = strict_upper(E) + diag(E)/2
+//        Y = X (I - U)                         (= (R D^-1)^-1 to O(|E|^2))
+//        Z = Rt + Rt (I - Y Rt)                (Newton step for Y^-1)
+//   4. R = Z D, R^-1 = D^-1 Y
+// In exact arithmetic R is the Cholesky factor of C, i.e. the sign-normalised
+// Householder R of B.  Rank deficiency is reported when an FP32 pivot is not
+// positive, when the FP32 factor needs a correction larger than 1/4 (the
+// equilibrated sketch is numerically singular at FP32 precision), or when
+// the equilibrated diag(R) spans more than 2^20.
+#include "lsk_internal.cuh"
+
+namespace {
+
+constexpr int TT = 16;   // tile edge of the FP64 triangular products (one output per thread)
+
+// e_j = floor(log2 sqrt(C_jj)) and the exact scale 2^-e_j.
+__global__ void equil_exponents_kernel(const double* __restrict__ C, int d, int* __restrict__ e,
+                                       double* __restrict__ sc, int* flag) {
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double c = C[(int64_t)j * d + j];
+        int ex = 0;
+        if (c > 0.0 && isfinite(c)) {
+            int b2;
+            frexp(c, &b2);                  // c = m 2^b2, m in [0.5, 1)
+            ex = (b2 - 1) >> 1;
+        } else {
+            set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+        }
+        e[j] = ex;
+        sc[j] = ldexp(1.0, -ex);
+    }
+}
+
+// Ct64 = C 2^{-e_i-e_j} (two exact multiplications), Ct32 = float(Ct64).
+__global__ void equil_scale_kernel(const double* __restrict__ C, int d, const double* __restrict__ sc,
+                                   double* __restrict__ Ct64, float* __restrict__ Ct32) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+        const double v = C[t] * sc[t / d] * sc[t % d];
+        Ct64[t] = v;
+        Ct32[t] = (float)v;
+    }
+}
+
+// FP32 Cholesky of Ct (d <= 256) in one CTA, blocked by 32: the lower
+// triangle lives in shared memory as 32 x 33 (padded) tiles T(I, J), I >= J.
+// Per block column K: warp 0 factors T(K, K) with its rows in registers,
+// one thread per row solves the panel T(I, K) L_KK^-T, and the rank-32
+// trailing update T(I, J) -= L_IK L_JK^T runs one tile per warp with each
+// lane's column of L_JK in registers.  Dimensions beyond d are padded with
+// the identity.  Writes Rt = L^T (FP64 values, d x d, zeros below) and the
+// packed rows of L (row l at offset l(l+1)/2) for the inverse.
+constexpr int CB = 32;
+constexpr int CP = CB + 1;
+__device__ __forceinline__ float* ctile(float* S, int I, int J) { return S + (I * (I + 1) / 2 + J) * (CB * CP); }
+
+__global__ void __launch_bounds__(1024) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
+                                                      float* __restrict__ Lpk, int* flag) {
+    extern __shared__ float S[];
+    __shared__ float rdiag[CB];
+    const int nt = (d + CB - 1) / CB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int I = 0; I < nt; ++I)
+        for (int J = 0; J <= I; ++J) {
+            float* T = ctile(S, I, J);
+            for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+                const int r = e / CB, c = e % CB, i = I * CB + r, j = J * CB + c;
+                T[r * CP + c] = (i < d && j < d) ? Ct32[i * d + j] : (i == j ? 1.f : 0.f);
+            }
+        }
+    __syncthreads();
+    for (int K = 0; K < nt; ++K) {
+        float* D = ctile(S, K, K);
+        if (w == 0) {   // (1) diagonal tile, row `lane` in registers
+            float a[CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) a[k] = D[lane * CP + k];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                float piv = __shfl_sync(0xffffffffu, a[j], j);
+                if (!(piv > 0.f) || !isfinite(piv)) {
+                    if (lane == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+                    piv = 1.f;
+                }
+                const float l = sqrtf(piv), il = 1.f / l;
+                if (lane == j) a[j] = l;
+                if (lane > j) a[j] *= il;
+                D[lane * CP + j] = a[j];
+                __syncwarp();
+                if (lane > j) {
+#pragma unroll
+                    for (int k = j + 1; k < CB; ++k)
+                        if (k <= lane) a[k] -= a[j] * D[k * CP + j];
+                }
+                __syncwarp();
+            }
+            if (lane < CB) rdiag[lane] = 1.f / a[lane];
+            __syncwarp();
+        }
+        __syncthreads();
+        // (2) panel: thread per row of T(I, K), I > K
+        {
+            const int rows = (nt - K - 1) * CB;
+            for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+                const int I = K + 1 + t / CB, r = t % CB;
+                float* T = ctile(S, I, K);
+                float x[CB];
+#pragma unroll
+                for (int j = 0; j < CB; ++j) {
+                    float v = T[r * CP + j];
+#pragma unroll
+                    for (int l = 0; l < j; ++l) v -= x[l] * D[j * CP + l];
+                    x[j] = v * rdiag[j];
+                }
+#pragma unroll
+                for (int j = 0; j < CB; ++j) T[r * CP + j] = x[j];
+            }
+        }
+        __syncthreads();
+        // (3) trailing update, one tile (I, J), K < J <= I, per warp
+        {
+            const int T0 = nt - K - 1;
+            const int ntile = T0 * (T0 + 1) / 2;
+            for (int t = w; t < ntile; t += nw) {
+                int I = 0, tt = t;
+                while (tt > I) {   // lower pairs (J <= I) over the trailing blocks
+                    tt -= I + 1;
+                    ++I;
+                }
+                const int J = tt;
+                I += K + 1;
+                const int Jg = J + K + 1;
+                const float* LI = ctile(S, I, K);
+                const float* LJ = ctile(S, Jg, K);
+                float* T = ctile(S, I, Jg);
+                float lj[CB];
+#pragma unroll
+                for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * CP + k];   // column `lane` of L_JK^T
+                for (int a = 0; a < CB; ++a) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) acc = fmaf(LI[a * CP + k], lj[k], acc);
+                    T[a * CP + lane] -= acc;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+        const int i = t / d, j = t % d;   // Rt[i][j] = L[j][i] for j >= i
+        double v = 0.0;
+        if (j >= i) v = (double)ctile(S, j / CB, i / CB)[(j % CB) * CP + (i % CB)];
+        Rt[t] = v;
+    }
+    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += blockDim.x) {
+        int l = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);   // row of packed index t
+        while (l * (l + 1) / 2 > t) --l;
+        while ((l + 1) * (l + 2) / 2 <= t) ++l;
+        const int i = t - l * (l + 1) / 2;
+        Lpk[t] = ctile(S, l / CB, i / CB)[(l % CB) * CP + (i % CB)];
+    }
+}
+
+// X = Rt^-1 (upper) in FP32, one warp per column; stored as FP64 values.
+// The packed factor (row l of L = column l of Rt at offset l(l+1)/2) is
+// staged in shared memory so the back-substitution chain sees smem latency.
+__global__ void __launch_bounds__(128) trinv32_kernel(const float* __restrict__ Lpk, int d, double* __restrict__ X) {
+    extern __shared__ float P[];
+    __shared__ float rdiag[256];
+    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += blockDim.x) P[t] = Lpk[t];
+    __syncthreads();
+    for (int l = threadIdx.x; l < d; l += blockDim.x) rdiag[l] = 1.f / P[l * (l + 1) / 2 + l];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (j >= d) return;
+    float xr[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) xr[s] = (lane + 32 * s == j) ? 1.f : 0.f;
+    for (int l = j; l >= 0; --l) {
+        const int owner = l & 31, slot = l >> 5;
+        float v = 0.f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (s == slot) v = xr[s];
+        v = __shfl_sync(0xffffffffu, v, owner);
+        const float xl = v * rdiag[l];
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (s == slot && lane == owner) xr[s] = xl;
+        const float* col = P + l * (l + 1) / 2;   // Rt[i][l] = L[l][i]
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int i = lane + 32 * s;
+            if (i < l) xr[s] = fmaf(-col[i], xl, xr[s]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int i = lane + 32 * s;
+        if (i < d) X[(int64_t)i * d + j] = (i <= j) ? (double)xr[s] : 0.0;
+    }
+}
+
+// Out = alpha * op(A) * B + beta * Cin + diag_add * I on the upper triangle
+// (tiles I <= J), FP64.  op(A) = A or A^T.  The reduction index is limited to
+// where both factors can be non-zero: a_upper (op(A) upper: k >= i),
+// a_lower (op(A) lower: k <= i), b_upper (B upper: k <= j).  Entries below
+// the diagonal of Out are written as zero.
+struct TriGemm {
+    const double* A;
+    const double* B;
+    const double* Cin;
+    double* Out;
+    int d, transA, a_upper, a_lower, b_upper;
+    double alpha, beta, diag_add;
+};
+
+__global__ void __launch_bounds__(256) tri_gemm64_kernel(const TriGemm g) {
+    const int nt = (g.d + TT - 1) / TT;
+    int t = blockIdx.x, I = 0;
+    while (t >= nt - I) {   // upper tile pairs (I <= J)
+        t -= nt - I;
+        ++I;
+    }
+    const int J = I + t;
+    __shared__ double As[TT][TT + 1], Bs[TT][TT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // output (ty, tx)
+    const int i0 = I * TT, j0 = J * TT;
+    int klo = 0, khi = g.d;
+    if (g.a_upper) klo = i0;
+    if (g.a_lower) khi = min(khi, i0 + TT);
+    if (g.b_upper) khi = min(khi, j0 + TT);
+    double acc0 = 0.0, acc1 = 0.0;   // two chains for latency
+    for (int k0 = klo - (klo % TT); k0 < khi; k0 += TT) {
+        {
+            const int r = threadIdx.x / TT, c = threadIdx.x % TT;
+            const int ia = i0 + r, ka = k0 + c;
+            double a = 0.0;
+            if (ia < g.d && ka < g.d) a = g.transA ? g.A[(int64_t)ka * g.d + ia] : g.A[(int64_t)ia * g.d + ka];
+            As[r][c] = a;
+            const int kb = k0 + r, jb = j0 + c;
+            Bs[r][c] = (kb < g.d && jb < g.d) ? g.B[(int64_t)kb * g.d + jb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TT; kk += 2) {
+            acc0 = fma(As[ty][kk], Bs[kk][tx], acc0);
+            acc1 = fma(As[ty][kk + 1], Bs[kk + 1][tx], acc1);
+        }
+        __syncthreads();
+    }
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= g.d || j >= g.d) return;
+    double r = 0.0;
+    if (j >= i) {
+        r = g.alpha * (acc0 + acc1);
+        if (g.beta != 0.0) r += g.beta * g.Cin[(int64_t)i * g.d + j];
+        if (i == j) r += g.diag_add;
+    }
+    g.Out[(int64_t)i * g.d + j] = r;
+}
+
+// U = strict_upper(M - I) + diag(M - I) / 2, in place.  |M - I| > 1/4
+// anywhere means the FP32 factor was too far off for one correction: the
+// equilibrated sketch is numerically rank deficient at FP32 precision.
+__global__ void correction_kernel(double* __restrict__ M, int d, int* flag) {
+    bool big = false;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+        const int i = t / d, j = t % d;
+        if (i <= j) {
+            const double e = M[t] - (i == j ? 1.0 : 0.0);
+            if (!(fabs(e) <= 0.25)) big = true;
+            M[t] = (i == j) ? 0.5 * e : e;
+        } else {
+            M[t] = 0.0;
+        }
+    }
+    if (big) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+}
+
+// R = Z D, R^-1 = D^-1 Y (exact power-of-two scalings); FP32 copy of R^-1.
+__global__ void unscale_kernel(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
+                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+        const int i = t / d, j = t % d;
+        const bool up = j >= i;
+        const double r = (up && Z) ? ldexp(Z[t], e[j]) : 0.0;
+        const double ri = up ? ldexp(Y[t], -e[i]) : 0.0;
+        if (R) R[t] = r;
+        if (Rinv) Rinv[t] = ri;
+        if (Rinv32) Rinv32[t] = (float)ri;
+    }
+}
+
+// min_j Rt_jj <= 2^-20 max_j Rt_jj on the equilibrated factor, with
+// Rt_jj = 1 / Y_jj: beyond that conditioning a factor of the Gram cannot
+// resolve the sketch in FP64.
+__global__ void rank_check_r_kernel(const double* __restrict__ Y, int d, int* flag) {
+    double mn = INFINITY, mx = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double v = 1.0 / Y[(int64_t)j * d + j];
+        mn = fmin(mn, v);
+        mx = fmax(mx, v);
+    }
+    for (int o = 16; o; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ double smn[32], smx[32];
+    if ((threadIdx.x & 31) == 0) {
+        smn[threadIdx.x >> 5] = mn;
+        smx[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            mn = fmin(mn, smn[w]);
+            mx = fmax(mx, smx[w]);
+        }
+        if (!(mn > 9.5367431640625e-07 * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+    }
+}
+
+cudaError_t tri_gemm(const TriGemm& g, cudaStream_t st) {
+    const int nt = (g.d + TT - 1) / TT;
+    LSK_PROF("qr_refine64", st) tri_gemm64_kernel<<<nt * (nt + 1) / 2, 256, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t qr_mixed_workspace_bytes(int64_t d) {
+    return 6 * ws_round((size_t)d * d * 8) + ws_round((size_t)d * d * 4) + ws_round((size_t)d * (d + 1) / 2 * 4) +
+           ws_round((size_t)d * 4) + ws_round((size_t)d * 8) + 4096;
+}
+
+// C: FP64 Gram of the sketch (d x d, full).  Outputs as qr_launch; R is only
+// formed (one Newton step) when requested.
+cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
+                            cudaStream_t st) {
+    const int d = (int)d64;
+    WsCarver wc{(char*)ws, 0};
+    double* Ct = wc.take<double>((size_t)d * d);
+    float* Ct32 = wc.take<float>((size_t)d * d);
+    float* Lpk = wc.take<float>((size_t)d * (d + 1) / 2);
+    double* Rt = wc.take<double>((size_t)d * d);
+    double* X = wc.take<double>((size_t)d * d);
+    double* W = wc.take<double>((size_t)d * d);
+    double* M = wc.take<double>((size_t)d * d);
+    double* Y = wc.take<double>((size_t)d * d);
+    int* e = wc.take<int>(d);
+    double* sc = wc.take<double>(d);
+    const int zb = (d * d + 255) / 256 < 1024 ? (d * d + 255) / 256 : 1024;
+    LSK_PROF("qr_equil", st) equil_exponents_kernel<<<1, 256, 0, st>>>(C, d, e, sc, flag);
+    LSK_PROF("qr_equil", st) equil_scale_kernel<<<zb, 256, 0, st>>>(C, d, sc, Ct, Ct32);
+    const int nt = (d + CB - 1) / CB;
+    const size_t tiles = (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
+    cudaError_t err = cudaFuncSetAttribute(chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
+    if (err != cudaSuccess) return err;
+    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 1024, tiles, st>>>(Ct32, d, Rt, Lpk, flag);
+    const size_t pk = (size_t)d * (d + 1) / 2 * 4;
+    err = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
+    if (err != cudaSuccess) return err;
+    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 127) / 128, 128, pk, st>>>(Lpk, d, X);
+    // M = X^T (Ct X): W = Ct X on the upper triangle (only k <= j is needed by M)
+    TriGemm g{Ct, X, nullptr, W, d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
+    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+    g = TriGemm{X, W, nullptr, M, d, 1, 0, 1, 1, 1.0, 0.0, 0.0};
+    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+    LSK_PROF("qr_refine64", st) correction_kernel<<<zb, 256, 0, st>>>(M, d, flag);   // M -> U
+    // Y = X - X U
+    g = TriGemm{X, M, X, Y, d, 0, 1, 0, 1, -1.0, 1.0, 0.0};
+    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+    double* Z = nullptr;
+    if (R) {
+        // P = I - Y Rt ; Z = Rt + Rt P   (Newton step for Y^-1)
+        double* P = W;
+        Z = M;
+        g = TriGemm{Y, Rt, nullptr, P, d, 0, 1, 0, 1, -1.0, 0.0, 1.0};
+        if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+        g = TriGemm{Rt, P, Rt, Z, d, 0, 1, 0, 1, 1.0, 1.0, 0.0};
+        if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+    }
+    LSK_PROF("qr_finish", st) unscale_kernel<<<zb, 256, 0, st>>>(Z, Y, e, d, R, Rinv, Rinv32);
+    LSK_PROF("qr_finish", st) rank_check_r_kernel<<<1, 256, 0, st>>>(Y, d, flag);
+    return cudaGetLastError();
+}

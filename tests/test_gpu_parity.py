@@ -150,7 +150,9 @@ def test_cs_sketch_bad_csr_reported(lsk):
 
 # ---------------------------------------------------------------- G * SA ---
 @pytest.mark.parametrize("r,d,k,prec", [(2500, 50, 100, "fp32"), (40_000, 200, 400, "fp32"),
-                                        (3000, 256, 512, "bf16"), (777, 3, 5, "fp32"), (1000, 129, 70, "bf16")])
+                                        (3000, 256, 512, "bf16"), (777, 3, 5, "fp32"), (1000, 129, 70, "bf16"),
+                                        (65_536, 256, 512, "bf16"), (40_000, 200, 400, "bf16"), (31, 7, 3, "bf16"),
+                                        (2500, 50, 100, "bf16")])
 def test_gauss_sketch(lsk, r, d, k, prec):
     SA = workloads.dense_normal(r, d, seed=r + d)
     got = host(lsk.gauss_sketch(dev(SA), k, 21, prec)).astype(np.float64)
