@@ -155,6 +155,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller for profiling)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-problems", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     N_ROWS = args.rows
     if args.impl == "reference":
@@ -274,6 +278,9 @@ def main():
     e2e = {"value": world * a_bytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
            "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": N_ROWS * 4}
 
+    batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
+    served = None if args.no_serve else run_served(args, lsk, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nb, dt = oracle_sample(args.cpu_rows)
@@ -289,10 +296,93 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "e2e": e2e, "clocks": clk, "cpu_baseline": cpu,
+            "plain_fp32": plain, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "cpu_baseline": cpu,
         }))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, lsk, torch, ctx, plain):
+    """512 independent problems (n log-uniform 1e4..1e6, d in {32..256}, half
+    CSR), r = d^2, k = 2d, BF16 stages, one batch call (CUDA graph)."""
+    specs = workloads.batch_specs(args.batch_problems, seed=3)
+    probs, a_bytes = [], 0
+    for sp in specs:
+        if sp["kind"] == "dense":
+            A = workloads.batch_problem_torch(sp)
+            a_bytes += A.numel() * 4
+        else:
+            V, J, I = workloads.batch_problem_torch(sp)
+            A = lsk.CSR(V, J, I, sp["n"], sp["d"])
+            a_bytes += V.numel() * 8 + I.numel() * 8
+        probs.append((A, sp["r"], sp["k"], sp["sketch_seed"]))
+    outs = lsk.batch_leverage_scores(probs, prec="bf16", autotune=True, ctx=ctx)
+    ctx.sync()
+    streams = lsk.batch_streams(probs, prec="bf16", ctx=ctx)
+    lsk.batch_leverage_scores(probs, prec="bf16", graph=True, outs=outs, ctx=ctx)   # capture
+    ctx.sync()
+    reps = 3
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        lsk.batch_leverage_scores(probs, prec="bf16", graph=True, outs=outs, ctx=ctx)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ms = e0.elapsed_time(e1) / reps
+    value = a_bytes / (ms * 1e-3) / 1e9
+    out = {"workload": "batch_512_leverage", "problems": len(probs), "input_bytes": a_bytes,
+           "ms_per_batch": ms, "value": value, "unit": "GB/s", "streams": streams, "graph": True,
+           "vs_plain_fp32_single": (value / plain["value"]) if plain else None}
+    del probs, outs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_served(args, lsk, torch):
+    """Poisson arrivals (200 req/s) of sketch-and-precondition least-squares
+    requests drawn from the batch size distribution; continuous batching."""
+    from paper_2203_02798_gb300.serve import Request, Server, latency_summary
+    specs = workloads.batch_specs(512, seed=3)
+    pool_specs = specs[:24] + specs[256:280]
+    pool = []
+    for sp in pool_specs:
+        if sp["kind"] == "dense":
+            A = workloads.batch_problem_torch(sp)
+            mv = (lambda x, A=A: (A @ x.float()).double())
+        else:
+            V, J, I = workloads.batch_problem_torch(sp)
+            A = lsk.CSR(V, J, I, sp["n"], sp["d"])
+            rows = torch.repeat_interleave(torch.arange(sp["n"], device="cuda"), I[1:] - I[:-1])
+            mv = (lambda x, V=V, J=J, rows=rows, n=sp["n"]: torch.zeros(n, dtype=torch.float64, device="cuda")
+                  .index_add_(0, rows, V.double() * x[J.long()]))
+        pool.append((sp, A, mv))
+    arrivals = workloads.poisson_arrivals(200.0, args.serve_requests, seed=4)
+    rng = np.random.default_rng(4)
+    server = Server(slots=8)
+    reqs = []
+    for i, t in enumerate(arrivals):
+        sp, A, mv = pool[int(rng.integers(len(pool)))]
+        _, b = workloads.lsq_rhs_torch(mv, sp["n"], sp["d"], seed=10_000 + i)
+        reqs.append(Request(i, float(t), Server.footprint(sp["n"], sp["d"], r=sp["r"], k=sp["k"]),
+                            {"A": A, "b": b, "opts": {"r": sp["r"], "k": sp["k"], "seed": sp["sketch_seed"]}}))
+    torch.cuda.synchronize()
+    # warm-up: one request per slot outside the trace
+    for s in range(server.slots):
+        p = reqs[s].payload
+        server.solve(s, p["A"], p["b"], **p["opts"])
+    done, rejected = server.run(reqs, hbm_budget=150 * 10**9)
+    summ = latency_summary(done)
+    etas = [c.result[1]["eta"] for c in done if c.error is None]
+    summ.update({"workload": "served_lsq_poisson200", "requests": len(reqs), "rejected": len(rejected),
+                 "slots": server.slots, "pool_problems": len(pool),
+                 "converged": int(sum(e <= 1e-10 for e in etas)), "max_eta": float(max(etas)) if etas else None})
+    server.close()
+    del pool, reqs
+    torch.cuda.empty_cache()
+    return summ
 
 
 def algorithmic_work(kernel):

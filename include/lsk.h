@@ -162,6 +162,36 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                         uint64_t seed, int32_t prec, float* ell,
                         double* R_out);
 
+/* ---- batches of independent problems ------------------------------------ */
+/* One problem of a batch: A (dense or CSR, device), its sketch sizes and
+ * seed, and its output ell (device, A.n floats). */
+typedef struct lsk_batch_item {
+    lsk_mat A;
+    int64_t r;
+    int64_t k;
+    uint64_t seed;
+    float* ell;
+} lsk_batch_item;
+
+#define LSK_BATCH_STREAMS_MASK 0xFF    /* low byte: force this many streams    */
+#define LSK_BATCH_GRAPH        0x100   /* capture the batch into a CUDA graph  */
+                                       /* (cached; replayed when the same      */
+                                       /* items come again)                    */
+#define LSK_BATCH_AUTOTUNE     0x200   /* time stream counts on this batch and */
+                                       /* keep the fastest (per signature;     */
+                                       /* file LSK_AUTOTUNE_CACHE if set)      */
+
+/* Leverage scores (as lsk_leverage_scores) of `count` independent problems.
+ * The problems run concurrently on internal streams forked from and joined
+ * back into the context stream (asynchronous; deferred errors as usual).
+ * Batching is not in the paper: it applies the same per-problem method to
+ * many problems at once.  The batch's internal workspaces are owned by the
+ * context.  The items array is read during the call only. */
+int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items,
+                              int32_t prec, int32_t flags);
+/* Stream count chosen for this batch signature (0 if none yet). */
+int lsk_batch_streams(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec);
+
 /* ---- sketch-and-precondition least squares (Alg. 12) ------------------- */
 typedef struct lsk_lsq_opts {
     int64_t r;              /* CountSketch rows (e.g. d*d)                  */

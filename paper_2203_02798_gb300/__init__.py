@@ -49,6 +49,15 @@ class _Mat(ctypes.Structure):
                 ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("nnz", ctypes.c_int64)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("A", _Mat), ("r", ctypes.c_int64), ("k", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("ell", ctypes.c_void_p)]
+
+
+BATCH_GRAPH = 0x100
+BATCH_AUTOTUNE = 0x200
+
+
 class LsqOpts(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int64), ("k", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_refine", ctypes.c_int32),
@@ -82,6 +91,8 @@ _SIGS = {
                                                    ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
     "lsk_debug_hash": (ctypes.c_int, [_P, _I64, _I64, _U64, _P, _P]),
     "lsk_debug_gauss": (ctypes.c_int, [_P, _I64, _I64, _U64, _I32, _P]),
+    "lsk_batch_leverage_scores": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32, _I32]),
+    "lsk_batch_streams": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32]),
     "lsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "lsk_profile_reset": (ctypes.c_int, [_P]),
     "lsk_profile_count": (ctypes.c_int, [_P]),
@@ -279,6 +290,42 @@ def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=No
     ctx._call("lsk_leverage_scores", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), _ptr(ell),
               _ptr(R))
     return (ell, R) if return_R else ell
+
+
+def batch_leverage_scores(problems, prec="bf16", graph=False, autotune=False, streams=0, outs=None,
+                          ctx=None):
+    """lsk_batch_leverage_scores: problems = [(A, r, k, seed), ...] -> [ell, ...].
+
+    A is a dense CUDA tensor or a CSR; all problems run in one call on
+    concurrent internal streams (graph=True: captured into a cached CUDA
+    graph; autotune=True: the stream count is timed and chosen)."""
+    n = len(problems)
+    items = (_BatchItem * max(n, 1))()
+    if outs is None:
+        outs = []
+        for (A, r, k, seed) in problems:
+            m, rows, d = _mat(A)
+            outs.append(torch.empty(rows, dtype=torch.float32, device=_dev(A)))
+    dev = _dev(problems[0][0]) if n else torch.device("cuda", torch.cuda.current_device())
+    for i, ((A, r, k, seed), ell) in enumerate(zip(problems, outs)):
+        m, rows, d = _mat(A)
+        items[i].A = m
+        items[i].r, items[i].k, items[i].seed = int(r), int(k), int(seed)
+        items[i].ell = ell.data_ptr()
+    ctx = ctx or context(dev.index)
+    flags = (int(streams) & 0xFF) | (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+    ctx._call("lsk_batch_leverage_scores", n, items, _prec(prec), flags)
+    return outs
+
+
+def batch_streams(problems, prec="bf16", ctx=None):
+    """Stream count the autotuner chose for this batch signature (0 if none)."""
+    items = (_BatchItem * max(len(problems), 1))()
+    for i, (A, r, k, seed) in enumerate(problems):
+        items[i].A = _mat(A)[0]
+        items[i].r, items[i].k, items[i].seed = int(r), int(k), int(seed)
+    ctx = ctx or context()
+    return int(ctx._lib.lsk_batch_streams(ctx.h, len(problems), items, _prec(prec)))
 
 
 def lsq_default_opts(d):

@@ -113,6 +113,7 @@ int lsk_destroy(lsk_ctx* ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->flag) cudaFree(ctx->flag);
     if (ctx->prof) lsk_prof_delete(ctx->prof);
+    lsk_batch_free(ctx);
     free(ctx);
     return LSK_OK;
 }
@@ -269,20 +270,24 @@ SketchBufs carve(void* ws, const lsk_mat* A, int64_t r, int64_t k) {
 }
 
 // SA -> (GSA) -> R, R^-1 on the device, all asynchronous.
-cudaError_t sketch_and_factor(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed,
-                              int32_t prec, const SketchBufs& b, double* R_out) {
-    cudaStream_t st = ctx->stream;
-    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, ctx->flag, ctx->sm_count, st);
+cudaError_t sketch_and_factor_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                                 const SketchBufs& b, double* R_out, int* flag, int sm, cudaStream_t st) {
+    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, flag, sm, st);
     if (e != cudaSuccess) return e;
     const float* sk = b.SA;
     int64_t rows = r;
     if (k > 0) {
-        e = gauss_launch(b.SA, r, A->d, k, seed, prec, b.GSA, b.scratch, ctx->sm_count, st);
+        e = gauss_launch(b.SA, r, A->d, k, seed, prec, b.GSA, b.scratch, sm, st);
         if (e != cudaSuccess) return e;
         sk = b.GSA;
         rows = k;
     }
-    return qr_launch(sk, rows, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, ctx->flag, ctx->sm_count, st);
+    return qr_launch(sk, rows, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, flag, sm, st);
+}
+
+cudaError_t sketch_and_factor(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed,
+                              int32_t prec, const SketchBufs& b, double* R_out) {
+    return sketch_and_factor_on(A, r, k, seed, prec, b, R_out, ctx->flag, ctx->sm_count, ctx->stream);
 }
 
 int check_sketch_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec) {
@@ -296,6 +301,27 @@ int check_sketch_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int3
     return LSK_OK;
 }
 }  // namespace
+}  // extern "C"
+
+// The whole leverage-score pipeline of one problem on (ws, st); used by
+// lsk_leverage_scores and by the batch driver.
+size_t leverage_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int sm) {
+    return sketch_bytes(A, r, k, prec, sm, 0);
+}
+cudaError_t leverage_pipeline(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, float* ell,
+                              double* R_out, void* ws, int* flag, int sm, cudaStream_t st) {
+    const SketchBufs b = carve(ws, A, r, k);
+    cudaError_t e = sketch_and_factor_on(A, r, k, seed, prec, b, R_out, flag, sm, st);
+    if (e != cudaSuccess) return e;
+    return rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, prec, ell, b.scratch, flag, sm, st);
+}
+int check_leverage_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec) {
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    return check_sketch_args(ctx, A, r, k, prec);
+}
+
+extern "C" {
 
 int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
                         float* ell, double* R_out) {

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
         *abort = 0;
         tc::fence_mbar_init();
     }
+    const uint32_t tcols = p.npad <= 32 ? 32u : p.npad <= 64 ? 64u : p.npad <= 128 ? 128u : 256u;
     if (warp == kMmaWarp) {
-        tc::tmem_alloc(tmem_slot, 256);
+        tc::tmem_alloc(tmem_slot, tcols);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
     __syncthreads();
     if (warp == kMmaWarp) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 256);
+        tc::tmem_dealloc(tmem, tcols);
     }
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }

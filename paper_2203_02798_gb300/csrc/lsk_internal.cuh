@@ -31,8 +31,10 @@ struct lsk_ctx {
     int* flag;            // device int, OR of LSK_FLAG_*
     LskProf* prof;        // per-kernel event timings (NULL until enabled)
     int prof_on;
+    struct LskBatch* batch;   // batch driver state (streams, workspaces, graph)
     char err[512];
 };
+void lsk_batch_free(lsk_ctx* ctx);
 
 LskProf* lsk_prof_new();
 void lsk_prof_delete(LskProf* p);
@@ -165,3 +167,9 @@ cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* R
 size_t lsq_workspace_bytes(const lsk_mat* A);
 int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
             const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info);
+
+// api.cu (used by the batch driver)
+size_t leverage_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int sm);
+cudaError_t leverage_pipeline(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, float* ell,
+                              double* R_out, void* ws, int* flag, int sm, cudaStream_t st);
+int check_leverage_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec);

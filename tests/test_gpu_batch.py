@@ -1,0 +1,88 @@
+"""Batched leverage scores: every problem of a mixed batch (dense / CSR,
+d in {32, 64, 128, 256}, uneven n) equals its single-problem result and the
+oracle's estimate (<= 1e-3), with and without CUDA-graph capture and with
+the stream-count autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import gaussian as oga
+from oracle import leverage as olev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsk():
+    from paper_2203_02798_gb300 import build
+    build.build()
+    import paper_2203_02798_gb300 as p
+    return p
+
+
+def make_batch(lsk, count=16, seed=11):
+    rng = np.random.default_rng(seed)
+    probs, host = [], []
+    for p in range(count):
+        d = int(rng.choice([32, 64, 128, 256]))
+        n = int(10 ** rng.uniform(3.7, 4.6))
+        r, k = max(d * d // 4, 4 * d), 2 * d
+        if p % 2 == 0:
+            A = workloads.dense_normal(n, d, seed=1000 + p)
+            probs.append((torch.from_numpy(A).cuda(), r, k, 77 + p))
+            host.append(("dense", A, n, d, r, k, 77 + p))
+        else:
+            V, J, I = workloads.csr_bernoulli(n, d, float(rng.uniform(0.05, 0.15)), seed=1000 + p)
+            probs.append((lsk.csr_from_numpy(V, J, I, d), r, k, 77 + p))
+            host.append(("csr", (V, J, I), n, d, r, k, 77 + p))
+    return probs, host
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_single_and_oracle(lsk, graph):
+    probs, host = make_batch(lsk)
+    outs = lsk.batch_leverage_scores(probs, prec="bf16", graph=graph, streams=4)
+    lsk.context().sync()
+    if graph:   # replay of the cached graph gives the same answer
+        again = lsk.batch_leverage_scores(probs, prec="bf16", graph=True, streams=4)
+        lsk.context().sync()
+        for a, b in zip(outs, again):
+            assert torch.allclose(a, b, rtol=1e-5, atol=0)
+    for (A, r, k, seed), ell, h in zip(probs, outs, host):
+        single = lsk.leverage_scores(A, r, k, seed, "bf16")
+        lsk.context().sync()
+        nz = single > 0
+        assert torch.all((ell[~nz] == 0))
+        assert torch.max(torch.abs(ell[nz] - single[nz]) / single[nz]).item() <= 1e-5
+    for (A, r, k, seed), ell, h in list(zip(probs, outs, host))[:6]:
+        kind, data, n, d, r, k, seed = h
+        if kind == "dense":
+            ref, _ = olev.leverage_scores_dense(data.astype(np.float64), r, k, seed, oga.PREC_BF16)
+        else:
+            V, J, I = data
+            ref, _ = olev.leverage_scores_csr(V, J, I, n, d, r, k, seed, oga.PREC_BF16)
+        got = ell.cpu().numpy().astype(np.float64)
+        nz = ref > 0
+        assert np.max(np.abs(got[nz] - ref[nz]) / ref[nz]) <= 1e-3
+
+
+def test_batch_autotune_chooses_streams(lsk):
+    probs, _ = make_batch(lsk, count=10, seed=5)
+    outs = lsk.batch_leverage_scores(probs, prec="bf16", autotune=True)
+    lsk.context().sync()
+    s = lsk.batch_streams(probs, prec="bf16")
+    assert s in (1, 4, 8, 16, 32)
+    single = lsk.leverage_scores(probs[0][0], *probs[0][1:], "bf16")
+    lsk.context().sync()
+    assert torch.allclose(outs[0], single, rtol=1e-5, atol=1e-30)
+
+
+def test_batch_empty_and_single(lsk):
+    assert lsk.batch_leverage_scores([], prec="bf16") == []
+    A = torch.from_numpy(workloads.dense_normal(5000, 32, seed=3)).cuda()
+    out = lsk.batch_leverage_scores([(A, 1024, 64, 9)], prec="fp32")
+    lsk.context().sync()
+    ref = lsk.leverage_scores(A, 1024, 64, 9, "fp32")
+    lsk.context().sync()
+    assert torch.allclose(out[0], ref, rtol=1e-5, atol=1e-30)

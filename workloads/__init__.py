@@ -123,3 +123,33 @@ def poisson_arrivals(rate=200.0, count=2000, seed=4):
     """Arrival times (s) of a Poisson process with the given mean rate."""
     gaps = _rng(seed, 13).exponential(1.0 / rate, size=count)
     return np.cumsum(gaps)
+
+
+def batch_problem_torch(spec, device="cuda"):
+    """One problem of :func:`batch_specs` drawn on the device (seeded torch
+    generator; same shapes and distributions as :func:`batch_problem`, not the
+    same numbers).  Dense: float32 tensor; CSR: (V, J, I) tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec["data_seed"]))
+    n, d = spec["n"], spec["d"]
+    if spec["kind"] == "dense":
+        return torch.randn((n, d), generator=g, device=device, dtype=torch.float32)
+    mask = torch.rand((n, d), generator=g, device=device) < spec["density"]
+    rows, cols = torch.nonzero(mask, as_tuple=True)     # row-major: columns ascending per row
+    del mask
+    counts = torch.bincount(rows, minlength=n)
+    I = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    I[1:] = torch.cumsum(counts, 0)
+    V = torch.randn(rows.numel(), generator=g, device=device, dtype=torch.float32)
+    return V, cols.to(torch.int32), I
+
+
+def lsq_rhs_torch(A_mv, n, d, seed, noise=1e-6, device="cuda"):
+    """(x*, b) on the device: x* ~ N(0,1)^d, b = A x* + noise N(0,1)^n (float64)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    xs = torch.randn(d, generator=g, device=device, dtype=torch.float64)
+    b = A_mv(xs) + noise * torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    return xs, b
