@@ -130,6 +130,53 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint3
 
 __global__ void write_total_kernel(uint32_t* off, int64_t r, uint32_t n) { off[r] = n; }
 
+// Exclusive scan of len <= 16384 counts in one block: rounds of 4096
+// (1024 threads x 4 consecutive counts, coalesced), carried across rounds;
+// then off[len] = total.
+__global__ void __launch_bounds__(1024) scan_one_block_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                              int64_t len) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t r0 = 0; r0 < len; r0 += 4096) {
+        const int64_t i0 = r0 + 4 * (int64_t)threadIdx.x;
+        uint32_t v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (i0 + q < len) ? in[i0 + q] : 0u;
+        const uint32_t run = v[0] + v[1] + v[2] + v[3];
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t x = wsum[lane];
+            uint32_t xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            wsum[lane] = xi - x;
+            if (lane == 31) carry_s = xi;
+        }
+        __syncthreads();
+        uint32_t acc = carry + wsum[w] + incl - run;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < len) out[i0 + q] = acc;
+            acc += v[q];
+        }
+        carry += carry_s;
+        __syncthreads();   // wsum / carry_s are rewritten next round
+    }
+    if (threadIdx.x == 0) out[len] = carry;
+}
+
 // ---- dense gather ---------------------------------------------------------
 // One warp per bucket.  Lanes own VEC consecutive columns in each of U
 // column groups of 32*VEC; the bucket's rows are fetched kBatch at a time so
@@ -323,9 +370,13 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)r * 4, st);
     if (e != cudaSuccess) return e;
     if (n > 0) LSK_PROF("cs_rank", st) cs_rank_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cnt, rank);
-    LSK_PROF("cs_scan", st) e = exclusive_scan(cnt, off, r, tmp, st);
-    if (e != cudaSuccess) return e;
-    write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
+    if (r <= 16384) {
+        LSK_PROF("cs_scan", st) scan_one_block_kernel<<<1, 1024, 0, st>>>(cnt, off, r);
+    } else {
+        LSK_PROF("cs_scan", st) e = exclusive_scan(cnt, off, r, tmp, st);
+        if (e != cudaSuccess) return e;
+        write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
+    }
     if (n > 0)
         LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, off, rank, perm);
 

@@ -260,7 +260,7 @@ bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
     P.npad = (int)((d + 31) / 32) * 32;
     P.tiles_m = (int)((k + kM - 1) / kM);
     int64_t want = (2 * (int64_t)sm_count + P.tiles_m - 1) / P.tiles_m;
-    const int64_t max_slices = (r + kKC - 1) / kKC;
+    const int64_t max_slices = (r + 8 * kKC - 1) / (8 * kKC);   // >= 8 chunks per block
     if (want > max_slices) want = max_slices;
     if (want < 1) want = 1;
     int64_t ks = (r + want - 1) / want;

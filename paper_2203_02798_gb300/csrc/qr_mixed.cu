@@ -61,49 +61,73 @@ __global__ void equil_scale_kernel(const double* __restrict__ C, int d, const do
 // packed rows of L (row l at offset l(l+1)/2) for the inverse.
 constexpr int CB = 32;
 constexpr int CP = CB + 1;
+
+// Unblocked Cholesky of one 32 x 32 tile by one warp, row `lane` in a[]:
+// compile-time recursion over (j, k) keeps every index static, so a[] stays
+// in registers (a nested #pragma unroll of this size is not fully unrolled).
+template <int J, int K>
+struct DiagUpdate {
+    static __device__ __forceinline__ void run(float (&a)[CB], float lij, int lane) {
+        const float lkj = __shfl_sync(0xffffffffu, lij, K);   // L[K][J] from lane K
+        if (K <= lane) a[K] -= lij * lkj;
+        DiagUpdate<J, K + 1>::run(a, lij, lane);
+    }
+};
+template <int J>
+struct DiagUpdate<J, CB> {
+    static __device__ __forceinline__ void run(float (&)[CB], float, int) {}
+};
+template <int J>
+struct DiagStep {
+    static __device__ __forceinline__ void run(float (&a)[CB], int lane, int* flag) {
+        float piv = __shfl_sync(0xffffffffu, a[J], J);
+        if (!(piv > 0.f) || !isfinite(piv)) {
+            if (lane == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+            piv = 1.f;
+        }
+        const float l = sqrtf(piv), il = 1.f / l;
+        if (lane == J) a[J] = l;
+        if (lane > J) a[J] *= il;
+        DiagUpdate<J, J + 1>::run(a, a[J], lane);
+        DiagStep<J + 1>::run(a, lane, flag);
+    }
+};
+template <>
+struct DiagStep<CB> {
+    static __device__ __forceinline__ void run(float (&)[CB], int, int*) {}
+};
 __device__ __forceinline__ float* ctile(float* S, int I, int J) { return S + (I * (I + 1) / 2 + J) * (CB * CP); }
 
-__global__ void __launch_bounds__(1024) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
+__global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
                                                       float* __restrict__ Lpk, int* flag) {
     extern __shared__ float S[];
     __shared__ float rdiag[CB];
     const int nt = (d + CB - 1) / CB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int I = 0; I < nt; ++I)
-        for (int J = 0; J <= I; ++J) {
-            float* T = ctile(S, I, J);
-            for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-                const int r = e / CB, c = e % CB, i = I * CB + r, j = J * CB + c;
-                T[r * CP + c] = (i < d && j < d) ? Ct32[i * d + j] : (i == j ? 1.f : 0.f);
-            }
+    {   // all tiles at once, many independent loads in flight per thread
+        const int ntl = nt * (nt + 1) / 2;
+#pragma unroll 4
+        for (int t = threadIdx.x; t < ntl * CB * CB; t += blockDim.x) {
+            const int tl = t / (CB * CB), e = t % (CB * CB);
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+            const int J = tl - I * (I + 1) / 2;
+            const int r = e / CB, c = e % CB, i = I * CB + r, j = J * CB + c;
+            S[tl * (CB * CP) + r * CP + c] = (i < d && j < d) ? __ldg(Ct32 + i * d + j) : (i == j ? 1.f : 0.f);
         }
+    }
     __syncthreads();
     for (int K = 0; K < nt; ++K) {
         float* D = ctile(S, K, K);
-        if (w == 0) {   // (1) diagonal tile, row `lane` in registers
+        if (w == 0) {   // (1) diagonal tile: row `lane` in registers (fully unrolled)
             float a[CB];
 #pragma unroll
             for (int k = 0; k < CB; ++k) a[k] = D[lane * CP + k];
+            DiagStep<0>::run(a, lane, flag);
 #pragma unroll
-            for (int j = 0; j < CB; ++j) {
-                float piv = __shfl_sync(0xffffffffu, a[j], j);
-                if (!(piv > 0.f) || !isfinite(piv)) {
-                    if (lane == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
-                    piv = 1.f;
-                }
-                const float l = sqrtf(piv), il = 1.f / l;
-                if (lane == j) a[j] = l;
-                if (lane > j) a[j] *= il;
-                D[lane * CP + j] = a[j];
-                __syncwarp();
-                if (lane > j) {
-#pragma unroll
-                    for (int k = j + 1; k < CB; ++k)
-                        if (k <= lane) a[k] -= a[j] * D[k * CP + j];
-                }
-                __syncwarp();
-            }
-            if (lane < CB) rdiag[lane] = 1.f / a[lane];
+            for (int k = 0; k < CB; ++k) D[lane * CP + k] = a[k];
+            __syncwarp();
+            rdiag[lane] = 1.f / D[lane * CP + lane];
             __syncwarp();
         }
         __syncthreads();
@@ -145,16 +169,25 @@ __global__ void __launch_bounds__(1024) chol32_kernel(const float* __restrict__ 
                 float lj[CB];
 #pragma unroll
                 for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * CP + k];   // column `lane` of L_JK^T
-                for (int a = 0; a < CB; ++a) {
-                    float acc = 0.f;
+                for (int a = 0; a < CB; a += 4) {   // four independent chains
+                    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 #pragma unroll
-                    for (int k = 0; k < CB; ++k) acc = fmaf(LI[a * CP + k], lj[k], acc);
-                    T[a * CP + lane] -= acc;
+                    for (int k = 0; k < CB; ++k) {
+                        acc0 = fmaf(LI[a * CP + k], lj[k], acc0);
+                        acc1 = fmaf(LI[(a + 1) * CP + k], lj[k], acc1);
+                        acc2 = fmaf(LI[(a + 2) * CP + k], lj[k], acc2);
+                        acc3 = fmaf(LI[(a + 3) * CP + k], lj[k], acc3);
+                    }
+                    T[a * CP + lane] -= acc0;
+                    T[(a + 1) * CP + lane] -= acc1;
+                    T[(a + 2) * CP + lane] -= acc2;
+                    T[(a + 3) * CP + lane] -= acc3;
                 }
             }
         }
         __syncthreads();
     }
+#pragma unroll 4
     for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
         const int i = t / d, j = t % d;   // Rt[i][j] = L[j][i] for j >= i
         double v = 0.0;
@@ -367,7 +400,7 @@ cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rin
     const size_t tiles = (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
     cudaError_t err = cudaFuncSetAttribute(chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
     if (err != cudaSuccess) return err;
-    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 1024, tiles, st>>>(Ct32, d, Rt, Lpk, flag);
+    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, Rt, Lpk, flag);
     const size_t pk = (size_t)d * (d + 1) / 2 * 4;
     err = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
     if (err != cudaSuccess) return err;

@@ -90,17 +90,27 @@ __global__ void __launch_bounds__(256) rownorm_dense_kernel(
     }
 }
 
-// Btilde[a][b] = sum_j B[a][j] B[b][j] (FP64 accumulation), full symmetric.
-__global__ void bbt_kernel(const float* __restrict__ B, int64_t d, int64_t c,
-                           float* __restrict__ M) {
-    const int64_t len = d * d;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-        const int64_t a = e / d, b = e % d;
-        double s = 0.0;
-        for (int64_t j = 0; j < c; ++j) s += (double)__ldg(B + a * c + j) * (double)__ldg(B + b * c + j);
-        M[e] = (float)s;
+// Btilde[a][b] = sum_j B[a][j] B[b][j], FP32, 16 x 16 output tiles (one
+// output per thread, two accumulation chains).
+__global__ void __launch_bounds__(256) bbt_kernel(const float* __restrict__ B, int64_t d, int64_t c,
+                                                  float* __restrict__ M) {
+    __shared__ float Ba[16][17], Bb[16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t a0 = (int64_t)blockIdx.y * 16, b0 = (int64_t)blockIdx.x * 16;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int64_t j0 = 0; j0 < c; j0 += 16) {
+        const int64_t ja = j0 + tx;
+        Ba[ty][tx] = (a0 + ty < d && ja < c) ? __ldg(B + (a0 + ty) * c + ja) : 0.f;
+        Bb[ty][tx] = (b0 + ty < d && ja < c) ? __ldg(B + (b0 + ty) * c + ja) : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            acc0 = fmaf(Ba[ty][j], Bb[tx][j], acc0);
+            acc1 = fmaf(Ba[ty][j + 1], Bb[tx][j + 1], acc1);
+        }
+        __syncthreads();
     }
+    if (a0 + ty < d && b0 + tx < d) M[(a0 + ty) * d + b0 + tx] = acc0 + acc1;
 }
 
 __global__ void rownorm_csr_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
@@ -161,9 +171,8 @@ cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double 
                                                    upper_tri ? 1 : 0, (float)alpha, (float)beta, x);
     } else {
         float* M = (float*)ws;
-        int64_t g = (d * d + 255) / 256;
-        if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
-        LSK_PROF("rownorm_bbt", st) bbt_kernel<<<(unsigned)g, 256, 0, st>>>(B, d, c, M);
+        const dim3 bg((unsigned)((d + 15) / 16), (unsigned)((d + 15) / 16));
+        LSK_PROF("rownorm_bbt", st) bbt_kernel<<<bg, 256, 0, st>>>(B, d, c, M);
         int64_t gr = (n + 255) / 256;
         if (gr > 16 * (int64_t)sm_count) gr = 16 * (int64_t)sm_count;
         LSK_PROF("rownorm_csr", st) rownorm_csr_kernel<<<(unsigned)gr, 256, 0, st>>>((const float*)A->values, A->colidx, A->rowptr,
