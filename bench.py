@@ -247,7 +247,7 @@ def main():
         achieved = algo["flops"] / (per_launch_ms * 1e-3) / 1e12
         peak, unit = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s"
     roofline = {"kernel": name, "bound": algo["bound"], "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind if algo["bound"] != "alu"
+                "frac": achieved / peak, "traffic": measured_traffic(name, N_ROWS), "peak_source": peak_kind if algo["bound"] != "alu"
                 else "152 SMs x 128 FP32 lanes x 2 x max SM clock", "per_launch_ms": per_launch_ms,
                 "algorithmic": algo["bytes"] if algo["bound"] == "hbm" else algo["flops"]}
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
@@ -383,6 +383,38 @@ def run_served(args, lsk, torch):
     del pool, reqs
     torch.cuda.empty_cache()
     return summ
+
+
+# DRAM traffic of one launch, from an ncu capture of a smaller case of the same
+# kernel (profiles/dram_traffic_<kernel>.txt: the capture's rows and
+# dram__bytes_read.sum + dram__bytes_write.sum, and a digest of the sources the
+# kernel is built from).  Scaled to the bench's rows (traffic grows with rows:
+# A is streamed once); reported as null once the sources differ from the
+# captured ones.
+def source_digest(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, rows):
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{kernel}.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if line and not line.startswith("#"):
+                    key, _, val = line.partition(" ")
+                    kv[key] = val.strip()
+        if source_digest(kv["sources"].split()) != kv["sha256"]:
+            return None
+        return float(kv["dram_bytes"]) * rows / float(kv["rows"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def algorithmic_work(kernel):
