@@ -180,10 +180,19 @@ typedef struct lsk_batch_item {
 #define LSK_BATCH_AUTOTUNE     0x200   /* time stream counts on this batch and */
                                        /* keep the fastest (per signature;     */
                                        /* file LSK_AUTOTUNE_CACHE if set)      */
+#define LSK_BATCH_PER_PROBLEM  0x400   /* no grouped stages: every problem's   */
+                                       /* whole pipeline on the worker streams */
 
 /* Leverage scores (as lsk_leverage_scores) of `count` independent problems.
- * The problems run concurrently on internal streams forked from and joined
- * back into the context stream (asynchronous; deferred errors as usual).
+ * With prec = LSK_PREC_BF16, problems with k > 0 and d <= 256 run in three
+ * phases: their CountSketches on internal worker streams; then the Gaussian
+ * stage and the R^-1 of every sketch as grouped launches (one grid per stage
+ * over all problems, so the small latency-bound stages of many problems
+ * share the GPU); then their row norms on the worker streams.  Other
+ * problems run their whole pipeline on the worker streams.  The streams
+ * fork from and join back into the context stream (asynchronous; deferred
+ * errors as usual).  The grouped phases keep every grouped problem's sketch
+ * resident at once (sum of r d 4 bytes plus small buffers).
  * Batching is not in the paper: it applies the same per-problem method to
  * many problems at once.  The batch's internal workspaces are owned by the
  * context.  The items array is read during the call only. */

@@ -56,6 +56,7 @@ class _BatchItem(ctypes.Structure):
 
 BATCH_GRAPH = 0x100
 BATCH_AUTOTUNE = 0x200
+BATCH_PER_PROBLEM = 0x400
 
 
 class LsqOpts(ctypes.Structure):
@@ -293,12 +294,14 @@ def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=No
 
 
 def batch_leverage_scores(problems, prec="bf16", graph=False, autotune=False, streams=0, outs=None,
-                          ctx=None):
+                          ctx=None, per_problem=False):
     """lsk_batch_leverage_scores: problems = [(A, r, k, seed), ...] -> [ell, ...].
 
-    A is a dense CUDA tensor or a CSR; all problems run in one call on
-    concurrent internal streams (graph=True: captured into a cached CUDA
-    graph; autotune=True: the stream count is timed and chosen)."""
+    A is a dense CUDA tensor or a CSR; all problems run in one call: their
+    sketches and row norms on concurrent internal streams, the Gaussian stage
+    and R^-1 of the BF16 problems with d <= 256 as grouped launches
+    (per_problem=True: no grouped stages).  graph=True: captured into a
+    cached CUDA graph; autotune=True: the stream count is timed and chosen."""
     n = len(problems)
     items = (_BatchItem * max(n, 1))()
     if outs is None:
@@ -313,7 +316,8 @@ def batch_leverage_scores(problems, prec="bf16", graph=False, autotune=False, st
         items[i].r, items[i].k, items[i].seed = int(r), int(k), int(seed)
         items[i].ell = ell.data_ptr()
     ctx = ctx or context(dev.index)
-    flags = (int(streams) & 0xFF) | (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+    flags = ((int(streams) & 0xFF) | (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+             | (BATCH_PER_PROBLEM if per_problem else 0))
     ctx._call("lsk_batch_leverage_scores", n, items, _prec(prec), flags)
     return outs
 

@@ -1,5 +1,16 @@
 // batch.cu -- many independent leverage-score problems in one call.
 //
+// Problems whose Gaussian stage runs on the tensor cores (BF16) and whose R
+// takes the mixed-precision path (d <= 256) are run in three phases:
+//   1. CountSketch of each problem on the worker streams (memory-bound
+//      passes over A, concurrent across problems), into a batch arena that
+//      holds every such problem's sketch;
+//   2. the Gaussian stage and the whole R^-1 computation as grouped
+//      launches: one grid per stage over all problems (qr.cu, qr_mixed.cu,
+//      gauss_tc.cu), so the latency-bound small stages of hundreds of
+//      problems run side by side instead of one after another;
+//   3. row norms of each problem on the worker streams.
+// Other problems run their whole pipeline on the worker streams in phase 1.
 // The problems are sorted by estimated cost (longest first) and assigned
 // greedily to the least-loaded of S worker streams; each stream owns a
 // workspace sized for the largest of its problems, so problems on different
@@ -25,12 +36,26 @@ struct LskBatch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
     cudaEvent_t fork = nullptr;
+    cudaStream_t gstream = nullptr;  // grouped launches
+    std::vector<cudaEvent_t> ev;     // wave events: [wave][stream] sketch done, then [wave] grouped done
     cudaStream_t cap = nullptr;      // capture stream (the caller's may be the legacy stream)
     std::vector<void*> ws;
     std::vector<size_t> ws_bytes;
     cudaGraphExec_t exec = nullptr;
     uint64_t exec_key = 0;
     std::map<uint64_t, int> tuned;   // batch signature -> stream count
+    // grouped phases
+    void* arena = nullptr;           // sketches, factors and scratch of the grouped problems
+    size_t arena_bytes = 0;
+    unsigned char* table = nullptr;  // device copy of the grouped launches' parameter table
+    size_t table_bytes = 0;
+    std::vector<unsigned char> table_host;   // what `table` holds
+    std::vector<char> grouped;       // per item: takes the grouped path
+    std::vector<int> wave;           // per grouped item: its wave
+    std::vector<float*> SA, Rinv32;  // per grouped item: its sketch and FP32 R^-1 in the arena
+    int waves = 0;
+    std::vector<GaussGroup> gg;      // per wave
+    std::vector<QrGroup> qg;
 };
 
 namespace {
@@ -60,6 +85,13 @@ int ensure_streams(lsk_ctx* ctx, int S) {
         b->ws_bytes.push_back(0);
     }
     if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
+    if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
+    const size_t nev = (size_t)std::max(b->waves, 1) * (S + 1);
+    while (b->ev.size() < nev) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
+        b->ev.push_back(e);
+    }
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
     return LSK_OK;
 }
@@ -84,8 +116,14 @@ int size_workspaces(lsk_ctx* ctx, const std::vector<std::vector<int>>& lanes, co
     LskBatch* b = ctx->batch;
     for (size_t s = 0; s < lanes.size(); ++s) {
         size_t need = 0;
-        for (int i : lanes[s])
-            need = std::max(need, leverage_workspace_bytes(&items[i].A, items[i].r, items[i].k, prec, ctx->sm_count));
+        for (int i : lanes[s]) {
+            const lsk_mat* A = &items[i].A;
+            if (b->grouped.size() == (size_t)0 || !b->grouped[i])
+                need = std::max(need, leverage_workspace_bytes(A, items[i].r, items[i].k, prec, ctx->sm_count));
+            else
+                need = std::max(need, std::max(cs_workspace_bytes(A->n, items[i].r),
+                                               rownorms_workspace_bytes(A, A->d, 1, prec)));
+        }
         if (need > b->ws_bytes[s]) {
             if (b->ws[s]) cudaFree(b->ws[s]);
             b->ws[s] = nullptr;
@@ -100,24 +138,170 @@ int size_workspaces(lsk_ctx* ctx, const std::vector<std::vector<int>>& lanes, co
     return LSK_OK;
 }
 
-// fork -> per-stream chains -> join, all on `main`'s timeline
+// The whole batch on `main`'s timeline.  Worker stream s runs, in order,
+// phase 1 of wave 0 (and the full pipelines of ungrouped problems), then for
+// w = 1.. phase 1 of wave w followed by phase 3 of wave w-1, then phase 3 of
+// the last wave; the grouped stream runs phase 2 of wave w once every worker
+// has finished its phase 1 of w.  So the compute-bound grouped stages of one
+// wave overlap the memory-bound passes over A of its neighbours.
 cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vector<int>>& lanes,
                    const lsk_batch_item* items, int32_t prec) {
     LskBatch* b = ctx->batch;
+    const int S = (int)lanes.size(), W = b->waves;
+    auto ev_sketch = [&](int w, int s) { return b->ev[(size_t)w * (S + 1) + s]; };
+    auto ev_group = [&](int w) { return b->ev[(size_t)w * (S + 1) + S]; };
     cudaError_t e = cudaEventRecord(b->fork, main);
     if (e != cudaSuccess) return e;
-    for (size_t s = 0; s < lanes.size(); ++s) {
+    for (int s = 0; s < S; ++s)
+        if ((e = cudaStreamWaitEvent(b->streams[s], b->fork, 0)) != cudaSuccess) return e;
+    if (W > 0 && (e = cudaStreamWaitEvent(b->gstream, b->fork, 0)) != cudaSuccess) return e;
+
+    auto phase1 = [&](int s, int w) -> cudaError_t {
         cudaStream_t st = b->streams[s];
-        if ((e = cudaStreamWaitEvent(st, b->fork, 0)) != cudaSuccess) return e;
         for (int i : lanes[s]) {
-            e = leverage_pipeline(&items[i].A, items[i].r, items[i].k, items[i].seed, prec, items[i].ell, nullptr,
-                                  b->ws[s], ctx->flag, ctx->sm_count, st);
-            if (e != cudaSuccess) return e;
+            const lsk_batch_item& it = items[i];
+            cudaError_t er = cudaSuccess;
+            if (b->grouped[i]) {
+                if (b->wave[i] == w)
+                    er = cs_launch(&it.A, it.r, it.seed, b->SA[i], b->ws[s], ctx->flag, ctx->sm_count, st);
+            } else if (w == 0) {
+                er = leverage_pipeline(&it.A, it.r, it.k, it.seed, prec, it.ell, nullptr, b->ws[s], ctx->flag,
+                                       ctx->sm_count, st);
+            }
+            if (er != cudaSuccess) return er;
         }
-        if ((e = cudaEventRecord(b->done[s], st)) != cudaSuccess) return e;
+        return W > 0 ? cudaEventRecord(ev_sketch(w, s), st) : cudaSuccess;
+    };
+    auto phase3 = [&](int s, int w) -> cudaError_t {
+        cudaStream_t st = b->streams[s];
+        cudaError_t er = cudaStreamWaitEvent(st, ev_group(w), 0);
+        for (int i : lanes[s]) {
+            if (er != cudaSuccess) return er;
+            if (!b->grouped[i] || b->wave[i] != w) continue;
+            const lsk_batch_item& it = items[i];
+            er = rownorms_launch(&it.A, b->Rinv32[i], it.A.d, 1.0, 0.0, 1, prec, it.ell, b->ws[s], ctx->flag,
+                                 ctx->sm_count, st);
+        }
+        return er;
+    };
+    auto phase2 = [&](int w) -> cudaError_t {
+        cudaError_t er;
+        for (int s = 0; s < S; ++s)
+            if ((er = cudaStreamWaitEvent(b->gstream, ev_sketch(w, s), 0)) != cudaSuccess) return er;
+        if ((er = gauss_group_launch(b->gg[w], b->table, b->gstream)) != cudaSuccess) return er;
+        if ((er = qr_group_launch(b->qg[w], b->table, b->gstream)) != cudaSuccess) return er;
+        return cudaEventRecord(ev_group(w), b->gstream);
+    };
+
+    for (int s = 0; s < S; ++s)
+        if ((e = phase1(s, 0)) != cudaSuccess) return e;
+    if (W > 0 && (e = phase2(0)) != cudaSuccess) return e;
+    for (int w = 1; w < W; ++w) {
+        for (int s = 0; s < S; ++s) {
+            if ((e = phase1(s, w)) != cudaSuccess) return e;
+            if ((e = phase3(s, w - 1)) != cudaSuccess) return e;
+        }
+        if ((e = phase2(w)) != cudaSuccess) return e;
+    }
+    for (int s = 0; s < S; ++s) {
+        if (W > 0 && (e = phase3(s, W - 1)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(b->done[s], b->streams[s])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(main, b->done[s], 0)) != cudaSuccess) return e;
     }
+    if (W > 0 && (e = cudaStreamWaitEvent(main, ev_group(W - 1), 0)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+constexpr int kMaxWaves = 4;           // grouped problems are split into up to 4 waves
+constexpr int kMinWaveProblems = 32;   // of at least 32 problems each
+
+bool groupable(const lsk_batch_item& it, int32_t prec) {
+    return prec == LSK_PREC_BF16 && it.k > 0 && it.A.n > 0 && gauss_tc_supported(it.r, it.A.d, it.k) &&
+           qr_group_supported(it.k, it.A.d);
+}
+
+// Arena layout of the grouped problems, their launch tables, and the upload
+// of the tables (only when they changed; the previous batch on the context
+// stream is finished first, since it may still read the old table).
+int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t prec, bool allow) {
+    LskBatch* b = ctx->batch;
+    b->grouped.assign(count, 0);
+    b->SA.assign(count, nullptr);
+    b->Rinv32.assign(count, nullptr);
+    size_t bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!allow || !groupable(items[i], prec)) continue;
+        const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
+        b->grouped[i] = 1;
+        bytes += ws_round((size_t)r * d * 4) + ws_round((size_t)k * d * 4) + gauss_group_part_bytes(r, d, k) +
+                 ws_round(qr_workspace_bytes(k, d)) + ws_round((size_t)d * d * 4);
+    }
+    if (bytes > b->arena_bytes) {
+        cudaStreamSynchronize(ctx->stream);
+        if (b->arena) cudaFree(b->arena);
+        b->arena = nullptr;
+        b->arena_bytes = 0;
+        if (cudaMalloc(&b->arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(ctx->err, sizeof(ctx->err), "batch: no room for the grouped arena (%zu bytes)", bytes);
+            return LSK_ERR_OOM;
+        }
+        b->arena_bytes = bytes;
+    }
+    // waves: grouped problems by decreasing cost, dealt round-robin
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i)
+        if (b->grouped[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost_of(items[x]) > cost_of(items[y]); });
+    const int ng = (int)order.size();
+    b->waves = ng == 0 ? 0 : std::max(1, std::min(kMaxWaves, ng / kMinWaveProblems));
+    b->wave.assign(count, 0);
+    for (int q = 0; q < ng; ++q) b->wave[order[q]] = q % std::max(b->waves, 1);
+    std::vector<std::vector<GaussJob>> gj(b->waves);
+    std::vector<std::vector<QrJob>> qj(b->waves);
+    WsCarver wc{(char*)b->arena, 0};
+    for (int i = 0; i < count; ++i) {
+        if (!b->grouped[i]) continue;
+        const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
+        float* SA = wc.take<float>((size_t)r * d);
+        float* GSA = wc.take<float>((size_t)k * d);
+        float* part = (float*)wc.take<char>(gauss_group_part_bytes(r, d, k));
+        void* qws = wc.take<char>(qr_workspace_bytes(k, d));
+        float* Ri32 = wc.take<float>((size_t)d * d);
+        b->SA[i] = SA;
+        b->Rinv32[i] = Ri32;
+        gj[b->wave[i]].push_back(GaussJob{SA, r, d, k, items[i].seed, GSA, part});
+        QrJob q{};
+        qr_group_job(q, GSA, k, d, qws, nullptr, Ri32, ctx->flag);
+        qj[b->wave[i]].push_back(q);
+    }
+    HostTable t;
+    b->gg.assign(b->waves, GaussGroup{});
+    b->qg.assign(b->waves, QrGroup{});
+    for (int w = 0; w < b->waves; ++w) {
+        gauss_group_build(gj[w], t, b->gg[w]);
+        qr_group_build(qj[w], t, b->qg[w]);
+    }
+    if (t.bytes.empty()) return LSK_OK;
+    if (t.bytes != b->table_host || !b->table) {
+        cudaStreamSynchronize(ctx->stream);
+        if (t.bytes.size() > b->table_bytes) {
+            if (b->table) cudaFree(b->table);
+            b->table = nullptr;
+            b->table_bytes = 0;
+            if (cudaMalloc(&b->table, t.bytes.size()) != cudaSuccess) {
+                cudaGetLastError();
+                return LSK_ERR_OOM;
+            }
+            b->table_bytes = t.bytes.size();
+        }
+        if (cudaMemcpy(b->table, t.bytes.data(), t.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            snprintf(ctx->err, sizeof(ctx->err), "batch: table upload failed");
+            return LSK_ERR_CUDA;
+        }
+        b->table_host.swap(t.bytes);
+    }
+    return LSK_OK;
 }
 
 uint64_t signature(const lsk_batch_item* items, int count, int32_t prec) {
@@ -132,8 +316,11 @@ uint64_t signature(const lsk_batch_item* items, int count, int32_t prec) {
     return h;
 }
 
-uint64_t exact_key(const lsk_batch_item* items, int count, int32_t prec, int S) {
+uint64_t exact_key(const LskBatch* b, const lsk_batch_item* items, int count, int32_t prec, int S) {
     uint64_t h = fnv(signature(items, count, prec), &S, sizeof(S));
+    h = fnv(h, &b->arena, sizeof(b->arena));
+    h = fnv(h, &b->table, sizeof(b->table));
+    for (size_t s = 0; s < b->ws.size(); ++s) h = fnv(h, &b->ws[s], sizeof(void*));
     return fnv(h, items, sizeof(lsk_batch_item) * (size_t)count);
 }
 
@@ -171,6 +358,10 @@ void lsk_batch_free(lsk_ctx* ctx) {
         cudaEventDestroy(b->done[s]);
         cudaStreamDestroy(b->streams[s]);
     }
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->arena) cudaFree(b->arena);
+    if (b->table) cudaFree(b->table);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -198,6 +389,10 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
     if (!ctx->batch) ctx->batch = new LskBatch();
     LskBatch* b = ctx->batch;
     const uint64_t sig = signature(items, count, prec);
+    {
+        const int rc = prepare_groups(ctx, items, count, prec, !(flags & LSK_BATCH_PER_PROBLEM));
+        if (rc) return rc;
+    }
 
     int S = (flags & LSK_BATCH_STREAMS_MASK) ? (flags & LSK_BATCH_STREAMS_MASK) : 0;
     if (!S) {
@@ -257,7 +452,7 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
         }
         return LSK_OK;
     }
-    const uint64_t key = exact_key(items, count, prec, S);
+    const uint64_t key = exact_key(b, items, count, prec, S);
     if (!b->exec || b->exec_key != key) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);

@@ -178,9 +178,12 @@ __global__ void __launch_bounds__(1024) scan_one_block_kernel(const uint32_t* __
 }
 
 // ---- dense gather ---------------------------------------------------------
-// One warp per bucket.  Lanes own VEC consecutive columns in each of U
-// column groups of 32*VEC; the bucket's rows are fetched kBatch at a time so
-// that each warp keeps kBatch rows of loads in flight.
+// One warp per bucket part.  Lanes own VEC consecutive columns in each of U
+// column groups of 32*VEC; the rows are fetched kBatch at a time so that
+// each warp keeps kBatch rows of loads in flight.  With few buckets (small r,
+// long buckets) each bucket's row list is cut into P contiguous parts, one
+// warp each, so that enough warps stream A; their sums are then added into
+// SA (zeroed first) atomically.  With P = 1 each warp stores its bucket.
 template <int VEC>
 struct VecT;
 template <>
@@ -201,6 +204,11 @@ __device__ __forceinline__ void vadd(float4& a, const float4& b, float s) {
 __device__ __forceinline__ void vadd(float& a, const float& b, float s) { a = fmaf(s, b, a); }
 __device__ __forceinline__ void vzero(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ void vzero(float& a) { a = 0.f; }
+__device__ __forceinline__ void vatomic_add(float4* p, const float4& v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void vatomic_add(float* p, const float& v) { atomicAdd(p, v); }
 
 template <int VEC>
 __device__ __forceinline__ typename VecT<VEC>::T ldg_stream(const float* p) {
@@ -220,15 +228,21 @@ __device__ __forceinline__ typename VecT<VEC>::T ldg_stream(const float* p) {
 template <int VEC, int U>
 __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
     const float* __restrict__ A, int64_t lda, int64_t d, uint32_t r,
-    const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA) {
+    const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA, int P) {
     using V = typename VecT<VEC>::T;
     constexpr int kCols = 32 * VEC * U;  // columns per pass
     constexpr int kBatch = (VEC * U >= 8) ? 8 : 4;   // rows of loads in flight per warp
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp; b < r; b += nwarps) {
-        const uint32_t s = off[b], e = off[b + 1];
+    const int64_t items = (int64_t)r * P;
+    for (int64_t vb = warp; vb < items; vb += nwarps) {
+        const int64_t b = vb / P;
+        const uint32_t part = (uint32_t)(vb % P);
+        const uint32_t s0 = off[b], len = off[b + 1] - s0;
+        const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
+        const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
+        if (P > 1 && s == e) continue;
         for (int64_t c0 = 0; c0 < d; c0 += kCols) {
             V acc[U];
 #pragma unroll
@@ -269,16 +283,22 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
                 }
             }
             float* out = SA + (int64_t)b * d + c0;
+            if (P == 1) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (colok[u]) *reinterpret_cast<V*>(out + (u * 32 + lane) * VEC) = acc[u];
+                for (int u = 0; u < U; ++u)
+                    if (colok[u]) *reinterpret_cast<V*>(out + (u * 32 + lane) * VEC) = acc[u];
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (colok[u]) vatomic_add(reinterpret_cast<V*>(out + (u * 32 + lane) * VEC), acc[u]);
+            }
         }
     }
 }
 
 // ---- CSR gather -----------------------------------------------------------
-// One warp per bucket; the bucket's row of SA lives in shared memory (d
-// floats per warp).  Lane t handles the t-th row of the bucket's list and
+// One warp per bucket part (P parts per bucket as in the dense gather); the
+// part's row of SA lives in shared memory (d floats per warp).  Lane t handles the t-th row of the bucket's list and
 // adds its nonzeros with shared-memory atomics (columns of different rows
 // may collide).  Out-of-range row pointers or column indices are skipped
 // and reported through the BAD_CSR flag.
@@ -286,16 +306,22 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
                                      const int64_t* __restrict__ I, int64_t nnz, int64_t d,
                                      uint32_t r, const uint32_t* __restrict__ off,
                                      const uint32_t* __restrict__ perm, float* __restrict__ SA,
-                                     int* flag) {
+                                     int* flag, int P) {
     extern __shared__ float srow[];
     const int lane = threadIdx.x & 31;
     float* acc = srow + (int64_t)(threadIdx.x >> 5) * d;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp; b < r; b += nwarps) {
+    const int64_t items = (int64_t)r * P;
+    for (int64_t vb = warp; vb < items; vb += nwarps) {
+        const int64_t b = vb / P;
+        const uint32_t part = (uint32_t)(vb % P);
+        const uint32_t s0 = off[b], len = off[b + 1] - s0;
+        const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
+        const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
+        if (P > 1 && s == e) continue;
         for (int64_t c = lane; c < d; c += 32) acc[c] = 0.0f;
         __syncwarp();
-        const uint32_t s = off[b], e = off[b + 1];
         bool bad = false;
         for (uint32_t t = s + lane; t < e; t += 32) {
             const uint32_t p = perm[t];
@@ -318,7 +344,12 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
         if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
         __syncwarp();
         float* out = SA + (int64_t)b * d;
-        for (int64_t c = lane; c < d; c += 32) out[c] = acc[c];
+        if (P == 1) {
+            for (int64_t c = lane; c < d; c += 32) out[c] = acc[c];
+        } else {
+            for (int64_t c = lane; c < d; c += 32)
+                if (acc[c] != 0.0f) atomicAdd(out + c, acc[c]);
+        }
         __syncwarp();
     }
 }
@@ -380,7 +411,12 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
     if (n > 0)
         LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, off, rank, perm);
 
-    const int64_t warps_needed = r;
+    // parts per bucket: enough warps to stream A when there are few buckets,
+    // while each part keeps several rows
+    int P = 1;
+    while (P < 32 && r * P < 16384 && n >= (int64_t)r * P * 8) P *= 2;
+    if (P > 1 && (e = cudaMemsetAsync(SA, 0, (size_t)r * d * 4, st)) != cudaSuccess) return e;
+    const int64_t warps_needed = r * P;
     if (A->kind == LSK_DENSE) {
         const float* Av = (const float*)A->values;
         const bool vec4 = (d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)Av & 15) == 0) &&
@@ -388,14 +424,14 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         const unsigned grid = grid_for(warps_needed * 32, 256, sm_count, 8);
         if (vec4) {
             if (d <= 128)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
         } else {
             if (d <= 32)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
         }
     } else {
         // shared-memory row per warp: pick warps per block to fit 200 KB
@@ -414,7 +450,7 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         if (g > cap) g = cap;
         if (g < 1) g = 1;
         LSK_PROF("cs_csr_gather", st) cs_csr_gather_kernel<<<(unsigned)g, threads, smem, st>>>(
-            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag);
+            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P);
     }
     return cudaGetLastError();
 }

@@ -3,14 +3,18 @@
 // G (k x r) is exactly representable in bfloat16 by definition of the BF16
 // mode (the bf16 rounding of z / sqrt(k)); SA is split into bf16 hi + lo.
 //     GSA = G SA_hi + G SA_lo       (FP32 accumulation in tensor memory)
-// A block owns one 128-row tile of G and one slice of the r dimension; the
-// k x d partials of the slices are added in FP64 in a fixed order afterwards
-// (deterministic).  Per 32-column chunk of the slice:
-//   - the 8 worker warps draw their part of the G chunk (Philox + Box-Muller,
-//     4 rows per draw) straight into the bf16 K-major operand tile, and load
-//     the 32 rows of SA (row-major, N contiguous) into a padded FP32 staging
-//     buffer, then transpose it into the K-major bf16 hi / lo tiles;
-//   - lane 0 of warp 8 issues the 4 MMAs (2 K-steps x {hi, lo}).
+// A block owns one 256-row band of G (two 128-row MMA tiles) and one slice
+// of the r dimension; the k x d partials of the slices are added afterwards
+// in a fixed order with a compensated FP32 sum (deterministic).  Per 32-column chunk of the slice:
+//   - the 16 worker warps draw the 256 x 32 G chunk (Philox + Box-Muller, 4
+//     rows per draw, two independent draws per thread) straight into the
+//     bf16 K-major operand tiles, and load the 32 rows of SA (row-major, N
+//     contiguous) into a padded FP32 staging buffer, then transpose it into
+//     the K-major bf16 hi / lo tiles, which both MMA tiles share;
+//   - lane 0 of warp 16 issues the 8 MMAs (2 K-steps x {hi, lo} x 2 tiles).
+// Drawing G is the bulk of the work (about 60 instructions per entry, with
+// long dependent chains), so the block runs 16 worker warps with two draws
+// each to keep every scheduler supplied; SA staging is split thin.
 // The draws of the next chunk overlap the loads of SA; the loads are always
 // consumed before the stage barrier is arrived on.  All workers move through
 // the chunks in lockstep (one thread waits on a stage and broadcasts the
@@ -19,9 +23,10 @@
 
 namespace {
 
-constexpr int kM = 128;            // rows of G per block
+constexpr int kM = 256;            // rows of G per block (two 128-row MMA tiles sharing each SA chunk)
+constexpr int kMT = 128;           // rows per MMA tile
 constexpr int kKC = 32;            // r-columns per chunk (64-byte swizzle rows)
-constexpr int kWorkers = 8;        // worker warps (also the epilogue, warps 0-3)
+constexpr int kWorkers = 16;       // worker warps (also the epilogue, warps 0-7)
 constexpr int kMmaWarp = kWorkers;
 constexpr int kThreads = (kWorkers + 1) * 32;
 constexpr int kWorkerThreads = kWorkers * 32;
@@ -40,15 +45,17 @@ struct GtParams {
     uint32_t k0, k1;
     float scale;
     int* flag;
+    float* out;        // GSA, k x d (read by the reduction)
 };
 
-__host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 8 KB
+__host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 16 KB (two tiles)
 __host__ __device__ inline uint32_t b_bytes(int npad) { return (uint32_t)npad * kKC * 2; }  // per hi / lo
 __host__ __device__ inline uint32_t stage_bytes(int npad) { return a_bytes() + 2 * b_bytes(npad); }
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkerThreads) : "memory"); }
 
-__global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p) {
+// One block: row tile and r-slice number `blk` of problem p.
+__device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbytes = stage_bytes(p.npad);
@@ -65,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
     volatile int* verdict = abort + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x % p.tiles_m, slice = blockIdx.x / p.tiles_m;
+    const int mt = blk % p.tiles_m, slice = blk / p.tiles_m;
     const int64_t j0 = (int64_t)mt * kM;
     const int64_t c_begin = (int64_t)slice * p.kslice;
     const int64_t c_end = min(p.r, c_begin + p.kslice);
@@ -81,7 +88,8 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
         *abort = 0;
         tc::fence_mbar_init();
     }
-    const uint32_t tcols = p.npad <= 32 ? 32u : p.npad <= 64 ? 64u : p.npad <= 128 ? 128u : 256u;
+    // two accumulators (one per MMA tile) at columns 0 and npad
+    const uint32_t tcols = p.npad <= 16 ? 32u : p.npad <= 32 ? 64u : p.npad <= 64 ? 128u : p.npad <= 128 ? 256u : 512u;
     if (warp == kMmaWarp) {
         tc::tmem_alloc(tmem_slot, tcols);
         tc::tmem_relinquish();
@@ -92,21 +100,21 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kWorkers) {
-        const int wt = threadIdx.x;   // 0 .. 255
+        const int wt = threadIdx.x;   // 0 .. kWorkerThreads - 1
         bool ok = true;
         for (int g = 0; g < nchunks; ++g) {
             const int s = g % kStages;
             const int64_t c0 = c_begin + (int64_t)g * kKC;
-            // (1) SA rows c0 .. c0+31 into registers: float4 f = wt + 256 i,
+            // (1) SA rows c0 .. c0+31 into registers: float4 f = wt + 512 i,
             //     row f / (npad/4), columns 4 (f % (npad/4))
             const int q4 = p.npad / 4;
-            const int nf = kKC * q4 / kWorkerThreads;   // float4 per thread (npad / 32)
-            float4 sa[8];
+            const int nf4 = kKC * q4;                     // float4 in the chunk (<= 4 per thread)
+            float4 sa[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < 4; ++i) {
                 sa[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < nf) {
-                    const int f = wt + kWorkerThreads * i;
+                const int f = wt + kWorkerThreads * i;
+                if (f < nf4) {
                     const int rr = f / q4, n = 4 * (f % q4);
                     const int64_t c = c0 + rr;
                     if (c < c_end) {
@@ -121,7 +129,9 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
                     }
                 }
             }
-            // (2) G chunk: item = wt + 256 i -> (row quad gq = item / 16, column pair cp = item % 16)
+            // (2) G chunk: item = wt + 512 i -> (row quad gq = item / 16, column pair cp = item % 16),
+            //     64 x 16 items = the 256 x 32 chunk, two independent draws per worker thread
+            static_assert(2 * kWorkerThreads == (kM / 4) * (kKC / 2), "two G items per worker thread");
             uint32_t gw[2][4];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
@@ -151,7 +161,8 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
                 break;
             }
             uint8_t* st = stages + s * sbytes;
-            // (4) G words: row 4 gq + t, columns 2cp, 2cp+1
+            // (4) G words: row 4 gq + t, columns 2cp, 2cp+1 (rows 128.. are the second tile,
+            //     8 KB further on: sw64 offsets continue linearly in the row)
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int item = wt + kWorkerThreads * i;
@@ -162,9 +173,9 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
             }
             // (5) SA into the FP32 staging buffer
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (i < nf) {
-                    const int f = wt + kWorkerThreads * i;
+            for (int i = 0; i < 4; ++i) {
+                const int f = wt + kWorkerThreads * i;
+                if (f < nf4) {
                     const int rr = f / q4, n = 4 * (f % q4);
                     *reinterpret_cast<float4*>(stagef + rr * ldf + n) = sa[i];
                 }
@@ -191,18 +202,20 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(full + s);
         }
-        // epilogue: warps 0-3 read the 128 x npad accumulator
-        if (warp < 4) {
+        // epilogue: warps 0-3 read tile 0 (columns 0..npad), warps 4-7 tile 1 (columns npad..2 npad);
+        // a warp may only read the TMEM lanes 32 (warp % 4) .. + 31
+        if (warp < 8) {
             int okw = 0;
             if (lane == 0) okw = (ok && tc::mbar_wait(done, 0, abort)) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
             if (okw) {
                 tc::fence_after_sync();
-                const int64_t j = j0 + warp * 32 + lane;
+                const int tile = warp >> 2, wq = warp & 3;
+                const int64_t j = j0 + tile * kMT + wq * 32 + lane;
                 float* dst = p.part + ((int64_t)slice * p.k + j) * p.d;
                 for (int col = 0; col < p.npad; col += 32) {
                     uint32_t v[32];
-                    tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+                    tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(tile * p.npad + col), v);
                     tc::tmem_ld_wait();
                     if (j < p.k) {
 #pragma unroll
@@ -228,8 +241,13 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
 #pragma unroll
                 for (int kk = 0; kk < kKC / 16; ++kk) {
                     const uint32_t ko = 32u * kk;
-                    tc::mma_bf16(tmem, tc::desc_sw64_kmajor(a + ko), tc::desc_sw64_kmajor(bh + ko), idesc, (g | kk) != 0);
-                    tc::mma_bf16(tmem, tc::desc_sw64_kmajor(a + ko), tc::desc_sw64_kmajor(bl + ko), idesc, 1);
+#pragma unroll
+                    for (int t = 0; t < kM / kMT; ++t) {
+                        const uint32_t at = a + (uint32_t)t * (kMT * kKC * 2) + ko;
+                        const uint32_t dt = tmem + (uint32_t)(t * p.npad);
+                        tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bh + ko), idesc, (g | kk) != 0);
+                        tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bl + ko), idesc, 1);
+                    }
                 }
                 tc::mma_commit(empty + s);
             }
@@ -249,6 +267,15 @@ __global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p)
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }
 
+__global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p) { gauss_tc_body(p, blockIdx.x); }
+
+// Grouped: the blocks of many problems in one grid.
+__global__ void __launch_bounds__(kThreads, 1) gauss_tc_grouped_kernel(const GtParams* __restrict__ ps,
+                                                                       const int* __restrict__ off, int count) {
+    const int g = group_of(off, count, blockIdx.x);
+    gauss_tc_body(ps[g], (int)blockIdx.x - __ldg(off + g));
+}
+
 struct Plan {
     int npad, tiles_m, slices;
     int64_t kslice;
@@ -259,7 +286,7 @@ bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
     if (d < 1 || d > kMaxN || k < 1 || r < 1) return false;
     P.npad = (int)((d + 31) / 32) * 32;
     P.tiles_m = (int)((k + kM - 1) / kM);
-    int64_t want = (2 * (int64_t)sm_count + P.tiles_m - 1) / P.tiles_m;
+    int64_t want = ((int64_t)sm_count + P.tiles_m - 1) / P.tiles_m;   // one wave of blocks
     const int64_t max_slices = (r + 8 * kKC - 1) / (8 * kKC);   // >= 8 chunks per block
     if (want > max_slices) want = max_slices;
     if (want < 1) want = 1;
@@ -271,15 +298,48 @@ bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
     return P.smem <= kSmemLimit;
 }
 
-__global__ void gauss_tc_reduce_kernel(const float* __restrict__ part, int slices, int64_t len,
-                                       float* __restrict__ out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-        double s = 0.0;
-        for (int z = 0; z < slices; ++z) s += (double)part[(int64_t)z * len + e];
-        out[e] = (float)s;
+__device__ __forceinline__ void reduce_body(const float* __restrict__ part, int slices, int64_t len,
+                                            float* __restrict__ out, int blk, int nblk) {
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    for (int64_t e = (int64_t)blk * blockDim.x + threadIdx.x; e < len; e += stride) {
+        // compensated FP32 sum (Neumaier) in slice order: about two roundings
+        // of error in total, without FP64 adds (scarce on this part)
+        float s = 0.f, c = 0.f;
+        for (int z = 0; z < slices; ++z) {
+            const float x = part[(int64_t)z * len + e];
+            const float t = s + x;
+            c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+            s = t;
+        }
+        out[e] = s + c;
     }
 }
+__global__ void gauss_tc_reduce_kernel(const float* __restrict__ part, int slices, int64_t len,
+                                       float* __restrict__ out) {
+    reduce_body(part, slices, len, out, blockIdx.x, gridDim.x);
+}
+__global__ void gauss_tc_reduce_grouped_kernel(const GtParams* __restrict__ ps, const int* __restrict__ roff,
+                                               int count) {
+    const int g = group_of(roff, count, blockIdx.x);
+    const int b0 = __ldg(roff + g), b1 = __ldg(roff + g + 1);
+    const GtParams& p = ps[g];
+    reduce_body(p.part, p.slices, p.k * p.d, p.out, (int)blockIdx.x - b0, b1 - b0);
+}
+
+// Grouped plan: the parallelism comes from the many problems, so a block
+// takes a longer slice (>= 128 chunks) and fewer partials are written.
+void plan_grouped(int64_t r, int64_t d, int64_t k, Plan& P) {
+    P.npad = (int)((d + 31) / 32) * 32;
+    P.tiles_m = (int)((k + kM - 1) / kM);
+    const int64_t want = (r + 128 * kKC - 1) / (128 * kKC);
+    int64_t ks = (r + want - 1) / want;
+    ks = ((ks + kKC - 1) / kKC) * kKC;
+    P.kslice = ks;
+    P.slices = (int)((r + ks - 1) / ks);
+    P.smem = (size_t)kStages * stage_bytes(P.npad) + (size_t)kKC * (P.npad + kStagePad) * 4 + 1024 + 128;
+}
+
+constexpr int kReduceBlockCap = 64;
 
 }  // namespace
 
@@ -312,6 +372,7 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     p.k1 = (uint32_t)(seed >> 32);
     p.scale = (float)(1.0 / sqrt((double)k));
     p.flag = nullptr;
+    p.out = GSA;
     cudaError_t e = cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
     if (e != cudaSuccess) return e;
     LSK_PROF("gauss_tc", st) gauss_tc_kernel<<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
@@ -319,5 +380,60 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     int64_t g = (len + 255) / 256;
     if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
     LSK_PROF("gauss_reduce", st) gauss_tc_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(p.part, P.slices, len, GSA);
+    return cudaGetLastError();
+}
+
+size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k) {
+    Plan P;
+    plan_grouped(r, d, k, P);
+    return ws_round((size_t)P.slices * k * d * 4);
+}
+
+void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGroup& g) {
+    std::vector<GtParams> ps(jobs.size());
+    std::vector<int> blocks(jobs.size()), rblocks(jobs.size()), off, roff;
+    g.smem = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const GaussJob& j = jobs[i];
+        Plan P;
+        plan_grouped(j.r, j.d, j.k, P);
+        GtParams& p = ps[i];
+        p.SA = j.SA;
+        p.part = j.part;
+        p.r = j.r;
+        p.k = j.k;
+        p.d = (int)j.d;
+        p.npad = P.npad;
+        p.kslice = P.kslice;
+        p.tiles_m = P.tiles_m;
+        p.slices = P.slices;
+        p.k0 = (uint32_t)j.seed;
+        p.k1 = (uint32_t)(j.seed >> 32);
+        p.scale = (float)(1.0 / sqrt((double)j.k));
+        p.flag = nullptr;
+        p.out = j.GSA;
+        blocks[i] = P.tiles_m * P.slices;
+        const int64_t rb = (j.k * j.d + 255) / 256;
+        rblocks[i] = (int)(rb < kReduceBlockCap ? rb : kReduceBlockCap);
+        if (P.smem > g.smem) g.smem = P.smem;
+    }
+    g.count = (int)jobs.size();
+    g.blocks = group_offsets(blocks, off);
+    g.rblocks = group_offsets(rblocks, roff);
+    g.params_off = t.put(ps.data(), ps.size());
+    g.off_off = t.put(off.data(), off.size());
+    g.roff_off = t.put(roff.data(), roff.size());
+}
+
+cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, cudaStream_t st) {
+    if (g.count == 0) return cudaSuccess;
+    const GtParams* ps = reinterpret_cast<const GtParams*>(table + g.params_off);
+    const int* off = reinterpret_cast<const int*>(table + g.off_off);
+    const int* roff = reinterpret_cast<const int*>(table + g.roff_off);
+    cudaError_t e = cudaFuncSetAttribute(gauss_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)g.smem);
+    if (e != cudaSuccess) return e;
+    LSK_PROF("gauss_tc_grouped", st) gauss_tc_grouped_kernel<<<g.blocks, kThreads, g.smem, st>>>(ps, off, g.count);
+    LSK_PROF("gauss_reduce_grouped", st) gauss_tc_reduce_grouped_kernel<<<g.rblocks, 256, 0, st>>>(ps, roff, g.count);
     return cudaGetLastError();
 }

@@ -8,6 +8,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <string.h>
+
+#include <vector>
 
 #include "../../include/lsk.h"
 #include "prof.cuh"
@@ -58,6 +61,41 @@ struct WsCarver {
     }
 };
 inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// grouped launches: one grid runs the blocks of many independent problems.
+// Problem p owns blocks [off[p], off[p + 1]); off has count + 1 ascending
+// entries.  Per-problem parameters and offsets are packed on the host into one
+// table (HostTable), copied to the device once per batch plan, and read by the
+// grouped kernels through offsets into that device copy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int group_of(const int* __restrict__ off, int count, int b) {
+    int lo = 0, hi = count;   // off[lo] <= b < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct HostTable {
+    std::vector<unsigned char> bytes;
+    template <class T>
+    size_t put(const T* p, size_t n) {
+        const size_t o = (bytes.size() + 15) & ~size_t(15);
+        bytes.resize(o + sizeof(T) * n);
+        if (n) memcpy(bytes.data() + o, p, sizeof(T) * n);
+        return o;
+    }
+};
+
+// Offsets of `count` problems with blocks[p] blocks each; returns the total.
+inline int group_offsets(const std::vector<int>& blocks, std::vector<int>& off) {
+    off.assign(blocks.size() + 1, 0);
+    for (size_t p = 0; p < blocks.size(); ++p) off[p + 1] = off[p] + blocks[p];
+    return off.back();
+}
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon et al., SC'11).  Round: multiply words 0 and 2 by
@@ -135,6 +173,24 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
 
+// gauss_tc.cu: grouped Gaussian stage (BF16) over many sketches
+struct GaussJob {
+    const float* SA;
+    int64_t r, d, k;
+    uint64_t seed;
+    float* GSA;
+    float* part;             // gauss_group_part_bytes(r, d, k) bytes
+};
+struct GaussGroup {
+    size_t params_off, off_off, roff_off;
+    int count, blocks, rblocks;
+    size_t smem;
+};
+bool gauss_tc_supported(int64_t r, int64_t d, int64_t k);
+size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k);
+void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGroup& g);
+cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, cudaStream_t st);
+
 // gauss.cu
 size_t gauss_workspace_bytes(int64_t r, int64_t d, int64_t k, int32_t prec, int sm_count);
 cudaError_t gauss_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
@@ -162,6 +218,35 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
 size_t qr_workspace_bytes(int64_t k, int64_t d);
 cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv,
                       float* Rinv32, void* ws, int* flag, int sm_count, cudaStream_t st);
+
+// Grouped R^-1 of many sketches (d <= 256, the mixed-precision path): every
+// stage of qr_launch, each one grid over all problems.  R is not formed.
+struct QrJob {
+    const float* B;          // sketch, k x d row-major
+    int64_t k, rows_per;
+    int d, nchunks, ntiles;
+    double* part;            // Gram partials
+    double* C;               // FP64 Gram
+    double *Ct, *Rt, *X, *W, *M, *Y, *sc;
+    float *Ct32, *Lpk;
+    int* e;
+    double* Rinv;            // nullable
+    float* Rinv32;
+    int* flag;
+};
+enum QrShape { QS_GRAM, QS_GRAMRED, QS_ONE, QS_EW, QS_TRINV, QS_TRI, QS_N };
+struct QrGroup {
+    size_t jobs_off, off_off[QS_N];
+    int count, blocks[QS_N], dmax;
+};
+bool qr_group_supported(int64_t k, int64_t d);
+void qr_group_job(QrJob& j, const float* B, int64_t k, int64_t d, void* ws, double* Rinv, float* Rinv32, int* flag);
+void qr_group_build(const std::vector<QrJob>& jobs, HostTable& t, QrGroup& g);
+cudaError_t qr_group_launch(const QrGroup& g, const unsigned char* table, cudaStream_t st);
+// qr_mixed.cu (pieces of the grouped path)
+void qr_mixed_carve(QrJob& j, void* ws);
+int qr_mixed_blocks(int d, int shape);
+cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, cudaStream_t st);
 
 // lsq.cu
 size_t lsq_workspace_bytes(const lsk_mat* A);

@@ -3,8 +3,9 @@
 // The paper factors the small sketch B (k x d) with an SVD; the reading used
 // here takes the QR factor R with a positive diagonal, computed as the
 // Cholesky factor of B^T B:
-//   1. C = B^T B in FP64 (products of FP32 values are exact in FP64), split
-//      over row chunks of B and tiles of C, partials added in fixed order;
+//   1. C = B^T B with exact products of the FP32 values summed in FP32
+//      pairs (near-FP64 accuracy at FP32 rates), split over row chunks of B
+//      and tiles of C, chunk partials added in FP64 in a fixed order;
 //   2. C = L L^T by right-looking blocked Cholesky, 16x16 blocks, two
 //      launches per block column (panel, trailing update), so the FP64 work
 //      is spread over the whole GPU (FP64 is scarce on this part);
@@ -16,6 +17,8 @@
 // triangular products), which avoids FP64 dependency chains; the all-FP64
 // blocked path below serves larger d.
 #include "lsk_internal.cuh"
+
+#include <algorithm>
 
 size_t qr_mixed_workspace_bytes(int64_t d);
 cudaError_t qr_mixed_launch(const double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws,
@@ -35,20 +38,45 @@ __device__ __forceinline__ void utile_of(int t, int nt, int& ta, int& tb) {
     tb = ta + t;
 }
 
-__global__ void __launch_bounds__(256) sketch_gram64_kernel(const float* __restrict__ B, int64_t k,
-                                                            int64_t d, int64_t rows_per,
-                                                            double* __restrict__ part) {
+// s + c += x y in FP32 pairs: the product is split exactly (x y = p + e,
+// one FMA) and the sum s + p by TwoSum, whose rounding error goes to c.
+// The _rn intrinsics keep the compiler from fusing any of these steps.
+__device__ __forceinline__ void df_mac(float x, float y, float& s, float& c) {
+    const float p = __fmul_rn(x, y);
+    const float e = fmaf(x, y, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    c = __fadd_rn(c, __fadd_rn(err, e));
+    s = t;
+}
+
+// (s, c) <- TwoSum(s, c): keeps |c| at most half an ulp of s.
+__device__ __forceinline__ void df_renorm(float& s, float& c) {
+    const float t = __fadd_rn(s, c);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
+    s = t;
+}
+
+// Block (tile, chunk): upper tile `tile` of C over row chunk `chunk` of B.
+// Each product of two FP32 values is formed exactly and summed in FP32
+// pairs, renormalised every 32 rows: the error is of order k 2^-48 relative
+// to sum |x y| (FP64 summation: k 2^-53), and the FP64 units, scarce on
+// this part, are not used.  The chunk partials are written as FP64 (s + c).
+__device__ __forceinline__ void sketch_gram64_body(const float* __restrict__ B, int64_t k, int64_t d, int64_t rows_per,
+                                                   double* __restrict__ part, const int tile, const int chunk) {
     __shared__ float Xa[QT][QT + 1];
     __shared__ float Xb[QT][QT + 1];
     const int nt = (int)((d + QT - 1) / QT);
     int ta, tb;
-    utile_of(blockIdx.x, nt, ta, tb);
+    utile_of(tile, nt, ta, tb);
     const int64_t a0 = (int64_t)ta * QT, b0 = (int64_t)tb * QT;
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;   // outputs (2ty+u, 2tx+v)
-    const int64_t r0 = (int64_t)blockIdx.y * rows_per;
+    const int64_t r0 = (int64_t)chunk * rows_per;
     const int64_t r1 = min(k, r0 + rows_per);
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, cmp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int64_t i0 = r0; i0 < r1; i0 += QT) {
 #pragma unroll
         for (int t = 0; t < (QT * QT) / 256; ++t) {
@@ -61,30 +89,34 @@ __global__ void __launch_bounds__(256) sketch_gram64_kernel(const float* __restr
         __syncthreads();
 #pragma unroll 8
         for (int rr = 0; rr < QT; ++rr) {
-            const double x0 = Xa[rr][2 * ty], x1 = Xa[rr][2 * ty + 1];
-            const double y0 = Xb[rr][2 * tx], y1 = Xb[rr][2 * tx + 1];
-            acc[0][0] = fma(x0, y0, acc[0][0]);
-            acc[0][1] = fma(x0, y1, acc[0][1]);
-            acc[1][0] = fma(x1, y0, acc[1][0]);
-            acc[1][1] = fma(x1, y1, acc[1][1]);
+            const float x0 = Xa[rr][2 * ty], x1 = Xa[rr][2 * ty + 1];
+            const float y0 = Xb[rr][2 * tx], y1 = Xb[rr][2 * tx + 1];
+            df_mac(x0, y0, acc[0][0], cmp[0][0]);
+            df_mac(x0, y1, acc[0][1], cmp[0][1]);
+            df_mac(x1, y0, acc[1][0], cmp[1][0]);
+            df_mac(x1, y1, acc[1][1], cmp[1][1]);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) df_renorm(acc[u][v], cmp[u][v]);
         __syncthreads();
     }
     const int ntiles = nt * (nt + 1) / 2;
-    double* P = part + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * QT * QT;
+    double* P = part + ((int64_t)chunk * ntiles + tile) * QT * QT;
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int v = 0; v < 2; ++v) P[(2 * ty + u) * QT + 2 * tx + v] = acc[u][v];
+        for (int v = 0; v < 2; ++v) P[(2 * ty + u) * QT + 2 * tx + v] = (double)acc[u][v] + (double)cmp[u][v];
 }
 
-__global__ void sketch_gram64_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
-                                            int64_t d, double* __restrict__ C) {
+__device__ __forceinline__ void sketch_gram64_reduce_body(const double* __restrict__ part, int64_t nchunks, int64_t d,
+                                                          double* __restrict__ C, const int blk, const int nblk) {
     const int nt = (int)((d + QT - 1) / QT);
     const int ntiles = nt * (nt + 1) / 2;
     const int64_t len = d * d;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    for (int64_t e = (int64_t)blk * blockDim.x + threadIdx.x; e < len; e += stride) {
         int64_t a = e / d, b = e % d;
         if (a > b) {
             const int64_t t = a;
@@ -98,6 +130,30 @@ __global__ void sketch_gram64_reduce_kernel(const double* __restrict__ part, int
         for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * QT * QT + w];
         C[e] = s;
     }
+}
+
+__global__ void __launch_bounds__(256) sketch_gram64_kernel(const float* __restrict__ B, int64_t k, int64_t d,
+                                                            int64_t rows_per, double* __restrict__ part) {
+    sketch_gram64_body(B, k, d, rows_per, part, blockIdx.x, blockIdx.y);
+}
+__global__ void sketch_gram64_reduce_kernel(const double* __restrict__ part, int64_t nchunks, int64_t d,
+                                            double* __restrict__ C) {
+    sketch_gram64_reduce_body(part, nchunks, d, C, blockIdx.x, gridDim.x);
+}
+// grouped over QrJob tables: local block b of a job = (tile b % ntiles, chunk b / ntiles)
+__global__ void __launch_bounds__(256) sketch_gram64_grouped_kernel(const QrJob* __restrict__ jobs,
+                                                                    const int* __restrict__ off, int count) {
+    const int g = group_of(off, count, blockIdx.x);
+    const QrJob& j = jobs[g];
+    const int b = (int)blockIdx.x - __ldg(off + g);
+    sketch_gram64_body(j.B, j.k, j.d, j.rows_per, j.part, b % j.ntiles, b / j.ntiles);
+}
+__global__ void sketch_gram64_reduce_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
+                                                    int count) {
+    const int g = group_of(off, count, blockIdx.x);
+    const QrJob& j = jobs[g];
+    const int b0 = __ldg(off + g);
+    sketch_gram64_reduce_body(j.part, j.nchunks, j.d, j.C, (int)blockIdx.x - b0, __ldg(off + g + 1) - b0);
 }
 
 // Factor the diagonal block K of C (lower part) in shared memory.  Every
@@ -333,4 +389,57 @@ cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* R
     else
         LSK_PROF("qr_trinv", st) trinv_kernel<32><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
     return cudaGetLastError();
+}
+
+bool qr_group_supported(int64_t k, int64_t d) { return d >= 1 && d <= 256 && k >= d; }
+
+// The same workspace layout as qr_launch (C, Gram partials, then the
+// mixed-precision factorisation's buffers).
+void qr_group_job(QrJob& j, const float* B, int64_t k, int64_t d, void* ws, double* Rinv, float* Rinv32, int* flag) {
+    const QrPlan p = qr_plan(k, d);
+    WsCarver wc{(char*)ws, 0};
+    j.B = B;
+    j.k = k;
+    j.d = (int)d;
+    j.rows_per = p.rows_per;
+    j.nchunks = (int)p.nchunks;
+    j.ntiles = p.ntiles;
+    j.C = wc.take<double>((size_t)d * d);
+    j.part = wc.take<double>((size_t)p.nchunks * p.ntiles * QT * QT);
+    const int64_t nbk = (d + NB - 1) / NB;
+    void* rest = wc.take<double>((size_t)nbk * NB * NB);
+    qr_mixed_carve(j, rest);
+    j.Rinv = Rinv;
+    j.Rinv32 = Rinv32;
+    j.flag = flag;
+}
+
+void qr_group_build(const std::vector<QrJob>& jobs, HostTable& t, QrGroup& g) {
+    g.count = (int)jobs.size();
+    g.dmax = 1;
+    std::vector<int> blocks(jobs.size()), off;
+    for (int s = 0; s < QS_N; ++s) {
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            const QrJob& j = jobs[i];
+            if (j.d > g.dmax) g.dmax = j.d;
+            if (s == QS_GRAM) blocks[i] = j.ntiles * j.nchunks;
+            else if (s == QS_GRAMRED) blocks[i] = std::min((j.d * j.d + 255) / 256, 64);
+            else blocks[i] = qr_mixed_blocks(j.d, s);
+        }
+        g.blocks[s] = group_offsets(blocks, off);
+        g.off_off[s] = t.put(off.data(), off.size());
+    }
+    g.jobs_off = t.put(jobs.data(), jobs.size());
+}
+
+cudaError_t qr_group_launch(const QrGroup& g, const unsigned char* table, cudaStream_t st) {
+    if (g.count == 0) return cudaSuccess;
+    const QrJob* jobs = reinterpret_cast<const QrJob*>(table + g.jobs_off);
+    LSK_PROF("qr_gram64", st) sketch_gram64_grouped_kernel<<<g.blocks[QS_GRAM], 256, 0, st>>>(
+        jobs, reinterpret_cast<const int*>(table + g.off_off[QS_GRAM]), g.count);
+    LSK_PROF("qr_gram64", st) sketch_gram64_reduce_grouped_kernel<<<g.blocks[QS_GRAMRED], 256, 0, st>>>(
+        jobs, reinterpret_cast<const int*>(table + g.off_off[QS_GRAMRED]), g.count);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return qr_mixed_group_launch(g, table, st);
 }

@@ -19,13 +19,15 @@
 // the equilibrated diag(R) spans more than 2^20.
 #include "lsk_internal.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int TT = 16;   // tile edge of the FP64 triangular products (one output per thread)
 
 // e_j = floor(log2 sqrt(C_jj)) and the exact scale 2^-e_j.
-__global__ void equil_exponents_kernel(const double* __restrict__ C, int d, int* __restrict__ e,
-                                       double* __restrict__ sc, int* flag) {
+__device__ __forceinline__ void equil_exponents_body(const double* __restrict__ C, int d, int* __restrict__ e,
+                                       double* __restrict__ sc, int* flag, const int blk, const int nblk) {
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const double c = C[(int64_t)j * d + j];
         int ex = 0;
@@ -40,15 +42,23 @@ __global__ void equil_exponents_kernel(const double* __restrict__ C, int d, int*
         sc[j] = ldexp(1.0, -ex);
     }
 }
+__global__ void equil_exponents_kernel(const double* __restrict__ C, int d, int* __restrict__ e,
+                                       double* __restrict__ sc, int* flag) {
+    equil_exponents_body(C, d, e, sc, flag, blockIdx.x, gridDim.x);
+}
 
 // Ct64 = C 2^{-e_i-e_j} (two exact multiplications), Ct32 = float(Ct64).
-__global__ void equil_scale_kernel(const double* __restrict__ C, int d, const double* __restrict__ sc,
-                                   double* __restrict__ Ct64, float* __restrict__ Ct32) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void equil_scale_body(const double* __restrict__ C, int d, const double* __restrict__ sc,
+                                   double* __restrict__ Ct64, float* __restrict__ Ct32, const int blk, const int nblk) {
+    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
         const double v = C[t] * sc[t / d] * sc[t % d];
         Ct64[t] = v;
         Ct32[t] = (float)v;
     }
+}
+__global__ void equil_scale_kernel(const double* __restrict__ C, int d, const double* __restrict__ sc,
+                                   double* __restrict__ Ct64, float* __restrict__ Ct32) {
+    equil_scale_body(C, d, sc, Ct64, Ct32, blockIdx.x, gridDim.x);
 }
 
 // FP32 Cholesky of Ct (d <= 256) in one CTA, blocked by 32: the lower
@@ -98,8 +108,8 @@ struct DiagStep<CB> {
 };
 __device__ __forceinline__ float* ctile(float* S, int I, int J) { return S + (I * (I + 1) / 2 + J) * (CB * CP); }
 
-__global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
-                                                      float* __restrict__ Lpk, int* flag) {
+__device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
+                                                      float* __restrict__ Lpk, int* flag, const int blk, const int nblk) {
     extern __shared__ float S[];
     __shared__ float rdiag[CB];
     const int nt = (d + CB - 1) / CB;
@@ -202,19 +212,31 @@ __global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ C
         Lpk[t] = ctile(S, l / CB, i / CB)[(l % CB) * CP + (i % CB)];
     }
 }
+__global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
+                                                      float* __restrict__ Lpk, int* flag) {
+    chol32_body(Ct32, d, Rt, Lpk, flag, blockIdx.x, gridDim.x);
+}
 
 // X = Rt^-1 (upper) in FP32, one warp per column; stored as FP64 values.
 // The packed factor (row l of L = column l of Rt at offset l(l+1)/2) is
-// staged in shared memory so the back-substitution chain sees smem latency.
-__global__ void __launch_bounds__(128) trinv32_kernel(const float* __restrict__ Lpk, int d, double* __restrict__ X) {
+// staged in shared memory (once per 16 columns: 512-thread blocks) so the
+// back-substitution chain sees shared-memory latency.
+__device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int d, double* __restrict__ X, const int blk, const int nblk) {
     extern __shared__ float P[];
     __shared__ float rdiag[256];
-    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += blockDim.x) P[t] = Lpk[t];
+    {   // stage the packed factor with 16-byte loads, several in flight per thread
+        const int np = d * (d + 1) / 2, n4 = np >> 2;
+        const float4* src4 = reinterpret_cast<const float4*>(Lpk);
+        float4* P4 = reinterpret_cast<float4*>(P);
+#pragma unroll 4
+        for (int t = threadIdx.x; t < n4; t += blockDim.x) P4[t] = __ldg(src4 + t);
+        for (int t = 4 * n4 + threadIdx.x; t < np; t += blockDim.x) P[t] = __ldg(Lpk + t);
+    }
     __syncthreads();
     for (int l = threadIdx.x; l < d; l += blockDim.x) rdiag[l] = 1.f / P[l * (l + 1) / 2 + l];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int j = (int)(((int64_t)blk * blockDim.x + threadIdx.x) >> 5);
     if (j >= d) return;
     float xr[8];
 #pragma unroll
@@ -243,6 +265,9 @@ __global__ void __launch_bounds__(128) trinv32_kernel(const float* __restrict__ 
         if (i < d) X[(int64_t)i * d + j] = (i <= j) ? (double)xr[s] : 0.0;
     }
 }
+__global__ void __launch_bounds__(512) trinv32_kernel(const float* __restrict__ Lpk, int d, double* __restrict__ X) {
+    trinv32_body(Lpk, d, X, blockIdx.x, gridDim.x);
+}
 
 // Out = alpha * op(A) * B + beta * Cin + diag_add * I on the upper triangle
 // (tiles I <= J), FP64.  op(A) = A or A^T.  The reduction index is limited to
@@ -258,9 +283,9 @@ struct TriGemm {
     double alpha, beta, diag_add;
 };
 
-__global__ void __launch_bounds__(256) tri_gemm64_kernel(const TriGemm g) {
+__device__ __forceinline__ void tri_gemm64_body(const TriGemm g, const int blk, const int nblk) {
     const int nt = (g.d + TT - 1) / TT;
-    int t = blockIdx.x, I = 0;
+    int t = blk, I = 0;
     while (t >= nt - I) {   // upper tile pairs (I <= J)
         t -= nt - I;
         ++I;
@@ -302,13 +327,16 @@ __global__ void __launch_bounds__(256) tri_gemm64_kernel(const TriGemm g) {
     }
     g.Out[(int64_t)i * g.d + j] = r;
 }
+__global__ void __launch_bounds__(256) tri_gemm64_kernel(const TriGemm g) {
+    tri_gemm64_body(g, blockIdx.x, gridDim.x);
+}
 
 // U = strict_upper(M - I) + diag(M - I) / 2, in place.  |M - I| > 1/4
 // anywhere means the FP32 factor was too far off for one correction: the
 // equilibrated sketch is numerically rank deficient at FP32 precision.
-__global__ void correction_kernel(double* __restrict__ M, int d, int* flag) {
+__device__ __forceinline__ void correction_body(double* __restrict__ M, int d, int* flag, const int blk, const int nblk) {
     bool big = false;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
         const int i = t / d, j = t % d;
         if (i <= j) {
             const double e = M[t] - (i == j ? 1.0 : 0.0);
@@ -320,11 +348,14 @@ __global__ void correction_kernel(double* __restrict__ M, int d, int* flag) {
     }
     if (big) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
 }
+__global__ void correction_kernel(double* __restrict__ M, int d, int* flag) {
+    correction_body(M, d, flag, blockIdx.x, gridDim.x);
+}
 
 // R = Z D, R^-1 = D^-1 Y (exact power-of-two scalings); FP32 copy of R^-1.
-__global__ void unscale_kernel(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
-                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void unscale_body(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
+                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32, const int blk, const int nblk) {
+    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
         const int i = t / d, j = t % d;
         const bool up = j >= i;
         const double r = (up && Z) ? ldexp(Z[t], e[j]) : 0.0;
@@ -334,11 +365,15 @@ __global__ void unscale_kernel(const double* __restrict__ Z, const double* __res
         if (Rinv32) Rinv32[t] = (float)ri;
     }
 }
+__global__ void unscale_kernel(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
+                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32) {
+    unscale_body(Z, Y, e, d, R, Rinv, Rinv32, blockIdx.x, gridDim.x);
+}
 
 // min_j Rt_jj <= 2^-20 max_j Rt_jj on the equilibrated factor, with
 // Rt_jj = 1 / Y_jj: beyond that conditioning a factor of the Gram cannot
 // resolve the sketch in FP64.
-__global__ void rank_check_r_kernel(const double* __restrict__ Y, int d, int* flag) {
+__device__ __forceinline__ void rank_check_r_body(const double* __restrict__ Y, int d, int* flag, const int blk, const int nblk) {
     double mn = INFINITY, mx = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const double v = 1.0 / Y[(int64_t)j * d + j];
@@ -363,6 +398,72 @@ __global__ void rank_check_r_kernel(const double* __restrict__ Y, int d, int* fl
         if (!(mn > 9.5367431640625e-07 * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
     }
 }
+__global__ void rank_check_r_kernel(const double* __restrict__ Y, int d, int* flag) {
+    rank_check_r_body(Y, d, flag, blockIdx.x, gridDim.x);
+}
+
+// ---- grouped: one grid per stage over many sketches (QrJob table) --------
+__device__ __forceinline__ const QrJob& job_of(const QrJob* jobs, const int* off, int count, int& blk, int& nblk) {
+    const int g = group_of(off, count, blockIdx.x);
+    const int b0 = __ldg(off + g);
+    blk = (int)blockIdx.x - b0;
+    nblk = __ldg(off + g + 1) - b0;
+    return jobs[g];
+}
+
+__global__ void equil_exponents_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    equil_exponents_body(j.C, j.d, j.e, j.sc, j.flag, blk, nblk);
+}
+__global__ void equil_scale_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    equil_scale_body(j.C, j.d, j.sc, j.Ct, j.Ct32, blk, nblk);
+}
+__global__ void __launch_bounds__(512) chol32_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
+                                                             int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    chol32_body(j.Ct32, j.d, j.Rt, j.Lpk, j.flag, blk, nblk);
+}
+__global__ void __launch_bounds__(512) trinv32_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
+                                                              int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    trinv32_body(j.Lpk, j.d, j.X, blk, nblk);
+}
+// which: 0 W = Ct X, 1 M = X^T W, 2 Y = X - X U (the products of qr_mixed_launch without the Newton step)
+__global__ void __launch_bounds__(256) tri_gemm64_grouped_kernel(const QrJob* __restrict__ jobs,
+                                                                 const int* __restrict__ off, int count, int which) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    TriGemm g;
+    if (which == 0) g = TriGemm{j.Ct, j.X, nullptr, j.W, j.d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
+    else if (which == 1) g = TriGemm{j.X, j.W, nullptr, j.M, j.d, 1, 0, 1, 1, 1.0, 0.0, 0.0};
+    else g = TriGemm{j.X, j.M, j.X, j.Y, j.d, 0, 1, 0, 1, -1.0, 1.0, 0.0};
+    tri_gemm64_body(g, blk, nblk);
+}
+__global__ void correction_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    correction_body(j.M, j.d, j.flag, blk, nblk);
+}
+__global__ void unscale_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    unscale_body(nullptr, j.Y, j.e, j.d, nullptr, j.Rinv, j.Rinv32, blk, nblk);
+}
+__global__ void rank_check_r_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    rank_check_r_body(j.Y, j.d, j.flag, blk, nblk);
+}
+
+size_t chol32_smem(int d) {
+    const int nt = (d + CB - 1) / CB;
+    return (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
+}
 
 cudaError_t tri_gemm(const TriGemm& g, cudaStream_t st) {
     const int nt = (g.d + TT - 1) / TT;
@@ -375,6 +476,60 @@ cudaError_t tri_gemm(const TriGemm& g, cudaStream_t st) {
 size_t qr_mixed_workspace_bytes(int64_t d) {
     return 6 * ws_round((size_t)d * d * 8) + ws_round((size_t)d * d * 4) + ws_round((size_t)d * (d + 1) / 2 * 4) +
            ws_round((size_t)d * 4) + ws_round((size_t)d * 8) + 4096;
+}
+
+void qr_mixed_carve(QrJob& j, void* ws) {
+    const size_t d = (size_t)j.d;
+    WsCarver wc{(char*)ws, 0};   // the same layout as qr_mixed_launch
+    j.Ct = wc.take<double>(d * d);
+    j.Ct32 = wc.take<float>(d * d);
+    j.Lpk = wc.take<float>(d * (d + 1) / 2);
+    j.Rt = wc.take<double>(d * d);
+    j.X = wc.take<double>(d * d);
+    j.W = wc.take<double>(d * d);
+    j.M = wc.take<double>(d * d);
+    j.Y = wc.take<double>(d * d);
+    j.e = wc.take<int>(d);
+    j.sc = wc.take<double>(d);
+}
+
+int qr_mixed_blocks(int d, int shape) {
+    switch (shape) {
+        case QS_ONE: return 1;
+        case QS_EW: return std::min((d * d + 255) / 256, 64);
+        case QS_TRINV: return (d * 32 + 511) / 512;
+        case QS_TRI: {
+            const int nt = (d + TT - 1) / TT;
+            return nt * (nt + 1) / 2;
+        }
+        default: return 0;
+    }
+}
+
+cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, cudaStream_t st) {
+    const QrJob* jobs = reinterpret_cast<const QrJob*>(table + g.jobs_off);
+    const int* one = reinterpret_cast<const int*>(table + g.off_off[QS_ONE]);
+    const int* ew = reinterpret_cast<const int*>(table + g.off_off[QS_EW]);
+    const int* tinv = reinterpret_cast<const int*>(table + g.off_off[QS_TRINV]);
+    const int* tri = reinterpret_cast<const int*>(table + g.off_off[QS_TRI]);
+    const int n = g.count;
+    LSK_PROF("qr_equil", st) equil_exponents_grouped_kernel<<<g.blocks[QS_ONE], 256, 0, st>>>(jobs, one, n);
+    LSK_PROF("qr_equil", st) equil_scale_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
+    const size_t tiles = chol32_smem(g.dmax);
+    cudaError_t err = cudaFuncSetAttribute(chol32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
+    if (err != cudaSuccess) return err;
+    LSK_PROF("qr_chol32", st) chol32_grouped_kernel<<<g.blocks[QS_ONE], 512, tiles, st>>>(jobs, one, n);
+    const size_t pk = (size_t)g.dmax * (g.dmax + 1) / 2 * 4;
+    err = cudaFuncSetAttribute(trinv32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
+    if (err != cudaSuccess) return err;
+    LSK_PROF("qr_trinv32", st) trinv32_grouped_kernel<<<g.blocks[QS_TRINV], 512, pk, st>>>(jobs, tinv, n);
+    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 0);
+    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 1);
+    LSK_PROF("qr_refine64", st) correction_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
+    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 2);
+    LSK_PROF("qr_finish", st) unscale_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
+    LSK_PROF("qr_finish", st) rank_check_r_grouped_kernel<<<g.blocks[QS_ONE], 256, 0, st>>>(jobs, one, n);
+    return cudaGetLastError();
 }
 
 // C: FP64 Gram of the sketch (d x d, full).  Outputs as qr_launch; R is only
@@ -396,15 +551,14 @@ cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rin
     const int zb = (d * d + 255) / 256 < 1024 ? (d * d + 255) / 256 : 1024;
     LSK_PROF("qr_equil", st) equil_exponents_kernel<<<1, 256, 0, st>>>(C, d, e, sc, flag);
     LSK_PROF("qr_equil", st) equil_scale_kernel<<<zb, 256, 0, st>>>(C, d, sc, Ct, Ct32);
-    const int nt = (d + CB - 1) / CB;
-    const size_t tiles = (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
+    const size_t tiles = chol32_smem(d);
     cudaError_t err = cudaFuncSetAttribute(chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
     if (err != cudaSuccess) return err;
     LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, Rt, Lpk, flag);
     const size_t pk = (size_t)d * (d + 1) / 2 * 4;
     err = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
     if (err != cudaSuccess) return err;
-    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 127) / 128, 128, pk, st>>>(Lpk, d, X);
+    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 511) / 512, 512, pk, st>>>(Lpk, d, X);
     // M = X^T (Ct X): W = Ct X on the upper triangle (only k <= j is needed by M)
     TriGemm g{Ct, X, nullptr, W, d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
     if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
