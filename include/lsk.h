@@ -242,6 +242,13 @@ int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed,
  * lsk_gauss_sketch with the same precision mode. */
 int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed,
                     int32_t prec, float* G);
+/* Failure-detection check (no paper counterpart): one block runs the
+ * bounded mbarrier wait that every tensor-core pipeline of this library uses,
+ * on a barrier nothing arrives on, with a limit of limit_us microseconds
+ * (1 .. 1,000,000).  The wait gives up, sets the context's TIMEOUT flag and
+ * the kernel returns; the next lsk_sync reports LSK_ERR_TIMEOUT and the
+ * context stays usable.  Asynchronous on the context stream. */
+int lsk_debug_wait_timeout(lsk_ctx* ctx, int64_t limit_us);
 
 /* ---- fixed-capacity CountSketch (no device allocation) ------------------ */
 /* The paper has no counterpart to this call: it is an interface for callers

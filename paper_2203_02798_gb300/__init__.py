@@ -92,6 +92,7 @@ _SIGS = {
                                                    ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
     "lsk_debug_hash": (ctypes.c_int, [_P, _I64, _I64, _U64, _P, _P]),
     "lsk_debug_gauss": (ctypes.c_int, [_P, _I64, _I64, _U64, _I32, _P]),
+    "lsk_debug_wait_timeout": (ctypes.c_int, [_P, _I64]),
     "lsk_batch_leverage_scores": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32, _I32]),
     "lsk_batch_streams": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32]),
     "lsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -360,6 +361,13 @@ def debug_hash(n, r, seed, device=None, ctx=None):
     s = torch.empty(n, dtype=torch.int8, device=ctx.device)
     ctx._call("lsk_debug_hash", int(n), int(r), int(seed), _ptr(b), _ptr(s))
     return b, s
+
+
+def debug_wait_timeout(limit_us, device=None, ctx=None):
+    """lsk_debug_wait_timeout: a bounded device wait that must give up; the
+    next ctx.sync() raises LskError TIMEOUT."""
+    ctx = ctx or context(device)
+    ctx._call("lsk_debug_wait_timeout", int(limit_us))
 
 
 def debug_gauss(k, r, seed, prec="fp32", device=None, ctx=None):

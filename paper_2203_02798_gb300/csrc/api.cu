@@ -406,6 +406,14 @@ int lsk_debug_hash(lsk_ctx* ctx, int64_t n, int64_t r, uint64_t seed, int32_t* b
     return finish(ctx, "lsk_debug_hash");
 }
 
+int lsk_debug_wait_timeout(lsk_ctx* ctx, int64_t limit_us) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    if (limit_us < 1 || limit_us > 1000000) return fail(ctx, LSK_ERR_INVALID_ARG, "limit_us must be in [1, 1e6]");
+    cudaError_t e = debug_wait_timeout_launch(limit_us, ctx->flag, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_debug_wait_timeout");
+    return finish(ctx, "lsk_debug_wait_timeout");
+}
+
 int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed, int32_t prec, float* G) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     if (k < 1 || r < 1 || !G) return fail(ctx, LSK_ERR_INVALID_ARG, "bad k / r / G");

@@ -253,6 +253,9 @@ size_t lsq_workspace_bytes(const lsk_mat* A);
 int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
             const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info);
 
+// debug_wait.cu
+cudaError_t debug_wait_timeout_launch(int64_t limit_us, int* flag, cudaStream_t st);
+
 // api.cu (used by the batch driver)
 size_t leverage_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int sm);
 cudaError_t leverage_pipeline(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, float* ell,

@@ -16,6 +16,8 @@
 #include "lsk_internal.cuh"
 
 #include <math.h>
+
+#include <algorithm>
 #include <string.h>
 
 namespace {
@@ -119,13 +121,50 @@ __global__ void __launch_bounds__(kPassThreads) resid64_csr_kernel(
     }
 }
 
+// p = N v (FP32, N upper triangular), one warp per row (coalesced reads of
+// row i of N); the caller has synchronised the block after writing v.
+__device__ __forceinline__ void next_p(const float* __restrict__ N32, int64_t d, const float* v, float* p) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t i = threadIdx.x >> 5; i < d; i += nw) {
+        float s = 0.f;
+        for (int64_t j = i + lane; j < d; j += 32) s = fmaf(N32[i * d + j], v[j], s);
+        s = warp_sum(s);
+        if (lane == 0) p[i] = s;
+    }
+}
+
+// out[j] = sum_z part[z][j] in z order groups: with blockDim >= 4d the
+// partials are split four ways (z mod 4) and the four sums added in order.
+__device__ __forceinline__ void reduce_partials(const float* __restrict__ part, int nblocks, int64_t d,
+                                                float* __restrict__ out) {
+    __shared__ float red4[4][256];
+    if (d <= 256 && blockDim.x >= 4 * d) {
+        const int j = threadIdx.x % d, g = threadIdx.x / d;
+        if (g < 4) {
+            float s = 0.f;
+            for (int z = g; z < nblocks; z += 4) s += part[(int64_t)z * d + j];
+            red4[g][j] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < d) out[threadIdx.x] = (red4[0][threadIdx.x] + red4[1][threadIdx.x]) +
+                                                (red4[2][threadIdx.x] + red4[3][threadIdx.x]);
+    } else {
+        for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+            float s = 0.f;
+            for (int z = 0; z < nblocks; ++z) s += part[(int64_t)z * d + j];
+            out[j] = s;
+        }
+    }
+}
+
 // Reduce the residual pass: A^T r, eta, beta_1; then the LSQR start vectors
 // v_1 = N^T A^T r / (beta_1 alpha_1), w_1 = v_1, y = 0.  One block.
 __global__ void resid_finish_kernel(const double* __restrict__ qpart, const double* __restrict__ sspart,
                                     int nblocks, int64_t d, const double* __restrict__ N64,
                                     int first, LsqrState* st, float* __restrict__ v,
                                     float* __restrict__ w, double* __restrict__ y,
-                                    double* __restrict__ atr) {
+                                    double* __restrict__ atr, const float* __restrict__ N32,
+                                    float* __restrict__ p) {
     __shared__ double red[32];
     for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
         double s = 0.0;
@@ -194,20 +233,90 @@ __global__ void resid_finish_kernel(const double* __restrict__ qpart, const doub
         w[j] = (float)vj;
         y[j] = 0.0;
     }
+    __syncthreads();
+    next_p(N32, d, v, p);
 }
 
-// p = N v (FP32, N upper triangular).  One block.
-__global__ void pv_kernel(const float* __restrict__ N32, int64_t d, const float* __restrict__ v,
-                          const LsqrState* __restrict__ st, float* __restrict__ p) {
+// u <- A p - (alpha/beta) u; partial sums of u^2 and of A^T u.  Dense,
+// d <= 256: a warp takes RB rows at a time (all RB rows' loads in flight
+// before any arithmetic), lane l owns columns l, l + 32, ... (CPL of them),
+// so p and the warp's share of A^T u stay in registers.
+template <int CPL, int RB>
+__global__ void __launch_bounds__(kPassThreads, 2) lsqr_pass_dense_rows_kernel(
+    const float* __restrict__ A, int64_t lda, int64_t n, int64_t d, const float* __restrict__ p,
+    const LsqrState* __restrict__ st, float* __restrict__ u, float* __restrict__ qpart,
+    double* __restrict__ sspart) {
+    __shared__ float qs[kPassThreads / 32][CPL * 32];
+    __shared__ double ssw[kPassThreads / 32];
     if (st->done) return;
-    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
-        float s = 0.f;
-        for (int64_t j = i; j < d; ++j) s = fmaf(N32[i * d + j], v[j], s);
-        p[i] = s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float pr[CPL], q[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        const int j = lane + 32 * c;
+        pr[c] = j < d ? p[j] : 0.f;
+        q[c] = 0.f;
+    }
+    const float ab = (st->beta > 0.0) ? (float)(st->alpha / st->beta) : 0.f;
+    double ss = 0.0;
+    const int64_t nw = (int64_t)gridDim.x * (kPassThreads / 32);
+    for (int64_t i0 = ((int64_t)blockIdx.x * (kPassThreads / 32) + w) * RB; i0 < n; i0 += nw * RB) {
+        float a[RB][CPL];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int64_t row = i0 + r;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int j = lane + 32 * c;
+                a[r][c] = (row < n && j < d) ? __ldg(A + row * lda + j) : 0.f;
+            }
+        }
+        const float uold = (lane < RB && i0 + lane < n) ? u[i0 + lane] : 0.f;
+        float dot[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            float t = 0.f;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) t = fmaf(a[r][c], pr[c], t);
+            dot[r] = t;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], o);
+        float unew = 0.f;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const float ui = (i0 + r < n) ? dot[r] - ab * __shfl_sync(0xffffffffu, uold, r) : 0.f;
+            if (lane == r) unew = ui;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) q[c] = fmaf(a[r][c], ui, q[c]);
+        }
+        if (lane < RB && i0 + lane < n) {
+            u[i0 + lane] = unew;
+            ss = fma((double)unew, (double)unew, ss);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) qs[w][lane + 32 * c] = q[c];
+    ss = warp_sum(ss);
+    if (lane == 0) ssw[w] = ss;
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        float t = 0.f;
+#pragma unroll
+        for (int z = 0; z < kPassThreads / 32; ++z) t += qs[z][j];
+        qpart[(int64_t)blockIdx.x * d + j] = t;
+    }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int z = 0; z < kPassThreads / 32; ++z) t += ssw[z];
+        sspart[blockIdx.x] = t;
     }
 }
 
-// u <- A p - (alpha/beta) u; partial sums of u^2 and of A^T u.  Dense, warp per row.
+// u <- A p - (alpha/beta) u; partial sums of u^2 and of A^T u.  Dense, any d:
+// warp per row.
 __global__ void __launch_bounds__(kPassThreads) lsqr_pass_dense_kernel(
     const float* __restrict__ A, int64_t lda, int64_t n, int64_t d, const float* __restrict__ p,
     const LsqrState* __restrict__ st, float* __restrict__ u, float* __restrict__ qpart,
@@ -302,7 +411,8 @@ __global__ void __launch_bounds__(kPassThreads) lsqr_pass_csr_kernel(
 __global__ void lsqr_step_kernel(const float* __restrict__ qpart, const double* __restrict__ sspart,
                                  int nblocks, int64_t d, const float* __restrict__ N32,
                                  LsqrState* st, float* __restrict__ v, float* __restrict__ w,
-                                 double* __restrict__ y, float* __restrict__ qtmp, double inner_tol) {
+                                 double* __restrict__ y, float* __restrict__ qtmp, double inner_tol,
+                                 float* __restrict__ p) {
     __shared__ double red[32];
     __shared__ double sc[8];
     if (st->done) return;
@@ -311,11 +421,7 @@ __global__ void lsqr_step_kernel(const float* __restrict__ qpart, const double* 
     for (int z = threadIdx.x; z < nblocks; z += blockDim.x) s2 += sspart[z];
     s2 = warp_sum(s2);
     if (lane == 0) red[wid] = s2;
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < nblocks; ++z) s += qpart[(int64_t)z * d + j];
-        qtmp[j] = s;
-    }
+    reduce_partials(qpart, nblocks, d, qtmp);
     __syncthreads();
     if (threadIdx.x == 0) {
         double S2 = 0.0;
@@ -370,6 +476,8 @@ __global__ void lsqr_step_kernel(const float* __restrict__ qpart, const double* 
         v[j] = (float)vj;
         w[j] = (float)(vj - ws * wj);
     }
+    __syncthreads();
+    if (!st->done) next_p(N32, d, v, p);
 }
 
 // x <- x + N y (FP64).  One block.
@@ -385,13 +493,56 @@ __global__ void update_x_kernel(const double* __restrict__ N64, int64_t d, const
     }
 }
 
-int pass_blocks(int sm_count) { return 2 * sm_count; }
+constexpr int kMaxPassBlocks = 2432;   // >= 8 x the SM count of any sm_103 part
+
+// Blocks of a pass over A: enough to keep every SM streaming, few enough
+// that each block covers several row groups (fewer partials to reduce).
+int pass_grid(const lsk_mat* A, int sm_count) {
+    const int64_t n = A->n;
+    const bool rows_kernel = A->kind == LSK_DENSE && A->d <= 256;
+    const int64_t per_block = rows_kernel ? (kPassThreads / 32) * (A->d <= 64 ? 16 : 8) * 2 : kPassThreads * 2;
+    int64_t g = (n + per_block - 1) / per_block;
+    const int64_t cap = std::min<int64_t>(rows_kernel ? 4 * sm_count : 8 * sm_count, kMaxPassBlocks);
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <int CPL, int RB>
+void launch_rows_pass(const lsk_mat* A, int nb, const float* p, const LsqrState* S, float* u, float* qpart,
+                      double* sspart, cudaStream_t st) {
+    LSK_PROF("lsq_pass", st) lsqr_pass_dense_rows_kernel<CPL, RB><<<nb, kPassThreads, 0, st>>>(
+        (const float*)A->values, A->ld, A->n, A->d, p, S, u, qpart, sspart);
+}
+
+void lsqr_pass(const lsk_mat* A, int nb, size_t sh32, const float* p, const LsqrState* S, float* u,
+               float* qpart, double* sspart, cudaStream_t st) {
+    const int64_t n = A->n, d = A->d;
+    if (A->kind == LSK_DENSE && d <= 256) {
+        switch ((d + 31) / 32) {
+            case 1: launch_rows_pass<1, 16>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 2: launch_rows_pass<2, 16>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 3: launch_rows_pass<3, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 4: launch_rows_pass<4, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 5: launch_rows_pass<5, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 6: launch_rows_pass<6, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+            case 7: launch_rows_pass<7, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+            default: launch_rows_pass<8, 8>(A, nb, p, S, u, qpart, sspart, st); break;
+        }
+    } else if (A->kind == LSK_DENSE) {
+        LSK_PROF("lsq_pass", st) lsqr_pass_dense_kernel<<<nb, kPassThreads, sh32, st>>>(
+            (const float*)A->values, A->ld, n, d, p, S, u, qpart, sspart);
+    } else {
+        LSK_PROF("lsq_pass", st) lsqr_pass_csr_kernel<<<nb, kPassThreads, sh32, st>>>(
+            (const float*)A->values, A->colidx, A->rowptr, n, A->nnz, d, p, S, u, qpart, sspart);
+    }
+}
 
 }  // namespace
 
 size_t lsq_workspace_bytes(const lsk_mat* A) {
     const int64_t n = A->n, d = A->d;
-    const int nb = pass_blocks(152 * 2);
+    const int nb = kMaxPassBlocks;
     return ws_round(sizeof(LsqrState)) + ws_round((size_t)n * 4) + 4 * ws_round((size_t)d * 8) +
            ws_round((size_t)nb * d * 8) + ws_round((size_t)nb * 8) + 3 * ws_round((size_t)d * 4) +
            ws_round((size_t)2 * d * 4) + 4096;
@@ -401,7 +552,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
             const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info) {
     cudaStream_t st = ctx->stream;
     const int64_t n = A->n, d = A->d;
-    const int nb = pass_blocks(ctx->sm_count);
+    const int nb = pass_grid(A, ctx->sm_count);
     WsCarver wc{(char*)ws, 0};
     LsqrState* S = wc.take<LsqrState>(1);
     float* u = wc.take<float>(n > 0 ? n : 1);
@@ -439,7 +590,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
             LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
                                                                A->nnz, d, b, x, u, qpart64, sspart, ctx->flag);
         resid_finish_kernel<<<1, 256, 0, st>>>(qpart64, sspart, nb, d, Rinv64, t == 0 ? 1 : 0, S, v, w, y,
-                                               atr);
+                                               atr, Rinv32, p);
         e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return LSK_ERR_CUDA;
@@ -452,16 +603,9 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         if (t == o->max_refine) break;
         int it = 0;
         while (!h.done && it < o->max_iter) {
-            pv_kernel<<<1, 256, 0, st>>>(Rinv32, d, v, S, p);
-            if (dense)
-                LSK_PROF("lsq_pass", st) lsqr_pass_dense_kernel<<<nb, kPassThreads, sh32, st>>>((const float*)A->values, A->ld, n, d, p,
-                                                                       S, u, qpart32, sspart);
-            else
-                LSK_PROF("lsq_pass", st) lsqr_pass_csr_kernel<<<nb, kPassThreads, sh32, st>>>((const float*)A->values, A->colidx,
-                                                                     A->rowptr, n, A->nnz, d, p, S, u,
-                                                                     qpart32, sspart);
-            lsqr_step_kernel<<<1, 256, 0, st>>>(qpart32, sspart, nb, d, Rinv32, S, v, w, y, qtmp,
-                                                o->inner_tol);
+            lsqr_pass(A, nb, sh32, p, S, u, qpart32, sspart, st);
+            lsqr_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv32, S, v, w, y, qtmp,
+                                                 o->inner_tol, p);
             ++it;
             if ((it & 3) == 0 || it >= o->max_iter) {   // stopping test every 4 iterations
                 e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);

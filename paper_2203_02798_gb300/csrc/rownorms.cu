@@ -7,8 +7,8 @@
 //   upper triangular (B = R^-1) the k-loop of column tile [c0, c0+64) stops
 //   at c0+64, skipping the zero blocks.  This is the CUDA-core (SIMT) path
 //   (LSK_PREC_FP32); the tensor-core path lives in rownorms_tc.cu.
-// CSR (csrsqn, Alg. 8): Btilde = B B^T is formed once (FP64 accumulation,
-//   FP32 result); then one thread per row evaluates
+// CSR (csrsqn, Alg. 8): Btilde = B B^T is formed once (FP32, 16 x 16 output
+//   tiles); then one thread per row evaluates
 //   sum_{p,q in row} v_p v_q Btilde[J_p, J_q] using the symmetry of Btilde.
 #include "lsk_internal.cuh"
 

@@ -328,3 +328,23 @@ def test_sketch_precondition_lsq(lsk, kind):
     assert eta <= 1e-10, (eta, info)
     assert info["status"] == 0 and info["eta"] <= 1e-10
     assert np.linalg.norm(x - xs) <= 1e-3 * np.linalg.norm(xs)
+
+
+# ------------------------------------------------------- failure detection -
+def test_bounded_wait_gives_up_and_context_stays_usable(lsk):
+    """A device wait on a barrier that nothing arrives on ends after its limit
+    with the TIMEOUT status (no trap, no hang); the same context then runs a
+    leverage-score call normally."""
+    import time
+    ctx = lsk.context()
+    t0 = time.perf_counter()
+    lsk.debug_wait_timeout(20_000, ctx=ctx)          # 20 ms
+    with pytest.raises(lsk.LskError) as ei:
+        ctx.sync()
+    assert ei.value.name == "TIMEOUT"
+    assert time.perf_counter() - t0 < 5.0
+    A = workloads.dense_normal(4000, 16, seed=5)
+    ell = lsk.leverage_scores(dev(A), 256, 32, 1, "bf16")
+    ctx.sync()
+    ref, _ = olev.leverage_scores_dense(A.astype(np.float64), 256, 32, 1, oga.PREC_BF16)
+    assert np.max(np.abs(host(ell) - ref) / ref) <= 1e-3
