@@ -7,17 +7,17 @@
 //     A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi     (FP32 accumulation),
 // the dropped A_lo B_lo term being ~2^-18 relative.
 //
-// Persistent kernel, one CTA per SM (672 threads):
+// Persistent kernel, one CTA per SM (640 threads, 96 registers each):
 //   warps 0-3   epilogue: tcgen05.ld the accumulator rows, square, sum, store
 //   warp  4     TMEM allocation; lane 0 issues every MMA and commit
-//   warps 5-20  converters: each owns every 16th half-chunk (64 rows x 32 K)
+//   warps 5-19  converters: each owns every 15th half-chunk (64 rows x 32 K)
 //               of the operand stream: it loads its piece from HBM (fully
 //               coalesced 16-byte loads), splits it into bf16 hi/lo and
 //               writes the 64-byte-swizzled K-major tile into the stage
 //               ring.  A warp arrives on the stage barrier only after its own
 //               loads have landed (the arrive has release semantics and would
-//               otherwise wait for loads still in flight), while the other 15
-//               warps keep 8 chunks (128 KB) of loads in flight per SM.  The
+//               otherwise wait for loads still in flight), while the other 14
+//               warps keep 7.5 chunks (120 KB) of loads in flight per SM.  The
 //               uses of each stage are handed out in order (a per-stage count
 //               of stored halves), so no warp waits on a stage barrier more
 //               than one phase ahead of it.
@@ -33,7 +33,7 @@ namespace {
 constexpr int kRows = 128;
 constexpr int kKC = 32;                              // K per chunk (one 64-byte swizzle row)
 constexpr int kMaxQ = 8;                             // d <= 256
-constexpr int kConvWarps = 16;
+constexpr int kConvWarps = 15;      // odd: 20 warps in all, which leaves 96 registers a thread
 constexpr int kPieceRows = 64;                       // rows of one converter piece (half a chunk)
 constexpr int kPieces = kRows / kPieceRows;          // pieces per chunk (2)
 constexpr int kF4 = kPieceRows * kKC / 4 / 32;       // float4 loads per lane per piece (16)
@@ -90,6 +90,21 @@ __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnPara
 // 16-byte pieces, four 128-byte row segments per warp instruction.
 template <bool VEC>
 __device__ __forceinline__ void load_piece(const RnParams& p, int tile, int q, int half, int lane, float4 (&v)[kF4]) {
+    const int64_t row0 = (int64_t)tile * kRows + half * kPieceRows + (lane >> 3);
+    const int k0 = kKC * q + 4 * (lane & 7);
+    if (VEC && row0 - (lane >> 3) + kPieceRows <= p.n && kKC * q + kKC <= p.d) {
+        // interior piece: no bounds checks, rows 4 apart per step
+        const float* src = p.A + row0 * p.lda + k0;
+        const int64_t step = 4 * p.lda;
+#pragma unroll
+        for (int i = 0; i < kF4; ++i) {
+            asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                         : "=f"(v[i].x), "=f"(v[i].y), "=f"(v[i].z), "=f"(v[i].w)
+                         : "l"(src));
+            src += step;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kF4; ++i) {
         const int f = lane + 32 * i;
@@ -214,17 +229,23 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
+            // One thread issues everything, so its per-chunk instruction chain
+            // is on the critical path: stage and phase advance incrementally
+            // (no division), and the K-chunk loop is unrolled so the per-chunk
+            // constants of p are read with static indices (no local copy).
             const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
             bool ok = true;
-            int g = 0;
+            int s = 0;
+            uint32_t ph = 0;
             for (int i = 0; i < my_tiles && ok; ++i) {
                 const int acc = i & 1;
                 if (!tc::mbar_wait(tempty + acc, ((uint32_t)(i >> 1) & 1u) ^ 1u, abort)) break;
                 tc::fence_after_sync();
                 const uint32_t d_base = tmem + (uint32_t)acc * kAccCols;
-                for (int q = 0; q < p.nq; ++q, ++g) {
-                    const int s = g % S;
-                    if (!tc::mbar_wait(full + s, (uint32_t)(g / S) & 1u, abort)) {
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) {
+                    if (q >= p.nq) break;
+                    if (!tc::mbar_wait(full + s, ph, abort)) {
                         ok = false;
                         break;
                     }
@@ -242,6 +263,10 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
                         tc::mma_bf16(d_tmem, tc::desc_sw64_kmajor(a_lo + ko), tc::desc_sw64_kmajor(b_hi + ko), idesc, 1);
                     }
                     tc::mma_commit(empty + s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (ok) tc::mma_commit(tfull + acc);
             }
@@ -254,14 +279,15 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
     } else {
         // ------------------------------------------------------------ converters
         // piece number pc = kPieces * g + half goes to converter warp pc % kConvWarps
+        // (kConvWarps is odd, so a warp's pieces alternate between the halves)
         const int cw = warp - kConvWarp0;
-        const int half = cw % kPieces;
         const int G = my_tiles * p.nq;
-        const int gstep = kConvWarps / kPieces;
         float4 buf[kF4];
-        for (int g = cw / kPieces; g < G; g += gstep) {
-            load_piece<VEC>(p, (int)blockIdx.x + (g / p.nq) * (int)gridDim.x, g % p.nq, half, lane, buf);
-            const int s = g % S, u = g / S;
+        // piece pc: chunk g = pc / 2 = (tile t, K-chunk q), stage s, use u -- advanced without division
+        int pc = cw, g = pc / kPieces, t = g / p.nq, q = g % p.nq, s = g % S, u = g / S;
+        for (; g < G;) {
+            const int half = pc % kPieces;
+            load_piece<VEC>(p, (int)blockIdx.x + t * (int)gridDim.x, q, half, lane, buf);
             int ok = 1;
             if (lane == 0) {
                 // both halves of this stage's previous use are stored: the stage
@@ -277,6 +303,11 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
                 tc::mbar_arrive(full + s);
                 atomicAdd(stored + s, 1);
             }
+            pc += kConvWarps;
+            const int dg = pc / kPieces - g;
+            g += dg;
+            for (q += dg; q >= p.nq; q -= p.nq) ++t;
+            for (s += dg; s >= S; s -= S) ++u;
         }
     }
 
