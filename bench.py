@@ -103,6 +103,25 @@ def oracle_sample(n_sample):
     return A.nbytes, dt
 
 
+def max_over_ranks(x):
+    """The largest x over all ranks (x itself when torch.distributed is not
+    initialised): the job takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(bytes_per_rank, world, ms):
+    """GB/s of the whole job: every rank processes bytes_per_rank (replicas,
+    weak scaling), in the time of the slowest rank (ms)."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -206,11 +225,7 @@ def main():
         torch.cuda.synchronize()
         t1 = time.time()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(e0.elapsed_time(e1))
         return ms, t0, t1
 
     for _ in range(max(3, args.warmup)):
@@ -230,7 +245,7 @@ def main():
     kern = ctx.profile_totals()
     ms_step = ms / args.steps
     a_bytes = N_ROWS * D * 4
-    value = world * a_bytes / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(a_bytes, world, ms_step)
 
     # roofline of the dominant kernel
     top = max(kern.items(), key=lambda kv: kv[1][1]) if kern else ("none", (1, 0.0))
@@ -266,7 +281,7 @@ def main():
     e2e_step()
     ems, _, _ = timed(e2e_step, e2e_steps)
     ems /= e2e_steps
-    e2e = {"value": world * a_bytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+    e2e = {"value": whole_job_rate(a_bytes, world, ems), "unit": "GB/s", "ms_per_step": ems,
            "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": N_ROWS * 4}
 
     # the plain FP32 single-problem path on the same GPU
@@ -276,7 +291,7 @@ def main():
             step("fp32")
         pms, _, _ = timed(lambda: step("fp32"), max(3, args.steps // 5))
         pms /= max(3, args.steps // 5)
-        plain = {"value": world * a_bytes / (pms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": pms}
+        plain = {"value": whole_job_rate(a_bytes, world, pms), "unit": "GB/s", "ms_per_step": pms}
 
     batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve else run_served(args, lsk, torch)
