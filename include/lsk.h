@@ -128,6 +128,15 @@ int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
  * partial sums are folded into FP64 before the final FP32 store. */
 int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
              float* C);
+/* lsk_gram with a precision: LSK_PREC_FP32 / LSK_PREC_TF32 as lsk_gram;
+ * LSK_PREC_BF16 forms the products of dense A with d <= 256 on the tensor
+ * cores from a bfloat16 split of A (a = hi + lo; hi^T hi + hi^T lo + lo^T hi,
+ * about 2^-16 relative per product), accumulating at most 1024 rows in FP32
+ * before the slices are added (compensated FP32, alpha and beta in FP64).
+ * CSR A or d > 256 take the lsk_gram path.  Workspace: ceil(n / 1024) d*d
+ * floats for the BF16 path. */
+int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
+                  int32_t prec, float* C);
 
 /* Squared row norms x <- alpha * diag(A B B^T A^T) + beta * x (csrsqn /
  * rmsqn, Sec. 5; Alg. 8 for CSR A).  B: device d*c floats row-major.

@@ -84,6 +84,7 @@ _SIGS = {
     "lsk_cs_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _P]),
     "lsk_gauss_sketch": (ctypes.c_int, [_P, _P, _I64, _I64, _I64, _U64, _I32, _P]),
     "lsk_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _P]),
+    "lsk_gram_prec": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _I32, _P]),
     "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _I32, _P]),
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
@@ -247,14 +248,18 @@ def gauss_sketch(SA, k, seed, prec="fp32", out=None, ctx=None):
     return GSA
 
 
-def gram(A, alpha=1.0, beta=0.0, C=None, ctx=None):
-    """lsk_gram: alpha A^T A + beta C (d x d float32, C updated in place if given)."""
+def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):
+    """lsk_gram / lsk_gram_prec: alpha A^T A + beta C (d x d float32, C updated
+    in place if given); prec="bf16": tensor-core products of a bf16 split."""
     m, n, d = _mat(A)
     ctx = ctx or context(_dev(A).index)
     if C is None:
         C = torch.empty((d, d), dtype=torch.float32, device=_dev(A))
         beta = 0.0
-    ctx._call("lsk_gram", ctypes.byref(m), float(alpha), float(beta), _ptr(C))
+    if prec == "fp32":
+        ctx._call("lsk_gram", ctypes.byref(m), float(alpha), float(beta), _ptr(C))
+    else:
+        ctx._call("lsk_gram_prec", ctypes.byref(m), float(alpha), float(beta), _prec(prec), _ptr(C))
     return C
 
 

@@ -192,6 +192,23 @@ int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C
     return finish(ctx, "lsk_gram");
 }
 
+int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, int32_t prec, float* C) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (prec != LSK_PREC_BF16) return lsk_gram(ctx, A, alpha, beta, C);
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (!C) return fail(ctx, LSK_ERR_INVALID_ARG, "C is NULL");
+    if (!gram_tc_supported(A)) return lsk_gram(ctx, A, alpha, beta, C);   // CSR or d > 256: the FP32 path
+    rc = ws_ensure(ctx, gram_tc_workspace_bytes(A, ctx->sm_count));
+    if (rc) return rc;
+    cudaError_t e = gram_tc_launch(A, alpha, beta, C, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_gram_prec");
+    return finish(ctx, "lsk_gram_prec");
+}
+
 int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B, int64_t c, double alpha,
                       double beta, int32_t upper_triangular, int32_t prec, float* x) {
     if (!ctx) return LSK_ERR_INVALID_ARG;

@@ -203,6 +203,12 @@ size_t gram_workspace_bytes(const lsk_mat* A, int sm_count);
 cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws,
                         int* flag, int sm_count, cudaStream_t st);
 
+// gram_tc.cu (dense, d <= 256, BF16x3 on tcgen05)
+bool gram_tc_supported(const lsk_mat* A);
+size_t gram_tc_workspace_bytes(const lsk_mat* A, int sm_count);
+cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag,
+                           int sm_count, cudaStream_t st);
+
 // rownorms.cu
 size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec);
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha,

@@ -187,6 +187,38 @@ def test_gram_dense_integer_exact_and_alpha_beta(lsk):
     assert rel_fro(host(Ct).astype(np.float64), ref) <= 1e-6
 
 
+@pytest.mark.parametrize("n,d", [(100_003, 256), (5_000, 50), (2_049, 130), (1, 7), (4_096, 128)])
+def test_gram_dense_bf16_tensor_cores(lsk, n, d):
+    """BF16x3 Gram on tcgen05: two M tiles (d > 128), ragged d and slices,
+    one row.  Bound per entry: the split leaves at most 2^-16 |a_i a_j| per
+    product, and at most 3 * 1024 products are added in FP32 per slice."""
+    A = workloads.dense_normal(n, d, seed=d + 7) * (10.0 ** np.linspace(-1, 1, d)).astype(np.float32)
+    C = host(lsk.gram(dev(A), prec="bf16")).astype(np.float64)
+    lsk.context().sync()
+    A64 = A.astype(np.float64)
+    ref = ogr.gram_dense(A64)
+    absg = np.abs(A64).T @ np.abs(A64)
+    assert np.all(np.abs(C - ref) <= (2.0**-16 + 3 * 1024 * U32) * absg + 1e-30)
+    assert rel_fro(C, ref) <= 1e-5
+    assert np.array_equal(C, C.T)
+
+
+def test_gram_bf16_alpha_beta_and_empty(lsk):
+    A = workloads.dense_normal(3000, 96, seed=4)
+    C0 = workloads.dense_normal(96, 96, seed=5)
+    Ct = dev(C0.copy())
+    lsk.gram(dev(A), alpha=0.25, beta=3.0, C=Ct, prec="bf16")
+    lsk.context().sync()
+    ref = ogr.gram_dense(A.astype(np.float64), 0.25, 3.0, C0.astype(np.float64))
+    assert rel_fro(host(Ct).astype(np.float64), ref) <= 1e-5
+    import torch
+    E = torch.zeros((0, 16), dtype=torch.float32, device="cuda")
+    Ce = dev(C0[:16, :16].copy())
+    lsk.gram(E, alpha=1.0, beta=2.0, C=Ce, prec="bf16")       # no rows: C <- beta C
+    lsk.context().sync()
+    assert np.allclose(host(Ce), 2.0 * C0[:16, :16], rtol=1e-6, atol=0)
+
+
 @pytest.mark.parametrize("n,d,p", [(200_000, 200, 0.01), (30_000, 256, 0.05), (4000, 20, 0.5)])
 def test_gram_csr(lsk, n, d, p):
     V, J, I = workloads.csr_bernoulli(n, d, p, seed=d)
