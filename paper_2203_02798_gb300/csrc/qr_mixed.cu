@@ -95,7 +95,7 @@ struct DiagStep {
             if (lane == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
             piv = 1.f;
         }
-        const float l = sqrtf(piv), il = 1.f / l;
+        const float il = rsqrtf(piv), l = piv * il;   // FP32 factor: the FP64 correction absorbs its rounding
         if (lane == J) a[J] = l;
         if (lane > J) a[J] *= il;
         DiagUpdate<J, J + 1>::run(a, a[J], lane);
@@ -114,15 +114,21 @@ __device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int 
     __shared__ float rdiag[CB];
     const int nt = (d + CB - 1) / CB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    {   // all tiles at once, many independent loads in flight per thread
+    {   // all tiles at once: flat index over (tile, element), tile -> (I, J) from a
+        // small table, eight independent loads in flight per thread
+        __shared__ unsigned char tI[36], tJ[36];   // nt <= 8
         const int ntl = nt * (nt + 1) / 2;
-#pragma unroll 4
+        if (threadIdx.x < ntl) {
+            int I = 0, t = threadIdx.x;
+            while (t > I) t -= ++I;
+            tI[threadIdx.x] = (unsigned char)I;
+            tJ[threadIdx.x] = (unsigned char)t;
+        }
+        __syncthreads();
+#pragma unroll 8
         for (int t = threadIdx.x; t < ntl * CB * CB; t += blockDim.x) {
-            const int tl = t / (CB * CB), e = t % (CB * CB);
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-            const int J = tl - I * (I + 1) / 2;
-            const int r = e / CB, c = e % CB, i = I * CB + r, j = J * CB + c;
+            const int tl = t >> 10, e = t & 1023;
+            const int r = e >> 5, c = e & 31, i = tI[tl] * CB + r, j = tJ[tl] * CB + c;
             S[tl * (CB * CP) + r * CP + c] = (i < d && j < d) ? __ldg(Ct32 + i * d + j) : (i == j ? 1.f : 0.f);
         }
     }
@@ -198,18 +204,16 @@ __device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int 
         __syncthreads();
     }
 #pragma unroll 4
-    for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
-        const int i = t / d, j = t % d;   // Rt[i][j] = L[j][i] for j >= i
-        double v = 0.0;
-        if (j >= i) v = (double)ctile(S, j / CB, i / CB)[(j % CB) * CP + (i % CB)];
-        Rt[t] = v;
+    // Rt[i][j] = L[j][i] for j >= i (only when the caller forms R), then the
+    // packed rows of L (row l at l(l+1)/2): warp per row, lanes along it
+    if (Rt) {
+        for (int i = w; i < d; i += nw)
+            for (int j = lane; j < d; j += 32)
+                Rt[(int64_t)i * d + j] = (j >= i) ? (double)ctile(S, j >> 5, i >> 5)[(j & 31) * CP + (i & 31)] : 0.0;
     }
-    for (int t = threadIdx.x; t < d * (d + 1) / 2; t += blockDim.x) {
-        int l = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);   // row of packed index t
-        while (l * (l + 1) / 2 > t) --l;
-        while ((l + 1) * (l + 2) / 2 <= t) ++l;
-        const int i = t - l * (l + 1) / 2;
-        Lpk[t] = ctile(S, l / CB, i / CB)[(l % CB) * CP + (i % CB)];
+    for (int l = w; l < d; l += nw) {
+        float* dst = Lpk + l * (l + 1) / 2;
+        for (int i = lane; i <= l; i += 32) dst[i] = ctile(S, l >> 5, i >> 5)[(l & 31) * CP + (i & 31)];
     }
 }
 __global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(512) chol32_grouped_kernel(const QrJob* __rest
                                                              int count) {
     int blk, nblk;
     const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    chol32_body(j.Ct32, j.d, j.Rt, j.Lpk, j.flag, blk, nblk);
+    chol32_body(j.Ct32, j.d, nullptr, j.Lpk, j.flag, blk, nblk);   // R is not formed in a group
 }
 __global__ void __launch_bounds__(512) trinv32_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
                                                               int count) {
@@ -554,7 +558,7 @@ cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rin
     const size_t tiles = chol32_smem(d);
     cudaError_t err = cudaFuncSetAttribute(chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
     if (err != cudaSuccess) return err;
-    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, Rt, Lpk, flag);
+    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, R ? Rt : nullptr, Lpk, flag);
     const size_t pk = (size_t)d * (d + 1) / 2 * 4;
     err = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
     if (err != cudaSuccess) return err;
