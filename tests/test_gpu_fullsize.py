@@ -1,0 +1,159 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration bench.py times.  The oracle forms the whole FP64 sketch and R
+(Householder QR of the sketch) and then computes exact scores for a sample of
+rows, one by one; properties that hold at any size are checked on all rows.
+
+  config 2: CSR 1,000,000 x 200, p = 0.01, r = 40,000, k = 400, FP32
+  config 3: dense 4,000,000 x 256 (column scales 10^U(-3,3)), r = 65,536,
+            k = 512, BF16 stages -- the bench's step
+  config 4: the 512-problem batch (graph-captured, grouped stages), three
+            problems checked against the oracle, every problem's scores in
+            [0, 1.5] with sum within the sketch's distortion band
+  config 5: one large served least-squares problem against the Householder
+            least-squares solution
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import countsketch as ocs
+from oracle import gaussian as oga
+from oracle import leverage as olev
+from oracle import lsq as olsq
+from oracle import qr as oqr
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def lsk():
+    from paper_2203_02798_gb300 import build
+    build.build()
+    import paper_2203_02798_gb300 as p
+    return p
+
+
+def sampled_scores(rows_dense, R):
+    """ell_i = ||a_i R^-1||^2 for the given dense rows (FP64 definition)."""
+    Rinv = oqr.upper_triangular_inverse(R)
+    Y = np.asarray(rows_dense, dtype=np.float64) @ Rinv
+    return np.sum(Y * Y, axis=1)
+
+
+def sample_rows(n, step, rng_seed=0):
+    rng = np.random.default_rng(rng_seed)
+    return np.unique(np.concatenate([np.arange(0, n, step), rng.integers(0, n, 2000), [n - 1]]))
+
+
+def test_config3_dense_4M_x_256_bf16(lsk):
+    n, d, r, k, seed = 4_000_000, 256, 65_536, 512, 2
+    A = np.empty((n, d), dtype=np.float32)
+    workloads.dense_colscaled(n=n, d=d, seed=2, out=A)
+    Ad = torch.from_numpy(A).cuda()
+    ell, R = lsk.leverage_scores(Ad, r, k, seed, "bf16", return_R=True)
+    lsk.context().sync()
+    ell = ell.cpu().numpy().astype(np.float64)
+    Rg = R.cpu().numpy()
+    del Ad
+    torch.cuda.empty_cache()
+    SA = ocs.cs_sketch_dense(A, r, seed)                       # FP64, all 4M rows
+    Ro = olev.sketch_R(oga.gauss_sketch(SA, k, seed, oga.PREC_BF16))
+    rows = sample_rows(n, 997)
+    ref = sampled_scores(A[rows], Ro)
+    assert np.max(np.abs(ell[rows] - ref) / ref) <= 1e-3
+    colnorm = np.linalg.norm(Ro, axis=0)
+    assert np.all(np.abs(Rg - Ro) <= 1e-4 * colnorm[None, :])
+    assert np.all(ell >= 0) and np.all(np.isfinite(ell))
+    # sum of the estimates = ||A R^-1||_F^2 = sum of sigma_j^2 of A R^-1: d up to the
+    # sketch's distortion (k = 2d Gaussian after CountSketch)
+    assert 0.2 * d <= ell.sum() <= 5.0 * d
+
+
+def test_config2_csr_1M_x_200_fp32(lsk):
+    n, d, r, k, seed = 1_000_000, 200, 40_000, 400, 1
+    V, J, I = workloads.csr_bernoulli(n, d, 0.01, seed=1)
+    ell = lsk.leverage_scores(lsk.csr_from_numpy(V, J, I, d), r, k, seed, "fp32")
+    lsk.context().sync()
+    ell = ell.cpu().numpy().astype(np.float64)
+    SA = ocs.cs_sketch_csr(V, J, I, n, d, r, seed)
+    Ro = olev.sketch_R(oga.gauss_sketch(SA, k, seed, oga.PREC_FP32))
+    rows = sample_rows(n, 499, 1)
+    dense = np.zeros((rows.size, d))
+    for t, i in enumerate(rows):
+        dense[t, J[I[i]:I[i + 1]]] = V[I[i]:I[i + 1]]
+    ref = sampled_scores(dense, Ro)
+    nz = ref > 0
+    assert np.all(ell[rows][~nz] == 0)                         # empty rows score zero
+    assert np.max(np.abs(ell[rows][nz] - ref[nz]) / ref[nz]) <= 1e-3
+    empty = np.diff(I) == 0
+    assert np.all(ell[empty] == 0)
+    assert 0.2 * d <= ell.sum() <= 5.0 * d
+
+
+def test_config4_batch_512_problems(lsk):
+    specs = workloads.batch_specs(512, seed=3)
+    probs = []
+    for sp in specs:
+        if sp["kind"] == "dense":
+            A = workloads.batch_problem_torch(sp)
+        else:
+            V, J, I = workloads.batch_problem_torch(sp)
+            A = lsk.CSR(V, J, I, sp["n"], sp["d"])
+        probs.append((A, sp["r"], sp["k"], sp["sketch_seed"]))
+    outs = lsk.batch_leverage_scores(probs, prec="bf16", graph=True, autotune=True)
+    lsk.context().sync()
+    for (A, r, k, s), ell, sp in zip(probs, outs, specs):
+        e = ell.cpu().numpy()
+        assert np.all(np.isfinite(e)) and np.all(e >= 0) and np.all(e <= 1.5), sp
+        assert 0.2 * sp["d"] <= e.sum() <= 5.0 * sp["d"], sp
+    # against the oracle: the largest dense d = 256 problem, the largest CSR
+    # d = 256 problem and the smallest CSR d = 32 problem
+    dense256 = max((i for i, sp in enumerate(specs) if sp["kind"] == "dense" and sp["d"] == 256),
+                   key=lambda i: specs[i]["n"])
+    csr256 = max((i for i, sp in enumerate(specs) if sp["kind"] == "csr" and sp["d"] == 256),
+                 key=lambda i: specs[i]["n"])
+    csr32 = min((i for i, sp in enumerate(specs) if sp["kind"] == "csr" and sp["d"] == 32),
+                key=lambda i: specs[i]["n"])
+    for i in (dense256, csr256, csr32):
+        sp = specs[i]
+        A, r, k, s = probs[i]
+        ell = outs[i].cpu().numpy().astype(np.float64)
+        n, d = sp["n"], sp["d"]
+        if sp["kind"] == "dense":
+            Ah = A.cpu().numpy()
+            SA = ocs.cs_sketch_dense(Ah, r, s)
+        else:
+            V, J, I = (A.V.cpu().numpy(), A.J.cpu().numpy(), A.I.cpu().numpy())
+            SA = ocs.cs_sketch_csr(V, J, I, n, d, r, s)
+        Ro = olev.sketch_R(oga.gauss_sketch(SA, k, s, oga.PREC_BF16))
+        rows = sample_rows(n, max(1, n // 3000), i)
+        if sp["kind"] == "dense":
+            dense = Ah[rows]
+        else:
+            dense = np.zeros((rows.size, d))
+            for t, j in enumerate(rows):
+                dense[t, J[I[j]:I[j + 1]]] = V[I[j]:I[j + 1]]
+        ref = sampled_scores(dense, Ro)
+        nz = ref > 0
+        assert np.all(ell[rows][~nz] == 0)
+        assert np.max(np.abs(ell[rows][nz] - ref[nz]) / ref[nz]) <= 1e-3, sp
+
+
+def test_config5_large_served_least_squares(lsk):
+    specs = workloads.batch_specs(512, seed=3)
+    i = max((i for i, sp in enumerate(specs) if sp["kind"] == "dense" and sp["d"] == 256),
+            key=lambda i: specs[i]["n"])
+    sp = specs[i]
+    A = workloads.batch_problem_torch(sp)
+    xs, b = workloads.lsq_rhs_torch(lambda x: (A.double() @ x), sp["n"], sp["d"], seed=10_000 + i)
+    x, info = lsk.sketch_precondition_lsq(A, b, r=sp["r"], k=sp["k"], seed=sp["sketch_seed"])
+    lsk.context().sync()
+    assert info["status"] == 0 and info["eta"] <= 1e-10
+    Ah = A.cpu().numpy().astype(np.float64)
+    bh = b.cpu().numpy()
+    xh = x.cpu().numpy()
+    eta = olsq.normal_equation_residual(lambda v: Ah @ v, lambda v: Ah.T @ v, bh, xh)
+    assert eta <= 1e-10                                        # recomputed on the host in FP64
+    x_ls = olsq.least_squares_qr(Ah, bh)
+    assert np.linalg.norm(xh - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
