@@ -178,6 +178,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--no-gram", action="store_true", help="skip the A^T A leg")
+    ap.add_argument("--gram-only", action="store_true",
+                    help="time only lsk_gram_prec (BF16x3 and FP32) on the workload's A (for profiling)")
     args = ap.parse_args()
     N_ROWS = args.rows
     if args.impl == "reference":
@@ -209,6 +212,22 @@ def main():
     def step(prec):
         lsk.leverage_scores(A, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
 
+    def gram_leg(steps):
+        """A^T A of the workload's A (csrrk), BF16x3 on tensor cores and FP32 SIMT,
+        with the relative Frobenius error of each against an FP64 product."""
+        C = torch.empty((D, D), dtype=torch.float32, device="cuda")
+        ref = A.double().T @ A.double()
+        out = {}
+        for prec in ("bf16", "fp32"):
+            lsk.gram(A, C=C, prec=prec, ctx=ctx)
+            ctx.sync()
+            gms, _, _ = timed(lambda: lsk.gram(A, C=C, prec=prec, ctx=ctx), steps)
+            gms /= steps
+            err = float(torch.linalg.norm(C.double() - ref) / torch.linalg.norm(ref))
+            out[prec] = {"ms": gms, "GB/s": N_ROWS * D * 4 / (gms * 1e-3) / 1e9, "rel_fro_err": err}
+        del ref
+        return out
+
     def barrier():
         if world > 1:
             dist.barrier()
@@ -227,6 +246,12 @@ def main():
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1))
         return ms, t0, t1
+
+    if args.gram_only:
+        g = gram_leg(args.steps)
+        if rank == 0:
+            print(json.dumps({"gram": g, "config": workload_config(args)}))
+        return
 
     for _ in range(max(3, args.warmup)):
         step(args.prec)
@@ -293,6 +318,7 @@ def main():
         pms /= max(3, args.steps // 5)
         plain = {"value": whole_job_rate(a_bytes, world, pms), "unit": "GB/s", "ms_per_step": pms}
 
+    gram = None if args.no_gram else gram_leg(max(3, args.steps // 5))
     batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve else run_served(args, lsk, torch)
 
@@ -311,7 +337,7 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "gram": gram, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
     if world > 1:
