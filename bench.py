@@ -417,9 +417,11 @@ def run_served(args, lsk, torch):
     done, rejected = server.run(reqs, hbm_budget=150 * 10**9)
     summ = latency_summary(done)
     etas = [c.result[1]["eta"] for c in done if c.error is None]
+    errors = sorted({c.error for c in done if c.error is not None})
     summ.update({"workload": "served_lsq_poisson200", "requests": len(reqs), "rejected": len(rejected),
                  "slots": server.slots, "pool_problems": len(pool),
-                 "converged": int(sum(e <= 1e-10 for e in etas)), "max_eta": float(max(etas)) if etas else None})
+                 "converged": int(sum(e <= 1e-10 for e in etas)), "max_eta": float(max(etas)) if etas else None,
+                 "error_samples": errors[:3]})
     server.close()
     del pool, reqs
     torch.cuda.empty_cache()

@@ -440,8 +440,7 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         const size_t smem = (size_t)warps * d * 4;
         if (smem > 200 * 1024) return cudaErrorInvalidValue;
         if (smem > 48 * 1024) {
-            e = cudaFuncSetAttribute(cs_csr_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+            e = allow_dynamic_smem(cs_csr_gather_kernel);
             if (e != cudaSuccess) return e;
         }
         const int threads = warps * 32;

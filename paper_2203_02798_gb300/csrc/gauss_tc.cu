@@ -373,7 +373,7 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     p.scale = (float)(1.0 / sqrt((double)k));
     p.flag = nullptr;
     p.out = GSA;
-    cudaError_t e = cudaFuncSetAttribute(gauss_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    cudaError_t e = allow_dynamic_smem(gauss_tc_kernel);
     if (e != cudaSuccess) return e;
     LSK_PROF("gauss_tc", st) gauss_tc_kernel<<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
     const int64_t len = k * d;
@@ -430,8 +430,7 @@ cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, 
     const GtParams* ps = reinterpret_cast<const GtParams*>(table + g.params_off);
     const int* off = reinterpret_cast<const int*>(table + g.off_off);
     const int* roff = reinterpret_cast<const int*>(table + g.roff_off);
-    cudaError_t e = cudaFuncSetAttribute(gauss_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)g.smem);
+    cudaError_t e = allow_dynamic_smem(gauss_tc_grouped_kernel);
     if (e != cudaSuccess) return e;
     LSK_PROF("gauss_tc_grouped", st) gauss_tc_grouped_kernel<<<g.blocks, kThreads, g.smem, st>>>(ps, off, g.count);
     LSK_PROF("gauss_reduce_grouped", st) gauss_tc_reduce_grouped_kernel<<<g.rblocks, 256, 0, st>>>(ps, roff, g.count);

@@ -238,8 +238,7 @@ cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, v
     } else {
         const CsrPlan p = csr_plan(n, d, sm_count);
         if (p.smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(gram_csr_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+            cudaError_t e = allow_dynamic_smem(gram_csr_kernel);
             if (e != cudaSuccess) return e;
         }
         float* part = (float*)ws;

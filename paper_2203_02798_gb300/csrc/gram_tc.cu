@@ -316,7 +316,7 @@ bool gram_tc_supported(const lsk_mat* A) {
 template <int NPAD>
 cudaError_t launch_npad(const GrParams& p, int grid, cudaStream_t st) {
     const size_t smem = smem_bytes(NPAD);
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(gram_tc_kernel<NPAD>);
     if (e != cudaSuccess) return e;
     LSK_PROF("gram_tc", st) gram_tc_kernel<NPAD><<<grid, kThreads, smem, st>>>(p);
     return cudaGetLastError();

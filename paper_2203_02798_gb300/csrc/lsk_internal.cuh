@@ -62,6 +62,15 @@ struct WsCarver {
 };
 inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Allow `fn` the largest dynamic shared memory it can use on the current
+// device (the opt-in maximum less its static shared memory), once per function
+// and device.  The attribute is process-wide: setting it to each launch's own
+// size would race between host threads launching different sizes (a launch
+// could see another thread's smaller limit and fail with invalid argument).
+cudaError_t allow_dynamic_smem(const void* fn);
+template <class F>
+inline cudaError_t allow_dynamic_smem(F* fn) { return allow_dynamic_smem(reinterpret_cast<const void*>(fn)); }
+
 // ---------------------------------------------------------------------------
 // grouped launches: one grid runs the blocks of many independent problems.
 // Problem p owns blocks [off[p], off[p + 1]); off has count + 1 ascending

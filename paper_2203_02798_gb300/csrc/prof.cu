@@ -119,3 +119,25 @@ int lsk_profile_get(lsk_ctx* ctx, int idx, char* name, size_t name_len, long lon
 }
 
 }  // extern "C"
+
+// ---- dynamic shared memory limits (see lsk_internal.cuh) ----------------------
+#include <mutex>
+#include <set>
+#include <utility>
+
+cudaError_t allow_dynamic_smem(const void* fn) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({fn, dev})) return cudaSuccess;
+    cudaFuncAttributes a;
+    if ((e = cudaFuncGetAttributes(&a, fn)) != cudaSuccess) return e;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert({fn, dev});
+    return e;
+}

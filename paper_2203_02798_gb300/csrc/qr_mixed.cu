@@ -203,7 +203,6 @@ __device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int 
         }
         __syncthreads();
     }
-#pragma unroll 4
     // Rt[i][j] = L[j][i] for j >= i (only when the caller forms R), then the
     // packed rows of L (row l at l(l+1)/2): warp per row, lanes along it
     if (Rt) {
@@ -520,11 +519,11 @@ cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, 
     LSK_PROF("qr_equil", st) equil_exponents_grouped_kernel<<<g.blocks[QS_ONE], 256, 0, st>>>(jobs, one, n);
     LSK_PROF("qr_equil", st) equil_scale_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
     const size_t tiles = chol32_smem(g.dmax);
-    cudaError_t err = cudaFuncSetAttribute(chol32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
+    cudaError_t err = allow_dynamic_smem(chol32_grouped_kernel);
     if (err != cudaSuccess) return err;
     LSK_PROF("qr_chol32", st) chol32_grouped_kernel<<<g.blocks[QS_ONE], 512, tiles, st>>>(jobs, one, n);
     const size_t pk = (size_t)g.dmax * (g.dmax + 1) / 2 * 4;
-    err = cudaFuncSetAttribute(trinv32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
+    err = allow_dynamic_smem(trinv32_grouped_kernel);
     if (err != cudaSuccess) return err;
     LSK_PROF("qr_trinv32", st) trinv32_grouped_kernel<<<g.blocks[QS_TRINV], 512, pk, st>>>(jobs, tinv, n);
     LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 0);
@@ -556,11 +555,11 @@ cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rin
     LSK_PROF("qr_equil", st) equil_exponents_kernel<<<1, 256, 0, st>>>(C, d, e, sc, flag);
     LSK_PROF("qr_equil", st) equil_scale_kernel<<<zb, 256, 0, st>>>(C, d, sc, Ct, Ct32);
     const size_t tiles = chol32_smem(d);
-    cudaError_t err = cudaFuncSetAttribute(chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles);
+    cudaError_t err = allow_dynamic_smem(chol32_kernel);
     if (err != cudaSuccess) return err;
     LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, R ? Rt : nullptr, Lpk, flag);
     const size_t pk = (size_t)d * (d + 1) / 2 * 4;
-    err = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk);
+    err = allow_dynamic_smem(trinv32_kernel);
     if (err != cudaSuccess) return err;
     LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 511) / 512, 512, pk, st>>>(Lpk, d, X);
     // M = X^T (Ct X): W = Ct X on the upper triangle (only k <= j is needed by M)

@@ -386,11 +386,11 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     const int grid = p.ntiles < sm_count ? p.ntiles : sm_count;
     cudaError_t e;
     if (vec) {
-        e = cudaFuncSetAttribute(rownorm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dynamic_smem(rownorm_tc_kernel<true>);
         if (e != cudaSuccess) return e;
         LSK_PROF("rownorm_dense_tc", st) rownorm_tc_kernel<true><<<grid, kThreads, smem, st>>>(p, img);
     } else {
-        e = cudaFuncSetAttribute(rownorm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_dynamic_smem(rownorm_tc_kernel<false>);
         if (e != cudaSuccess) return e;
         LSK_PROF("rownorm_dense_tc", st) rownorm_tc_kernel<false><<<grid, kThreads, smem, st>>>(p, img);
     }

@@ -71,3 +71,45 @@ def test_served_trace_converges_and_overlaps(server):
     x_alone = alone[0].result[0]
     x_mix = by_id[4].result[0]
     assert np.linalg.norm(x_alone - x_mix) <= 1e-8 * np.linalg.norm(x_alone)
+
+
+def test_concurrent_contexts_launch_different_sizes():
+    """Eight host threads, each with its own context and stream, run leverage
+    scores of problems whose d (and so the kernels' shared-memory needs)
+    differ, 24 times each: every call succeeds and equals the same problem
+    computed alone.  (The kernels' dynamic shared-memory limits are process-
+    wide; per-launch values raced between such threads.)"""
+    import threading
+    import paper_2203_02798_gb300 as lsk
+    dims = [48, 96, 160, 256, 64, 200, 128, 32]
+    probs = []
+    for t, d in enumerate(dims):
+        A = torch.from_numpy(workloads.dense_normal(3000 + 97 * t, d, seed=70 + t)).cuda()
+        probs.append((A, max(4 * d, 1024), 2 * d, 11 + t))
+    ref = []
+    for A, r, k, s in probs:
+        ref.append(lsk.leverage_scores(A, r, k, s, "bf16"))
+        lsk.context().sync()
+    errors, bad = [], []
+
+    def worker(t):
+        try:
+            A, r, k, s = probs[t]
+            stream = torch.cuda.Stream()
+            ctx = lsk.Context(0)
+            with torch.cuda.stream(stream):
+                for _ in range(24):
+                    ell = lsk.leverage_scores(A, r, k, s, "bf16", ctx=ctx)
+                    ctx.sync()
+                    if torch.max(torch.abs(ell - ref[t]) / ref[t]).item() > 1e-4:
+                        bad.append(t)
+            ctx.close()
+        except Exception as e:   # collected and asserted below
+            errors.append(f"{t}: {e}")
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(len(dims))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert errors == [] and bad == []
