@@ -7,7 +7,8 @@
 //      Ct = D^-1 C D^-1, D_j = 2^round(log2 sqrt(C_jj))            (exact)
 //   2. Ct ~ Rt^T Rt by FP32 Cholesky (one CTA, packed lower triangle in
 //      shared memory), X = Rt^-1 by FP32 back substitution
-//   3. one correction step in FP64, all products of triangular matrices:
+//   3. one correction step with FP64-accurate products of triangular matrices
+//      (FP32-pair arithmetic on the FP32 units, FP64 inputs and outputs):
 //        M = X^T Ct X = I + E,  U = strict_upper(E) + diag(E)/2
 //        Y = X (I - U)                         (= (R D^-1)^-1 to O(|E|^2))
 //        Z = Rt + Rt (I - Y Rt)                (Newton step for Y^-1)
@@ -220,9 +221,28 @@ __global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ C
     chol32_body(Ct32, d, Rt, Lpk, flag, blockIdx.x, gridDim.x);
 }
 
+// Back substitution steps l = min(j, 32 SL + 31) .. 32 SL of column j: the
+// rows of block SL hold the pivot; rows i < l of blocks <= SL are updated.
+template <int SL>
+__device__ __forceinline__ void trinv_block(float (&xr)[8], const float* P, const float* rdiag, int j, int lane) {
+    if (j < 32 * SL) return;
+    const int top = j < 32 * SL + 31 ? j : 32 * SL + 31;
+    for (int l = top; l >= 32 * SL; --l) {
+        const int owner = l & 31;
+        const float xl = __shfl_sync(0xffffffffu, xr[SL], owner) * rdiag[l];
+        if (lane == owner) xr[SL] = xl;
+        const float* col = P + l * (l + 1) / 2;   // Rt[i][l] = L[l][i]
+#pragma unroll
+        for (int s = 0; s <= SL; ++s) {
+            const int i = lane + 32 * s;
+            if (i < l) xr[s] = fmaf(-col[i], xl, xr[s]);
+        }
+    }
+}
+
 // X = Rt^-1 (upper) in FP32, one warp per column; stored as FP64 values.
 // The packed factor (row l of L = column l of Rt at offset l(l+1)/2) is
-// staged in shared memory (once per 16 columns: 512-thread blocks) so the
+// staged in shared memory (once per block of 4 or 16 columns) so the
 // back-substitution chain sees shared-memory latency.
 __device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int d, double* __restrict__ X, const int blk, const int nblk) {
     extern __shared__ float P[];
@@ -244,24 +264,16 @@ __device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int 
     float xr[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) xr[s] = (lane + 32 * s == j) ? 1.f : 0.f;
-    for (int l = j; l >= 0; --l) {
-        const int owner = l & 31, slot = l >> 5;
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (s == slot) v = xr[s];
-        v = __shfl_sync(0xffffffffu, v, owner);
-        const float xl = v * rdiag[l];
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (s == slot && lane == owner) xr[s] = xl;
-        const float* col = P + l * (l + 1) / 2;   // Rt[i][l] = L[l][i]
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int i = lane + 32 * s;
-            if (i < l) xr[s] = fmaf(-col[i], xl, xr[s]);
-        }
-    }
+    // row blocks from the top one down; within block SL the pivot entry is
+    // xr[SL], a static index (no per-step selection among the 8 registers)
+    trinv_block<7>(xr, P, rdiag, j, lane);
+    trinv_block<6>(xr, P, rdiag, j, lane);
+    trinv_block<5>(xr, P, rdiag, j, lane);
+    trinv_block<4>(xr, P, rdiag, j, lane);
+    trinv_block<3>(xr, P, rdiag, j, lane);
+    trinv_block<2>(xr, P, rdiag, j, lane);
+    trinv_block<1>(xr, P, rdiag, j, lane);
+    trinv_block<0>(xr, P, rdiag, j, lane);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const int i = lane + 32 * s;
@@ -273,10 +285,18 @@ __global__ void __launch_bounds__(512) trinv32_kernel(const float* __restrict__ 
 }
 
 // Out = alpha * op(A) * B + beta * Cin + diag_add * I on the upper triangle
-// (tiles I <= J), FP64.  op(A) = A or A^T.  The reduction index is limited to
+// (tiles I <= J).  op(A) = A or A^T.  The reduction index is limited to
 // where both factors can be non-zero: a_upper (op(A) upper: k >= i),
 // a_lower (op(A) lower: k <= i), b_upper (B upper: k <= j).  Entries below
 // the diagonal of Out are written as zero.
+//
+// Arithmetic: the FP64 inputs are split into FP32 pairs (x = hi + lo, ~48
+// bits), each product is formed as hi*hi exactly (one FMA gives its rounding
+// error) plus the cross terms, and the sum is kept as an FP32 pair (TwoSum),
+// renormalised every 16 terms: about 2^-46 relative per product and d 2^-47
+// of max |term| in the sum -- far inside what the correction step needs --
+// on the FP32 units (FP64 runs at 1/64 of that rate on this part).  alpha,
+// beta and the final combination are FP64.
 struct TriGemm {
     const double* A;
     const double* B;
@@ -286,6 +306,28 @@ struct TriGemm {
     double alpha, beta, diag_add;
 };
 
+__device__ __forceinline__ float2 split_pair(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+// (s, c) += a * b with a, b FP32 pairs
+__device__ __forceinline__ void pair_mac(float2 a, float2 b, float& s, float& c) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float e = fmaf(a.x, b.x, -p);                       // a.x b.x = p + e exactly
+    const float cross = fmaf(a.x, b.y, __fmul_rn(a.y, b.x));
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    c = __fadd_rn(c, __fadd_rn(err, __fadd_rn(e, cross)));
+    s = t;
+}
+__device__ __forceinline__ void pair_renorm(float& s, float& c) {
+    const float t = __fadd_rn(s, c);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
+    s = t;
+}
+
 __device__ __forceinline__ void tri_gemm64_body(const TriGemm g, const int blk, const int nblk) {
     const int nt = (g.d + TT - 1) / TT;
     int t = blk, I = 0;
@@ -294,37 +336,39 @@ __device__ __forceinline__ void tri_gemm64_body(const TriGemm g, const int blk, 
         ++I;
     }
     const int J = I + t;
-    __shared__ double As[TT][TT + 1], Bs[TT][TT + 1];
+    __shared__ float2 As[TT][TT + 1], Bs[TT][TT + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // output (ty, tx)
     const int i0 = I * TT, j0 = J * TT;
     int klo = 0, khi = g.d;
     if (g.a_upper) klo = i0;
     if (g.a_lower) khi = min(khi, i0 + TT);
     if (g.b_upper) khi = min(khi, j0 + TT);
-    double acc0 = 0.0, acc1 = 0.0;   // two chains for latency
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;   // two chains for latency
     for (int k0 = klo - (klo % TT); k0 < khi; k0 += TT) {
         {
             const int r = threadIdx.x / TT, c = threadIdx.x % TT;
             const int ia = i0 + r, ka = k0 + c;
             double a = 0.0;
             if (ia < g.d && ka < g.d) a = g.transA ? g.A[(int64_t)ka * g.d + ia] : g.A[(int64_t)ia * g.d + ka];
-            As[r][c] = a;
+            As[r][c] = split_pair(a);
             const int kb = k0 + r, jb = j0 + c;
-            Bs[r][c] = (kb < g.d && jb < g.d) ? g.B[(int64_t)kb * g.d + jb] : 0.0;
+            Bs[r][c] = split_pair((kb < g.d && jb < g.d) ? g.B[(int64_t)kb * g.d + jb] : 0.0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TT; kk += 2) {
-            acc0 = fma(As[ty][kk], Bs[kk][tx], acc0);
-            acc1 = fma(As[ty][kk + 1], Bs[kk + 1][tx], acc1);
+            pair_mac(As[ty][kk], Bs[kk][tx], s0, c0);
+            pair_mac(As[ty][kk + 1], Bs[kk + 1][tx], s1, c1);
         }
+        pair_renorm(s0, c0);
+        pair_renorm(s1, c1);
         __syncthreads();
     }
     const int i = i0 + ty, j = j0 + tx;
     if (i >= g.d || j >= g.d) return;
     double r = 0.0;
     if (j >= i) {
-        r = g.alpha * (acc0 + acc1);
+        r = g.alpha * (((double)s0 + (double)s1) + ((double)c0 + (double)c1));
         if (g.beta != 0.0) r += g.beta * g.Cin[(int64_t)i * g.d + j];
         if (i == j) r += g.diag_add;
     }
@@ -561,7 +605,7 @@ cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rin
     const size_t pk = (size_t)d * (d + 1) / 2 * 4;
     err = allow_dynamic_smem(trinv32_kernel);
     if (err != cudaSuccess) return err;
-    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 511) / 512, 512, pk, st>>>(Lpk, d, X);
+    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 127) / 128, 128, pk, st>>>(Lpk, d, X);
     // M = X^T (Ct X): W = Ct X on the upper triangle (only k <= j is needed by M)
     TriGemm g{Ct, X, nullptr, W, d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
     if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
