@@ -28,6 +28,7 @@ import numpy as np
 from .philox import philox4x32_10, split_seed
 
 STREAM_G = 1
+STREAM_PI = 2   # the right JL projection of Alg. 15
 
 PREC_FP32 = 0
 PREC_TF32 = 1
@@ -49,12 +50,13 @@ def gaussian_matrix(k, r, seed, prec=PREC_FP32):
     return gaussian_columns(k, 0, r, seed, prec)
 
 
-def gaussian_columns(k, c0, c1, seed, prec=PREC_FP32):
-    """Columns c0..c1-1 of G (k x (c1-c0), float64)."""
+def gaussian_columns(k, c0, c1, seed, prec=PREC_FP32, stream=STREAM_G):
+    """Columns c0..c1-1 of G (k x (c1-c0), float64); ``stream`` is the third
+    counter word (STREAM_G for the Gaussian stage of Alg. 3)."""
     j = np.arange(k, dtype=np.uint64)[:, None]
     c = np.arange(c0, c1, dtype=np.uint64)[None, :]
     k0, k1 = split_seed(seed)
-    w = philox4x32_10(c & np.uint64(0xFFFFFFFF), c >> np.uint64(32), STREAM_G,
+    w = philox4x32_10(c & np.uint64(0xFFFFFFFF), c >> np.uint64(32), stream,
                       j >> np.uint64(2), k0, k1)
     p = ((j >> np.uint64(1)) & np.uint64(1)).astype(bool)
     a = (np.where(p, w[2], w[0]) >> np.uint32(8)).astype(np.float64)
@@ -68,6 +70,16 @@ def gaussian_columns(k, c0, c1, seed, prec=PREC_FP32):
     if prec == PREC_BF16:
         return float32_to_bf16_rne(g.astype(np.float32))
     return g
+
+
+def jl_matrix(d, m, seed):
+    """Pi (d x m, float64) of Alg. 15: a Gaussian scaled by 1/sqrt(m).
+
+    Pi[i, c] is entry (c, i) of the m x d matrix drawn as G above (column
+    index i, row index c) on stream STREAM_PI, i.e. z / sqrt(m) with the same
+    Philox-4x32-10 / Box-Muller construction.
+    """
+    return gaussian_columns(m, 0, d, seed, PREC_FP32, STREAM_PI).T.copy()
 
 
 def gauss_sketch(SA, k, seed, prec=PREC_FP32, batch=4096):

@@ -1,9 +1,11 @@
-"""Leverage scores: sketched (Alg. 15 without Pi) and exact (oracle).
+"""Leverage scores: sketched (Alg. 15, without and with its Pi) and exact.
 
 Alg. 15 (Sec. 4.3): sketch A (here G*S*A, Alg. 3; k = 0 means S*A alone,
 as the m = 0 convention of csrcgs, Sec. 5), factor the sketch, and return
-the squared row norms of A times the factor's inverse (Alg. 8).  The right
-Gaussian Pi of Alg. 15 is not applied (the scores are ||A_i R^-1||^2).
+the squared row norms of A times the factor's inverse (Alg. 8):
+``leverage_scores_*`` return ||A_i R^-1||^2; ``leverage_scores_jl_*`` apply
+Alg. 15's right Gaussian Pi (d x m, scaled by 1/sqrt(m)) and return
+||A_i R^-1 Pi||^2.
 
 Exact scores (Alg. 13, and the definition ||Q_i||^2 for A = Q R) pin the
 sketched ones.
@@ -46,6 +48,21 @@ def leverage_scores_csr(V, J, I, n, d, r, k, seed, prec=gaussian.PREC_FP32):
     R = sketch_R(sketch_csr(V, J, I, n, d, r, k, seed, prec))
     Rinv = qr.upper_triangular_inverse(R)
     return rownorms.rownorms_prod_csr_alg8(V, J, I, n, Rinv), R
+
+
+def leverage_scores_jl_dense(A, r, k, m, seed, prec=gaussian.PREC_FP32):
+    """Alg. 15 with the right JL projection: ell_i ~ ||A_i R^-1 Pi||^2, R from
+    the sketch of A (QR in place of the SVD), Pi = jl_matrix(d, m, seed)."""
+    A = np.asarray(A, dtype=np.float64)
+    R = sketch_R(sketch_dense(A, r, k, seed, prec))
+    X = qr.upper_triangular_inverse(R) @ gaussian.jl_matrix(A.shape[1], m, seed)
+    return rownorms.rownorms_prod_dense(A, X), R
+
+
+def leverage_scores_jl_csr(V, J, I, n, d, r, k, m, seed, prec=gaussian.PREC_FP32):
+    R = sketch_R(sketch_csr(V, J, I, n, d, r, k, seed, prec))
+    X = qr.upper_triangular_inverse(R) @ gaussian.jl_matrix(d, m, seed)
+    return rownorms.rownorms_prod_csr_alg8(V, J, I, n, X), R
 
 
 def leverage_scores_exact_qr(A):

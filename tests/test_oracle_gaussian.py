@@ -85,3 +85,23 @@ def test_gauss_sketch_batching_only_changes_rounding():
     G = ga.gaussian_matrix(10, 1000, 5)
     assert np.allclose(a, G @ SA, rtol=1e-13, atol=1e-13)
     assert np.allclose(b, G @ SA, rtol=1e-13, atol=1e-13)
+
+
+def test_jl_projection_scale_distribution_and_stream():
+    """Pi of Alg. 15: entries N(0, 1/m) (so E ||x Pi||^2 = ||x||^2), drawn on
+    their own counter stream (not the Gaussian stage's G)."""
+    d, m, seed = 64, 4000, 17
+    P = ga.jl_matrix(d, m, seed)
+    assert P.shape == (d, m)
+    z = P.ravel() * np.sqrt(m)
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / z.size)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        x = rng.standard_normal(d)
+        ratio = np.sum((x @ P) ** 2) / np.sum(x * x)
+        assert abs(ratio - 1.0) < 5 * np.sqrt(2.0 / m)        # chi^2_m / m
+    G = ga.gaussian_matrix(m, d, seed)                        # stream 1, same shape as Pi^T
+    assert abs(np.corrcoef(G.ravel(), P.T.ravel())[0, 1]) < 5 / np.sqrt(G.size)
+    # the construction: Pi[i, c] is G's entry (c, i) on the Pi stream
+    assert np.array_equal(P[5:9, 40:48], ga.gaussian_columns(m, 5, 9, seed, stream=ga.STREAM_PI)[40:48].T)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import gaussian as ga
-from oracle import leverage, lsq, qr
+from oracle import leverage, lsq, qr, rownorms
 
 
 def test_householder_qr_properties():
@@ -124,3 +124,39 @@ def test_sketch_precondition_lsq_reaches_tolerance():
     assert np.linalg.norm(x - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
     eta_ls = lsq.normal_equation_residual(lambda v: A @ v, lambda u: A.T @ u, b, x_ls)
     assert eta_ls < 1e-10
+
+
+def test_jl_scores_unbiased_and_concentrated():
+    """Alg. 15 with Pi: with R fixed, the mean of ||A_i R^-1 Pi||^2 over
+    independent Pi is ||A_i R^-1||^2; with large m the scores of
+    leverage_scores_jl_dense approach those without Pi (same sketch seed)."""
+    A = np.random.default_rng(8).standard_normal((3000, 12)).astype(np.float64)
+    A[:4] *= 30.0
+    ell, R = leverage.leverage_scores_dense(A, 600, 48, 5)
+    Rinv = qr.upper_triangular_inverse(R)
+    acc = np.zeros(A.shape[0])
+    trials = 400
+    for s in range(trials):
+        acc += rownorms.rownorms_prod_dense(A, Rinv @ ga.jl_matrix(12, 4, 1000 + s))
+    mean = acc / trials
+    # ||x Pi||^2 / ||x||^2 ~ chi^2_4 / 4 per trial: relative sd sqrt(2/4) / sqrt(trials)
+    assert np.all(np.abs(mean / ell - 1.0) < 5 * np.sqrt(0.5 / trials))
+    big, R2 = leverage.leverage_scores_jl_dense(A, 600, 48, 2000, 5)
+    assert np.array_equal(R2, R)                                  # same sketch, same R
+    assert np.all(np.abs(big / ell - 1.0) < 6 * np.sqrt(2.0 / 2000))
+    V, J, I = _csr_bernoulli(4000, 10, 0.3, 6)
+    ell_c, _ = leverage.leverage_scores_csr(V, J, I, 4000, 10, 400, 40, 2)
+    big_c, _ = leverage.leverage_scores_jl_csr(V, J, I, 4000, 10, 400, 40, 2000, 2)
+    nz = ell_c > 0
+    assert np.all(big_c[~nz] == 0)
+    assert np.all(np.abs(big_c[nz] / ell_c[nz] - 1.0) < 6 * np.sqrt(2.0 / 2000))
+
+
+def _csr_bernoulli(n, d, p, seed):
+    """CSR (V, J, I) with each entry kept with probability p (test input)."""
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n, d)) < p
+    I = np.concatenate([[0], np.cumsum(mask.sum(axis=1))]).astype(np.int64)
+    J = np.nonzero(mask)[1].astype(np.int32)
+    V = rng.standard_normal(J.size).astype(np.float32)
+    return V, J, I
