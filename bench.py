@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-gram", action="store_true", help="skip the A^T A leg")
+    ap.add_argument("--no-jl", action="store_true", help="skip the Alg. 15 right-projection leg")
+    ap.add_argument("--jl-m", type=int, default=64, help="columns of the right JL projection Pi")
     ap.add_argument("--gram-only", action="store_true",
                     help="time only lsk_gram_prec (BF16x3 and FP32) on the workload's A (for profiling)")
     args = ap.parse_args()
@@ -227,6 +229,25 @@ def main():
             out[prec] = {"ms": gms, "GB/s": N_ROWS * D * 4 / (gms * 1e-3) / 1e9, "rel_fro_err": err}
         del ref
         return out
+
+    def jl_leg(steps):
+        """Alg. 15 with the d x m right projection Pi on the same workload:
+        ||A_i R^-1 Pi||^2, timed like the main step, with the spread of the
+        estimates around ||A_i R^-1||^2 (expected sqrt(2/m))."""
+        m = args.jl_m
+        out_jl = torch.empty_like(ell)
+        run = lambda: lsk.leverage_scores_jl(A, R_SKETCH, K_GAUSS, m, SEED, args.prec, out=out_jl, ctx=ctx)
+        for _ in range(2):
+            run()
+        ctx.sync()
+        jms, _, _ = timed(run, steps)
+        jms /= steps
+        step(args.prec)
+        ctx.sync()
+        ratio = (out_jl.double() / ell.double().clamp_min(1e-30))
+        return {"m": m, "ms": jms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, jms),
+                "ratio_mean": float(ratio.mean()), "ratio_std": float(ratio.std()),
+                "expected_std": (2.0 / m) ** 0.5}
 
     def barrier():
         if world > 1:
@@ -319,6 +340,7 @@ def main():
         plain = {"value": whole_job_rate(a_bytes, world, pms), "unit": "GB/s", "ms_per_step": pms}
 
     gram = None if args.no_gram else gram_leg(max(3, args.steps // 5))
+    jl = None if args.no_jl else jl_leg(max(3, args.steps // 5))
     batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve else run_served(args, lsk, torch)
 
@@ -337,7 +359,7 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "gram": gram, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "gram": gram, "jl": jl, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
     if world > 1:

@@ -171,6 +171,22 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                         uint64_t seed, int32_t prec, float* ell,
                         double* R_out);
 
+/* Leverage-score estimates of Alg. 15 with its right JL projection: R from
+ * the sketch exactly as in lsk_leverage_scores (a QR in place of the SVD of
+ * Alg. 15 step 3: both give the same A R^-1 up to a d x d rotation, which
+ * the Gaussian Pi does not see), then ell_i = ||A_i R^-1 Pi||^2 (Alg. 8 with
+ * B = R^-1 Pi).  Pi is d x m with entries z / sqrt(m), z the standard normal
+ * entries of the Gaussian stage's construction drawn on counter stream 2:
+ * Pi[i][c] = entry (row c, column i) of that construction with the same
+ * seed.  R^-1 Pi is formed in FP64 and stored in FP32.  m in [1, 4096]
+ * (else LSK_ERR_INVALID_ARG); with prec = LSK_PREC_BF16 and d, m <= 256 the
+ * row norms run on the tensor cores.  ell: device n floats; R_out: NULL or
+ * device d*d doubles.  Each estimate is ||A_i R^-1||^2 times a chi^2_m / m
+ * variable: unbiased, relative spread sqrt(2/m). */
+int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                           int64_t m, uint64_t seed, int32_t prec, float* ell,
+                           double* R_out);
+
 /* ---- batches of independent problems ------------------------------------ */
 /* One problem of a batch: A (dense or CSR, device), its sketch sizes and
  * seed, and its output ell (device, A.n floats). */

@@ -88,6 +88,7 @@ _SIGS = {
     "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _I32, _P]),
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
+    "lsk_leverage_scores_jl": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
     "lsk_sketch_precondition_lsq": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _P,
                                                    ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
@@ -296,6 +297,18 @@ def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=No
     R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
     ctx._call("lsk_leverage_scores", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), _ptr(ell),
               _ptr(R))
+    return (ell, R) if return_R else ell
+
+
+def leverage_scores_jl(A, r, k, m, seed, prec="fp32", out=None, return_R=False, ctx=None):
+    """lsk_leverage_scores_jl: ell_i = ||A_i R^-1 Pi||^2 with the d x m JL
+    projection Pi of Alg. 15 (n float32); optionally R."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    ell = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
+    ctx._call("lsk_leverage_scores_jl", ctypes.byref(mat), int(r), int(k), int(m), int(seed), _prec(prec),
+              _ptr(ell), _ptr(R))
     return (ell, R) if return_R else ell
 
 

@@ -361,6 +361,35 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, ui
     return finish(ctx, "lsk_leverage_scores");
 }
 
+int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int64_t m, uint64_t seed,
+                           int32_t prec, float* ell, double* R_out) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    rc = check_sketch_args(ctx, A, r, k, prec);
+    if (rc) return rc;
+    if (m < 1 || m > 4096) return fail(ctx, LSK_ERR_INVALID_ARG, "m must be in [1, 4096]");
+    if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    // stage scratch after the factorisation: [X = R^-1 Pi, d*m f32][Pi | row-norm workspace]
+    const size_t xb = ws_round((size_t)A->d * m * 4);
+    const size_t jw = jl_workspace_bytes(A->d, m);
+    const size_t rw = rownorms_workspace_bytes(A, m, 0, prec);
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, xb + (jw > rw ? jw : rw)));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    cudaError_t e = sketch_and_factor(ctx, A, r, k, seed, prec, b, R_out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_jl (sketch)");
+    float* X = (float*)b.scratch;
+    void* rest = (char*)b.scratch + xb;
+    e = jl_launch(b.Rinv64, A->d, m, seed, X, rest, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_jl (R^-1 Pi)");
+    e = rownorms_launch(A, X, m, 1.0, 0.0, 0, prec, ell, rest, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_jl (row norms)");
+    return finish(ctx, "lsk_leverage_scores_jl");
+}
+
 void lsk_lsq_default_opts(lsk_lsq_opts* o, int64_t d) {
     if (!o) return;
     memset(o, 0, sizeof(*o));

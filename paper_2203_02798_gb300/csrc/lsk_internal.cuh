@@ -145,9 +145,10 @@ __device__ __forceinline__ float2 box_muller24(uint32_t wa, uint32_t wb) {
 }
 
 // Four Gaussian entries G[4q + t, c], t = 0..3, unscaled (pairs (w0, w1) and
-// (w2, w3); even rows take the cosine branch).
-__device__ __forceinline__ float4 gauss4(uint64_t c, uint32_t q, uint32_t k0, uint32_t k1) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 1u, q), k0, k1);
+// (w2, w3); even rows take the cosine branch).  stream: the third counter
+// word (1 for the Gaussian stage G, 2 for the right projection Pi of Alg. 15).
+__device__ __forceinline__ float4 gauss4(uint64_t c, uint32_t q, uint32_t k0, uint32_t k1, uint32_t stream = 1u) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), stream, q), k0, k1);
     const float2 z01 = box_muller24(w.x, w.y);
     const float2 z23 = box_muller24(w.z, w.w);
     return make_float4(z01.x, z01.y, z23.x, z23.y);
@@ -267,6 +268,11 @@ cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, 
 size_t lsq_workspace_bytes(const lsk_mat* A);
 int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
             const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info);
+
+// jl.cu: X = R^-1 Pi for Alg. 15 (Pi: d x m Gaussian / sqrt(m), stream 2)
+size_t jl_workspace_bytes(int64_t d, int64_t m);
+cudaError_t jl_launch(const double* Rinv64, int64_t d, int64_t m, uint64_t seed, float* X32, void* ws,
+                      cudaStream_t st);
 
 // debug_wait.cu
 cudaError_t debug_wait_timeout_launch(int64_t limit_us, int* flag, cudaStream_t st);

@@ -336,6 +336,59 @@ def test_leverage_csr(lsk):
     assert np.max(np.abs(ell[nz] - ref[nz]) / ref[nz]) <= 1e-3
 
 
+# ------------------------------------------ Alg. 15 with the right JL Pi -
+@pytest.mark.parametrize("prec,m", [("fp32", 64), ("bf16", 64), ("bf16", 200), ("fp32", 1), ("bf16", 300)])
+def test_leverage_jl_dense(lsk, prec, m):
+    """||A_i R^-1 Pi||^2 against the oracle on the same seeds: the tensor-core
+    row norms for m <= 256 (a ragged m = 200 tile), the SIMT path for m = 300
+    and FP32, and the single-column m = 1."""
+    A = workloads.dense_outliers().astype(np.float32)
+    op = oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32
+    ell, R = lsk.leverage_scores_jl(dev(A), 2500, 100, m, 4, prec, return_R=True)
+    lsk.context().sync()
+    ell = host(ell).astype(np.float64)
+    ref, Ro = olev.leverage_scores_jl_dense(A.astype(np.float64), 2500, 100, m, 4, op)
+    if m >= 16:
+        assert np.max(np.abs(ell - ref) / ref) <= 1e-3
+    else:
+        # few columns: a score (A_i x)^2 can cancel to ~0, so the error is
+        # measured against its expectation ||A_i R^-1||^2 (same sketch and R)
+        expect, _ = olev.leverage_scores_dense(A.astype(np.float64), 2500, 100, 4, op)
+        assert np.max(np.abs(ell - ref) / expect) <= 1e-3
+    colnorm = np.linalg.norm(Ro, axis=0)
+    assert np.all(np.abs(host(R) - Ro) <= 1e-4 * colnorm[None, :])
+
+
+def test_leverage_jl_csr(lsk):
+    n, d, m = 200_000, 100, 48
+    V, J, I = workloads.csr_bernoulli(n, d, 0.02, seed=2)
+    ell = lsk.leverage_scores_jl(csr_dev(lsk, V, J, I, d), 10_000, 200, m, 1, "fp32")
+    lsk.context().sync()
+    ell = host(ell).astype(np.float64)
+    ref, _ = olev.leverage_scores_jl_csr(V, J, I, n, d, 10_000, 200, m, 1)
+    nz = ref > 0
+    assert np.all(ell[~nz] == 0)
+    assert np.max(np.abs(ell[nz] - ref[nz]) / ref[nz]) <= 1e-3
+
+
+def test_leverage_jl_edges(lsk):
+    A = workloads.dense_normal(3000, 16, seed=5)
+    with pytest.raises(RuntimeError):
+        lsk.leverage_scores_jl(dev(A), 500, 64, 0, 1)
+    with pytest.raises(RuntimeError):
+        lsk.leverage_scores_jl(dev(A), 500, 64, 4097, 1)
+    # an empty A has rank 0 < d: no scores, and the deferred rank-deficiency status
+    e = torch.zeros((0, 16), dtype=torch.float32, device="cuda")
+    assert lsk.leverage_scores_jl(e, 500, 64, 8, 1).numel() == 0
+    with pytest.raises(lsk.LskError, match="RANK_DEFICIENT"):
+        lsk.context().sync()
+    # a larger m concentrates the estimate on ||A_i R^-1||^2 (relative spread sqrt(2/m))
+    full = host(lsk.leverage_scores(dev(A), 500, 64, 1)).astype(np.float64)
+    jl = host(lsk.leverage_scores_jl(dev(A), 500, 64, 4096, 1)).astype(np.float64)
+    lsk.context().sync()
+    assert np.max(np.abs(jl / full - 1)) <= 8 * np.sqrt(2 / 4096)
+
+
 # ------------------------------------------------------------ least squares -
 @pytest.mark.parametrize("kind", ["dense", "csr"])
 def test_sketch_precondition_lsq(lsk, kind):
