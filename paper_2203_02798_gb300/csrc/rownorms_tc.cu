@@ -7,6 +7,11 @@
 //     A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi     (FP32 accumulation),
 // the dropped A_lo B_lo term being ~2^-18 relative.
 //
+// Two forms share the pipeline below.  The CTA-pair form (rownorm_tc2_kernel)
+// runs M = 256 MMAs across two SMs so each SM holds only half of B and a
+// deeper ring; it is used where B is large enough to keep the single-CTA ring
+// short of its full depth (d = c = 256 triangular: 5 stages against 9) and
+// clusters of two fit.  Single-CTA form:
 // Persistent kernel, one CTA per SM (640 threads, 96 registers each):
 //   warps 0-3   epilogue: tcgen05.ld the accumulator rows, square, sum, store
 //   warp  4     TMEM allocation; lane 0 issues every MMA and commit
@@ -28,6 +33,11 @@
 // the epilogue of one tile overlaps the MMAs of the next.
 #include "tc_common.cuh"
 
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace {
 
 constexpr int kRows = 128;
@@ -48,6 +58,8 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;
 constexpr size_t kSmemLimit = 232448;
 constexpr size_t kSmemExtra = 1024 + 256;            // alignment slack + barriers
+constexpr int kMaxStages2 = 12;                      // CTA-pair ring
+constexpr size_t kSmemExtra2 = 1024 + 1024 + 512;    // alignment slack + pad after B + barriers
 
 struct RnParams {
     const float* A;
@@ -59,6 +71,11 @@ struct RnParams {
     uint32_t n0[kMaxQ], nn[kMaxQ], boff[kMaxQ];
     uint32_t b_bytes;
     int* flag;
+    // CTA-pair form: each CTA holds rows [n0 + h nn / 2, n0 + (h + 1) nn / 2)
+    // of every K-chunk's B tile (h = its rank in the pair)
+    uint32_t hoff[kMaxQ];
+    uint32_t hb_bytes;
+    int pair, stages2, ntiles2;
 };
 
 // B (d x c, row-major) -> the shared-memory image of its bf16 hi / lo parts:
@@ -79,9 +96,17 @@ __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnPara
         const float b1 = (k + 1 < p.d && j < p.c) ? B[(int64_t)(k + 1) * p.c + j] : 0.f;
         uint32_t hi, lo;
         tc::split_bf16x2(b0, b1, hi, lo);
-        const uint32_t off = p.boff[q] + tc::sw64_offset(r, kl);
-        *reinterpret_cast<uint32_t*>(img + off) = hi;
-        *reinterpret_cast<uint32_t*>(img + p.b_bytes + off) = lo;
+        if (p.pair) {
+            // [half 0: hi, lo][half 1: hi, lo], half h = rows h nn / 2 .. of the tile
+            const uint32_t hn = p.nn[q] / 2, h = r / hn;
+            const uint32_t off = h * 2 * p.hb_bytes + p.hoff[q] + tc::sw64_offset(r - h * hn, kl);
+            *reinterpret_cast<uint32_t*>(img + off) = hi;
+            *reinterpret_cast<uint32_t*>(img + p.hb_bytes + off) = lo;
+        } else {
+            const uint32_t off = p.boff[q] + tc::sw64_offset(r, kl);
+            *reinterpret_cast<uint32_t*>(img + off) = hi;
+            *reinterpret_cast<uint32_t*>(img + p.b_bytes + off) = lo;
+        }
     }
 }
 
@@ -89,8 +114,9 @@ __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnPara
 // piece, columns 4 (f % 8) .. +3): consecutive lanes read consecutive
 // 16-byte pieces, four 128-byte row segments per warp instruction.
 template <bool VEC>
-__device__ __forceinline__ void load_piece(const RnParams& p, int tile, int q, int half, int lane, float4 (&v)[kF4]) {
-    const int64_t row0 = (int64_t)tile * kRows + half * kPieceRows + (lane >> 3);
+__device__ __forceinline__ void load_piece(const RnParams& p, int64_t rowbase, int q, int half, int lane,
+                                           float4 (&v)[kF4]) {
+    const int64_t row0 = rowbase + half * kPieceRows + (lane >> 3);
     const int k0 = kKC * q + 4 * (lane & 7);
     if (VEC && row0 - (lane >> 3) + kPieceRows <= p.n && kKC * q + kKC <= p.d) {
         // interior piece: no bounds checks, rows 4 apart per step
@@ -109,7 +135,7 @@ __device__ __forceinline__ void load_piece(const RnParams& p, int tile, int q, i
     for (int i = 0; i < kF4; ++i) {
         const int f = lane + 32 * i;
         const int m = half * kPieceRows + (f >> 3), c4 = f & 7;
-        const int64_t row = (int64_t)tile * kRows + m;
+        const int64_t row = rowbase + m;
         const int k = kKC * q + 4 * c4;
         v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row < p.n && k < p.d) {
@@ -287,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
         int pc = cw, g = pc / kPieces, t = g / p.nq, q = g % p.nq, s = g % S, u = g / S;
         for (; g < G;) {
             const int half = pc % kPieces;
-            load_piece<VEC>(p, (int)blockIdx.x + t * (int)gridDim.x, q, half, lane, buf);
+            load_piece<VEC>(p, ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * kRows, q, half, lane, buf);
             int ok = 1;
             if (lane == 0) {
                 // both halves of this stage's previous use are stored: the stage
@@ -320,6 +346,192 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }
 
+// CTA-pair form (cluster of 2 SMs, cta_group::2): one M = 256 MMA covers 256
+// rows, 128 in each CTA, and each CTA keeps only its half of every K-chunk's B
+// tile, so B takes half the shared memory and the ring is nearly twice as
+// deep (9 stages at d = 256).  The even CTA's MMA thread issues for both;
+// the converters of both CTAs arrive on its stage barriers and its commits
+// are multicast to both CTAs' barriers; each CTA's epilogue reads its own
+// TMEM rows and reports to the even CTA.
+template <bool VEC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    rownorm_tc2_kernel(const RnParams p, const uint8_t* __restrict__ img) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int S = p.stages2;
+    const uint32_t rank = tc::cluster_ctarank();
+    const int cid = (int)tc::cluster_id_x(), ncl = (int)tc::nclusters_x();
+    uint8_t* sA = smem;                                  // S stages of (hi, lo), this CTA's 128 rows
+    uint8_t* sB = smem + S * kStageBytes;                // this CTA's half of B: hi image, then lo image
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * p.hb_bytes + 1024);
+    uint64_t* full = bars;                       // [S] even CTA: stage filled in both CTAs (2 kPieces arrivals)
+    uint64_t* empty = bars + kMaxStages2;        // [S] stage consumed (multicast commit)
+    uint64_t* tfull = bars + 2 * kMaxStages2;    // [2] accumulator done (multicast commit)
+    uint64_t* tempty = tfull + 2;                // [2] even CTA: accumulator read in both (2 kEpiWarps arrivals)
+    uint64_t* fin = tfull + 4;                   // all MMAs complete (multicast commit)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* stored = const_cast<int*>(abort) + 1;   // [S] halves stored per stage (in use order)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full + s, 2 * kPieces);
+            tc::mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tfull + a, 1);
+            tc::mbar_init(tempty + a, 2 * kEpiWarps);
+        }
+        tc::mbar_init(fin, 1);
+        *abort = 0;
+        for (int s = 0; s < kMaxStages2; ++s) stored[s] = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc_pair(tmem_slot, kTmemCols);
+        tc::tmem_relinquish_pair();
+    }
+    {   // this CTA's half of B (hi and lo images), 16-byte copies
+        const uint4* src = reinterpret_cast<const uint4*>(img + (size_t)rank * 2 * p.hb_bytes);
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        const uint32_t n16 = (2 * p.hb_bytes) >> 4;
+        for (uint32_t i = threadIdx.x; i < n16; i += kThreads) dst[i] = __ldg(src + i);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    tc::cluster_sync();   // barriers of both CTAs initialised, B halves in place
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const int my_tiles = (cid < p.ntiles2) ? (p.ntiles2 - 1 - cid) / ncl + 1 : 0;
+
+    if (warp < kEpiWarps) {
+        // ------------------------------------------------------------ epilogue
+        for (int i = 0; i < my_tiles; ++i) {
+            const int acc = i & 1;
+            if (!warp_wait(tfull + acc, (uint32_t)(i >> 1) & 1u, abort)) break;
+            tc::fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * kAccCols;
+            float sum = 0.f;
+            for (int col = 0; col < p.npad; col += 64) {
+                uint32_t v0[32], v1[32];
+                tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col, v0);
+                const bool two = col + 32 < p.npad;
+                if (two) tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col + 32u, v1);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v0[e]), __uint_as_float(v0[e]), sum);
+                if (two) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v1[e]), __uint_as_float(v1[e]), sum);
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) tc::mbar_arrive(tempty + acc);
+                else tc::mbar_arrive_cluster(tempty + acc, 0);
+            }
+            const int64_t row = ((int64_t)cid + (int64_t)i * ncl) * (2 * kRows) + rank * kRows + warp * 32 + lane;
+            if (row < p.n) p.x[row] = (p.beta != 0.f) ? fmaf(p.alpha, sum, p.beta * p.x[row]) : p.alpha * sum;
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------ MMA issue (even CTA)
+        if (lane == 0 && rank == 0) {
+            const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
+            bool ok = true;
+            int s = 0;
+            uint32_t ph = 0;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int acc = i & 1;
+                if (!tc::mbar_wait_cluster(tempty + acc, ((uint32_t)(i >> 1) & 1u) ^ 1u, abort)) break;
+                tc::fence_after_sync();
+                const uint32_t d_base = tmem + (uint32_t)acc * kAccCols;
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) {
+                    if (q >= p.nq) break;
+                    if (!tc::mbar_wait_cluster(full + s, ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_hi = sA_u32 + (uint32_t)s * kStageBytes, a_lo = a_hi + kHalfStage;
+                    const uint32_t b_hi = sB_u32 + p.hoff[q], b_lo = b_hi + p.hb_bytes;
+                    const uint32_t idesc = tc::idesc_bf16_f32(2 * kRows, p.nn[q]);
+                    const uint32_t d_tmem = d_base + p.n0[q];
+#pragma unroll
+                    for (int kk = 0; kk < kKC / 16; ++kk) {
+                        const uint32_t ko = 32u * kk;
+                        tc::mma_bf16_pair(d_tmem, tc::desc_sw64_kmajor(a_hi + ko), tc::desc_sw64_kmajor(b_hi + ko),
+                                          idesc, (q | kk) != 0);
+                        tc::mma_bf16_pair(d_tmem, tc::desc_sw64_kmajor(a_hi + ko), tc::desc_sw64_kmajor(b_lo + ko),
+                                          idesc, 1);
+                        tc::mma_bf16_pair(d_tmem, tc::desc_sw64_kmajor(a_lo + ko), tc::desc_sw64_kmajor(b_hi + ko),
+                                          idesc, 1);
+                    }
+                    tc::mma_commit_pair(empty + s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) tc::mma_commit_pair(tfull + acc);
+            }
+            tc::mma_commit_pair(fin);
+        }
+        if (lane == 0) {
+            // both CTAs: the last multicast commit has landed here, so no
+            // arrival is still on its way when the CTA leaves
+            volatile int never = 0;
+            tc::mbar_wait(fin, 0, &never);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ converters
+        const int cw = warp - kConvWarp0;
+        const int G = my_tiles * p.nq;
+        float4 buf[kF4];
+        int pc = cw, g = pc / kPieces, t = g / p.nq, q = g % p.nq, s = g % S, u = g / S;
+        for (; g < G;) {
+            const int half = pc % kPieces;
+            const int64_t rowbase = ((int64_t)cid + (int64_t)t * ncl) * (2 * kRows) + rank * kRows;
+            load_piece<VEC>(p, rowbase, q, half, lane, buf);
+            int ok = 1;
+            if (lane == 0) {
+                ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + s), kPieces * u, abort) &&
+                     tc::mbar_wait(empty + s, ((uint32_t)u & 1u) ^ 1u, abort);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            store_piece(sA + s * kStageBytes, half, lane, buf);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) tc::mbar_arrive(full + s);
+                else tc::mbar_arrive_cluster(full + s, 0);
+                atomicAdd(stored + s, 1);
+            }
+            pc += kConvWarps;
+            const int dg = pc / kPieces - g;
+            g += dg;
+            for (q += dg; q >= p.nq; q -= p.nq) ++t;
+            for (s += dg; s >= S; s -= S) ++u;
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::cluster_sync();   // no CTA leaves while its peer may still arrive on its barriers
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc_pair(tmem, kTmemCols);
+    }
+    if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
+}
+
+size_t smem_bytes2(const RnParams& p) {
+    return (size_t)p.stages2 * kStageBytes + 2 * (size_t)p.hb_bytes + kSmemExtra2;
+}
+
 size_t smem_bytes(const RnParams& p) {
     return (size_t)p.stages * kStageBytes + 2 * (size_t)p.b_bytes + kSmemExtra;
 }
@@ -345,19 +557,63 @@ bool make_plan(const lsk_mat* A, int64_t c, int upper_tri, RnParams& p) {
         }
     }
     p.b_bytes = off;   // multiple of 2048 (nn multiple of 32, 64-byte rows)
-    // the deepest ring that fits next to B (at least 2 stages)
+    uint32_t hoff = 0;
+    for (int q = 0; q < kMaxQ; ++q) {
+        p.hoff[q] = hoff;
+        hoff += (p.nn[q] / 2) * (kKC * 2);
+    }
+    p.hb_bytes = hoff;   // multiple of 1024 (nn / 2 multiple of 16)
+    // the deepest rings that fit next to B (at least 2 stages)
+    p.stages2 = 0;
+    for (int s = kMaxStages2; s >= 2; --s) {
+        p.stages2 = s;
+        if (smem_bytes2(p) <= kSmemLimit) break;
+        p.stages2 = 0;
+    }
+    p.stages = 0;
     for (int s = kMaxStages; s >= 2; --s) {
         p.stages = s;
-        if (smem_bytes(p) <= kSmemLimit) return true;
+        if (smem_bytes(p) <= kSmemLimit) break;
+        p.stages = 0;
     }
-    return false;
+    return p.stages >= 2 || p.stages2 >= 2;
+}
+
+// clusters of two that fit on the device at once with this shared memory (0:
+// none; cached per device, variant and size)
+int pair_clusters(bool vec, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, bool, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, vec, smem);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const void* fn = vec ? (const void*)rownorm_tc2_kernel<true> : (const void*)rownorm_tc2_kernel<false>;
+    cudaError_t e = vec ? allow_dynamic_smem(rownorm_tc2_kernel<true>) : allow_dynamic_smem(rownorm_tc2_kernel<false>);
+    int n = 0;
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    cache[key] = n;
+    return n;
 }
 
 }  // namespace
 
 bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri) {
     RnParams p{};
-    return make_plan(A, c, upper_tri, p);
+    if (!make_plan(A, c, upper_tri, p)) return false;
+    if (p.stages >= 2) return true;
+    // only the CTA-pair form fits: it needs clusters of two on this device
+    const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
+    return pair_clusters(vec, smem_bytes2(p)) > 0;
 }
 
 size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri) {
@@ -380,11 +636,32 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     p.ntiles = (int)((A->n + kRows - 1) / kRows);
     if (p.ntiles == 0) return cudaSuccess;
     uint8_t* img = (uint8_t*)ws;
-    LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
-    const size_t smem = smem_bytes(p);
     const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
-    const int grid = p.ntiles < sm_count ? p.ntiles : sm_count;
+    p.ntiles2 = (int)((A->n + 2 * kRows - 1) / (2 * kRows));
+    // LSK_ROWNORM_SINGLE_CTA=1 selects the single-CTA form (for testing it)
+    const char* single = getenv("LSK_ROWNORM_SINGLE_CTA");
+    const bool allow_pair = !(single && single[0] == '1');
+    // the pair form pays for its cross-SM hand-offs only where B leaves the
+    // single-CTA ring short of its full depth
+    const bool want_pair = p.stages2 >= 2 && (p.stages < 2 || (allow_pair && p.stages < kMaxStages &&
+                                                               p.stages2 > p.stages));
+    const int ncl = want_pair ? pair_clusters(vec, smem_bytes2(p)) : 0;
+    p.pair = ncl > 0 ? 1 : 0;
+    if (!p.pair && p.stages < 2) return cudaErrorNotSupported;
+    LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
     cudaError_t e;
+    if (p.pair) {
+        const size_t smem2 = smem_bytes2(p);
+        const int grid2 = 2 * (p.ntiles2 < ncl ? p.ntiles2 : ncl);
+        if (vec) {
+            LSK_PROF("rownorm_dense_tc", st) rownorm_tc2_kernel<true><<<grid2, kThreads, smem2, st>>>(p, img);
+        } else {
+            LSK_PROF("rownorm_dense_tc", st) rownorm_tc2_kernel<false><<<grid2, kThreads, smem2, st>>>(p, img);
+        }
+        return cudaGetLastError();
+    }
+    const size_t smem = smem_bytes(p);
+    const int grid = p.ntiles < sm_count ? p.ntiles : sm_count;
     if (vec) {
         e = allow_dynamic_smem(rownorm_tc_kernel<true>);
         if (e != cudaSuccess) return e;

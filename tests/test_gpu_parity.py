@@ -255,6 +255,25 @@ def test_rownorms_dense(lsk, n, d, c, tri, prec):
     assert np.max(np.abs(x - ref) / ref) <= (1e-5 if prec == "fp32" else 1e-3)
 
 
+@pytest.mark.parametrize("n,d,c,tri", [RN_CASES[0], RN_CASES[1], RN_CASES[5], RN_CASES[7]])
+def test_rownorms_dense_bf16_single_cta_form(lsk, monkeypatch, n, d, c, tri):
+    """Both tensor-core forms on the same inputs: the single-CTA kernel
+    (forced) and the default choice (the CTA-pair kernel where B is large,
+    e.g. d = c = 256).  Both split and sum identically, so they agree to the
+    FP32 accumulation order."""
+    A = workloads.dense_normal(n, d, seed=c) * (10.0 ** np.linspace(-2, 2, d)).astype(np.float32)
+    B = workloads.dense_normal(d, c, seed=d + 1)
+    if tri:
+        B = np.triu(B)
+    pair = host(lsk.rownorms_prod(dev(A), dev(B), upper_triangular=tri, prec="bf16")).astype(np.float64)
+    monkeypatch.setenv("LSK_ROWNORM_SINGLE_CTA", "1")
+    single = host(lsk.rownorms_prod(dev(A), dev(B), upper_triangular=tri, prec="bf16")).astype(np.float64)
+    lsk.context().sync()
+    ref = orn.rownorms_prod_dense(A.astype(np.float64), B.astype(np.float64))
+    assert np.max(np.abs(single - ref) / ref) <= 1e-3
+    assert np.max(np.abs(single - pair) / ref) <= 1e-5
+
+
 def test_rownorms_alpha_beta(lsk):
     A = workloads.dense_normal(1000, 20, seed=1)
     B = workloads.dense_normal(20, 7, seed=2)
