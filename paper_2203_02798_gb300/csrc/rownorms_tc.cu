@@ -155,17 +155,28 @@ __device__ __forceinline__ void load_piece(const RnParams& p, int64_t rowbase, i
     }
 }
 
+// Element (m, 4 c4) of the piece, m = 64 half + 4 i + l8 (l8 = lane / 8,
+// c4 = lane % 8), sits at tc::sw64_offset(m, 4 c4).  Because l8 < 4, the row
+// atom (m / 8 = 8 half + i / 2), the row in the atom (4 (i % 2) + l8) and the
+// swizzle phase ((m / 2) % 4 = 2 (i % 2) + l8 / 2) split into a per-lane part
+// that depends only on the parity of i and a constant 512 (i / 2): two base
+// offsets per lane, and every store takes an immediate offset.
 __device__ __forceinline__ void store_piece(uint8_t* stage, int half, int lane, const float4 (&v)[kF4]) {
+    const uint32_t l8 = (uint32_t)lane >> 3, c4 = (uint32_t)lane & 7u;
+    const uint32_t lane_part = l8 * 64u + (c4 & 1u) * 8u;
+    const uint32_t b_even = (uint32_t)half * (kPieceRows * 64u) + lane_part + ((((c4 >> 1) ^ (l8 >> 1)) & 3u) << 4);
+    const uint32_t b_odd = (uint32_t)half * (kPieceRows * 64u) + 256u + lane_part +
+                           ((((c4 >> 1) ^ (2u + (l8 >> 1))) & 3u) << 4);
+    uint8_t* const s_even = stage + b_even;
+    uint8_t* const s_odd = stage + b_odd;
 #pragma unroll
     for (int i = 0; i < kF4; ++i) {
-        const int f = lane + 32 * i;
-        const uint32_t m = half * kPieceRows + (f >> 3), c4 = f & 7;
         uint2 hi, lo;
         tc::split_bf16x2(v[i].x, v[i].y, hi.x, lo.x);
         tc::split_bf16x2(v[i].z, v[i].w, hi.y, lo.y);
-        const uint32_t off = tc::sw64_offset(m, 4 * c4);
-        *reinterpret_cast<uint2*>(stage + off) = hi;
-        *reinterpret_cast<uint2*>(stage + kHalfStage + off) = lo;
+        uint8_t* const dst = ((i & 1) ? s_odd : s_even) + (i >> 1) * 512;
+        *reinterpret_cast<uint2*>(dst) = hi;
+        *reinterpret_cast<uint2*>(dst + kHalfStage) = lo;
     }
 }
 
