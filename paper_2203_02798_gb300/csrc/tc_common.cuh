@@ -279,12 +279,17 @@ __host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t row, uint32_t 
 }
 
 // hi = bf16(x), lo = bf16(x - hi): x = hi + lo to ~16 significant bits.
+// Packed as bf16x2 words with a (resp. a - hi_a) in the low half.  Six
+// instructions a pair: two round-to-nearest-even conversions (cvt packs its
+// first source into the high half), the exact widening of hi by shifting /
+// masking the bf16 bit patterns into float position, and two subtractions.
 __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
+    uint32_t h, l;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(b), "f"(a));
+    const float ha = __uint_as_float(h << 16), hb = __uint_as_float(h & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(b - hb), "f"(a - ha));
+    hi = h;
+    lo = l;
 }
 
 }  // namespace tc
