@@ -22,6 +22,11 @@ reading, and it caps |z| at sqrt(48 ln 2) = 5.77).
 In the BF16 precision mode G is *defined* as the bfloat16 value nearest
 (ties to even) to the float32 rounding of z / sqrt(k); that rounding is the
 one decision both the oracle and the GPU take in float32.
+
+The same construction, with the third counter word changed, draws the other
+Gaussian matrices of the paper: stream 2 the right projection Pi of Alg. 15
+(``jl_matrix``), stream 3 the m x n matrix of the Gaussian CSR sketch of
+Alg. 4 (``csrjlt``, column index = row index of A, scaled by 1/sqrt(m)).
 """
 import numpy as np
 
@@ -29,6 +34,7 @@ from .philox import philox4x32_10, split_seed
 
 STREAM_G = 1
 STREAM_PI = 2   # the right JL projection of Alg. 15
+STREAM_JLT = 3  # the Gaussian sketch of a CSR matrix (Alg. 4, csrjlt)
 
 PREC_FP32 = 0
 PREC_TF32 = 1
@@ -95,4 +101,26 @@ def gauss_sketch(SA, k, seed, prec=PREC_FP32, batch=4096):
     for c0 in range(0, r, batch):
         c1 = min(r, c0 + batch)
         C += gaussian_columns(k, c0, c1, seed, prec) @ SA[c0:c1]
+    return C
+
+
+def csrjlt(V, J, I, n, d, m, seed, prec=PREC_FP32, batch=4096):
+    """C = G A (m x d, float64) for CSR A (Alg. 4, ``csrjlt``).
+
+    G is m x n, drawn like the Gaussian stage's G (z / sqrt(m), bfloat16-
+    rounded in the BF16 mode) with column index = row index of A, on counter
+    stream STREAM_JLT.  C = G A is a plain product; as in Alg. 4 the rows of A
+    are taken in order (here in batches, each with its own columns of G), so
+    G is never held whole.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    J = np.asarray(J)
+    I = np.asarray(I)
+    C = np.zeros((m, d), dtype=np.float64)
+    for r0 in range(0, n, batch):
+        r1 = min(n, r0 + batch)
+        blk = np.zeros((r1 - r0, d), dtype=np.float64)
+        for i in range(r0, r1):
+            blk[i - r0, J[I[i]:I[i + 1]]] += V[I[i]:I[i + 1]]
+        C += gaussian_columns(m, r0, r1, seed, prec, STREAM_JLT) @ blk
     return C

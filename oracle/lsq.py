@@ -1,4 +1,5 @@
-"""Sketch-and-precondition least squares (Alg. 12) with LSQR (oracle).
+"""Least squares through sketches (oracle): sketch-and-precondition (Alg. 12)
+with LSQR, and sketch-and-solve (Alg. 11).
 
 Alg. 12 (Sec. 4.2): sketch A, factor the sketch, take N as the inverse
 factor, solve min_y ||A N y - b|| with "a parallel preconditioned iterative
@@ -105,3 +106,41 @@ def least_squares_qr(A, b):
     qtb = qr.apply_qt(refl, signs, b)
     Rinv = qr.upper_triangular_inverse(R)
     return Rinv @ qtb
+
+
+def sketch_solve(SAb):
+    """Alg. 11 on a sketched augmented matrix SAb = (A~ b~) (rows x (d + 1)):
+    x = argmin ||A~ x - b~||, from the Householder QR of A~ (full column
+    rank required; the QR stands in for the SVD of Alg. 11 step 2, which gives
+    the same minimiser when A~ has full rank)."""
+    SAb = np.asarray(SAb, dtype=np.float64)
+    At, bt = SAb[:, :-1], SAb[:, -1]
+    refl, R, signs = qr.householder_qr(At)
+    qr.check_full_rank(R)
+    return qr.upper_triangular_inverse(R) @ qr.apply_qt(refl, signs, bt)
+
+
+def sketch_solve_dense(A, b, r, k, seed, prec=0):
+    """Alg. 11 for dense A: (A~ b~) = G S (A b) (k = 0: S (A b)), then solve."""
+    A = np.asarray(A, dtype=np.float64)
+    Ab = np.hstack([A, np.asarray(b, dtype=np.float64)[:, None]])
+    return sketch_solve(leverage.sketch_dense(Ab, r, k, seed, prec))
+
+
+def sketch_solve_csr(V, J, I, n, d, b, r, k, seed, prec=0):
+    """Alg. 11 for CSR A: the augmented column b joins every row (CSR of (A b))."""
+    V = np.asarray(V, dtype=np.float64)
+    J = np.asarray(J)
+    I = np.asarray(I)
+    b = np.asarray(b, dtype=np.float64)
+    cnt = np.diff(I) + 1
+    I2 = np.concatenate([[0], np.cumsum(cnt)])
+    V2 = np.empty(I2[-1])
+    J2 = np.empty(I2[-1], dtype=np.int64)
+    for i in range(n):
+        a, e = I[i], I[i + 1]
+        V2[I2[i]:I2[i + 1] - 1] = V[a:e]
+        J2[I2[i]:I2[i + 1] - 1] = J[a:e]
+        V2[I2[i + 1] - 1] = b[i]
+        J2[I2[i + 1] - 1] = d
+    return sketch_solve(leverage.sketch_csr(V2, J2, I2, n, d + 1, r, k, seed, prec))
