@@ -187,6 +187,30 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                            int64_t m, uint64_t seed, int32_t prec, float* ell,
                            double* R_out);
 
+/* Gaussian sketch of a CSR matrix (Alg. 4, csrjlt): C = G A, G m x n with
+ * entries z / sqrt(m) drawn like the Gaussian stage's G (Philox-4x32-10,
+ * 24-bit Box-Muller) on counter stream 3, G[j][i] = entry (row j, column i)
+ * of that construction (column index = row index of A); bfloat16-rounded in
+ * the BF16 mode.  A: CSR only (LSK_ERR_UNSUPPORTED otherwise; a dense A is a
+ * plain GEMM).  C: device m x d floats, row-major (written).  FP32 partial
+ * sums over row ranges of A, summed in FP64 in a fixed order.  Malformed
+ * CSR sets the deferred LSK_ERR_BAD_CSR.  m in [1, 2^20], d <= 1280. */
+int lsk_csrjlt(lsk_ctx* ctx, const lsk_mat* A, int64_t m, uint64_t seed,
+               int32_t prec, float* C);
+
+/* Sketch-and-solve least squares (Alg. 11): (A~ b~) = G S (A b) with the
+ * sketch sizes and draws of lsk_leverage_scores (k == 0: S (A b)), then
+ * x = argmin ||A~ x - b~|| through R of A~ (a QR in place of the SVD of
+ * Alg. 11 step 2; same minimiser at full rank): the seminormal equations
+ * x = R^-1 R^-T A~^T b~ plus one corrected step, in FP64.  b~ uses the same
+ * hash and the same G entries as A~ (bfloat16-rounded in the BF16 mode),
+ * accumulated in FP64.  b: device n doubles; x: device d doubles (written).
+ * The solution is approximate: ||A x - b|| is within the sketch's distortion
+ * of the least-squares residual.  Rank deficiency of A~ is the deferred
+ * LSK_ERR_RANK_DEFICIENT (as lsk_sketch_qr); d <= 1024. */
+int lsk_sketch_solve(lsk_ctx* ctx, const lsk_mat* A, const double* b, int64_t r,
+                     int64_t k, uint64_t seed, int32_t prec, double* x);
+
 /* ---- batches of independent problems ------------------------------------ */
 /* One problem of a batch: A (dense or CSR, device), its sketch sizes and
  * seed, and its output ell (device, A.n floats). */

@@ -89,6 +89,8 @@ _SIGS = {
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_leverage_scores_jl": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _I64, _U64, _I32, _P, _P]),
+    "lsk_sketch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I64, _U64, _I32, _P]),
+    "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
     "lsk_sketch_precondition_lsq": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _P,
                                                    ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
@@ -310,6 +312,26 @@ def leverage_scores_jl(A, r, k, m, seed, prec="fp32", out=None, return_R=False, 
     ctx._call("lsk_leverage_scores_jl", ctypes.byref(mat), int(r), int(k), int(m), int(seed), _prec(prec),
               _ptr(ell), _ptr(R))
     return (ell, R) if return_R else ell
+
+
+def csrjlt(A, m, seed, prec="fp32", out=None, ctx=None):
+    """lsk_csrjlt (Alg. 4): C = G A for a CSR A (m x d float32)."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    C = out if out is not None else torch.empty((m, d), dtype=torch.float32, device=_dev(A))
+    ctx._call("lsk_csrjlt", ctypes.byref(mat), int(m), int(seed), _prec(prec), _ptr(C))
+    return C
+
+
+def sketch_solve(A, b, r, k, seed, prec="fp32", out=None, ctx=None):
+    """lsk_sketch_solve (Alg. 11): x = argmin ||G S (A x - b)|| (d float64)."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    if b.dtype != torch.float64 or not b.is_contiguous() or b.device != _dev(A):
+        raise ValueError("b must be a contiguous float64 tensor on A's device")
+    x = out if out is not None else torch.empty(d, dtype=torch.float64, device=_dev(A))
+    ctx._call("lsk_sketch_solve", ctypes.byref(mat), _ptr(b), int(r), int(k), int(seed), _prec(prec), _ptr(x))
+    return x
 
 
 def batch_leverage_scores(problems, prec="bf16", graph=False, autotune=False, streams=0, outs=None,

@@ -390,6 +390,45 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
     return finish(ctx, "lsk_leverage_scores_jl");
 }
 
+int lsk_csrjlt(lsk_ctx* ctx, const lsk_mat* A, int64_t m, uint64_t seed, int32_t prec, float* C) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (A->kind != LSK_CSR) return fail(ctx, LSK_ERR_UNSUPPORTED, "lsk_csrjlt takes a CSR matrix");
+    if (!C) return fail(ctx, LSK_ERR_INVALID_ARG, "C is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (m < 1 || !jlt_supported(A->d, m)) return fail(ctx, LSK_ERR_UNSUPPORTED, "m in [1, 2^20], d <= 1280");
+    rc = ws_ensure(ctx, jlt_workspace_bytes(A->n, A->d, m, ctx->sm_count));
+    if (rc) return rc;
+    cudaError_t e = jlt_launch(A, m, seed, prec, C, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_csrjlt");
+    return finish(ctx, "lsk_csrjlt");
+}
+
+int lsk_sketch_solve(lsk_ctx* ctx, const lsk_mat* A, const double* b, int64_t r, int64_t k, uint64_t seed,
+                     int32_t prec, double* x) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    rc = check_sketch_args(ctx, A, r, k, prec);
+    if (rc) return rc;
+    if (!x || (!b && A->n > 0)) return fail(ctx, LSK_ERR_INVALID_ARG, "b / x is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, solve_workspace_bytes(r, k, A->d)));
+    if (rc) return rc;
+    const SketchBufs bufs = carve(ctx->ws, A, r, k);
+    cudaError_t e = sketch_and_factor(ctx, A, r, k, seed, prec, bufs, nullptr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_solve (sketch)");
+    e = solve_launch(A, b, r, k, seed, prec, k > 0 ? bufs.GSA : bufs.SA, bufs.Rinv64, x, bufs.scratch,
+                     ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_solve (solve)");
+    return finish(ctx, "lsk_sketch_solve");
+}
+
 void lsk_lsq_default_opts(lsk_lsq_opts* o, int64_t d) {
     if (!o) return;
     memset(o, 0, sizeof(*o));

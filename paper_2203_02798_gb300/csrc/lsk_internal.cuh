@@ -274,6 +274,17 @@ size_t jl_workspace_bytes(int64_t d, int64_t m);
 cudaError_t jl_launch(const double* Rinv64, int64_t d, int64_t m, uint64_t seed, float* X32, void* ws,
                       cudaStream_t st);
 
+// jlt.cu: Gaussian sketch of a CSR matrix (Alg. 4), C = G A, stream 3
+bool jlt_supported(int64_t d, int64_t m);
+size_t jlt_workspace_bytes(int64_t n, int64_t d, int64_t m, int sm_count);
+cudaError_t jlt_launch(const lsk_mat* A, int64_t m, uint64_t seed, int32_t prec, float* C, void* ws, int* flag,
+                       int sm_count, cudaStream_t st);
+
+// solve.cu: sketch-and-solve (Alg. 11) given the sketch A~ of A and R^-1
+size_t solve_workspace_bytes(int64_t r, int64_t k, int64_t d);
+cudaError_t solve_launch(const lsk_mat* A, const double* b, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                         const float* At, const double* Rinv64, double* x, void* ws, int sm_count, cudaStream_t st);
+
 // debug_wait.cu
 cudaError_t debug_wait_timeout_launch(int64_t limit_us, int* flag, cudaStream_t st);
 
