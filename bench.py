@@ -180,6 +180,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-gram", action="store_true", help="skip the A^T A leg")
     ap.add_argument("--no-jl", action="store_true", help="skip the Alg. 15 right-projection leg")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the sketch-and-solve (Alg. 11) and csrjlt (Alg. 4) legs")
     ap.add_argument("--jl-m", type=int, default=64, help="columns of the right JL projection Pi")
     ap.add_argument("--gram-only", action="store_true",
                     help="time only lsk_gram_prec (BF16x3 and FP32) on the workload's A (for profiling)")
@@ -248,6 +250,34 @@ def main():
         return {"m": m, "ms": jms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, jms),
                 "ratio_mean": float(ratio.mean()), "ratio_std": float(ratio.std()),
                 "expected_std": (2.0 / m) ** 0.5}
+
+    def next_legs(steps):
+        """Sketch-and-solve (Alg. 11) on the workload's A with a synthetic b, and
+        the Gaussian CSR sketch (Alg. 4) of the 1,000,000 x 200 CSR workload
+        (p = 0.01, m = 2 d = 400): ms per call and the rate of the main input."""
+        out = {}
+        g = torch.Generator(device="cuda").manual_seed(DATA_SEED)
+        b = torch.randn(N_ROWS, dtype=torch.float64, device="cuda", generator=g)
+        x = torch.empty(D, dtype=torch.float64, device="cuda")
+        run = lambda: lsk.sketch_solve(A, b, R_SKETCH, K_GAUSS, SEED, args.prec, out=x, ctx=ctx)
+        run()
+        ctx.sync()
+        ms, _, _ = timed(run, steps)
+        ms /= steps
+        out["sketch_solve"] = {"ms": ms, "GB/s": whole_job_rate(N_ROWS * D * 4 + N_ROWS * 8, world, ms),
+                               "workload": "dense 4M x 256 + b, r = 65,536, k = 512"}
+        del b
+        V, J, I = workloads.csr_bernoulli(1_000_000, 200, 0.01, seed=1)
+        Acsr = lsk.csr_from_numpy(V, J, I, 200)
+        C = torch.empty((400, 200), dtype=torch.float32, device="cuda")
+        runj = lambda: lsk.csrjlt(Acsr, 400, SEED, "fp32", out=C, ctx=ctx)
+        runj()
+        ctx.sync()
+        jms, _, _ = timed(runj, steps)
+        jms /= steps
+        out["csrjlt"] = {"ms": jms, "gaussians_per_s": 400 * 1_000_000 / (jms * 1e-3),
+                         "nnz": int(len(V)), "workload": "CSR 1M x 200, p = 0.01, m = 400"}
+        return out
 
     def barrier():
         if world > 1:
@@ -341,6 +371,7 @@ def main():
 
     gram = None if args.no_gram else gram_leg(max(3, args.steps // 5))
     jl = None if args.no_jl else jl_leg(max(3, args.steps // 5))
+    nxt = None if args.no_next else next_legs(max(3, args.steps // 5))
     batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve else run_served(args, lsk, torch)
 
@@ -359,7 +390,7 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "gram": gram, "jl": jl, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "gram": gram, "jl": jl, "next": nxt, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
     if world > 1:
