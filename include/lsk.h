@@ -187,6 +187,32 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                            int64_t m, uint64_t seed, int32_t prec, float* ell,
                            double* R_out);
 
+/* Column subset selection (Alg. 9): B = G S A (k > 0; S A when k == 0)
+ * with the draws of lsk_leverage_scores, then the first c pivots of a
+ * column-pivoted QR of B, taken as the diagonally pivoted Cholesky of
+ * B^T B (FP64, exact products): the same pivot rule (largest remaining
+ * column norm, lowest index on ties) in exact arithmetic, on a d x d matrix.
+ * cols: device c int32 column indices of A, in pivot order (written).
+ * c in [1, d], d <= 1024.  A numerically exhausted rank before c pivots
+ * sets the deferred LSK_ERR_RANK_DEFICIENT and fills the rest of cols with
+ * the remaining columns in order. */
+int lsk_column_select(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                      uint64_t seed, int32_t prec, int64_t c, int32_t* cols);
+
+/* Leverage scores on the columns K selected by lsk_column_select:
+ * exact != 0: Alg. 14 -- the exact scores (Alg. 13) of A[:, K]: the Gram
+ *   A^T A in FP64, its K x K block, R from it (FP64 accurate; Cholesky in
+ *   place of the SVD at full rank), theta_i = ||A[i, K] R^-1||^2;
+ * exact == 0: Alg. 16 -- Alg. 15 on A[:, K] with the Alg. 9 sketch
+ *   restricted to K (column selection commutes with the left sketch), R
+ *   from its QR, theta_i = ||A[i, K] R^-1||^2.
+ * The row norms run on A itself with B = E_K R^-1 (d x c, zero outside the
+ * rows K): A[:, K] is never copied.  theta: device n floats; cols: NULL or
+ * device c int32 (the selection).  Rank deficiency is deferred as above. */
+int lsk_leverage_scores_hrn(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                            uint64_t seed, int32_t prec, int64_t c, int32_t exact,
+                            float* theta, int32_t* cols);
+
 /* Gaussian sketch of a CSR matrix (Alg. 4, csrjlt): C = G A, G m x n with
  * entries z / sqrt(m) drawn like the Gaussian stage's G (Philox-4x32-10,
  * 24-bit Box-Muller) on counter stream 3, G[j][i] = entry (row j, column i)

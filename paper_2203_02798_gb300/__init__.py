@@ -91,6 +91,8 @@ _SIGS = {
     "lsk_leverage_scores_jl": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_sketch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I64, _U64, _I32, _P]),
     "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
+    "lsk_column_select": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
+    "lsk_leverage_scores_hrn": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _I32, _P, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
     "lsk_sketch_precondition_lsq": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _P,
                                                    ctypes.POINTER(LsqOpts), ctypes.POINTER(LsqInfo)]),
@@ -312,6 +314,27 @@ def leverage_scores_jl(A, r, k, m, seed, prec="fp32", out=None, return_R=False, 
     ctx._call("lsk_leverage_scores_jl", ctypes.byref(mat), int(r), int(k), int(m), int(seed), _prec(prec),
               _ptr(ell), _ptr(R))
     return (ell, R) if return_R else ell
+
+
+def column_select(A, r, k, seed, c, prec="fp32", ctx=None):
+    """lsk_column_select (Alg. 9): the c selected columns of A (int32, pivot order)."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    cols = torch.empty(int(c), dtype=torch.int32, device=_dev(A))
+    ctx._call("lsk_column_select", ctypes.byref(mat), int(r), int(k), int(seed), _prec(prec), int(c), _ptr(cols))
+    return cols
+
+
+def leverage_scores_hrn(A, r, k, seed, c, exact=True, prec="fp32", out=None, ctx=None):
+    """lsk_leverage_scores_hrn: Alg. 14 (exact=True) or Alg. 16 scores on the
+    c columns Alg. 9 selects -> (theta, cols)."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    theta = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    cols = torch.empty(int(c), dtype=torch.int32, device=_dev(A))
+    ctx._call("lsk_leverage_scores_hrn", ctypes.byref(mat), int(r), int(k), int(seed), _prec(prec), int(c),
+              1 if exact else 0, _ptr(theta), _ptr(cols))
+    return theta, cols
 
 
 def csrjlt(A, m, seed, prec="fp32", out=None, ctx=None):

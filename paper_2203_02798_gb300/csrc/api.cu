@@ -429,6 +429,144 @@ int lsk_sketch_solve(lsk_ctx* ctx, const lsk_mat* A, const double* b, int64_t r,
     return finish(ctx, "lsk_sketch_solve");
 }
 
+// ---- column subset selection (Alg. 9) and Alg. 14 / 16 -------------------
+namespace {
+
+// S A (k = 0) or G S A into the sketch buffers, without factoring it
+cudaError_t sketch_only(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                        const SketchBufs& b, const float** sk, int64_t* rows) {
+    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return e;
+    *sk = b.SA;
+    *rows = r;
+    if (k > 0) {
+        e = gauss_launch(b.SA, r, A->d, k, seed, prec, b.GSA, b.scratch, ctx->sm_count, ctx->stream);
+        *sk = b.GSA;
+        *rows = k;
+    }
+    return e;
+}
+
+// scratch after the sketch: [C = B^T B][its partials][pivoted factor][columns K]
+struct CssBufs {
+    double* C;
+    void* gpart;
+    void* L;
+    int32_t* cols;
+    void* rest;
+};
+size_t css_bytes(int64_t rows, int64_t d, int64_t c) {
+    return ws_round((size_t)d * d * 8) + ws_round(sketch_gram64_workspace_bytes(rows, d)) +
+           ws_round(pivchol_workspace_bytes(d, c)) + ws_round((size_t)c * 4) + 1024;
+}
+CssBufs css_carve(void* scratch, int64_t rows, int64_t d, int64_t c) {
+    WsCarver wc{(char*)scratch, 0};
+    CssBufs b;
+    b.C = wc.take<double>((size_t)d * d);
+    b.gpart = wc.take<char>(sketch_gram64_workspace_bytes(rows, d));
+    b.L = wc.take<char>(pivchol_workspace_bytes(d, c));
+    b.cols = wc.take<int32_t>((size_t)c);
+    b.rest = wc.take<char>(0);
+    return b;
+}
+
+int css_checks(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int64_t c) {
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    rc = check_sketch_args(ctx, A, r, k, prec);
+    if (rc) return rc;
+    if (c < 1 || c > A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "c must be in [1, d]");
+    if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "column selection supports d <= 1024");
+    return LSK_OK;
+}
+
+// Alg. 9 into scratch: returns the sketch (for Alg. 16) and the CSS buffers
+cudaError_t css_run(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, int64_t c,
+                    const SketchBufs& b, const float** sk, int64_t* rows, CssBufs* cb) {
+    cudaError_t e = sketch_only(ctx, A, r, k, seed, prec, b, sk, rows);
+    if (e != cudaSuccess) return e;
+    *cb = css_carve(b.scratch, *rows, A->d, c);
+    e = sketch_gram64_launch(*sk, *rows, A->d, cb->C, cb->gpart, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return e;
+    return pivchol_launch(cb->C, A->d, c, cb->cols, cb->L, ctx->flag, ctx->stream);
+}
+
+}  // namespace
+
+int lsk_column_select(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                      int64_t c, int32_t* cols) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = css_checks(ctx, A, r, k, prec, c);
+    if (rc) return rc;
+    if (!cols) return fail(ctx, LSK_ERR_INVALID_ARG, "cols is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int64_t rows = k > 0 ? k : r;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, A->d, c)));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    const float* sk;
+    int64_t sr;
+    CssBufs cb;
+    cudaError_t e = css_run(ctx, A, r, k, seed, prec, c, b, &sk, &sr, &cb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cols, cb.cols, (size_t)c * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_column_select");
+    return finish(ctx, "lsk_column_select");
+}
+
+int lsk_leverage_scores_hrn(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                            int64_t c, int32_t exact, float* theta, int32_t* cols) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = css_checks(ctx, A, r, k, prec, c);
+    if (rc) return rc;
+    if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int64_t d = A->d, rows = k > 0 ? k : r;
+    // after the selection: [Gram of A or B[:, K]][its workspace][C_KK][factor ws][E_K R^-1][row-norm ws]
+    const size_t gws = exact ? ws_round(gram_workspace_bytes(A, ctx->sm_count)) + ws_round((size_t)d * d * 8)
+                             : ws_round((size_t)rows * c * 4) + ws_round(qr_workspace_bytes(rows, c));
+    const size_t tail = gws + ws_round((size_t)c * c * 8) + ws_round(qr_from_gram_workspace_bytes(c)) +
+                        ws_round((size_t)d * c * 4) + ws_round(rownorms_workspace_bytes(A, c, 0, prec)) + 4096;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, d, c) + tail));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    const float* sk;
+    int64_t sr;
+    CssBufs cb;
+    cudaError_t e = css_run(ctx, A, r, k, seed, prec, c, b, &sk, &sr, &cb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_hrn (selection)");
+    WsCarver wc{(char*)cb.rest, 0};
+    if (exact) {
+        // Alg. 14: Alg. 13 on A[:, K] -- the Gram of A in FP64, its K x K block,
+        // R from it (FP64 accurate) and ||A_i E_K R^-1||^2
+        void* gw = wc.take<char>(gram_workspace_bytes(A, ctx->sm_count));
+        double* G = wc.take<double>((size_t)d * d);
+        double* Csub = wc.take<double>((size_t)c * c);
+        void* qw = wc.take<char>(qr_from_gram_workspace_bytes(c));
+        e = gram64_launch(A, G, gw, ctx->flag, ctx->sm_count, ctx->stream);
+        if (e == cudaSuccess) e = gather_sub_gram_launch(G, d, cb.cols, c, Csub, ctx->stream);
+        if (e == cudaSuccess) e = qr_from_gram_launch(Csub, c, nullptr, b.Rinv64, b.Rinv32, qw, ctx->flag, ctx->stream);
+    } else {
+        // Alg. 16: Alg. 15 on A[:, K] with the sketch restricted to K
+        float* Bk = wc.take<float>((size_t)rows * c);
+        void* qw = wc.take<char>(qr_workspace_bytes(rows, c));
+        e = gather_cols_launch(sk, rows, d, cb.cols, c, Bk, ctx->stream);
+        if (e == cudaSuccess)
+            e = qr_launch(Bk, rows, c, nullptr, b.Rinv64, b.Rinv32, qw, ctx->flag, ctx->sm_count, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_hrn (factor)");
+    float* Bf = wc.take<float>((size_t)d * c);
+    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, prec));
+    e = embed_rows_launch(b.Rinv32, c, cb.cols, d, Bf, ctx->stream);
+    if (e == cudaSuccess)
+        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e == cudaSuccess && cols)
+        e = cudaMemcpyAsync(cols, cb.cols, (size_t)c * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_hrn (row norms)");
+    return finish(ctx, "lsk_leverage_scores_hrn");
+}
+
 void lsk_lsq_default_opts(lsk_lsq_opts* o, int64_t d) {
     if (!o) return;
     memset(o, 0, sizeof(*o));

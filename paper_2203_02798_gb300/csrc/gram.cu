@@ -93,9 +93,10 @@ __global__ void __launch_bounds__(256) gram_dense_kernel(const float* __restrict
         for (int b = 0; b < 4; ++b) P[(4 * ty + a) * GT + 4 * tx + b] = acc64[a][b] + (double)acc[a][b];
 }
 
+template <typename OutT>
 __global__ void gram_dense_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
                                          int64_t d, double alpha, double beta,
-                                         float* __restrict__ C) {
+                                         OutT* __restrict__ C) {
     const int nt = (int)((d + GT - 1) / GT);
     const int ntiles = nt * (nt + 1) / 2;
     const int64_t len = d * d;
@@ -114,7 +115,7 @@ __global__ void gram_dense_reduce_kernel(const double* __restrict__ part, int64_
         for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * GT * GT + w];
         double v = alpha * s;
         if (beta != 0.0) v += beta * (double)C[e];
-        C[e] = (float)v;
+        C[e] = (OutT)v;
     }
 }
 
@@ -160,8 +161,9 @@ __global__ void gram_csr_kernel(const float* __restrict__ V, const int32_t* __re
     for (int64_t e = threadIdx.x; e < sl * d; e += blockDim.x) P[e] = S[e];
 }
 
+template <typename OutT>
 __global__ void gram_csr_reduce_kernel(const float* __restrict__ part, int64_t nblocks, int64_t d,
-                                       double alpha, double beta, float* __restrict__ C) {
+                                       double alpha, double beta, OutT* __restrict__ C) {
     const int64_t len = d * d;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
@@ -169,7 +171,7 @@ __global__ void gram_csr_reduce_kernel(const float* __restrict__ part, int64_t n
         for (int64_t z = 0; z < nblocks; ++z) s += (double)part[z * len + e];
         double v = alpha * s;
         if (beta != 0.0) v += beta * (double)C[e];
-        C[e] = (float)v;
+        C[e] = (OutT)v;
     }
 }
 
@@ -223,8 +225,9 @@ size_t gram_workspace_bytes(const lsk_mat* A, int sm_count) {
     return ws_round((size_t)p.nblocks * A->d * A->d * 4);
 }
 
-cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag,
-                        int sm_count, cudaStream_t st) {
+template <typename OutT>
+cudaError_t gram_launch_t(const lsk_mat* A, double alpha, double beta, OutT* C, void* ws, int* flag,
+                          int sm_count, cudaStream_t st) {
     const int64_t n = A->n, d = A->d;
     const int64_t len = d * d;
     int64_t rg = (len + 255) / 256;
@@ -234,7 +237,7 @@ cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, v
         double* part = (double*)ws;
         dim3 grid((unsigned)p.ntiles, (unsigned)p.nchunks);
         LSK_PROF("gram_dense", st) gram_dense_kernel<<<grid, 256, 0, st>>>((const float*)A->values, A->ld, n, d, p.rows_per, part);
-        LSK_PROF("gram_reduce", st) gram_dense_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(part, p.nchunks, d, alpha, beta, C);
+        LSK_PROF("gram_reduce", st) gram_dense_reduce_kernel<OutT><<<(unsigned)rg, 256, 0, st>>>(part, p.nchunks, d, alpha, beta, C);
     } else {
         const CsrPlan p = csr_plan(n, d, sm_count);
         if (p.smem > 48 * 1024) {
@@ -245,7 +248,16 @@ cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, v
         dim3 grid((unsigned)p.nblocks, (unsigned)p.nslices);
         LSK_PROF("gram_csr", st) gram_csr_kernel<<<grid, 256, p.smem, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
                                                    A->nnz, d, p.slice_rows, p.rows_per, part, flag);
-        LSK_PROF("gram_reduce", st) gram_csr_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(part, p.nblocks, d, alpha, beta, C);
+        LSK_PROF("gram_reduce", st) gram_csr_reduce_kernel<OutT><<<(unsigned)rg, 256, 0, st>>>(part, p.nblocks, d, alpha, beta, C);
     }
     return cudaGetLastError();
+}
+
+cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag,
+                        int sm_count, cudaStream_t st) {
+    return gram_launch_t<float>(A, alpha, beta, C, ws, flag, sm_count, st);
+}
+
+cudaError_t gram64_launch(const lsk_mat* A, double* C, void* ws, int* flag, int sm_count, cudaStream_t st) {
+    return gram_launch_t<double>(A, 1.0, 0.0, C, ws, flag, sm_count, st);
 }

@@ -210,6 +210,8 @@ cudaError_t gauss_debug_launch(int64_t k, int64_t r, uint64_t seed, int32_t prec
 
 // gram.cu
 size_t gram_workspace_bytes(const lsk_mat* A, int sm_count);
+// A^T A with FP64 output (the same partials, summed and stored in FP64)
+cudaError_t gram64_launch(const lsk_mat* A, double* C, void* ws, int* flag, int sm_count, cudaStream_t st);
 cudaError_t gram_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws,
                         int* flag, int sm_count, cudaStream_t st);
 
@@ -232,6 +234,14 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
 
 // qr.cu
 size_t qr_workspace_bytes(int64_t k, int64_t d);
+// the two halves of qr_launch: C = B^T B in FP64 (pair-FP32 products), then
+// R, R^-1 from an FP64 Gram C (d <= 1024; C is overwritten when d > 256)
+size_t sketch_gram64_workspace_bytes(int64_t k, int64_t d);
+cudaError_t sketch_gram64_launch(const float* B, int64_t k, int64_t d, double* C, void* ws, int sm_count,
+                                 cudaStream_t st);
+size_t qr_from_gram_workspace_bytes(int64_t d);
+cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
+                                cudaStream_t st);
 cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv,
                       float* Rinv32, void* ws, int* flag, int sm_count, cudaStream_t st);
 
@@ -273,6 +283,16 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
 size_t jl_workspace_bytes(int64_t d, int64_t m);
 cudaError_t jl_launch(const double* Rinv64, int64_t d, int64_t m, uint64_t seed, float* X32, void* ws,
                       cudaStream_t st);
+
+// css.cu: column subset selection (Alg. 9) pieces
+size_t pivchol_workspace_bytes(int64_t d, int64_t c);
+cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, int32_t* cols, void* ws, int* flag,
+                           cudaStream_t st);
+cudaError_t gather_sub_gram_launch(const double* C, int64_t d, const int32_t* cols, int64_t c, double* Csub,
+                                   cudaStream_t st);
+cudaError_t gather_cols_launch(const float* B, int64_t rows, int64_t d, const int32_t* cols, int64_t c, float* Bk,
+                               cudaStream_t st);
+cudaError_t embed_rows_launch(const float* X, int64_t c, const int32_t* cols, int64_t d, float* Bf, cudaStream_t st);
 
 // jlt.cu: Gaussian sketch of a CSR matrix (Alg. 4), C = G A, stream 3
 bool jlt_supported(int64_t d, int64_t m);

@@ -352,29 +352,36 @@ QrPlan qr_plan(int64_t k, int64_t d) {
 
 }  // namespace
 
-size_t qr_workspace_bytes(int64_t k, int64_t d) {
+size_t sketch_gram64_workspace_bytes(int64_t k, int64_t d) {
     const QrPlan p = qr_plan(k, d);
-    const int64_t nbk = (d + NB - 1) / NB;
-    size_t rest = ws_round((size_t)nbk * NB * NB * 8);
-    if (d <= 256 && qr_mixed_workspace_bytes(d) > rest) rest = qr_mixed_workspace_bytes(d);
-    return ws_round((size_t)d * d * 8) + ws_round((size_t)p.nchunks * p.ntiles * QT * QT * 8) + rest;
+    return ws_round((size_t)p.nchunks * p.ntiles * QT * QT * 8);
 }
 
-cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv, float* Rinv32,
-                      void* ws, int* flag, int sm_count, cudaStream_t st) {
-    if (d > 1024) return cudaErrorInvalidValue;
+cudaError_t sketch_gram64_launch(const float* B, int64_t k, int64_t d, double* C, void* ws, int sm_count,
+                                 cudaStream_t st) {
     const QrPlan p = qr_plan(k, d);
-    WsCarver wc{(char*)ws, 0};
-    double* C = wc.take<double>((size_t)d * d);
-    double* part = wc.take<double>((size_t)p.nchunks * p.ntiles * QT * QT);
-    const int64_t nbk = (d + NB - 1) / NB;
-    double* Ldiag = wc.take<double>((size_t)nbk * NB * NB);
+    double* part = (double*)ws;
     LSK_PROF("qr_gram64", st) sketch_gram64_kernel<<<dim3((unsigned)p.ntiles, (unsigned)p.nchunks), 256, 0, st>>>(B, k, d, p.rows_per,
                                                                                       part);
     int64_t g = (d * d + 255) / 256;
     if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
     LSK_PROF("qr_gram64", st) sketch_gram64_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, p.nchunks, d, C);
-    if (d <= 256) return qr_mixed_launch(C, d, R, Rinv, Rinv32, Ldiag, flag, st);
+    return cudaGetLastError();
+}
+
+size_t qr_from_gram_workspace_bytes(int64_t d) {
+    const int64_t nbk = (d + NB - 1) / NB;
+    size_t rest = ws_round((size_t)nbk * NB * NB * 8);
+    if (d <= 256 && qr_mixed_workspace_bytes(d) > rest) rest = qr_mixed_workspace_bytes(d);
+    return rest;
+}
+
+cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
+                                cudaStream_t st) {
+    if (d > 1024) return cudaErrorInvalidValue;
+    if (d <= 256) return qr_mixed_launch(C, d, R, Rinv, Rinv32, ws, flag, st);
+    const int64_t nbk = (d + NB - 1) / NB;
+    double* Ldiag = (double*)ws;
     for (int64_t K = 0; K < nbk; ++K) {
         const unsigned panel_blocks = (unsigned)(nbk - K);   // diag + blocks below
         LSK_PROF("qr_cholesky", st) chol_panel_kernel<<<panel_blocks, 64, 0, st>>>(C, d, K, Ldiag, flag);
@@ -384,11 +391,24 @@ cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* R
     LSK_PROF("qr_cholesky", st) copy_diag_kernel<<<(unsigned)nbk, NB * NB, 0, st>>>(C, d, Ldiag);
     rank_check_kernel<<<1, 256, 0, st>>>(C, d, flag);
     const unsigned tg = (unsigned)((d * 32 + 127) / 128);
-    if (d <= 256)
-        LSK_PROF("qr_trinv", st) trinv_kernel<8><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
-    else
-        LSK_PROF("qr_trinv", st) trinv_kernel<32><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
+    LSK_PROF("qr_trinv", st) trinv_kernel<32><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
     return cudaGetLastError();
+}
+
+size_t qr_workspace_bytes(int64_t k, int64_t d) {
+    return ws_round((size_t)d * d * 8) + sketch_gram64_workspace_bytes(k, d) + qr_from_gram_workspace_bytes(d);
+}
+
+cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv, float* Rinv32,
+                      void* ws, int* flag, int sm_count, cudaStream_t st) {
+    if (d > 1024) return cudaErrorInvalidValue;
+    WsCarver wc{(char*)ws, 0};
+    double* C = wc.take<double>((size_t)d * d);
+    void* part = wc.take<char>(sketch_gram64_workspace_bytes(k, d));
+    void* rest = wc.take<char>(qr_from_gram_workspace_bytes(d));
+    cudaError_t e = sketch_gram64_launch(B, k, d, C, part, sm_count, st);
+    if (e != cudaSuccess) return e;
+    return qr_from_gram_launch(C, d, R, Rinv, Rinv32, rest, flag, st);
 }
 
 bool qr_group_supported(int64_t k, int64_t d) { return d >= 1 && d <= 256 && k >= d; }

@@ -1,0 +1,105 @@
+"""GPU parity of column subset selection (Alg. 9) and the leverage scores on
+the selected columns (Alg. 14, Alg. 16) against the oracle, same seeds."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import css as ocss
+from oracle import gaussian as oga
+from oracle import leverage as olev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsk():
+    from paper_2203_02798_gb300 import build
+    build.build()
+    import paper_2203_02798_gb300 as p
+    return p
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def scaled(n, d, seed, lo=0.0, hi=2.0):
+    return workloads.dense_normal(n, d, seed=seed) * np.logspace(lo, hi, d).astype(np.float32)
+
+
+def test_column_select_dominant_columns(lsk):
+    A = workloads.dense_normal(20_000, 32, seed=1)
+    big = [29, 3, 17, 8]
+    A[:, big] *= np.array([1000.0, 300.0, 100.0, 30.0], dtype=np.float32)
+    cols = host(lsk.column_select(dev(A), 2048, 128, 5, 4))
+    lsk.context().sync()
+    assert list(cols) == big
+
+
+@pytest.mark.parametrize("prec,k", [("fp32", 128), ("bf16", 128), ("fp32", 0)])
+def test_column_select_matches_oracle(lsk, prec, k):
+    """Well-separated column norms: the pivot sequence is unique, so the
+    GPU's Gram-pivoted order equals the oracle's pivoted Householder order."""
+    n, d, r, c = 30_000, 48, 2304, 24
+    A = scaled(n, d, 2, 0.0, 3.0)
+    op = oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32
+    cols = host(lsk.column_select(dev(A), r, k, 7, c, prec))
+    lsk.context().sync()
+    ref = ocss.column_select_dense(A.astype(np.float64), r, k, 7, op, c)
+    assert list(cols) == list(ref)
+
+
+def test_column_select_csr(lsk):
+    n, d = 100_000, 40
+    V, J, I = workloads.csr_bernoulli(n, d, 0.05, seed=3)
+    scale = np.logspace(0, 3, d)
+    V = (V * scale[J]).astype(np.float32)
+    cols = host(lsk.column_select(lsk.csr_from_numpy(V, J, I, d), 1600, 96, 2, 12))
+    lsk.context().sync()
+    ref = ocss.column_select_csr(V, J, I, n, d, 1600, 96, 2, oga.PREC_FP32, 12)
+    assert list(cols) == list(ref)
+
+
+@pytest.mark.parametrize("exact", [True, False])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_leverage_scores_hrn(lsk, exact, prec):
+    n, d, r, k, c = 40_000, 64, 4096, 128, 20
+    A = scaled(n, d, 4, 0.0, 2.0)
+    op = oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32
+    theta, cols = lsk.leverage_scores_hrn(dev(A), r, k, 3, c, exact=exact, prec=prec)
+    lsk.context().sync()
+    theta = host(theta).astype(np.float64)
+    fn = ocss.hrn_exact_dense if exact else ocss.hrn_approx_dense
+    ref, K = fn(A.astype(np.float64), r, k, 3, op, c)
+    assert list(host(cols)) == list(K)
+    assert np.max(np.abs(theta - ref) / ref) <= 1e-3
+    if exact:
+        assert abs(theta.sum() - c) <= 1e-3 * c                 # trace of the projector
+
+
+def test_hrn_approx_with_all_columns_is_leverage(lsk):
+    """c = d: Alg. 16 is Alg. 15 (the column order does not change A R^-1's row norms)."""
+    A = scaled(30_000, 32, 5)
+    theta, _ = lsk.leverage_scores_hrn(dev(A), 1024, 64, 9, 32, exact=False)
+    ell = lsk.leverage_scores(dev(A), 1024, 64, 9)
+    lsk.context().sync()
+    theta, ell = host(theta).astype(np.float64), host(ell).astype(np.float64)
+    assert np.max(np.abs(theta - ell) / ell) <= 1e-4
+
+
+def test_column_select_planted_rank(lsk):
+    """Rank 6 of d = 16: six independent pivots, then the deferred rank error."""
+    rng = np.random.default_rng(6)
+    basis = rng.standard_normal((10_000, 6))
+    A = np.hstack([basis, basis @ rng.standard_normal((6, 10))]).astype(np.float32)
+    cols = lsk.column_select(dev(A), 1024, 64, 1, 10)
+    with pytest.raises(lsk.LskError, match="RANK_DEFICIENT"):
+        lsk.context().sync()
+    cols = host(cols)
+    assert np.linalg.matrix_rank(A[:, cols[:6]].astype(np.float64)) == 6
+    assert sorted(set(cols)) == sorted(cols)                    # a selection, no repeats
