@@ -277,6 +277,22 @@ def main():
         jms /= steps
         out["csrjlt"] = {"ms": jms, "gaussians_per_s": 400 * 1_000_000 / (jms * 1e-3),
                          "nnz": int(len(V)), "workload": "CSR 1M x 200, p = 0.01, m = 400"}
+        del Acsr, V, J, I
+        # column subset selection (Alg. 9) of 64 columns and the scores on them
+        # (Alg. 16 sketched, Alg. 14 exact) on the workload's A
+        c = 64
+        runs = {"column_select": lambda: lsk.column_select(A, R_SKETCH, K_GAUSS, SEED, c, args.prec, ctx=ctx),
+                "hrn_approx": lambda: lsk.leverage_scores_hrn(A, R_SKETCH, K_GAUSS, SEED, c, exact=False,
+                                                              prec=args.prec, out=ell, ctx=ctx),
+                "hrn_exact": lambda: lsk.leverage_scores_hrn(A, R_SKETCH, K_GAUSS, SEED, c, exact=True,
+                                                             prec=args.prec, out=ell, ctx=ctx)}
+        for name, fn in runs.items():
+            fn()
+            ctx.sync()
+            cms, _, _ = timed(fn, steps)
+            cms /= steps
+            out[name] = {"ms": cms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, cms), "c": c,
+                         "workload": "dense 4M x 256, r = 65,536, k = 512"}
         return out
 
     def barrier():

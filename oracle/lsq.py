@@ -1,5 +1,6 @@
-"""Least squares through sketches (oracle): sketch-and-precondition (Alg. 12)
-with LSQR, and sketch-and-solve (Alg. 11).
+"""Least squares (oracle): through the Gram pseudoinverse (Alg. 10), through
+sketches: sketch-and-precondition (Alg. 12) with LSQR, and sketch-and-solve
+(Alg. 11).
 
 Alg. 12 (Sec. 4.2): sketch A, factor the sketch, take N as the inverse
 factor, solve min_y ||A N y - b|| with "a parallel preconditioned iterative
@@ -144,3 +145,14 @@ def sketch_solve_csr(V, J, I, n, d, b, r, k, seed, prec=0):
         V2[I2[i + 1] - 1] = b[i]
         J2[I2[i + 1] - 1] = d
     return sketch_solve(leverage.sketch_csr(V2, J2, I2, n, d + 1, r, k, seed, prec))
+
+
+def least_squares_gram(A, b, rcond=1e-12):
+    """Alg. 10: B = A^T A, B = V Sigma V^T (eigen-decomposition of the
+    symmetric B, the library step), c = A^T b, x = V Sigma^+ V^T c, with
+    eigenvalues below rcond * max truncated."""
+    A = np.asarray(A, dtype=np.float64)
+    w, V = np.linalg.eigh(A.T @ A)
+    keep = w > rcond * w.max()
+    c = A.T @ np.asarray(b, dtype=np.float64)
+    return V[:, keep] @ ((V[:, keep].T @ c) / w[keep])

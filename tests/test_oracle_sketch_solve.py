@@ -126,3 +126,15 @@ def test_csrjlt_stream_is_its_own():
     c = ga.gaussian_columns(8, 0, 16, 5, ga.PREC_FP32, ga.STREAM_PI)
     assert not np.allclose(a, b) and not np.allclose(a, c)
     assert abs(np.corrcoef(a.ravel(), b.ravel())[0, 1]) < 0.35
+
+
+def test_least_squares_gram_matches_qr_and_recovers_consistent_systems():
+    """Alg. 10 against the Householder least-squares solution (a different
+    route) on a well-conditioned problem, and exact on b = A x*."""
+    rng = np.random.default_rng(20)
+    A = rng.standard_normal((3000, 15)) * np.logspace(0, 1, 15)
+    b = rng.standard_normal(3000)
+    x_qr = lsq.least_squares_qr(A, b)
+    assert np.linalg.norm(lsq.least_squares_gram(A, b) - x_qr) <= 1e-11 * np.linalg.norm(x_qr)
+    xs = np.linspace(-2, 2, 15)
+    assert np.linalg.norm(lsq.least_squares_gram(A, A @ xs) - xs) <= 1e-11 * np.linalg.norm(xs)
