@@ -187,6 +187,23 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                            int64_t m, uint64_t seed, int32_t prec, float* ell,
                            double* R_out);
 
+/* Exact leverage scores (Alg. 13): B = A^T A in FP64 (FP32 partial sums
+ * over row blocks, folded in FP64), R from B (FP64 accurate; Cholesky in
+ * place of the SVD of step 2 at full rank), theta_i = ||A_i R^-1||^2
+ * (Alg. 8).  theta: device n floats; R_out: NULL or device d*d doubles.
+ * Rank deficiency is the deferred LSK_ERR_RANK_DEFICIENT; d <= 1024. */
+int lsk_leverage_scores_exact(lsk_ctx* ctx, const lsk_mat* A, int32_t prec,
+                              float* theta, double* R_out);
+
+/* Least squares through the Gram matrix (Alg. 10): B = A^T A in FP64, R
+ * from B, x = R^-1 R^-T A^T b (the pseudoinverse of step 2 at full rank),
+ * then `refine` (0..10) steps x += R^-1 R^-T A^T (b - A x), all in FP64.
+ * b: device n doubles; x: device d doubles (written).  The error of the
+ * Gram route grows with cond(A)^2; the refinement steps bring it back to
+ * cond(A) eps while cond(A)^2 times the Gram's rounding stays below 1. */
+int lsk_least_squares_gram(lsk_ctx* ctx, const lsk_mat* A, const double* b,
+                           int32_t refine, double* x);
+
 /* Column subset selection (Alg. 9): B = G S A (k > 0; S A when k == 0)
  * with the draws of lsk_leverage_scores, then the first c pivots of a
  * column-pivoted QR of B, taken as the diagonally pivoted Cholesky of

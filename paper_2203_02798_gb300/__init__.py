@@ -92,6 +92,8 @@ _SIGS = {
     "lsk_sketch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I64, _U64, _I32, _P]),
     "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
     "lsk_column_select": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
+    "lsk_leverage_scores_exact": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I32, _P, _P]),
+    "lsk_least_squares_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I32, _P]),
     "lsk_leverage_scores_hrn": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _I32, _P, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
     "lsk_sketch_precondition_lsq": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _P,
@@ -314,6 +316,27 @@ def leverage_scores_jl(A, r, k, m, seed, prec="fp32", out=None, return_R=False, 
     ctx._call("lsk_leverage_scores_jl", ctypes.byref(mat), int(r), int(k), int(m), int(seed), _prec(prec),
               _ptr(ell), _ptr(R))
     return (ell, R) if return_R else ell
+
+
+def leverage_scores_exact(A, prec="fp32", out=None, return_R=False, ctx=None):
+    """lsk_leverage_scores_exact (Alg. 13): ||A_i R^-1||^2 with R from A^T A."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    theta = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
+    ctx._call("lsk_leverage_scores_exact", ctypes.byref(mat), _prec(prec), _ptr(theta), _ptr(R))
+    return (theta, R) if return_R else theta
+
+
+def least_squares_gram(A, b, refine=2, out=None, ctx=None):
+    """lsk_least_squares_gram (Alg. 10): x from R of A^T A, refined in FP64."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    if b.dtype != torch.float64 or not b.is_contiguous() or b.device != _dev(A):
+        raise ValueError("b must be a contiguous float64 tensor on A's device")
+    x = out if out is not None else torch.empty(d, dtype=torch.float64, device=_dev(A))
+    ctx._call("lsk_least_squares_gram", ctypes.byref(mat), _ptr(b), int(refine), _ptr(x))
+    return x
 
 
 def column_select(A, r, k, seed, c, prec="fp32", ctx=None):

@@ -567,6 +567,78 @@ int lsk_leverage_scores_hrn(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k
     return finish(ctx, "lsk_leverage_scores_hrn");
 }
 
+// ---- Alg. 13 and Alg. 10: through the FP64 Gram of A ----------------------
+namespace {
+// G = A^T A (FP64) and R^-1 from it into Rinv64 / Rinv32 (d x d); scratch carved after
+cudaError_t gram_factor(lsk_ctx* ctx, const lsk_mat* A, double* G, void* gws, void* qws, double* R_out,
+                        double* Rinv64, float* Rinv32) {
+    cudaError_t e = gram64_launch(A, G, gws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return e;
+    return qr_from_gram_launch(G, A->d, R_out, Rinv64, Rinv32, qws, ctx->flag, ctx->stream);
+}
+size_t gram_factor_bytes(const lsk_mat* A, int sm) {
+    return ws_round((size_t)A->d * A->d * 8) * 3 + ws_round((size_t)A->d * A->d * 4) +
+           ws_round(gram_workspace_bytes(A, sm)) + ws_round(qr_from_gram_workspace_bytes(A->d)) + 2048;
+}
+}  // namespace
+
+int lsk_leverage_scores_exact(lsk_ctx* ctx, const lsk_mat* A, int32_t prec, float* theta, double* R_out) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "d <= 1024");
+    if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    const int64_t d = A->d;
+    rc = ws_ensure(ctx, gram_factor_bytes(A, ctx->sm_count) + ws_round(rownorms_workspace_bytes(A, d, 1, prec)));
+    if (rc) return rc;
+    WsCarver wc{(char*)ctx->ws, 0};
+    double* G = wc.take<double>((size_t)d * d);
+    double* Rinv64 = wc.take<double>((size_t)d * d);
+    float* Rinv32 = wc.take<float>((size_t)d * d);
+    void* gws = wc.take<char>(gram_workspace_bytes(A, ctx->sm_count));
+    void* qws = wc.take<char>(qr_from_gram_workspace_bytes(d));
+    void* rws = wc.take<char>(rownorms_workspace_bytes(A, d, 1, prec));
+    cudaError_t e = gram_factor(ctx, A, G, gws, qws, R_out, Rinv64, Rinv32);
+    if (e == cudaSuccess)
+        e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, prec, theta, rws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_exact");
+    return finish(ctx, "lsk_leverage_scores_exact");
+}
+
+int lsk_least_squares_gram(lsk_ctx* ctx, const lsk_mat* A, const double* b, int32_t refine, double* x) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "d <= 1024");
+    if (!x || (!b && A->n > 0)) return fail(ctx, LSK_ERR_INVALID_ARG, "b / x is NULL");
+    if (refine < 0 || refine > 10) return fail(ctx, LSK_ERR_INVALID_ARG, "refine must be in [0, 10]");
+    const int64_t d = A->d;
+    rc = ws_ensure(ctx, gram_factor_bytes(A, ctx->sm_count) + ws_round(atr64_workspace_bytes(A)) +
+                            ws_round((size_t)d * 8));
+    if (rc) return rc;
+    WsCarver wc{(char*)ctx->ws, 0};
+    double* G = wc.take<double>((size_t)d * d);
+    double* Rinv64 = wc.take<double>((size_t)d * d);
+    float* Rinv32 = wc.take<float>((size_t)d * d);
+    void* gws = wc.take<char>(gram_workspace_bytes(A, ctx->sm_count));
+    void* qws = wc.take<char>(qr_from_gram_workspace_bytes(d));
+    void* aws = wc.take<char>(atr64_workspace_bytes(A));
+    double* atr = wc.take<double>((size_t)d);
+    cudaError_t e = gram_factor(ctx, A, G, gws, qws, nullptr, Rinv64, Rinv32);
+    // x = R^-1 R^-T A^T b, then refinement steps on the residual
+    for (int t = 0; t <= refine && e == cudaSuccess; ++t) {
+        e = atr64_launch(A, b, t ? x : nullptr, atr, aws, ctx->flag, ctx->sm_count, ctx->stream);
+        if (e == cudaSuccess) e = seminormal_launch(atr, Rinv64, d, t ? 1 : 0, x, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_least_squares_gram");
+    return finish(ctx, "lsk_least_squares_gram");
+}
+
 void lsk_lsq_default_opts(lsk_lsq_opts* o, int64_t d) {
     if (!o) return;
     memset(o, 0, sizeof(*o));

@@ -300,6 +300,13 @@ size_t jlt_workspace_bytes(int64_t n, int64_t d, int64_t m, int sm_count);
 cudaError_t jlt_launch(const lsk_mat* A, int64_t m, uint64_t seed, int32_t prec, float* C, void* ws, int* flag,
                        int sm_count, cudaStream_t st);
 
+// lsq.cu: atr = A^T (b - A x) in FP64 (x == nullptr: x = 0)
+size_t atr64_workspace_bytes(const lsk_mat* A);
+cudaError_t atr64_launch(const lsk_mat* A, const double* b, const double* x, double* atr, void* ws, int* flag,
+                         int sm_count, cudaStream_t st);
+// solve.cu: x (+)= R^-1 R^-T c (one block, d <= 1024)
+cudaError_t seminormal_launch(const double* c, const double* Rinv64, int64_t d, int add, double* x, cudaStream_t st);
+
 // solve.cu: sketch-and-solve (Alg. 11) given the sketch A~ of A and R^-1
 size_t solve_workspace_bytes(int64_t r, int64_t k, int64_t d);
 cudaError_t solve_launch(const lsk_mat* A, const double* b, int64_t r, int64_t k, uint64_t seed, int32_t prec,

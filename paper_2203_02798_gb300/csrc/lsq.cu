@@ -540,6 +540,54 @@ void lsqr_pass(const lsk_mat* A, int nb, size_t sh32, const float* p, const Lsqr
 
 }  // namespace
 
+// atr = A^T (b - A x) in FP64 (the residual pass of the refinement loop,
+// reduced in block order); x == nullptr means x = 0.
+namespace {
+__global__ void sum_qpart_kernel(const double* __restrict__ qpart, int nblocks, int64_t d, double* __restrict__ atr) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < nblocks; ++z) s += qpart[(int64_t)z * d + j];
+        atr[j] = s;
+    }
+}
+}  // namespace
+
+size_t atr64_workspace_bytes(const lsk_mat* A) {
+    const int nb = kMaxPassBlocks;
+    return ws_round((size_t)(A->n > 0 ? A->n : 1) * 4) + ws_round((size_t)nb * A->d * 8) + ws_round((size_t)nb * 8) +
+           ws_round((size_t)A->d * 8) + 1024;
+}
+
+cudaError_t atr64_launch(const lsk_mat* A, const double* b, const double* x, double* atr, void* ws, int* flag,
+                         int sm_count, cudaStream_t st) {
+    const int64_t n = A->n, d = A->d;
+    const int nb = pass_grid(A, sm_count);
+    WsCarver wc{(char*)ws, 0};
+    float* u = wc.take<float>(n > 0 ? n : 1);
+    double* qpart = wc.take<double>((size_t)nb * d);
+    double* sspart = wc.take<double>(nb);
+    double* zero = wc.take<double>(d);
+    cudaError_t e = cudaSuccess;
+    if (!x) {
+        if ((e = cudaMemsetAsync(zero, 0, (size_t)d * 8, st)) != cudaSuccess) return e;
+        x = zero;
+    }
+    const bool dense = A->kind == LSK_DENSE;
+    const size_t sh64 = dense ? (size_t)9 * d * 8 : (size_t)2 * d * 8;
+    if (sh64 > 48 * 1024) {
+        if ((e = allow_dynamic_smem(resid64_dense_kernel)) != cudaSuccess) return e;
+        if ((e = allow_dynamic_smem(resid64_csr_kernel)) != cudaSuccess) return e;
+    }
+    if (dense)
+        LSK_PROF("lsq_resid64", st) resid64_dense_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->ld, n, d, b, x,
+                                                                                          u, qpart, sspart);
+    else
+        LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr,
+                                                                                        n, A->nnz, d, b, x, u, qpart, sspart, flag);
+    sum_qpart_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(qpart, nb, d, atr);
+    return cudaGetLastError();
+}
+
 size_t lsq_workspace_bytes(const lsk_mat* A) {
     const int64_t n = A->n, d = A->d;
     const int nb = kMaxPassBlocks;

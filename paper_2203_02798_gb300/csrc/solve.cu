@@ -112,6 +112,12 @@ __global__ void __launch_bounds__(1024) seminormal_kernel(const double* __restri
 
 }  // namespace
 
+cudaError_t seminormal_launch(const double* c, const double* Rinv64, int64_t d, int add, double* x, cudaStream_t st) {
+    if (d > 1024) return cudaErrorInvalidValue;
+    seminormal_kernel<<<1, 1024, 0, st>>>(c, Rinv64, (int)d, add, x);
+    return cudaGetLastError();
+}
+
 size_t solve_workspace_bytes(int64_t r, int64_t k, int64_t d) {
     const int64_t rows = k > 0 ? k : r;
     const int64_t gblk = (r + kColsPerBlock - 1) / kColsPerBlock;

@@ -124,3 +124,48 @@ def test_csrjlt_empty_rows_and_dense_rejected(lsk):
     assert np.all(C == 0)
     with pytest.raises(lsk.LskError, match="UNSUPPORTED"):
         lsk.csrjlt(dev(workloads.dense_normal(100, 4, seed=1)), 8, 1)
+
+
+# ------------------------------------------- Alg. 13 and Alg. 10 (Gram route)
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_leverage_scores_exact_dense(lsk, prec):
+    n, d = 50_000, 48
+    A = workloads.dense_normal(n, d, seed=8) * np.logspace(0, 1.5, d).astype(np.float32)
+    A[:7] *= 40.0                                                # a few high-leverage rows
+    theta = host(lsk.leverage_scores_exact(dev(A), prec)).astype(np.float64)
+    lsk.context().sync()
+    ref = olev.leverage_scores_exact_gram(A.astype(np.float64))
+    assert np.max(np.abs(theta - ref) / ref) <= 1e-3
+    assert abs(theta.sum() - d) <= 1e-3 * d
+
+
+def test_leverage_scores_exact_csr(lsk):
+    n, d = 80_000, 30
+    V, J, I = workloads.csr_bernoulli(n, d, 0.1, seed=9)
+    theta = host(lsk.leverage_scores_exact(lsk.csr_from_numpy(V, J, I, d))).astype(np.float64)
+    lsk.context().sync()
+    ref = olev.leverage_scores_exact_gram(dense_csr(V.astype(np.float64), J, I, n, d))
+    nz = ref > 0
+    assert np.all(theta[~nz] == 0)
+    assert np.max(np.abs(theta[nz] - ref[nz]) / ref[nz]) <= 1e-3
+
+
+@pytest.mark.parametrize("kind", ["dense", "csr"])
+def test_least_squares_gram(lsk, kind):
+    n, d = 60_000, 40
+    rng = np.random.default_rng(11)
+    if kind == "dense":
+        A = workloads.dense_normal(n, d, seed=12) * np.logspace(0, 1.5, d).astype(np.float32)
+        A64 = A.astype(np.float64)
+        Ad = dev(A)
+    else:
+        V, J, I = workloads.csr_bernoulli(n, d, 0.2, seed=12)
+        A64 = dense_csr(V.astype(np.float64), J, I, n, d)
+        Ad = lsk.csr_from_numpy(V, J, I, d)
+    b = A64 @ rng.standard_normal(d) + 0.2 * rng.standard_normal(n)
+    x = host(lsk.least_squares_gram(Ad, dev(b), refine=2))
+    lsk.context().sync()
+    x_ls = olsq.least_squares_qr(A64, b)
+    assert np.linalg.norm(x - x_ls) <= 1e-9 * np.linalg.norm(x_ls)
+    xo = olsq.least_squares_gram(A64, b)
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
