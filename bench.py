@@ -266,7 +266,6 @@ def main():
         ms /= steps
         out["sketch_solve"] = {"ms": ms, "GB/s": whole_job_rate(N_ROWS * D * 4 + N_ROWS * 8, world, ms),
                                "workload": "dense 4M x 256 + b, r = 65,536, k = 512"}
-        del b
         V, J, I = workloads.csr_bernoulli(1_000_000, 200, 0.01, seed=1)
         Acsr = lsk.csr_from_numpy(V, J, I, 200)
         C = torch.empty((400, 200), dtype=torch.float32, device="cuda")
@@ -285,14 +284,20 @@ def main():
                 "hrn_approx": lambda: lsk.leverage_scores_hrn(A, R_SKETCH, K_GAUSS, SEED, c, exact=False,
                                                               prec=args.prec, out=ell, ctx=ctx),
                 "hrn_exact": lambda: lsk.leverage_scores_hrn(A, R_SKETCH, K_GAUSS, SEED, c, exact=True,
-                                                             prec=args.prec, out=ell, ctx=ctx)}
+                                                             prec=args.prec, out=ell, ctx=ctx),
+                "leverage_exact": lambda: lsk.leverage_scores_exact(A, args.prec, out=ell, ctx=ctx),
+                "lsq_gram": lambda: lsk.least_squares_gram(A, bvec, refine=2, out=x, ctx=ctx)}
+        bvec = torch.randn(N_ROWS, dtype=torch.float64, device="cuda", generator=g)
         for name, fn in runs.items():
             fn()
             ctx.sync()
             cms, _, _ = timed(fn, steps)
             cms /= steps
-            out[name] = {"ms": cms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, cms), "c": c,
-                         "workload": "dense 4M x 256, r = 65,536, k = 512"}
+            out[name] = {"ms": cms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, cms),
+                         "workload": "dense 4M x 256" + (f", r = 65,536, k = 512, c = {c}"
+                                                         if name in ("column_select", "hrn_approx", "hrn_exact")
+                                                         else "")}
+        del b, bvec
         return out
 
     def barrier():
