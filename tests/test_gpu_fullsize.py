@@ -5,7 +5,9 @@ rows, one by one; properties that hold at any size are checked on all rows.
 
   config 2: CSR 1,000,000 x 200, p = 0.01, r = 40,000, k = 400, FP32
   config 3: dense 4,000,000 x 256 (column scales 10^U(-3,3)), r = 65,536,
-            k = 512, BF16 stages -- the bench's step
+            k = 512, BF16 stages -- the bench's step; also the "next" rows
+            on it: Alg. 15 with Pi, sketch-and-solve, column selection and
+            the Alg. 16 scores
   config 4: the 512-problem batch (graph-captured, grouped stages), three
             problems checked against the oracle, every problem's scores in
             [0, 1.5] with sum within the sketch's distortion band
@@ -18,6 +20,7 @@ import torch
 
 import workloads
 from oracle import countsketch as ocs
+from oracle import css as ocss
 from oracle import gaussian as oga
 from oracle import leverage as olev
 from oracle import lsq as olsq
@@ -46,19 +49,30 @@ def sample_rows(n, step, rng_seed=0):
     return np.unique(np.concatenate([np.arange(0, n, step), rng.integers(0, n, 2000), [n - 1]]))
 
 
-def test_config3_dense_4M_x_256_bf16(lsk):
+@pytest.fixture(scope="module")
+def config3():
+    """Config 3's A (4,000,000 x 256, column scales 10^U(-3,3)) and the
+    oracle's FP64 sketches of it (CountSketch r = 65,536, BF16 G with
+    k = 512), formed once for the tests of this module."""
     n, d, r, k, seed = 4_000_000, 256, 65_536, 512, 2
     A = np.empty((n, d), dtype=np.float32)
     workloads.dense_colscaled(n=n, d=d, seed=2, out=A)
+    SA = ocs.cs_sketch_dense(A, r, seed)                       # FP64, all 4M rows
+    GSA = oga.gauss_sketch(SA, k, seed, oga.PREC_BF16)
+    return dict(A=A, n=n, d=d, r=r, k=k, seed=seed, SA=SA, GSA=GSA, R=olev.sketch_R(GSA))
+
+
+def test_config3_dense_4M_x_256_bf16(lsk, config3):
+    c3 = config3
+    A, n, d = c3["A"], c3["n"], c3["d"]
     Ad = torch.from_numpy(A).cuda()
-    ell, R = lsk.leverage_scores(Ad, r, k, seed, "bf16", return_R=True)
+    ell, R = lsk.leverage_scores(Ad, c3["r"], c3["k"], c3["seed"], "bf16", return_R=True)
     lsk.context().sync()
     ell = ell.cpu().numpy().astype(np.float64)
     Rg = R.cpu().numpy()
     del Ad
     torch.cuda.empty_cache()
-    SA = ocs.cs_sketch_dense(A, r, seed)                       # FP64, all 4M rows
-    Ro = olev.sketch_R(oga.gauss_sketch(SA, k, seed, oga.PREC_BF16))
+    Ro = c3["R"]
     rows = sample_rows(n, 997)
     ref = sampled_scores(A[rows], Ro)
     assert np.max(np.abs(ell[rows] - ref) / ref) <= 1e-3
@@ -68,6 +82,57 @@ def test_config3_dense_4M_x_256_bf16(lsk):
     # sum of the estimates = ||A R^-1||_F^2 = sum of sigma_j^2 of A R^-1: d up to the
     # sketch's distortion (k = 2d Gaussian after CountSketch)
     assert 0.2 * d <= ell.sum() <= 5.0 * d
+
+
+def test_config3_jl_sketch_solve_and_column_selection(lsk, config3):
+    """The "next" rows at the bench's size: Alg. 15 with Pi (m = 64), sketch-
+    and-solve (Alg. 11) and column selection with the Alg. 16 scores (c = 64),
+    each against the oracle on the same FP64 sketch."""
+    c3 = config3
+    A, n, d, r, k, seed = c3["A"], c3["n"], c3["d"], c3["r"], c3["k"], c3["seed"]
+    Ro = c3["R"]
+    Ad = torch.from_numpy(A).cuda()
+    rows = sample_rows(n, 1999, 7)
+    # Alg. 15 with the right projection
+    ell = lsk.leverage_scores_jl(Ad, r, k, 64, seed, "bf16").cpu().numpy().astype(np.float64)
+    X = oqr.upper_triangular_inverse(Ro) @ oga.jl_matrix(d, 64, seed)
+    ref = np.sum((A[rows].astype(np.float64) @ X) ** 2, axis=1)
+    assert np.max(np.abs(ell[rows] - ref) / ref) <= 1e-3
+    # sketch-and-solve: b through the same S and G
+    rng = np.random.default_rng(31)
+    xs = rng.standard_normal(d) / np.linalg.norm(Ro, axis=0)
+    b = np.empty(n)
+    for i0 in range(0, n, 1 << 18):
+        b[i0:i0 + (1 << 18)] = A[i0:i0 + (1 << 18)].astype(np.float64) @ xs
+    b += rng.standard_normal(n) * 0.1 * np.std(b)
+    x = lsk.sketch_solve(Ad, torch.from_numpy(b).cuda(), r, k, seed, "bf16").cpu().numpy()
+    Sb = ocs.cs_sketch_dense(b[:, None], r, seed)
+    bt = oga.gauss_sketch(Sb, k, seed, oga.PREC_BF16)[:, 0]
+    xo = olsq.sketch_solve(np.hstack([c3["GSA"], bt[:, None]]))
+    res = lambda v: np.linalg.norm(c3["GSA"] @ v - bt)
+    assert res(x) <= (1 + 1e-6) * res(xo)
+    # column selection and the Alg. 16 scores on the selected columns
+    theta, cols = lsk.leverage_scores_hrn(Ad, r, k, seed, 64, exact=False, prec="bf16")
+    lsk.context().sync()
+    cols = cols.cpu().numpy()
+    perm, rdiag = ocss.pivoted_qr(c3["GSA"], 64)
+    assert len(set(cols)) == 64
+    mism = [j for j in range(64) if cols[j] != perm[j]]
+    if mism:
+        # the two sketches differ by rounding, so the order is unique only up to
+        # near-ties: at the first difference both columns must be (nearly)
+        # farthest from the span of the common prefix
+        j = mism[0]
+        Q = np.linalg.qr(c3["GSA"][:, perm[:j]])[0]
+        dist = lambda col: np.linalg.norm(c3["GSA"][:, col] - Q @ (Q.T @ c3["GSA"][:, col]))
+        assert abs(dist(cols[j]) - dist(perm[j])) <= 1e-5 * dist(perm[j])
+    Rk = olev.sketch_R(c3["GSA"][:, cols])
+    Y = A[rows][:, cols].astype(np.float64) @ oqr.upper_triangular_inverse(Rk)
+    ref = np.sum(Y * Y, axis=1)
+    theta = theta.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(theta[rows] - ref) / ref) <= 1e-3
+    del Ad
+    torch.cuda.empty_cache()
 
 
 def test_config2_csr_1M_x_200_fp32(lsk):
