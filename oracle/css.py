@@ -10,6 +10,12 @@ is swapped to position j, ties going to the lowest column index; then the
 reflector is applied.  Everything is float64.
 
 Alg. 14 (ls_hrn_exact): the exact leverage scores (Alg. 13) of A[:, K].
+
+"Truncate if needed" (Alg. 15 step 3, Alg. 13 step 2), read as a
+rank-revealing truncation: the numerical rank of the sketch is the number
+of column-pivoted QR steps with |R_jj| > rcond |R_00|, and the scores are
+those of A restricted to the columns those steps pick (they span the
+dominant column space): ``leverage_scores_truncated_dense``.
 Alg. 16 (ls_hrn_approx): Alg. 15 on A[:, K].  Reading: the sketch of A[:, K]
 is the sketch of A restricted to the columns K (column selection commutes
 with the left sketch G S), so the B of Alg. 9 is reused; R from the QR of
@@ -73,3 +79,22 @@ def hrn_approx_dense(A, r, k, seed, prec, c):
     K = perm[:c].copy()
     R = leverage.sketch_R(B[:, K])
     return rownorms.rownorms_prod_dense(A[:, K], qr.upper_triangular_inverse(R)), K
+
+
+def numerical_rank(rdiag, rcond):
+    """Steps of a column-pivoted QR with |R_jj| > rcond |R_00|."""
+    if len(rdiag) == 0 or rdiag[0] == 0.0:
+        return 0
+    return int(np.sum(rdiag > rcond * rdiag[0]))
+
+
+def leverage_scores_truncated_dense(A, r, k, seed, prec, rcond):
+    """(theta, rank, K): scores on the numerical-rank column subset of the
+    sketch (Alg. 15 with its truncation), R from the QR of B[:, K]."""
+    A = np.asarray(A, dtype=np.float64)
+    B = leverage.sketch_dense(A, r, k, seed, prec)
+    perm, rdiag = pivoted_qr(B)
+    rank = numerical_rank(rdiag, rcond)
+    K = perm[:rank].copy()
+    R = qr.qr_r(B[:, K])
+    return rownorms.rownorms_prod_dense(A[:, K], qr.upper_triangular_inverse(R)), rank, K

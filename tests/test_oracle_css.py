@@ -83,3 +83,27 @@ def test_hrn_scores_of_a_subset_sum_to_k():
     assert len(K) == 5 and abs(theta.sum() - 5.0) <= 1e-9
     theta2, K2 = css.hrn_approx_dense(A, 400, 48, 1, ga.PREC_FP32, 5)
     assert list(K2) == list(K) and 0.5 * 5 <= theta2.sum() <= 2.0 * 5
+
+
+def test_truncated_scores_on_planted_rank():
+    """A of rank 5 (d = 12): the truncation finds rank 5; the scores are those
+    of Alg. 15 on A[:, K] (the sketch of A restricted to K is the sketch of
+    A[:, K]); and they approximate the exact leverage scores of A, ||U_i||^2
+    over its 5 left singular vectors, within the sketch's distortion."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((4000, 5)) @ rng.standard_normal((5, 12))
+    A[:3] *= 20.0
+    theta, rank, K = css.leverage_scores_truncated_dense(A, 20000, 600, 3, ga.PREC_FP32, 1e-8)
+    assert rank == 5
+    alg15, _ = leverage.leverage_scores_dense(A[:, K], 20000, 600, 3, ga.PREC_FP32)
+    assert np.max(np.abs(theta - alg15) / alg15) <= 1e-9
+    U = np.linalg.svd(A, full_matrices=False)[0][:, :5]
+    exact = np.sum(U * U, axis=1)
+    assert np.all((theta / exact > 0.6) & (theta / exact < 1.6))
+
+
+def test_truncated_scores_full_rank_is_alg15():
+    A = np.random.default_rng(8).standard_normal((3000, 9)) * np.logspace(0, 2, 9)
+    theta, rank, K = css.leverage_scores_truncated_dense(A, 300, 36, 4, ga.PREC_FP32, 1e-10)
+    ref, _ = leverage.leverage_scores_dense(A, 300, 36, 4, ga.PREC_FP32)
+    assert rank == 9 and np.max(np.abs(theta - ref) / ref) <= 1e-10
