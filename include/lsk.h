@@ -204,6 +204,20 @@ int lsk_leverage_scores_exact(lsk_ctx* ctx, const lsk_mat* A, int32_t prec,
 int lsk_least_squares_gram(lsk_ctx* ctx, const lsk_mat* A, const double* b,
                            int32_t refine, double* x);
 
+/* Leverage scores with Alg. 15's "truncate if needed" read as a rank-revealing
+ * truncation: the numerical rank of the sketch B = G S A is the number of
+ * diagonally pivoted Cholesky steps of B^T B (the column-pivoted QR rule, as
+ * in lsk_column_select) whose pivot exceeds max(16 eps d, rcond^2) times the
+ * largest diagonal entry (rcond ~ a ratio of singular values); the scores
+ * are then those of Alg. 15 on the columns K those steps pick (they span the
+ * dominant column space): theta_i = ||A[i, K] R^-1||^2 with R from the QR of
+ * B[:, K].  rank: NULL or host int64 (written).  Synchronises the context
+ * stream to read the rank.  rcond in [0, 1); a numerically zero sketch is
+ * LSK_ERR_RANK_DEFICIENT; d <= 1024. */
+int lsk_leverage_scores_truncated(lsk_ctx* ctx, const lsk_mat* A, int64_t r,
+                                  int64_t k, uint64_t seed, int32_t prec,
+                                  double rcond, float* theta, int64_t* rank);
+
 /* Column subset selection (Alg. 9): B = G S A (k > 0; S A when k == 0)
  * with the draws of lsk_leverage_scores, then the first c pivots of a
  * column-pivoted QR of B, taken as the diagonally pivoted Cholesky of

@@ -93,6 +93,8 @@ _SIGS = {
     "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
     "lsk_column_select": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
     "lsk_leverage_scores_exact": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I32, _P, _P]),
+    "lsk_leverage_scores_truncated": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32,
+                                                     ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int64)]),
     "lsk_least_squares_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I32, _P]),
     "lsk_leverage_scores_hrn": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _I32, _P, _P]),
     "lsk_lsq_default_opts": (None, [ctypes.POINTER(LsqOpts), _I64]),
@@ -337,6 +339,18 @@ def least_squares_gram(A, b, refine=2, out=None, ctx=None):
     x = out if out is not None else torch.empty(d, dtype=torch.float64, device=_dev(A))
     ctx._call("lsk_least_squares_gram", ctypes.byref(mat), _ptr(b), int(refine), _ptr(x))
     return x
+
+
+def leverage_scores_truncated(A, r, k, seed, rcond=1e-6, prec="fp32", out=None, ctx=None):
+    """lsk_leverage_scores_truncated: Alg. 15 truncated to the sketch's
+    numerical rank -> (theta, rank)."""
+    mat, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    theta = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    rank = ctypes.c_int64(0)
+    ctx._call("lsk_leverage_scores_truncated", ctypes.byref(mat), int(r), int(k), int(seed), _prec(prec),
+              float(rcond), _ptr(theta), ctypes.byref(rank))
+    return theta, int(rank.value)
 
 
 def column_select(A, r, k, seed, c, prec="fp32", ctx=None):

@@ -488,10 +488,59 @@ cudaError_t css_run(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64
     *cb = css_carve(b.scratch, *rows, A->d, c);
     e = sketch_gram64_launch(*sk, *rows, A->d, cb->C, cb->gpart, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return e;
-    return pivchol_launch(cb->C, A->d, c, cb->cols, cb->L, ctx->flag, ctx->stream);
+    return pivchol_launch(cb->C, A->d, c, 0.0, 1, cb->cols, nullptr, cb->L, ctx->flag, ctx->stream);
 }
 
 }  // namespace
+
+int lsk_leverage_scores_truncated(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed,
+                                  int32_t prec, double rcond, float* theta, int64_t* rank) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    const int64_t d = A ? A->d : 0;
+    int rc = css_checks(ctx, A, r, k, prec, d);
+    if (rc) return rc;
+    if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
+    if (!(rcond >= 0.0 && rcond < 1.0)) return fail(ctx, LSK_ERR_INVALID_ARG, "rcond must be in [0, 1)");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int64_t rows = k > 0 ? k : r;
+    const size_t tail = ws_round((size_t)rows * d * 4) + ws_round(qr_workspace_bytes(rows, d)) +
+                        ws_round((size_t)d * d * 4) + ws_round(rownorms_workspace_bytes(A, d, 0, prec)) +
+                        ws_round(4) + 4096;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, d, d) + tail));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    const float* sk;
+    int64_t sr;
+    cudaError_t e = sketch_only(ctx, A, r, k, seed, prec, b, &sk, &sr);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_truncated (sketch)");
+    const CssBufs cb = css_carve(b.scratch, rows, d, d);
+    WsCarver wc{(char*)cb.rest, 0};
+    int* dev_rank = wc.take<int>(1);
+    e = sketch_gram64_launch(sk, rows, d, cb.C, cb.gpart, ctx->sm_count, ctx->stream);
+    if (e == cudaSuccess)
+        e = pivchol_launch(cb.C, d, d, rcond, 0, cb.cols, dev_rank, cb.L, ctx->flag, ctx->stream);
+    int h_rank = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_rank, dev_rank, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_truncated (rank)");
+    if (rank) *rank = h_rank;
+    if (h_rank < 1) return fail(ctx, LSK_ERR_RANK_DEFICIENT, "the sketch is numerically zero");
+    const int64_t c = h_rank;
+    // Alg. 15 on the c columns that carry the numerical rank
+    float* Bk = wc.take<float>((size_t)rows * c);
+    void* qw = wc.take<char>(qr_workspace_bytes(rows, c));
+    float* Bf = wc.take<float>((size_t)d * c);
+    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, prec));
+    e = gather_cols_launch(sk, rows, d, cb.cols, c, Bk, ctx->stream);
+    if (e == cudaSuccess)
+        e = qr_launch(Bk, rows, c, nullptr, b.Rinv64, b.Rinv32, qw, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e == cudaSuccess) e = embed_rows_launch(b.Rinv32, c, cb.cols, d, Bf, ctx->stream);
+    if (e == cudaSuccess)
+        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_truncated (row norms)");
+    return finish(ctx, "lsk_leverage_scores_truncated");
+}
 
 int lsk_column_select(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
                       int64_t c, int32_t* cols) {

@@ -13,9 +13,12 @@ namespace {
 
 // Left-looking pivoted Cholesky of C (d x d, FP64) for c steps, one block:
 // L[t * d + a] = column t of the factor at original index a.
-__global__ void __launch_bounds__(1024) pivchol_kernel(const double* __restrict__ C, int d, int c,
-                                                        double* __restrict__ L, int32_t* __restrict__ cols,
-                                                        int* flag) {
+// Stops at the first pivot <= max(16 eps d, rcond^2) times the largest
+// diagonal entry: with `flag_rank` that is the deferred rank error, else the
+// truncation point; *rank_out (if given) receives the pivots taken.
+__global__ void __launch_bounds__(1024) pivchol_kernel(const double* __restrict__ C, int d, int c, double rcond,
+                                                        int flag_rank, double* __restrict__ L,
+                                                        int32_t* __restrict__ cols, int* rank_out, int* flag) {
     __shared__ double dg[1024];
     __shared__ int perm[1024];
     __shared__ double lp[1024];
@@ -39,8 +42,9 @@ __global__ void __launch_bounds__(1024) pivchol_kernel(const double* __restrict_
         red_v[0] = m;
     }
     __syncthreads();
-    const double tol = 16.0 * 2.220446049250313e-16 * d * red_v[0];
+    const double tol = fmax(16.0 * 2.220446049250313e-16 * d, rcond * rcond) * red_v[0];
     __syncthreads();
+    int taken = c;
     for (int j = 0; j < c; ++j) {
         // largest remaining diagonal entry, lowest position on ties
         double bv = -INFINITY;
@@ -83,7 +87,8 @@ __global__ void __launch_bounds__(1024) pivchol_kernel(const double* __restrict_
         if (s_stop) {
             // numerically rank deficient: the remaining columns in their order
             for (int t = j + 1 + tid; t < c; t += blockDim.x) cols[t] = perm[t];
-            if (tid == 0) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+            if (tid == 0 && flag_rank) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+            taken = j;
             break;
         }
         const int pv = perm[j];
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(1024) pivchol_kernel(const double* __restrict_
         if (tid == 0) L[(int64_t)j * d + pv] = sqrt(piv);
         __syncthreads();
     }
+    if (tid == 0 && rank_out) *rank_out = taken;
 }
 
 __global__ void gather_sub_gram_kernel(const double* __restrict__ C, int64_t d, const int32_t* __restrict__ cols,
@@ -135,10 +141,11 @@ unsigned grid_of(int64_t total) {
 
 size_t pivchol_workspace_bytes(int64_t d, int64_t c) { return ws_round((size_t)d * c * 8); }
 
-cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, int32_t* cols, void* ws, int* flag,
-                           cudaStream_t st) {
+cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, double rcond, int flag_rank, int32_t* cols,
+                           int* rank_out, void* ws, int* flag, cudaStream_t st) {
     if (d < 1 || d > 1024 || c < 1 || c > d) return cudaErrorInvalidValue;
-    LSK_PROF("css_pivchol", st) pivchol_kernel<<<1, 1024, 0, st>>>(C, (int)d, (int)c, (double*)ws, cols, flag);
+    LSK_PROF("css_pivchol", st) pivchol_kernel<<<1, 1024, 0, st>>>(C, (int)d, (int)c, rcond, flag_rank, (double*)ws,
+                                                                    cols, rank_out, flag);
     return cudaGetLastError();
 }
 

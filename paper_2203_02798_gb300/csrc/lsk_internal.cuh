@@ -286,8 +286,8 @@ cudaError_t jl_launch(const double* Rinv64, int64_t d, int64_t m, uint64_t seed,
 
 // css.cu: column subset selection (Alg. 9) pieces
 size_t pivchol_workspace_bytes(int64_t d, int64_t c);
-cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, int32_t* cols, void* ws, int* flag,
-                           cudaStream_t st);
+cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, double rcond, int flag_rank, int32_t* cols,
+                           int* rank_out, void* ws, int* flag, cudaStream_t st);
 cudaError_t gather_sub_gram_launch(const double* C, int64_t d, const int32_t* cols, int64_t c, double* Csub,
                                    cudaStream_t st);
 cudaError_t gather_cols_launch(const float* B, int64_t rows, int64_t d, const int32_t* cols, int64_t c, float* Bk,

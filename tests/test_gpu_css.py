@@ -103,3 +103,29 @@ def test_column_select_planted_rank(lsk):
     cols = host(cols)
     assert np.linalg.matrix_rank(A[:, cols[:6]].astype(np.float64)) == 6
     assert sorted(set(cols)) == sorted(cols)                    # a selection, no repeats
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_leverage_scores_truncated(lsk, prec):
+    """Planted rank 7 of d = 24: the numerical rank is found and the scores
+    equal the oracle's truncated Alg. 15 on the same sketch."""
+    rng = np.random.default_rng(13)
+    A = (rng.standard_normal((30_000, 7)) @ rng.standard_normal((7, 24))).astype(np.float32)
+    A[:5] *= 30.0
+    op = oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32
+    theta, rank = lsk.leverage_scores_truncated(dev(A), 2048, 96, 4, rcond=1e-5, prec=prec)
+    lsk.context().sync()
+    ref, rank_o, K = ocss.leverage_scores_truncated_dense(A.astype(np.float64), 2048, 96, 4, op, 1e-5)
+    assert rank == rank_o == 7
+    theta = host(theta).astype(np.float64)
+    assert np.max(np.abs(theta - ref) / ref) <= 1e-3
+
+
+def test_leverage_scores_truncated_full_rank(lsk):
+    A = scaled(20_000, 16, 14)
+    theta, rank = lsk.leverage_scores_truncated(dev(A), 1024, 64, 2, rcond=1e-7)
+    ell = lsk.leverage_scores(dev(A), 1024, 64, 2)
+    lsk.context().sync()
+    assert rank == 16
+    theta, ell = host(theta).astype(np.float64), host(ell).astype(np.float64)
+    assert np.max(np.abs(theta - ell) / ell) <= 1e-4
