@@ -18,7 +18,7 @@
 // The draws of the next chunk overlap the loads of SA; the loads are always
 // consumed before the stage barrier is arrived on.  All workers move through
 // the chunks in lockstep (one thread waits on a stage and broadcasts the
-// verdict through a named barrier), so a timeout exits every worker alike.
+// result through a named barrier), so a timeout exits every worker alike.
 #include "tc_common.cuh"
 
 namespace {
@@ -69,7 +69,7 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     uint64_t* fin = done + 1;             // every MMA complete     (MMA commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* verdict = abort + 1;
+    volatile int* go_on = abort + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blk % p.tiles_m, slice = blk / p.tiles_m;
@@ -154,9 +154,9 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                 }
             }
             // (3) wait for the stage (one thread decides for all workers)
-            if (wt == 0) *verdict = tc::mbar_wait(empty + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
+            if (wt == 0) *go_on = tc::mbar_wait(empty + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
             named_sync();
-            if (!*verdict) {
+            if (!*go_on) {
                 ok = false;
                 break;
             }

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
     uint64_t* fin = done + 2;              // every MMA complete      (MMA commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* verdict = abort + 1;
+    volatile int* go_on = abort + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int ntiles = (NPAD + kMT - 1) / kMT;   // 1 or 2 M tiles
@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
             for (int g = 0; g < nchunks; ++g) {
                 if (g + 1 < nchunks) load_rows<NPAD>(p, r_begin + (int64_t)(g + 1) * kKC, r_end, wt, nx);
                 // (2) wait for the stage (one thread decides for all workers)
-                if (wt == 0) *verdict = tc::mbar_wait(empty + s, ph ^ 1u, abort) ? 1 : 0;
+                if (wt == 0) *go_on = tc::mbar_wait(empty + s, ph ^ 1u, abort) ? 1 : 0;
                 named_sync();
-                if (!*verdict) {
+                if (!*go_on) {
                     ok = false;
                     break;
                 }

@@ -180,7 +180,7 @@ __device__ __forceinline__ void store_piece(uint8_t* stage, int half, int lane, 
     }
 }
 
-// lane 0 waits, the warp follows its verdict
+// lane 0 waits, the warp follows its result
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     int ok = 0;
     if ((threadIdx.x & 31) == 0) ok = tc::mbar_wait(bar, parity, abort) ? 1 : 0;

@@ -3,15 +3,15 @@ configuration bench.py times.  The oracle forms the whole FP64 sketch and R
 (Householder QR of the sketch) and then computes exact scores for a sample of
 rows, one by one; properties that hold at any size are checked on all rows.
 
-  config 2: CSR 1,000,000 x 200, p = 0.01, r = 40,000, k = 400, FP32
-  config 3: dense 4,000,000 x 256 (column scales 10^U(-3,3)), r = 65,536,
+  CSR 1,000,000 x 200, p = 0.01, r = 40,000, k = 400, FP32
+  dense 4,000,000 x 256 (column scales 10^U(-3,3)), r = 65,536,
             k = 512, BF16 stages -- the bench's step; also the "next" rows
             on it: Alg. 15 with Pi, sketch-and-solve, column selection and
             the Alg. 16 scores
-  config 4: the 512-problem batch (graph-captured, grouped stages), three
+  the 512-problem batch (graph-captured, grouped stages), three
             problems checked against the oracle, every problem's scores in
             [0, 1.5] with sum within the sketch's distortion band
-  config 5: one large served least-squares problem against the Householder
+  one large served least-squares problem against the Householder
             least-squares solution
 """
 import numpy as np
@@ -50,8 +50,8 @@ def sample_rows(n, step, rng_seed=0):
 
 
 @pytest.fixture(scope="module")
-def config3():
-    """Config 3's A (4,000,000 x 256, column scales 10^U(-3,3)) and the
+def dense_4m():
+    """The 4,000,000 x 256 A (column scales 10^U(-3,3)) and the
     oracle's FP64 sketches of it (CountSketch r = 65,536, BF16 G with
     k = 512), formed once for the tests of this module."""
     n, d, r, k, seed = 4_000_000, 256, 65_536, 512, 2
@@ -62,8 +62,8 @@ def config3():
     return dict(A=A, n=n, d=d, r=r, k=k, seed=seed, SA=SA, GSA=GSA, R=olev.sketch_R(GSA))
 
 
-def test_config3_dense_4M_x_256_bf16(lsk, config3):
-    c3 = config3
+def test_dense_4M_x_256_bf16(lsk, dense_4m):
+    c3 = dense_4m
     A, n, d = c3["A"], c3["n"], c3["d"]
     Ad = torch.from_numpy(A).cuda()
     ell, R = lsk.leverage_scores(Ad, c3["r"], c3["k"], c3["seed"], "bf16", return_R=True)
@@ -84,11 +84,11 @@ def test_config3_dense_4M_x_256_bf16(lsk, config3):
     assert 0.2 * d <= ell.sum() <= 5.0 * d
 
 
-def test_config3_jl_sketch_solve_and_column_selection(lsk, config3):
+def test_dense_4M_x_256_jl_sketch_solve_and_column_selection(lsk, dense_4m):
     """The "next" rows at the bench's size: Alg. 15 with Pi (m = 64), sketch-
     and-solve (Alg. 11) and column selection with the Alg. 16 scores (c = 64),
     each against the oracle on the same FP64 sketch."""
-    c3 = config3
+    c3 = dense_4m
     A, n, d, r, k, seed = c3["A"], c3["n"], c3["d"], c3["r"], c3["k"], c3["seed"]
     Ro = c3["R"]
     Ad = torch.from_numpy(A).cuda()
@@ -135,7 +135,7 @@ def test_config3_jl_sketch_solve_and_column_selection(lsk, config3):
     torch.cuda.empty_cache()
 
 
-def test_config2_csr_1M_x_200_fp32(lsk):
+def test_csr_1M_x_200_fp32(lsk):
     n, d, r, k, seed = 1_000_000, 200, 40_000, 400, 1
     V, J, I = workloads.csr_bernoulli(n, d, 0.01, seed=1)
     ell = lsk.leverage_scores(lsk.csr_from_numpy(V, J, I, d), r, k, seed, "fp32")
@@ -156,7 +156,7 @@ def test_config2_csr_1M_x_200_fp32(lsk):
     assert 0.2 * d <= ell.sum() <= 5.0 * d
 
 
-def test_config4_batch_512_problems(lsk):
+def test_batch_512_problems(lsk):
     specs = workloads.batch_specs(512, seed=3)
     probs = []
     for sp in specs:
@@ -205,7 +205,7 @@ def test_config4_batch_512_problems(lsk):
         assert np.max(np.abs(ell[rows][nz] - ref[nz]) / ref[nz]) <= 1e-3, sp
 
 
-def test_config5_large_served_least_squares(lsk):
+def test_large_served_least_squares(lsk):
     specs = workloads.batch_specs(512, seed=3)
     i = max((i for i, sp in enumerate(specs) if sp["kind"] == "dense" and sp["d"] == 256),
             key=lambda i: specs[i]["n"])

@@ -321,7 +321,7 @@ def test_sketch_qr_rank_deficient(lsk):
 
 # ---------------------------------------------------------- leverage scores -
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_leverage_config1_dense_outliers(lsk, prec):
+def test_leverage_dense_outliers_20000x50(lsk, prec):
     A = workloads.dense_outliers().astype(np.float32)          # the FP32 path casts once
     ell, R = lsk.leverage_scores(dev(A), 2500, 100, 0, prec, return_R=True)
     lsk.context().sync()
