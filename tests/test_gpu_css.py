@@ -129,3 +129,38 @@ def test_leverage_scores_truncated_full_rank(lsk):
     assert rank == 16
     theta, ell = host(theta).astype(np.float64), host(ell).astype(np.float64)
     assert np.max(np.abs(theta - ell) / ell) <= 1e-4
+
+
+def test_new_entry_points_reject_bad_arguments(lsk):
+    """Argument errors are reported before any launch and leave the context usable."""
+    A = dev(workloads.dense_normal(2000, 8, seed=1))
+    b = torch.zeros(2000, dtype=torch.float64, device="cuda")
+    with pytest.raises(lsk.LskError, match="INVALID"):
+        lsk.column_select(A, 256, 32, 1, 0)                      # c = 0
+    with pytest.raises(lsk.LskError, match="INVALID"):
+        lsk.column_select(A, 256, 32, 1, 9)                      # c > d
+    with pytest.raises(lsk.LskError, match="INVALID"):
+        lsk.leverage_scores_truncated(A, 256, 32, 1, rcond=1.5)
+    with pytest.raises(lsk.LskError, match="INVALID"):
+        lsk.least_squares_gram(A, b, refine=11)
+    with pytest.raises(lsk.LskError, match="INVALID"):
+        lsk.sketch_solve(A, b, 4, 0, 1)                          # r < d
+    theta = lsk.leverage_scores_exact(A)
+    lsk.context().sync()
+    assert abs(host(theta).astype(np.float64).sum() - 8) <= 1e-3 * 8
+
+
+def test_new_entry_points_on_empty_and_single_column(lsk):
+    # d = 1: a single column selects itself; its exact scores are a_i^2 / ||a||^2
+    a = workloads.dense_normal(3000, 1, seed=2)
+    cols = host(lsk.column_select(dev(a), 64, 8, 1, 1))
+    theta = host(lsk.leverage_scores_exact(dev(a))).astype(np.float64)
+    lsk.context().sync()
+    assert list(cols) == [0]
+    ref = a[:, 0].astype(np.float64) ** 2 / np.sum(a.astype(np.float64) ** 2)
+    assert np.max(np.abs(theta - ref) / ref) <= 1e-5
+    # CSR with n = 0 rows: the Gaussian sketch is all zeros
+    V = np.zeros(0, dtype=np.float32); J = np.zeros(0, dtype=np.int32); I = np.zeros(1, dtype=np.int64)
+    C = host(lsk.csrjlt(lsk.csr_from_numpy(V, J, I, 5), 16, 1))
+    lsk.context().sync()
+    assert C.shape == (16, 5) and np.all(C == 0)
