@@ -313,14 +313,14 @@ typedef struct lsk_lsq_opts {
     int64_t k;              /* Gaussian rows (e.g. 2d; 0 = CountSketch only) */
     uint64_t seed;
     int32_t prec;           /* precision of the sketch (LSK_PREC_*)          */
-    int32_t max_iter;       /* LSQR iterations per refinement step           */
+    int32_t max_iter;       /* inner iterations per refinement step           */
     int32_t max_refine;     /* FP64 refinement steps                         */
     double tol;             /* target eta = ||A^T(b-Ax)|| / ||A^T b||         */
-    double inner_tol;       /* LSQR stopping tolerance of each inner solve   */
+    double inner_tol;       /* relative residual of each inner solve          */
 } lsk_lsq_opts;
 
 typedef struct lsk_lsq_info {
-    int32_t iters;          /* LSQR iterations in total                      */
+    int32_t iters;          /* inner iterations in total                      */
     int32_t refinements;    /* FP64 refinement steps taken                   */
     double eta;             /* final normal-equation residual (FP64)         */
     int32_t status;         /* LSK_OK or LSK_ERR_NOT_CONVERGED               */
@@ -330,11 +330,15 @@ typedef struct lsk_lsq_info {
  * k = 2d, BF16 sketch, tol 1e-10). */
 void lsk_lsq_default_opts(lsk_lsq_opts* opts, int64_t d);
 
-/* Alg. 12: R from the sketch of A, N = R^-1, then LSQR (Paige & Saunders
- * 1982) on min ||A N y - r_t|| with FP32 products, wrapped in FP64
- * iterative refinement r_t = b - A x_t, x_{t+1} = x_t + N y, until
- * eta <= opts->tol.  b: device n doubles; x: device d doubles (output).
- * info may be NULL.  Synchronises the stream (it reads scalars back). */
+/* Alg. 12: R from the sketch of A, N = R^-1, then FP64 iterative
+ * refinement r_t = b - A x_t, g_t = N^T A^T r_t (both FP64), an inner
+ * conjugate-gradient solve of N^T A^T A N z = g_t with FP32 products over A
+ * (the preconditioned normal equations, CGLS; the Krylov iterates of LSQR
+ * on min ||A N y - r_t||), x_{t+1} = x_t + N z, until
+ * eta = ||A^T r|| / ||A^T b|| <= opts->tol.  b: device n doubles; x: device
+ * d doubles (output).  info may be NULL.  Synchronises the stream (it reads
+ * scalars back); LSK_ERR_NOT_CONVERGED when max_refine steps do not reach
+ * tol. */
 int lsk_sketch_precondition_lsq(lsk_ctx* ctx, const lsk_mat* A,
                                 const double* b, double* x,
                                 const lsk_lsq_opts* opts, lsk_lsq_info* info);

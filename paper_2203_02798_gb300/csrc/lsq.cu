@@ -1,18 +1,23 @@
 // lsq.cu -- sketch-and-precondition least squares (Alg. 12).
 //
 // Alg. 12 leaves the "parallel preconditioned iterative method" open; the
-// reading used here is LSQR (Paige & Saunders, ACM TOMS 1982) on
-// min_y ||A N y - r_t|| with N = R^-1 from the sketch, wrapped in FP64
-// iterative refinement:
+// reading used here is a preconditioned Krylov solve with N = R^-1 from the
+// sketch, wrapped in FP64 iterative refinement:
 //     r_t = b - A x_t   (FP64, A's FP32 values taken exactly)
+//     g_t = N^T A^T r_t (FP64, from the same pass)
 //     eta_t = ||A^T r_t|| / ||A^T b||          stop when eta_t <= tol
-//     y = LSQR(A N, r_t) in FP32;  x_{t+1} = x_t + N y   (FP64)
-// Each LSQR iteration makes ONE pass over A: the block that forms
-// u_i = A_i p - (alpha/beta) u_i immediately adds u_i A_i^T into its partial
-// of A^T u while the row is still in registers.  The FP64 residual pass
-// likewise forms r_i and accumulates r_i A_i^T (giving A^T r for eta and
-// the first LSQR vector) in the same read.  Scalars live on the device; the
-// host reads them back once per iteration for the stopping test.
+//     z = CG(N^T A^T A N, g_t) to inner_tol;  x_{t+1} = x_t + N z   (FP64)
+// The inner solve is conjugate gradients on the preconditioned normal
+// equations (CGLS, Hestenes & Stiefel 1952), mathematically the same Krylov
+// iterates as LSQR on min ||A N y - r_t||, but with the right-hand side g_t
+// formed in FP64: its FP32 products are then relative to the correction
+// being sought, not to r_t, so a refinement step gains ~inner_tol even when
+// the residual is large (LSQR's FP32 vectors carry r_t and stall at about
+// eps32 sqrt(n) there).  Each CG iteration makes ONE pass over A: the block
+// that forms u_i = A_i p immediately adds u_i A_i^T into its partial of A^T u
+// while the row is still in registers.  The FP64 residual pass likewise forms
+// r_i and accumulates r_i A_i^T in the same read.  Scalars live on the
+// device; the host reads them back every few iterations for the stop test.
 #include "lsk_internal.cuh"
 
 #include <math.h>
@@ -26,6 +31,7 @@ struct LsqrState {
     double alpha, beta, rhobar, phibar, anorm2, atb_norm, eta, bnorm;
     double arnorm, rnorm;
     int done, it;
+    double rho, rho0;   // CG on the normal equations: ||s||^2 now and at the start
 };
 
 constexpr int kPassThreads = 256;
@@ -121,18 +127,6 @@ __global__ void __launch_bounds__(kPassThreads) resid64_csr_kernel(
     }
 }
 
-// p = N v (FP32, N upper triangular), one warp per row (coalesced reads of
-// row i of N); the caller has synchronised the block after writing v.
-__device__ __forceinline__ void next_p(const float* __restrict__ N32, int64_t d, const float* v, float* p) {
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int64_t i = threadIdx.x >> 5; i < d; i += nw) {
-        float s = 0.f;
-        for (int64_t j = i + lane; j < d; j += 32) s = fmaf(N32[i * d + j], v[j], s);
-        s = warp_sum(s);
-        if (lane == 0) p[i] = s;
-    }
-}
-
 // out[j] = sum_z part[z][j] in z order groups: with blockDim >= 4d the
 // partials are split four ways (z mod 4) and the four sums added in order.
 __device__ __forceinline__ void reduce_partials(const float* __restrict__ part, int nblocks, int64_t d,
@@ -155,86 +149,6 @@ __device__ __forceinline__ void reduce_partials(const float* __restrict__ part, 
             out[j] = s;
         }
     }
-}
-
-// Reduce the residual pass: A^T r, eta, beta_1; then the LSQR start vectors
-// v_1 = N^T A^T r / (beta_1 alpha_1), w_1 = v_1, y = 0.  One block.
-__global__ void resid_finish_kernel(const double* __restrict__ qpart, const double* __restrict__ sspart,
-                                    int nblocks, int64_t d, const double* __restrict__ N64,
-                                    int first, LsqrState* st, float* __restrict__ v,
-                                    float* __restrict__ w, double* __restrict__ y,
-                                    double* __restrict__ atr, const float* __restrict__ N32,
-                                    float* __restrict__ p) {
-    __shared__ double red[32];
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int z = 0; z < nblocks; ++z) s += qpart[(int64_t)z * d + j];
-        atr[j] = s;
-    }
-    __syncthreads();
-    // ||A^T r|| and ||r||^2
-    double a2 = 0.0;
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) a2 = fma(atr[j], atr[j], a2);
-    double s2 = 0.0;
-    for (int z = threadIdx.x; z < nblocks; z += blockDim.x) s2 += sspart[z];
-    a2 = warp_sum(a2);
-    s2 = warp_sum(s2);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) {
-        red[wid] = a2;
-        red[16 + wid] = s2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double A2 = 0.0, S2 = 0.0;
-        for (int t = 0; t < nw; ++t) {
-            A2 += red[t];
-            S2 += red[16 + t];
-        }
-        const double atrn = sqrt(A2);
-        if (first) st->atb_norm = atrn;
-        st->eta = (st->atb_norm > 0.0) ? atrn / st->atb_norm : 0.0;
-        st->beta = sqrt(S2);
-        st->bnorm = st->beta;
-    }
-    __syncthreads();
-    const double beta = st->beta;
-    // v_raw = N^T (A^T r) / beta   (N upper triangular: N^T v uses column j)
-    double vv = 0.0;
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int64_t i = 0; i <= j; ++i) s = fma(N64[i * d + j], atr[i], s);
-        s = (beta > 0.0) ? s / beta : 0.0;
-        y[j] = s;   // temporary
-        vv = fma(s, s, vv);
-    }
-    vv = warp_sum(vv);
-    __syncthreads();
-    if (lane == 0) red[wid] = vv;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double V2 = 0.0;
-        for (int t = 0; t < nw; ++t) V2 += red[t];
-        const double alpha = sqrt(V2);
-        st->alpha = alpha;
-        st->rhobar = alpha;
-        st->phibar = beta;
-        st->anorm2 = 0.0;
-        st->done = (alpha == 0.0 || beta == 0.0) ? 1 : 0;
-        st->it = 0;
-        st->arnorm = alpha * beta;
-        st->rnorm = beta;
-    }
-    __syncthreads();
-    const double alpha = st->alpha;
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        const double vj = (alpha > 0.0) ? y[j] / alpha : 0.0;
-        v[j] = (float)vj;
-        w[j] = (float)vj;
-        y[j] = 0.0;
-    }
-    __syncthreads();
-    next_p(N32, d, v, p);
 }
 
 // u <- A p - (alpha/beta) u; partial sums of u^2 and of A^T u.  Dense,
@@ -406,78 +320,132 @@ __global__ void __launch_bounds__(kPassThreads) lsqr_pass_csr_kernel(
     }
 }
 
-// One LSQR step after the pass (Paige & Saunders 1982, Sec. 4.1): beta,
-// v = (N^T A^T u)/beta... , the plane rotation and the y, w updates.  One block.
-__global__ void lsqr_step_kernel(const float* __restrict__ qpart, const double* __restrict__ sspart,
-                                 int nblocks, int64_t d, const float* __restrict__ N32,
-                                 LsqrState* st, float* __restrict__ v, float* __restrict__ w,
-                                 double* __restrict__ y, float* __restrict__ qtmp, double inner_tol,
-                                 float* __restrict__ p) {
+// ---- inner solve: CG on the preconditioned normal equations ----------------
+// N^T A^T A N z = g with g = N^T A^T r formed in FP64 by the residual pass.
+// The pass kernels run with alpha = 0 (u = A p): u = A N p_cg, A^T u and
+// ||u||^2 in FP32 / FP64; the d-vectors (z, s, p_cg) stay in FP64.  Unlike
+// LSQR on min ||A N y - r||, whose FP32 n-vectors carry r itself (mostly
+// orthogonal to range(A) when the residual is large), every FP32 quantity
+// here is relative to the correction being sought, so each refinement step
+// gains ~inner_tol whatever the size of the residual.
+
+// p = N v for an FP64 d-vector staged in shared memory (N upper triangular)
+__device__ __forceinline__ void apply_n(const double* __restrict__ N64, int64_t d, const double* vs, float* p) {
+    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+        double t = 0.0;
+        for (int64_t j = i; j < d; ++j) t = fma(N64[i * d + j], vs[j], t);
+        p[i] = (float)t;
+    }
+}
+
+// Start of an inner solve after the residual pass: A^T r, eta,
+// g = N^T A^T r, s = p_cg = g, z = 0, p = N p_cg.  One block.
+__global__ void cg_start_kernel(const double* __restrict__ qpart, int nblocks, int64_t d,
+                                const double* __restrict__ N64, int first, LsqrState* st,
+                                double* __restrict__ s, double* __restrict__ pc, double* __restrict__ z,
+                                double* __restrict__ atr, float* __restrict__ p) {
     __shared__ double red[32];
-    __shared__ double sc[8];
+    __shared__ double pcs[1024];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < nblocks; ++q) t += qpart[(int64_t)q * d + j];
+        atr[j] = t;
+    }
+    __syncthreads();
+    double a2 = 0.0, g2 = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        a2 = fma(atr[j], atr[j], a2);
+        double t = 0.0;
+        for (int64_t i = 0; i <= j; ++i) t = fma(N64[i * d + j], atr[i], t);   // (N^T A^T r)_j
+        s[j] = t;
+        pc[j] = t;
+        pcs[j] = t;
+        z[j] = 0.0;
+        g2 = fma(t, t, g2);
+    }
+    a2 = warp_sum(a2);
+    g2 = warp_sum(g2);
+    if (lane == 0) {
+        red[wid] = a2;
+        red[16 + wid] = g2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A2 = 0.0, G2 = 0.0;
+        for (int t = 0; t < nw; ++t) {
+            A2 += red[t];
+            G2 += red[16 + t];
+        }
+        const double atrn = sqrt(A2);
+        if (first) st->atb_norm = atrn;
+        st->eta = (st->atb_norm > 0.0) ? atrn / st->atb_norm : 0.0;
+        st->alpha = 0.0;           // the pass forms u = A p
+        st->beta = 1.0;
+        st->rho = G2;
+        st->rho0 = G2;
+        st->it = 0;
+        st->done = (G2 == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    apply_n(N64, d, pcs, p);
+}
+
+// One CG step after the pass: gamma = ||A N p_cg||^2, w = N^T (A^T u),
+// z += a p_cg, s -= a w, p_cg = s + b p_cg, p = N p_cg.  One block.
+__global__ void cg_step_kernel(const float* __restrict__ qpart, const double* __restrict__ sspart, int nblocks,
+                               int64_t d, const double* __restrict__ N64, LsqrState* st, double* __restrict__ s,
+                               double* __restrict__ pc, double* __restrict__ z, float* __restrict__ qtmp,
+                               double inner_tol, float* __restrict__ p) {
+    __shared__ double red[32];
+    __shared__ double sc[2];
+    __shared__ double pcs[1024];
     if (st->done) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double s2 = 0.0;
-    for (int z = threadIdx.x; z < nblocks; z += blockDim.x) s2 += sspart[z];
-    s2 = warp_sum(s2);
-    if (lane == 0) red[wid] = s2;
-    reduce_partials(qpart, nblocks, d, qtmp);
+    double g2 = 0.0;
+    for (int q = threadIdx.x; q < nblocks; q += blockDim.x) g2 += sspart[q];
+    g2 = warp_sum(g2);
+    if (lane == 0) red[wid] = g2;
+    reduce_partials(qpart, nblocks, d, qtmp);   // A^T u
     __syncthreads();
     if (threadIdx.x == 0) {
-        double S2 = 0.0;
-        for (int t = 0; t < nw; ++t) S2 += red[t];
-        sc[0] = sqrt(S2);   // beta_{i+1}
+        double G = 0.0;
+        for (int t = 0; t < nw; ++t) G += red[t];
+        sc[0] = (G > 0.0) ? st->rho / G : 0.0;   // step length
     }
     __syncthreads();
-    const double beta = sc[0];
-    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
-    // v_raw = N^T q / beta - beta v
-    double vv = 0.0;
+    const double a = sc[0];
+    double r2 = 0.0;
     for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        float s = 0.f;
-        for (int64_t i = 0; i <= j; ++i) s = fmaf(N32[i * d + j], qtmp[i], s);
-        const double vr = (double)s * ib - beta * (double)v[j];
-        qtmp[d + j] = (float)vr;
-        vv = fma(vr, vr, vv);
+        double w = 0.0;
+        for (int64_t i = 0; i <= j; ++i) w = fma(N64[i * d + j], (double)qtmp[i], w);   // (N^T A^T u)_j
+        z[j] = fma(a, pc[j], z[j]);
+        const double sj = fma(-a, w, s[j]);
+        s[j] = sj;
+        r2 = fma(sj, sj, r2);
     }
-    vv = warp_sum(vv);
+    r2 = warp_sum(r2);
     __syncthreads();
-    if (lane == 0) red[wid] = vv;
+    if (lane == 0) red[wid] = r2;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double V2 = 0.0;
-        for (int t = 0; t < nw; ++t) V2 += red[t];
-        const double alpha_new = sqrt(V2);
-        const double alpha_old = st->alpha;
-        st->anorm2 += alpha_old * alpha_old + beta * beta;
-        const double rho = hypot(st->rhobar, beta);
-        const double c = st->rhobar / rho, s = beta / rho;
-        const double theta = s * alpha_new;
-        st->rhobar = -c * alpha_new;
-        const double phi = c * st->phibar;
-        st->phibar = s * st->phibar;
-        sc[1] = phi / rho;         // y step
-        sc[2] = theta / rho;       // w step
-        sc[3] = alpha_new > 0.0 ? 1.0 / alpha_new : 0.0;
-        st->alpha = alpha_new;
-        st->beta = beta;
-        st->rnorm = st->phibar;
-        st->arnorm = st->phibar * alpha_new * fabs(c);
+        double R2 = 0.0;
+        for (int t = 0; t < nw; ++t) R2 += red[t];
+        sc[1] = (st->rho > 0.0) ? R2 / st->rho : 0.0;
+        st->rho = R2;
         st->it += 1;
-        if (st->arnorm <= inner_tol * sqrt(st->anorm2) * st->rnorm || alpha_new == 0.0 || beta == 0.0)
-            st->done = 1;
+        if (a == 0.0 || R2 <= inner_tol * inner_tol * st->rho0) st->done = 1;
     }
     __syncthreads();
-    const double ys = sc[1], ws = sc[2], ia = sc[3];
+    if (st->done) return;
+    const double bta = sc[1];
     for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
-        const double wj = (double)w[j];
-        y[j] = fma(ys, wj, y[j]);
-        const double vj = (double)qtmp[d + j] * ia;
-        v[j] = (float)vj;
-        w[j] = (float)(vj - ws * wj);
+        const double v = fma(bta, pc[j], s[j]);
+        pc[j] = v;
+        pcs[j] = v;
     }
     __syncthreads();
-    if (!st->done) next_p(N32, d, v, p);
+    apply_n(N64, d, pcs, p);
 }
 
 // x <- x + N y (FP64).  One block.
@@ -591,7 +559,7 @@ cudaError_t atr64_launch(const lsk_mat* A, const double* b, const double* x, dou
 size_t lsq_workspace_bytes(const lsk_mat* A) {
     const int64_t n = A->n, d = A->d;
     const int nb = kMaxPassBlocks;
-    return ws_round(sizeof(LsqrState)) + ws_round((size_t)n * 4) + 4 * ws_round((size_t)d * 8) +
+    return ws_round(sizeof(LsqrState)) + ws_round((size_t)n * 4) + 6 * ws_round((size_t)d * 8) +
            ws_round((size_t)nb * d * 8) + ws_round((size_t)nb * 8) + 3 * ws_round((size_t)d * 4) +
            ws_round((size_t)2 * d * 4) + 4096;
 }
@@ -608,10 +576,10 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
     double* atr = wc.take<double>(d);
     double* qpart64 = wc.take<double>((size_t)nb * d);
     double* sspart = wc.take<double>(nb);
-    float* v = wc.take<float>(d);
-    float* w = wc.take<float>(d);
     float* p = wc.take<float>(d);
     float* qtmp = wc.take<float>(2 * d);
+    double* cg_s = wc.take<double>(d);
+    double* cg_p = wc.take<double>(d);
     float* qpart32 = reinterpret_cast<float*>(qpart64);   // reused by the FP32 pass
 
     LsqrState h{};
@@ -637,8 +605,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         else
             LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
                                                                A->nnz, d, b, x, u, qpart64, sspart, ctx->flag);
-        resid_finish_kernel<<<1, 256, 0, st>>>(qpart64, sspart, nb, d, Rinv64, t == 0 ? 1 : 0, S, v, w, y,
-                                               atr, Rinv32, p);
+        cg_start_kernel<<<1, 256, 0, st>>>(qpart64, nb, d, Rinv64, t == 0 ? 1 : 0, S, cg_s, cg_p, y, atr, p);
         e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return LSK_ERR_CUDA;
@@ -652,8 +619,8 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         int it = 0;
         while (!h.done && it < o->max_iter) {
             lsqr_pass(A, nb, sh32, p, S, u, qpart32, sspart, st);
-            lsqr_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv32, S, v, w, y, qtmp,
-                                                 o->inner_tol, p);
+            cg_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv64, S, cg_s, cg_p, y, qtmp,
+                                               o->inner_tol, p);
             ++it;
             if ((it & 3) == 0 || it >= o->max_iter) {   // stopping test every 4 iterations
                 e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);

@@ -2,8 +2,8 @@
 
 A request is one least-squares problem min ||A x - b|| (A dense or CSR,
 resident on the device; b on the device) solved with
-``lsk_sketch_precondition_lsq`` (Alg. 12: sketch, R of the sketch, LSQR on
-A R^-1 with FP64 refinement).  The server keeps ``slots`` worker threads,
+``lsk_sketch_precondition_lsq`` (Alg. 12: sketch, R of the sketch, CG on the
+normal equations of A R^-1 within FP64 refinement).  The server keeps ``slots`` worker threads,
 each with its own CUDA stream and library context (its own workspace), so
 admitted requests run concurrently on the GPU.  Requests are admitted in
 arrival order as soon as a slot is free and their device footprint fits

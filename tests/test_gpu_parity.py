@@ -452,3 +452,29 @@ def test_bounded_wait_gives_up_and_context_stays_usable(lsk):
     ctx.sync()
     ref, _ = olev.leverage_scores_dense(A.astype(np.float64), 256, 32, 1, oga.PREC_BF16)
     assert np.max(np.abs(host(ell) - ref) / ref) <= 1e-3
+
+
+@pytest.mark.parametrize("kind", ["dense", "csr"])
+def test_sketch_precondition_lsq_large_residual(lsk, kind):
+    """b with no component to speak of in range(A) (pure noise): the residual
+    is large and nearly orthogonal to range(A); eta still reaches 1e-10 and x
+    matches the Householder least-squares solution."""
+    n, d = 200_000, 48
+    rng = np.random.default_rng(21)
+    if kind == "dense":
+        A = workloads.dense_normal(n, d, seed=22) * (10.0 ** np.linspace(0, 2, d)).astype(np.float32)
+        A64 = A.astype(np.float64)
+        Ad = dev(A)
+    else:
+        V, J, I = workloads.csr_bernoulli(n, d, 0.1, seed=22)
+        rows = np.repeat(np.arange(n), np.diff(I))
+        A64 = np.zeros((n, d))
+        A64[rows, J] = V
+        Ad = csr_dev(lsk, V, J, I, d)
+    b = rng.standard_normal(n)
+    x, info = lsk.sketch_precondition_lsq(Ad, dev(b), r=d * d, k=2 * d, seed=3)
+    lsk.context().sync()
+    assert info["status"] == 0 and info["eta"] <= 1e-10
+    x_ls = olsq.least_squares_qr(A64, b)
+    x = host(x)
+    assert np.linalg.norm(x - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
