@@ -329,12 +329,15 @@ __global__ void __launch_bounds__(kPassThreads) lsqr_pass_csr_kernel(
 // here is relative to the correction being sought, so each refinement step
 // gains ~inner_tol whatever the size of the residual.
 
-// p = N v for an FP64 d-vector staged in shared memory (N upper triangular)
+// p = N v for an FP64 d-vector staged in shared memory (N upper triangular):
+// one warp per row of N, so consecutive lanes read consecutive entries
 __device__ __forceinline__ void apply_n(const double* __restrict__ N64, int64_t d, const double* vs, float* p) {
-    for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t i = threadIdx.x >> 5; i < d; i += nw) {
         double t = 0.0;
-        for (int64_t j = i; j < d; ++j) t = fma(N64[i * d + j], vs[j], t);
-        p[i] = (float)t;
+        for (int64_t j = i + lane; j < d; j += 32) t = fma(N64[i * d + j], vs[j], t);
+        t = warp_sum(t);
+        if (lane == 0) p[i] = (float)t;
     }
 }
 
