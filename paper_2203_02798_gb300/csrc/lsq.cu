@@ -568,7 +568,8 @@ size_t lsq_workspace_bytes(const lsk_mat* A) {
 }
 
 int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const lsk_lsq_opts* o,
-            const double* Rinv64, const float* Rinv32, void* ws, lsk_lsq_info* info) {
+            const double* Rinv64, const float* /* FP32 factor: not used, the inner solve runs on Rinv64 */,
+            void* ws, lsk_lsq_info* info) {
     cudaStream_t st = ctx->stream;
     const int64_t n = A->n, d = A->d;
     const int nb = pass_grid(A, ctx->sm_count);
