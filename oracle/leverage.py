@@ -1,4 +1,5 @@
-"""Leverage scores: sketched (Alg. 15, without and with its Pi) and exact.
+"""Leverage scores: sketched (Alg. 15, without and with its Pi) and exact
+(oracle; test infrastructure).
 
 Alg. 15 (Sec. 4.3): sketch A (here G*S*A, Alg. 3; k = 0 means S*A alone,
 as the m = 0 convention of csrcgs, Sec. 5), factor the sketch, and return

@@ -1,4 +1,4 @@
-"""Least squares (oracle): through the Gram pseudoinverse (Alg. 10), through
+"""Least squares (oracle; test infrastructure): through the Gram pseudoinverse (Alg. 10), through
 sketches: sketch-and-precondition (Alg. 12) with LSQR, and sketch-and-solve
 (Alg. 11).
 
