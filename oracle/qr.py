@@ -1,5 +1,5 @@
-"""Householder QR of the sketch, R^-1, and the full-rank check (oracle; test
-infrastructure).
+"""Householder QR of the sketch, R^-1, the full-rank check.
+Oracle; test infrastructure.
 
 Alg. 12 and Alg. 15 factor the small sketch (G*S*A or S*A) with an SVD; the
 reading used here factors it with a QR, B = Q R, which yields the same

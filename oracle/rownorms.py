@@ -1,5 +1,5 @@
-"""Squared row norms x <- alpha * diag(A B B^T A^T) + beta * x (oracle; test
-infrastructure).
+"""Squared row norms x <- alpha * diag(A B B^T A^T) + beta * x.
+Oracle; test infrastructure.
 
 Sec. 3.3: csrsqn(alpha, A, B, beta, x) / rmsqn.  The plain definition is
 q_i = ||e_i^T A B||^2.  Alg. 8 evaluates the same quantity for a CSR A with
