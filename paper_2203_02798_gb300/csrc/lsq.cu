@@ -620,11 +620,16 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
             break;
         }
         if (t == o->max_refine) break;
+        // the inner solve need only reduce its residual by the factor left to
+        // reach tol (with a margin of 10), and never by less than inner_tol
+        double stop_rel = 0.1 * o->tol / eta;
+        if (stop_rel < o->inner_tol) stop_rel = o->inner_tol;
+        if (stop_rel > 0.5) stop_rel = 0.5;
         int it = 0;
         while (!h.done && it < o->max_iter) {
             lsqr_pass(A, nb, sh32, p, S, u, qpart32, sspart, st);
             cg_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv64, S, cg_s, cg_p, y, qtmp,
-                                               o->inner_tol, p);
+                                               stop_rel, p);
             ++it;
             if ((it & 3) == 0 || it >= o->max_iter) {   // stopping test every 4 iterations
                 e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
