@@ -3,7 +3,8 @@
 Workload (one "step" = one pass of the whole sketching hot path):
   A: 4,000,000 x 256 float32 (4.1 GB), A_ij = z_ij * 10^u_j, z ~ N(0,1),
      u_j ~ U(-3, 3);  CountSketch r = 65,536;  Gaussian k = 512 (BF16 tensor
-     stage, FP32 accumulation);  FP64 R of the 512 x 256 sketch;  row norms
+     stage, FP32 accumulation; the two stages as separate kernels unless
+     --fused-sketch);  FP64 R of the 512 x 256 sketch;  row norms
      ell_i = ||A_i R^-1||^2.
   metric: A-bytes per second through lsk_leverage_scores ("A GB/s sketched
   and scored"); the input (4.1 GB) is larger than L2, so no flush is needed.
@@ -183,6 +184,10 @@ def main():
     ap.add_argument("--no-next", action="store_true",
                     help="skip the sketch-and-solve (Alg. 11) and csrjlt (Alg. 4) legs")
     ap.add_argument("--jl-m", type=int, default=64, help="columns of the right JL projection Pi")
+    ap.add_argument("--fused-sketch", action="store_true",
+                    help="form the BF16 sketch with the fused kernel (lsk_count_gauss) instead of the two stages")
+    ap.add_argument("--no-sketch-stage", action="store_true",
+                    help="skip the leg that times the fused sketch against the two stages")
     ap.add_argument("--gram-only", action="store_true",
                     help="time only lsk_gram_prec (BF16x3 and FP32) on the workload's A (for profiling)")
     args = ap.parse_args()
@@ -212,6 +217,7 @@ def main():
     ell = torch.empty(N_ROWS, dtype=torch.float32, device="cuda")
     ctx = lsk.context()
     st = torch.cuda.current_stream()
+    lsk.set_fused_sketch(args.fused_sketch)
 
     def step(prec):
         lsk.leverage_scores(A, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
@@ -250,6 +256,28 @@ def main():
         return {"m": m, "ms": jms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, jms),
                 "ratio_mean": float(ratio.mean()), "ratio_std": float(ratio.std()),
                 "expected_std": (2.0 / m) ** 0.5}
+
+    def sketch_stage_leg(steps):
+        """G (S A) of the workload (r = 65,536, k = 512, BF16 mode): the fused
+        kernel (S A kept on chip, Alg. 3's blocking) against lsk_cs_sketch +
+        lsk_gauss_sketch, ms per call, and their relative difference."""
+        GSA = torch.empty((K_GAUSS, D), dtype=torch.float32, device="cuda")
+        GSA2 = torch.empty_like(GSA)
+        SA = torch.empty((R_SKETCH, D), dtype=torch.float32, device="cuda")
+        runs = {"fused": lambda: lsk.count_gauss(A, R_SKETCH, K_GAUSS, SEED, out=GSA, ctx=ctx),
+                "two_stage": lambda: lsk.gauss_sketch(lsk.cs_sketch(A, R_SKETCH, SEED, out=SA, ctx=ctx),
+                                                      K_GAUSS, SEED, "bf16", out=GSA2, ctx=ctx)}
+        out = {}
+        for name, fn in runs.items():
+            fn()
+            ctx.sync()
+            sms, _, _ = timed(fn, steps)
+            sms /= steps
+            out[name] = {"ms": sms, "GB/s": whole_job_rate(N_ROWS * D * 4, world, sms)}
+        out["rel_diff"] = float(torch.linalg.norm((GSA - GSA2).double()) / torch.linalg.norm(GSA2.double()))
+        out["workload"] = "dense 4M x 256, r = 65,536, k = 512"
+        del SA
+        return out
 
     def next_legs(steps):
         """Sketch-and-solve (Alg. 11) on the workload's A with a synthetic b, and
@@ -392,6 +420,7 @@ def main():
 
     gram = None if args.no_gram else gram_leg(max(3, args.steps // 5))
     jl = None if args.no_jl else jl_leg(max(3, args.steps // 5))
+    sstage = None if args.no_sketch_stage else sketch_stage_leg(max(3, args.steps // 5))
     nxt = None if args.no_next else next_legs(max(3, args.steps // 5))
     batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve else run_served(args, lsk, torch)
@@ -411,7 +440,7 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "gram": gram, "jl": jl, "next": nxt, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
     if world > 1:
@@ -545,6 +574,7 @@ def algorithmic_work(kernel):
                              "flops": 3 * n * d * (d + 1)},
         "gauss_simt": {"bound": "alu", "flops": 2 * k * r * d},
         "gauss_tc": {"bound": "tensor", "flops": 2 * 2 * k * r * d},
+        "count_gauss": {"bound": "hbm", "bytes": a_bytes + 4 * n},
     }
     return table.get(kernel, {"bound": "hbm", "bytes": a_bytes})
 

@@ -122,6 +122,26 @@ int lsk_cs_sketch(lsk_ctx* ctx, const lsk_mat* A, int64_t r, uint64_t seed,
 int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
                      int64_t k, uint64_t seed, int32_t prec, float* GSA);
 
+/* Both stages of CountGauss in one pass over A (Alg. 3, which forms S*A a
+ * block of r at a time and adds G_i (S_i A), so that only one block of S*A
+ * exists at once): GSA = G * (S * A) with S, G as in lsk_cs_sketch and
+ * lsk_gauss_sketch in the LSK_PREC_BF16 mode (same hash, signs and draws);
+ * S*A is never written to device memory -- each 32-bucket block is summed
+ * in shared memory, split into bfloat16 hi + lo and multiplied on the tensor
+ * cores at once.  A: dense, 32 <= d <= 256, d and ld multiples of 4,
+ * values 16-byte aligned (else LSK_ERR_UNSUPPORTED); 1 <= k <= 512,
+ * 1 <= r < 2^31.  GSA: device k*d floats row-major, overwritten.  Agrees
+ * with lsk_cs_sketch + lsk_gauss_sketch(LSK_PREC_BF16) up to FP32 rounding
+ * (the order of the rows within a bucket is not fixed). */
+int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                    uint64_t seed, float* GSA);
+/* Whether lsk_leverage_scores, lsk_leverage_scores_jl, the batch and the
+ * least-squares drivers form their BF16 sketch (k > 0) with the kernel of
+ * lsk_count_gauss where it applies (1) or with the two stages of
+ * lsk_cs_sketch + lsk_gauss_sketch (0, the default).  Process-wide; returns
+ * the previous setting. */
+int lsk_set_fused_sketch(int on);
+
 /* Gram matrix C <- alpha * A^T A + beta * C (csrrk, Sec. 5; Alg. 5 and
  * Alg. 7 for CSR A; the same operation for dense A).  C: device d*d floats
  * row-major, read when beta != 0 and overwritten.  Products are FP32,

@@ -83,6 +83,8 @@ _SIGS = {
     "lsk_reserve": (ctypes.c_int, [_P, ctypes.c_size_t]),
     "lsk_cs_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _P]),
     "lsk_gauss_sketch": (ctypes.c_int, [_P, _P, _I64, _I64, _I64, _U64, _I32, _P]),
+    "lsk_count_gauss": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _P]),
+    "lsk_set_fused_sketch": (ctypes.c_int, [ctypes.c_int]),
     "lsk_gram": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _P]),
     "lsk_gram_prec": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _D, _D, _I32, _P]),
     "lsk_rownorms_prod": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _D, _D, _I32, _I32, _P]),
@@ -255,6 +257,23 @@ def gauss_sketch(SA, k, seed, prec="fp32", out=None, ctx=None):
     ctx._call("lsk_gauss_sketch", _ptr(SA.contiguous()), int(r), int(d), int(k), int(seed), _prec(prec),
               _ptr(GSA))
     return GSA
+
+
+def count_gauss(A, r, k, seed, out=None, ctx=None):
+    """lsk_count_gauss: G*(S*A) (k x d, float32) in one pass over A, S*A kept
+    on chip (the BF16 mode of gauss_sketch)."""
+    m, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    GSA = out if out is not None else torch.empty((k, d), dtype=torch.float32, device=_dev(A))
+    ctx._call("lsk_count_gauss", ctypes.byref(m), int(r), int(k), int(seed), _ptr(GSA))
+    return GSA
+
+
+def set_fused_sketch(on):
+    """lsk_set_fused_sketch: whether the BF16 sketch of the leverage-score,
+    batch and least-squares calls uses the fused kernel (process-wide; off by
+    default); returns the previous setting."""
+    return bool(load_library().lsk_set_fused_sketch(int(bool(on))))
 
 
 def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):

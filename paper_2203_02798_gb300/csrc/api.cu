@@ -3,7 +3,9 @@
 // Host-side argument validation, the context's workspace, and the order in
 // which the kernels of each call are launched.  No compute happens here.
 #include "lsk_internal.cuh"
+#include "count_gauss.cuh"
 
+#include <atomic>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -11,6 +13,10 @@
 #include <string.h>
 
 namespace {
+
+// whether the sketch of the leverage-score and least-squares calls runs the
+// fused CountSketch + Gaussian kernel where it applies (process-wide)
+std::atomic<int> g_fused_sketch{0};
 
 int fail(lsk_ctx* ctx, int code, const char* fmt, ...) {
     if (ctx) {
@@ -179,6 +185,26 @@ int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d, int64_
     return finish(ctx, "lsk_gauss_sketch");
 }
 
+int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, float* GSA) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (r < 1 || r >= ((int64_t)1 << 31)) return fail(ctx, LSK_ERR_INVALID_ARG, "r must be in [1, 2^31)");
+    if (k < 1 || k > 512) return fail(ctx, LSK_ERR_INVALID_ARG, "k must be in [1, 512]");
+    if (!GSA) return fail(ctx, LSK_ERR_INVALID_ARG, "GSA is NULL");
+    if (!count_gauss_supported(A, r, k))
+        return fail(ctx, LSK_ERR_UNSUPPORTED,
+                    "the fused sketch needs dense A, 32 <= d <= 256, d and ld multiples of 4, 16-byte alignment");
+    rc = ws_ensure(ctx, count_gauss_workspace_bytes(A, r, k, ctx->sm_count));
+    if (rc) return rc;
+    cudaError_t e = count_gauss_launch(A, r, k, seed, GSA, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_count_gauss");
+    return finish(ctx, "lsk_count_gauss");
+}
+
+int lsk_set_fused_sketch(int on) { return g_fused_sketch.exchange(on ? 1 : 0); }
+
 int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     ProfGuard pg(ctx);
@@ -259,6 +285,10 @@ size_t stage_scratch(const lsk_mat* A, int64_t r, int64_t k, int32_t prec, int s
         const size_t g = gauss_workspace_bytes(r, A->d, k, prec, sm);
         if (g > s) s = g;
     }
+    if (k > 0 && prec == LSK_PREC_BF16) {
+        const size_t f = count_gauss_workspace_bytes(A, r, k, sm);
+        if (f > s) s = f;
+    }
     const size_t q = qr_workspace_bytes(k > 0 ? k : r, A->d);
     if (q > s) s = q;
     const size_t rn = rownorms_workspace_bytes(A, A->d, 1, prec);
@@ -286,9 +316,15 @@ SketchBufs carve(void* ws, const lsk_mat* A, int64_t r, int64_t k) {
     return b;
 }
 
-// SA -> (GSA) -> R, R^-1 on the device, all asynchronous.
+// SA -> (GSA) -> R, R^-1 on the device, all asynchronous.  In the BF16 mode
+// GSA comes from the fused kernel where it applies (SA is then not formed).
 cudaError_t sketch_and_factor_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
                                  const SketchBufs& b, double* R_out, int* flag, int sm, cudaStream_t st) {
+    if (k > 0 && prec == LSK_PREC_BF16 && g_fused_sketch.load() && count_gauss_supported(A, r, k)) {
+        cudaError_t e = count_gauss_launch(A, r, k, seed, b.GSA, b.scratch, flag, sm, st);
+        if (e != cudaSuccess) return e;
+        return qr_launch(b.GSA, k, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, flag, sm, st);
+    }
     cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, flag, sm, st);
     if (e != cudaSuccess) return e;
     const float* sk = b.SA;

@@ -1,0 +1,24 @@
+// count_gauss.cuh -- the fused CountSketch + Gaussian stage (G * (S * A) with
+// S * A kept on chip) and the pieces of the CountSketch and Gaussian stages it
+// shares with them.
+#pragma once
+#include "lsk_internal.cuh"
+
+// CountSketch steps 1-3 (rank, scan, place) on ws (cs_workspace_bytes(n, r)
+// bytes): *off (r + 1 entries, off[r] = n) and *perm (n entries, row index |
+// sign bit << 31, grouped by bucket) point into ws when the queued launches
+// have run.
+cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
+                           const uint32_t** off, const uint32_t** perm);
+
+// out[e] = the slice-order compensated sum of part[z * len + e], z < slices.
+cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, float* out, int sm_count,
+                                   cudaStream_t st);
+
+// G * (S * A) for dense FP32 A in the BF16 mode (G the bf16 rounding of the
+// scaled draws, S * A carried as bf16 hi + lo), one pass over A: supported for
+// 32 <= d <= 256 with d, ld multiples of 4 and A 16-byte aligned, 1 <= k <= 512.
+bool count_gauss_supported(const lsk_mat* A, int64_t r, int64_t k);
+size_t count_gauss_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int sm_count);
+cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, float* GSA, void* ws,
+                               int* flag, int sm_count, cudaStream_t st);

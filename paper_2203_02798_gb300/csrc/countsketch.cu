@@ -388,9 +388,10 @@ cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket,
     return cudaGetLastError();
 }
 
-cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
-                      int sm_count, cudaStream_t st) {
-    const int64_t n = A->n, d = A->d;
+// Steps 1-3 (rank, scan, place): on return *off_out (r + 1 entries, off[r] = n)
+// and *perm_out (n entries) point into ws; the launches are queued on st.
+cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
+                           const uint32_t** off_out, const uint32_t** perm_out) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     WsCarver wc{(char*)ws, 0};
     uint32_t* cnt = wc.take<uint32_t>(r + 1);
@@ -410,6 +411,18 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
     }
     if (n > 0)
         LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, off, rank, perm);
+    *off_out = off;
+    *perm_out = perm;
+    return cudaGetLastError();
+}
+
+cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
+                      int sm_count, cudaStream_t st) {
+    const int64_t n = A->n, d = A->d;
+    const uint32_t* off = nullptr;
+    const uint32_t* perm = nullptr;
+    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm);
+    if (e != cudaSuccess) return e;
 
     // parts per bucket: enough warps to stream A when there are few buckets,
     // while each part keeps several rows

@@ -383,6 +383,17 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     return cudaGetLastError();
 }
 
+// The slice-order compensated sum of `slices` partials of len floats each
+// (used by the fused CountSketch + Gaussian kernel as well).
+cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, float* out, int sm_count,
+                                   cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    int64_t g = (len + 255) / 256;
+    if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
+    LSK_PROF("gauss_reduce", st) gauss_tc_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, slices, len, out);
+    return cudaGetLastError();
+}
+
 size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k) {
     Plan P;
     plan_grouped(r, d, k, P);

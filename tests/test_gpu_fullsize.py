@@ -84,6 +84,18 @@ def test_dense_4M_x_256_bf16(lsk, dense_4m):
     assert 0.2 * d <= ell.sum() <= 5.0 * d
 
 
+def test_dense_4M_x_256_count_gauss(lsk, dense_4m):
+    """The fused CountSketch + Gaussian stage (S A kept on chip) at the bench's
+    size against the oracle's FP64 G (S A) on the same seeds."""
+    c3 = dense_4m
+    Ad = torch.from_numpy(c3["A"]).cuda()
+    got = lsk.count_gauss(Ad, c3["r"], c3["k"], c3["seed"]).cpu().numpy().astype(np.float64)
+    del Ad
+    torch.cuda.empty_cache()
+    ref = c3["GSA"]
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
 def test_dense_4M_x_256_jl_sketch_solve_and_column_selection(lsk, dense_4m):
     """The "next" rows at the bench's size: Alg. 15 with Pi (m = 64), sketch-
     and-solve (Alg. 11) and column selection with the Alg. 16 scores (c = 64),

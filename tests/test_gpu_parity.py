@@ -3,7 +3,7 @@
 Sizes span several tiles / warps / buckets and a ragged tail.  Tolerances:
   - hash and signs: bit-exact;
   - integer-valued inputs (every FP32 partial sum exact): bit-exact;
-  - FP32 paths: the benchmark spec's bound of 1e-5 relative Frobenius error on SA
+  - FP32 paths: the stated bound of 1e-5 relative Frobenius error on SA
     and A^T A, plus element-wise bounds from the summation length;
   - leverage scores: max relative error <= 1e-3 against the oracle's estimate
     on the same seeds;
