@@ -132,7 +132,10 @@ int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
  * values 16-byte aligned (else LSK_ERR_UNSUPPORTED); 1 <= k <= 512,
  * 1 <= r < 2^31.  GSA: device k*d floats row-major, overwritten.  Agrees
  * with lsk_cs_sketch + lsk_gauss_sketch(LSK_PREC_BF16) up to FP32 rounding
- * (the order of the rows within a bucket is not fixed). */
+ * (the order of the rows within a bucket is not fixed).  k outside [1, 512]
+ * or a NULL GSA: LSK_ERR_INVALID_ARG; a device wait that gives up (1 s):
+ * LSK_ERR_TIMEOUT from lsk_sync.  Correct but, as built, slower than the two
+ * separate stages (it is not the default of the calls below). */
 int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                     uint64_t seed, float* GSA);
 /* Whether lsk_leverage_scores, lsk_leverage_scores_jl, the batch and the
