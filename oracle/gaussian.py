@@ -104,6 +104,34 @@ def gauss_sketch(SA, k, seed, prec=PREC_FP32, batch=4096):
     return C
 
 
+def count_gauss_dense(A, r, k, seed, prec=PREC_BF16, block=32):
+    """rmcgs(A, m=k, r) in Alg. 3's blocked order (Sec. 2.2.2): G (S A), float64.
+
+    Alg. 3 never holds S*A whole: for each block of rows of S -- here the
+    buckets [c0, c1), ``block`` at a time -- it forms B = S_i A from the rows
+    of A that hash into those buckets (Def. 3: row i adds sigma_i A[i, :] to
+    row h(i)), draws the block's columns of G and accumulates C <- C + G_i B.
+    The hash is CountSketch's (same seed, stream 0) and G the one of
+    ``gauss_sketch`` (stream 1).  The blocking changes only the float64
+    summation order.
+    """
+    from .countsketch import countsketch_hash
+    A = np.asarray(A)
+    n, d = A.shape
+    bucket, sign = countsketch_hash(n, r, seed)
+    order = np.argsort(bucket, kind="stable")            # rows grouped by bucket
+    first = np.searchsorted(bucket[order], np.arange(r + 1))   # bucket b: order[first[b]:first[b + 1]]
+    sgn = np.asarray(sign, dtype=np.float64)
+    C = np.zeros((k, d), dtype=np.float64)
+    for c0 in range(0, r, block):
+        c1 = min(r, c0 + block)
+        rows = order[first[c0]:first[c1]]
+        B = np.zeros((c1 - c0, d), dtype=np.float64)
+        np.add.at(B, bucket[rows] - c0, sgn[rows, None] * A[rows].astype(np.float64))
+        C += gaussian_columns(k, c0, c1, seed, prec) @ B
+    return C
+
+
 def csrjlt(V, J, I, n, d, m, seed, prec=PREC_FP32, batch=4096):
     """C = G A (m x d, float64) for CSR A (Alg. 4, ``csrjlt``).
 

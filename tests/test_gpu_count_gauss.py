@@ -1,6 +1,6 @@
 """GPU parity of the fused CountSketch + Gaussian stage (lsk_count_gauss):
 G*(S*A) in one pass over A, S*A kept on chip (Alg. 3's blocked CountGauss),
-against the FP64 oracle's two stages on the same seeds.
+against the FP64 oracle's blocked CountGauss on the same seeds.
 
 Tolerances: the BF16 mode of the Gaussian stage -- G is the bf16 rounding of
 the scaled draws on both sides (rare one-ulp disagreements where the float32
@@ -56,8 +56,7 @@ def test_count_gauss_matches_oracle(lsk, n, d, r, k):
     A = workloads.dense_normal(n, d, seed=d + k)
     got = host(lsk.count_gauss(dev(A), r, k, seed)).astype(np.float64)
     A64 = A.astype(np.float64)
-    SA = ocs.cs_sketch_dense(A64, r, seed)
-    ref = oga.gauss_sketch(SA, k, seed, oga.PREC_BF16)
+    ref = oga.count_gauss_dense(A64, r, k, seed, oga.PREC_BF16)   # Alg. 3's blocked order
     assert rel_fro(got, ref) <= 1e-4
     bucket, sign = ocs.countsketch_hash(n, r, seed)
     absSA = ocs.countsketch_apply_dense(np.abs(A64), bucket, np.ones_like(sign), r)

@@ -105,3 +105,37 @@ def test_jl_projection_scale_distribution_and_stream():
     assert abs(np.corrcoef(G.ravel(), P.T.ravel())[0, 1]) < 5 / np.sqrt(G.size)
     # the construction: Pi[i, c] is G's entry (c, i) on the Pi stream
     assert np.array_equal(P[5:9, 40:48], ga.gaussian_columns(m, 5, 9, seed, stream=ga.STREAM_PI)[40:48].T)
+
+
+def test_count_gauss_blocked_equals_explicit_product():
+    """Alg. 3's blocked CountGauss against the plain product G S A with the
+    explicit S of Def. 3 (brute force on small inputs), for block sizes that
+    split buckets unevenly, one bucket per block and the whole of r; buckets
+    that no row hashes to (r > n) add nothing."""
+    from oracle import countsketch as cs
+    rng = np.random.default_rng(5)
+    for n, d, r, k in [(300, 7, 40, 9), (50, 3, 200, 4), (1, 5, 3, 2)]:
+        A = rng.standard_normal((n, d))
+        bucket, sign = cs.countsketch_hash(n, r, 11)
+        S = cs.countsketch_matrix(bucket, sign, r)
+        for prec in (ga.PREC_FP32, ga.PREC_BF16):
+            ref = ga.gaussian_matrix(k, r, 11, prec) @ (S @ A)
+            for block in (1, 7, 32, r):
+                got = ga.count_gauss_dense(A, r, k, 11, prec, block=block)
+                assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_count_gauss_blocked_equals_the_two_stages():
+    """The blocked form equals the separate stages S A, then G (S A)."""
+    from oracle import countsketch as cs
+    A = np.random.default_rng(6).standard_normal((5000, 16))
+    two = ga.gauss_sketch(cs.cs_sketch_dense(A, 700, 3), 48, 3, ga.PREC_BF16)
+    got = ga.count_gauss_dense(A, 700, 48, 3, ga.PREC_BF16)
+    assert np.allclose(got, two, rtol=1e-12, atol=1e-12 * np.abs(two).max())
+    # a sign flip of one row of A changes exactly its bucket's column of G times that row
+    A2 = A.copy()
+    A2[17] *= -1
+    bucket, sign = cs.countsketch_hash(5000, 700, 3)
+    g = ga.gaussian_columns(48, int(bucket[17]), int(bucket[17]) + 1, 3, ga.PREC_BF16)[:, 0]
+    diff = ga.count_gauss_dense(A2, 700, 48, 3, ga.PREC_BF16) - got
+    assert np.allclose(diff, -2 * sign[17] * np.outer(g, A[17]), atol=1e-12)
