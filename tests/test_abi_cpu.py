@@ -56,3 +56,13 @@ def test_binding_exports_same_names():
     for n in ["cs_sketch", "gauss_sketch", "gram", "rownorms_prod", "leverage_scores",
               "sketch_precondition_lsq", "sketch_qr", "debug_hash", "debug_gauss"]:
         assert callable(getattr(p, n))
+
+
+def test_fused_sketch_switch_is_host_state(lib):
+    """lsk_set_fused_sketch only flips process-wide host state (no CUDA call):
+    off by default, returns the previous setting."""
+    lib.lsk_set_fused_sketch.restype = ctypes.c_int
+    lib.lsk_set_fused_sketch.argtypes = [ctypes.c_int]
+    assert lib.lsk_set_fused_sketch(1) == 0
+    assert lib.lsk_set_fused_sketch(0) == 1
+    assert lib.lsk_set_fused_sketch(0) == 0
