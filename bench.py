@@ -184,8 +184,9 @@ def main():
     ap.add_argument("--no-next", action="store_true",
                     help="skip the sketch-and-solve (Alg. 11) and csrjlt (Alg. 4) legs")
     ap.add_argument("--jl-m", type=int, default=64, help="columns of the right JL projection Pi")
-    ap.add_argument("--fused-sketch", action="store_true",
-                    help="form the BF16 sketch with the fused kernel (lsk_count_gauss) instead of the two stages")
+    ap.add_argument("--fused-sketch", type=int, default=1, choices=[0, 1, 2],
+                    help="BF16 sketch: 0 the two stages, 1 the fused kernel (lsk_count_gauss) where the shape "
+                         "favours it (default), 2 the fused kernel wherever it applies")
     ap.add_argument("--no-sketch-stage", action="store_true",
                     help="skip the leg that times the fused sketch against the two stages")
     ap.add_argument("--gram-only", action="store_true",

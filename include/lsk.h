@@ -127,23 +127,29 @@ int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
  * exists at once): GSA = G * (S * A) with S, G as in lsk_cs_sketch and
  * lsk_gauss_sketch in the LSK_PREC_BF16 mode (same hash, signs and draws);
  * S*A is never written to device memory -- each 32-bucket block is summed
- * in shared memory, split into bfloat16 hi + lo and multiplied on the tensor
- * cores at once.  A: dense, 32 <= d <= 256, d and ld multiples of 4,
+ * on chip, split into bfloat16 hi + lo and multiplied on the tensor cores at
+ * once.  A: dense, 32 <= d <= 256, d and ld multiples of 4,
  * values 16-byte aligned (else LSK_ERR_UNSUPPORTED); 1 <= k <= 512,
  * 1 <= r < 2^31.  GSA: device k*d floats row-major, overwritten.  Agrees
  * with lsk_cs_sketch + lsk_gauss_sketch(LSK_PREC_BF16) up to FP32 rounding
  * (the order of the rows within a bucket is not fixed).  k outside [1, 512]
  * or a NULL GSA: LSK_ERR_INVALID_ARG; a device wait that gives up (1 s):
- * LSK_ERR_TIMEOUT from lsk_sync.  Correct but, as built, slower than the two
- * separate stages (it is not the default of the calls below). */
+ * LSK_ERR_TIMEOUT from lsk_sync.  Faster than the two separate stages for
+ * wide (d > 192), tall (n >= 8 r) problems with r >= 8 * 32 buckets per pair
+ * of SMs (4M x 256, r = 65,536, k = 512 on GB300: 0.70 ms against 0.92 ms);
+ * slower for narrower or smaller ones. */
 int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                     uint64_t seed, float* GSA);
-/* Whether lsk_leverage_scores, lsk_leverage_scores_jl, the batch and the
- * least-squares drivers form their BF16 sketch (k > 0) with the kernel of
- * lsk_count_gauss where it applies (1) or with the two stages of
- * lsk_cs_sketch + lsk_gauss_sketch (0, the default).  Process-wide; returns
- * the previous setting. */
-int lsk_set_fused_sketch(int on);
+/* How lsk_leverage_scores, lsk_leverage_scores_jl, the least-squares driver
+ * and the batch's ungrouped problems form their BF16 sketch (k > 0):
+ *   0  the two stages (lsk_cs_sketch + lsk_gauss_sketch);
+ *   1  the kernel of lsk_count_gauss where the shape favours it (see above),
+ *      else the two stages -- the default;
+ *   2  the kernel of lsk_count_gauss wherever it applies.
+ * The batch's grouped problems always take the two stages (their Gaussian
+ * stage is one grouped launch over all of them).  Process-wide; values
+ * outside [0, 2] are clamped; returns the previous setting. */
+int lsk_set_fused_sketch(int mode);
 
 /* Gram matrix C <- alpha * A^T A + beta * C (csrrk, Sec. 5; Alg. 5 and
  * Alg. 7 for CSR A; the same operation for dense A).  C: device d*d floats
@@ -391,14 +397,16 @@ int lsk_debug_wait_timeout(lsk_ctx* ctx, int64_t limit_us);
  *
  * Same result as lsk_cs_sketch (S*A, same hash, same layouts), but it takes
  * no context and allocates nothing: its scratch is one 12 MiB array in device
- * global memory reserved by the library on every GPU that loads it (held
- * until the process exits).  The caller passes A and the output SA (device
- * pointers) and the cudaStream_t to launch on (NULL = legacy default).
+ * global memory (held until the process exits).  The caller passes A and the
+ * output SA (device pointers) and the cudaStream_t to launch on (NULL =
+ * legacy default).
  *  - Limits: n <= LSK_NOALLOC_MAX_ROWS, 1 <= r <= LSK_NOALLOC_MAX_BUCKETS;
  *    larger sizes return LSK_ERR_UNSUPPORTED before anything is launched.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current).  The CUDA runtime
+ *    loads device code lazily, so that first call is when the array and the
+ *    CountSketch kernels' code are placed on the device: make it during
+ *    set-up, before any stream capture.  Later calls allocate nothing.
  *  - Every call shares the array and it keeps the last call's contents (the
  *    bucket counts are cleared at the start of each call), so calls whose
  *    GPU work overlaps -- on two streams or from two threads -- race and

@@ -269,11 +269,15 @@ def count_gauss(A, r, k, seed, out=None, ctx=None):
     return GSA
 
 
-def set_fused_sketch(on):
-    """lsk_set_fused_sketch: whether the BF16 sketch of the leverage-score,
-    batch and least-squares calls uses the fused kernel (process-wide; off by
-    default); returns the previous setting."""
-    return bool(load_library().lsk_set_fused_sketch(int(bool(on))))
+def set_fused_sketch(mode):
+    """lsk_set_fused_sketch: how the BF16 sketch of the leverage-score,
+    least-squares and batch calls is formed -- 0 the two stages, 1 the fused
+    kernel where the shape favours it (the default), 2 the fused kernel
+    wherever it applies (True is 2, False is 0); process-wide.  Returns the
+    previous mode."""
+    if isinstance(mode, bool):
+        mode = 2 if mode else 0
+    return int(load_library().lsk_set_fused_sketch(int(mode)))
 
 
 def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):

@@ -14,9 +14,10 @@
 
 namespace {
 
-// whether the sketch of the leverage-score and least-squares calls runs the
-// fused CountSketch + Gaussian kernel where it applies (process-wide)
-std::atomic<int> g_fused_sketch{0};
+// how the BF16 sketch of the leverage-score and least-squares calls is formed
+// (process-wide): 0 the two stages, 1 the fused CountSketch + Gaussian kernel
+// where the shape favours it, 2 the fused kernel wherever it applies
+std::atomic<int> g_fused_sketch{1};
 
 int fail(lsk_ctx* ctx, int code, const char* fmt, ...) {
     if (ctx) {
@@ -203,7 +204,7 @@ int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64
     return finish(ctx, "lsk_count_gauss");
 }
 
-int lsk_set_fused_sketch(int on) { return g_fused_sketch.exchange(on ? 1 : 0); }
+int lsk_set_fused_sketch(int mode) { return g_fused_sketch.exchange(mode < 0 ? 0 : mode > 2 ? 2 : mode); }
 
 int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
@@ -320,7 +321,9 @@ SketchBufs carve(void* ws, const lsk_mat* A, int64_t r, int64_t k) {
 // GSA comes from the fused kernel where it applies (SA is then not formed).
 cudaError_t sketch_and_factor_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
                                  const SketchBufs& b, double* R_out, int* flag, int sm, cudaStream_t st) {
-    if (k > 0 && prec == LSK_PREC_BF16 && g_fused_sketch.load() && count_gauss_supported(A, r, k)) {
+    const int fused = g_fused_sketch.load();
+    if (k > 0 && prec == LSK_PREC_BF16 &&
+        ((fused == 1 && count_gauss_preferred(A, r, k, sm)) || (fused == 2 && count_gauss_supported(A, r, k)))) {
         cudaError_t e = count_gauss_launch(A, r, k, seed, b.GSA, b.scratch, flag, sm, st);
         if (e != cudaSuccess) return e;
         return qr_launch(b.GSA, k, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, flag, sm, st);
@@ -804,3 +807,5 @@ int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed, int32_t p
 }
 
 }  // extern "C"
+
+int fused_sketch_on() { return g_fused_sketch.load(); }

@@ -318,6 +318,8 @@ uint64_t signature(const lsk_batch_item* items, int count, int32_t prec) {
 
 uint64_t exact_key(const LskBatch* b, const lsk_batch_item* items, int count, int32_t prec, int S) {
     uint64_t h = fnv(signature(items, count, prec), &S, sizeof(S));
+    const int fused = fused_sketch_on();   // ungrouped problems' sketch path is recorded in the graph
+    h = fnv(h, &fused, sizeof(fused));
     h = fnv(h, &b->arena, sizeof(b->arena));
     h = fnv(h, &b->table, sizeof(b->table));
     for (size_t s = 0; s < b->ws.size(); ++s) h = fnv(h, &b->ws[s], sizeof(void*));

@@ -4,19 +4,19 @@
 // Alg. 3 forms the sketch in blocks of r: B = S_i A for one block of rows of
 // S, then C += G_i B with a fresh Gaussian block G_i, so that only one block
 // of S A exists at a time.  Here a block is 32 buckets (one K-chunk of the
-// tensor-core product) and it lives in shared memory only.  A cluster of two
-// CTAs (a tcgen05 CTA pair) owns one slice of the buckets and the whole
-// k x d product of that slice:
-//   - producer warp: copies the rows of A bucket by bucket (the order of the
-//     CountSketch permutation, steps 1-3 of countsketch.cu) into a ring of
-//     row slots with 16-byte asynchronous copies (cp.async, one per lane and
-//     row) -- each CTA its half of the columns -- and writes each row's sign
-//     beside it;
-//   - 4 summing warps: walk the ring in order, add every row (with its sign)
-//     to the open bucket's sum (one column per lane), and when a bucket closes
-//     write its sum as bf16 hi + lo into the K-major B operand of the chunk;
-//   - 8 worker warps: draw this CTA's rows of the chunk's columns of G
-//     (the Gaussian stage's Philox + Box-Muller draws, bf16) into the A operand;
+// tensor-core product) and it lives in shared memory only, as bf16 hi + lo.
+// A cluster of two CTAs (a tcgen05 CTA pair) owns one slice of the buckets
+// and the whole k x d product of that slice:
+//   - 16 gather warps per CTA: CTA `rank` sums buckets [16 rank, 16 rank + 16)
+//     of every chunk, one per warp, whole rows at a time.  A bucket's rows are
+//     consecutive in the CountSketch permutation (steps 1-3 of countsketch.cu);
+//     they stream through a private ring of row slots in shared memory filled
+//     with per-lane 16-byte cp.async copies, several rows in flight per warp
+//     without holding registers.  When a bucket closes, its first half of
+//     columns goes as bf16 hi + lo into the even CTA's B operand of the chunk
+//     and its second half into the odd CTA's (distributed shared memory);
+//   - 8 worker warps: draw this CTA's rows of the chunk's columns of G (the
+//     Gaussian stage's Philox + Box-Muller draws, bf16) into the A operand;
 //   - the even CTA's MMA thread: M = 256 pair MMAs, G rows [0, 128) of each
 //     256-row set from the even CTA and [128, 256) from the odd one, B's first
 //     N / 2 = d_pad / 2 rows (S A columns) from the even CTA and the rest from
@@ -24,8 +24,16 @@
 //     keeps the whole 512 x 256 FP32 accumulator (2 x 512 columns);
 //   - the worker warps then copy the accumulator out as the slice's partial,
 //     and the partials are summed in slice order (compensated FP32).
-// Every wait is bounded (1 s); a timeout sets LSK_FLAG_TIMEOUT and the copies
-// in flight are waited for before the CTA leaves.
+// A ring of kStages chunk operands lets the gather warps and the draws run
+// ahead of the MMAs.  Every wait is bounded (1 s); a timeout sets
+// LSK_FLAG_TIMEOUT and every warp winds down (a gather warp waits for its own
+// copies in flight before it leaves).
+//
+// Why the rows go through shared memory: the gather is bound by the bytes in
+// flight per SM (Little's law: ~45 GB/s per SM at ~2 us loaded latency needs
+// ~90 KB).  Loads into registers capped that at 64 KB here (the draws, the
+// MMA and TMEM bookkeeping share the register file), 0.84 ms at 4M x 256;
+// the cp.async rings hold 80 KB without registers: 0.70 ms.
 #include "tc_common.cuh"
 #include "count_gauss.cuh"
 
@@ -41,19 +49,20 @@ constexpr int kHalfRows = 128;       // ... of which each CTA holds 128
 constexpr int kMaxSets = 2;          // k <= 512
 constexpr int kWorkers = 8;          // G-drawing warps 0..7 (also the epilogue)
 constexpr int kWorkerThreads = kWorkers * 32;
-constexpr int kCons0 = kWorkers;     // summing warps 8..11
-constexpr int kCons = 4;
-constexpr int kProdWarp = kCons0 + kCons;   // 12
-constexpr int kMmaWarp = kProdWarp + 1;     // 13
-constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kGath0 = kWorkers;     // first gather warp
 constexpr int kStages = 3;
-constexpr int kGroupRows = 8;        // ring rows per barrier
-constexpr int kGroups = 24;
-constexpr int kRing = kGroups * kGroupRows;   // row slots per CTA
 constexpr size_t kSmemLimit = 232448;
 
-static_assert(kCons * 32 >= 128, "the summing warps cover a 128-column half");
 static_assert(2 * kMaxSets * kWorkerThreads == kMaxSets * 32 * 16, "two G items per thread and set");
+
+// gather warps and rows in flight per gather warp
+template <int NG, int kRing>
+struct Shape {
+    static constexpr int kMmaWarp = kGath0 + NG;
+    static constexpr int kThreads = (kMmaWarp + 1) * 32;
+    static_assert(NG == 16, "a CTA sums 16 buckets of a chunk, one per gather warp");
+    static_assert(kRing >= 2 && kRing <= 16, "row slots per gather warp");
+};
 
 struct CgParams {
     const float* A;
@@ -74,50 +83,60 @@ struct CgParams {
 __host__ __device__ constexpr uint32_t a_bytes() { return kMaxSets * kHalfRows * kKC * 2; }   // 16 KB
 __host__ __device__ inline uint32_t b_bytes(int hw) { return (uint32_t)hw * kKC * 2; }        // hi or lo
 __host__ __device__ inline uint32_t stage_bytes(int hw) { return a_bytes() + 2 * b_bytes(hw); }
-inline size_t smem_bytes(int hw) {
-    return 1024 + (size_t)kStages * stage_bytes(hw) + (size_t)kRing * hw * 4 + (size_t)kRing * 4 +
-           (size_t)(2 * kStages + 2 * kGroups + 2) * 8 + 16;
+// stages, then the gather warps' row rings (16 warps x ring slots x 1 KB), then the barriers
+inline size_t smem_bytes(int hw, int ring) {
+    return 1024 + (size_t)kStages * stage_bytes(hw) + (size_t)16 * ring * 1024 + (size_t)(2 * kStages + 2) * 8 + 16;
 }
 
-// 16 bytes global -> shared, asynchronous, cached in L2 only (both addresses
-// 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
-// one arrival on `bar` once every cp.async this thread has issued so far has
-// landed (counted in the barrier's expected arrivals)
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void arrive_even(uint64_t* bar, uint32_t rank) {
     if (rank == 0) tc::mbar_arrive(bar);
     else tc::mbar_arrive_cluster(bar, 0);
 }
-// x as bf16 hi + lo at element (n, k) of the K-major hi / lo tiles
-__device__ __forceinline__ void store_split(uint8_t* bh, uint32_t bbytes, int n, int k, float x) {
-    uint32_t h, l;
-    tc::split_bf16x2(x, 0.f, h, l);
-    const uint32_t o = tc::sw64_offset((uint32_t)n, (uint32_t)k);
-    *reinterpret_cast<uint16_t*>(bh + o) = (uint16_t)(h & 0xFFFFu);
-    *reinterpret_cast<uint16_t*>(bh + bbytes + o) = (uint16_t)(l & 0xFFFFu);
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(local), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ void st_cluster_u16(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"((uint16_t)v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+// the four sums of a lane (rows n .. n + 3 of a B operand, bucket k of the
+// chunk) as bf16 hi + lo into the K-major hi / lo tiles at shared::cluster
+// address bh (this CTA's or the peer's)
+__device__ __forceinline__ void store_split4(uint32_t bh, uint32_t bbytes, int n, int k, float4 x) {
+    uint32_t h01, l01, h23, l23;
+    tc::split_bf16x2(x.x, x.y, h01, l01);
+    tc::split_bf16x2(x.z, x.w, h23, l23);
+    const uint32_t o0 = tc::sw64_offset((uint32_t)n, (uint32_t)k), o1 = tc::sw64_offset((uint32_t)n + 1, (uint32_t)k);
+    const uint32_t o2 = tc::sw64_offset((uint32_t)n + 2, (uint32_t)k), o3 = tc::sw64_offset((uint32_t)n + 3, (uint32_t)k);
+    st_cluster_u16(bh + o0, h01);
+    st_cluster_u16(bh + o1, h01 >> 16);
+    st_cluster_u16(bh + o2, h23);
+    st_cluster_u16(bh + o3, h23 >> 16);
+    st_cluster_u16(bh + bbytes + o0, l01);
+    st_cluster_u16(bh + bbytes + o1, l01 >> 16);
+    st_cluster_u16(bh + bbytes + o2, l23);
+    st_cluster_u16(bh + bbytes + o3, l23 >> 16);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_gauss_kernel(const CgParams p) {
+template <int NG, int kRing>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Shape<NG, kRing>::kThreads, 1)
+    count_gauss_kernel(const CgParams p) {
+    constexpr int kMmaWarp = Shape<NG, kRing>::kMmaWarp;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t rank = tc::cluster_ctarank();
     const int slice = (int)tc::cluster_id_x();
     const uint32_t sbytes = stage_bytes(p.hw), bbytes = b_bytes(p.hw);
     uint8_t* stages = smem;
-    float* ring = reinterpret_cast<float*>(smem + kStages * sbytes);   // kRing slots of hw floats
-    float* sgn = ring + kRing * p.hw;                                   // kRing signs
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sgn + kRing);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * sbytes + NG * kRing * 1024);
     uint64_t* fullS = bars;                  // [kStages] even CTA: chunk operands written in both CTAs
     uint64_t* emptyS = fullS + kStages;      // [kStages] chunk consumed (multicast commit)
-    uint64_t* fullR = emptyS + kStages;      // [kGroups] ring group landed (copy bytes)
-    uint64_t* emptyR = fullR + kGroups;      // [kGroups] ring group read by the summing warps
-    uint64_t* done = emptyR + kGroups;       // accumulator complete (multicast commit)
+    uint64_t* done = emptyS + kStages;       // accumulator complete (multicast commit)
     uint64_t* fin = done + 1;                // every MMA complete (multicast commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -126,19 +145,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_g
     const int64_t c_begin = (int64_t)slice * p.kslice;
     const int64_t c_end = min(p.r, c_begin + p.kslice);
     const int nchunks = c_begin < c_end ? (int)((c_end - c_begin + kKC - 1) / kKC) : 0;
-    const uint32_t T0 = c_begin < c_end ? __ldg(p.off + c_begin) : 0u;
-    const uint32_t T = c_begin < c_end ? __ldg(p.off + c_end) - T0 : 0u;   // rows of this slice
     const int col0 = (int)rank * p.hw;                                    // first column of S A here
     const int hv = max(0, min(p.hw, p.d - col0));                         // valid columns here
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(fullS + s, 2 * (kWorkers + kCons));
+            tc::mbar_init(fullS + s, 2 * (kWorkers + NG));
             tc::mbar_init(emptyS + s, 1);
-        }
-        for (int g = 0; g < kGroups; ++g) {
-            tc::mbar_init(fullR + g, 32 + 1);   // the producer's lanes (copies landed) + its signs
-            tc::mbar_init(emptyR + g, kCons);
         }
         tc::mbar_init(done, 1);
         tc::mbar_init(fin, 1);
@@ -162,27 +175,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_g
         for (int g = 0; g < nchunks; ++g) {
             const int s = g % kStages;
             const int64_t c0 = c_begin + (int64_t)g * kKC;
-            uint32_t gw[2 * kMaxSets][4];
-#pragma unroll
-            for (int i = 0; i < 2 * kMaxSets; ++i) {
-                const int item = wt + kWorkerThreads * i;
-                const int gq = item >> 4, cp = item & 15;
-                const int64_t jq = (int64_t)(gq >> 5) * kSetRows + (int64_t)rank * kHalfRows + 4 * (gq & 31);
-                const int64_t c = c0 + 2 * cp;
-                float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
-                if (item < items && jq < p.k) {
-                    if (c < c_end) z0 = gauss4((uint64_t)c, (uint32_t)(jq >> 2), p.k0, p.k1);
-                    if (c + 1 < c_end) z1 = gauss4((uint64_t)(c + 1), (uint32_t)(jq >> 2), p.k0, p.k1);
-                }
-                const float a0[4] = {z0.x, z0.y, z0.z, z0.w}, a1[4] = {z1.x, z1.y, z1.z, z1.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const bool rowok = jq + t < p.k;
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(rowok ? a0[t] * p.scale : 0.f,
-                                                                   rowok ? a1[t] * p.scale : 0.f);
-                    gw[i][t] = *reinterpret_cast<const uint32_t*>(&h);
-                }
-            }
+            // the ring keeps the workers ahead of the MMAs, so they claim the
+            // stage first and draw straight into it (few registers live)
             int w = 1;
             if (lane == 0) w = tc::mbar_wait(emptyS + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, w, 0)) {
@@ -196,9 +190,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_g
                 const int item = wt + kWorkerThreads * i;
                 if (item < items) {
                     const int gq = item >> 4, cp = item & 15;
+                    const int64_t jq = (int64_t)(gq >> 5) * kSetRows + (int64_t)rank * kHalfRows + 4 * (gq & 31);
+                    const int64_t c = c0 + 2 * cp;
+                    float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
+                    if (jq < p.k) {
+                        if (c < c_end) z0 = gauss4((uint64_t)c, (uint32_t)(jq >> 2), p.k0, p.k1);
+                        if (c + 1 < c_end) z1 = gauss4((uint64_t)(c + 1), (uint32_t)(jq >> 2), p.k0, p.k1);
+                    }
+                    const float a0[4] = {z0.x, z0.y, z0.z, z0.w}, a1[4] = {z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        *reinterpret_cast<uint32_t*>(st + tc::sw64_offset(4 * gq + t, 2 * cp)) = gw[i][t];
+                    for (int t = 0; t < 4; ++t) {
+                        const bool rowok = jq + t < p.k;
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(rowok ? a0[t] * p.scale : 0.f,
+                                                                       rowok ? a1[t] * p.scale : 0.f);
+                        *reinterpret_cast<uint32_t*>(st + tc::sw64_offset(4 * gq + t, 2 * cp)) =
+                            *reinterpret_cast<const uint32_t*>(&h);
+                    }
                 }
             }
             tc::fence_proxy_async_smem();
@@ -228,138 +235,157 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_g
                 }
             }
         }
-    } else if (warp < kProdWarp) {
-        // ------------------------------------------------------------ summing warps
-        const int col = (warp - kCons0) * 32 + lane;   // column of this CTA's half
-        const bool colv = col < hv, colb = col < p.hw;
-        // lane l: end (row of the slice) of bucket l of chunk g
-        auto ends_of = [&](int g) -> uint32_t {
-            const int64_t c = c_begin + (int64_t)g * kKC + lane;
-            return (g < nchunks && c < c_end) ? __ldg(p.off + c + 1) - T0 : T;
-        };
-        uint8_t* bh = stages + a_bytes();
-        auto claim = [&](int g) -> bool {
-            int w = 1;
-            if (lane == 0)
-                w = tc::mbar_wait(emptyS + g % kStages, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
-            bh = stages + (g % kStages) * sbytes + a_bytes();
-            return __shfl_sync(0xffffffffu, w, 0) != 0;
-        };
-        uint32_t ends_cur = ends_of(0), ends_nxt = ends_of(1);
-        int g = 0, bb = 0;
-        int nb = nchunks > 0 ? (int)min((int64_t)kKC, c_end - c_begin) : 0;
-        float acc = 0.f;
-        uint32_t t = 0;
-        bool ok = nchunks > 0 && claim(0);
-        uint32_t bend = __shfl_sync(0xffffffffu, ends_cur, 0);
-        // close every bucket that ends at row t, and each chunk they complete
-        auto advance = [&]() -> bool {
-            while (t == bend) {
-                if (colb) store_split(bh, bbytes, col, bb, acc);
-                acc = 0.f;
-                if (++bb == nb) {
-                    if (colb)
-                        for (int z = nb; z < kKC; ++z) store_split(bh, bbytes, col, z, 0.f);
-                    tc::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) arrive_even(fullS + g % kStages, rank);
-                    if (++g == nchunks) {
-                        bend = 0xFFFFFFFFu;
-                        return true;
-                    }
-                    bb = 0;
-                    nb = (int)min((int64_t)kKC, c_end - (c_begin + (int64_t)g * kKC));
-                    ends_cur = ends_nxt;
-                    ends_nxt = ends_of(g + 1);
-                    if (!claim(g)) return false;
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------ gather warps
+        // CTA `rank` sums buckets [16 rank, 16 rank + 16) of every chunk; gather
+        // warp gi sums bucket 16 rank + gi of each chunk, whole rows at a time
+        // (lane l: columns 4l.. of each half).  A bucket's first half goes to
+        // the even CTA's B operand and its second half to the odd CTA's.
+        //
+        // The rows stream through a private ring of kRing row slots in shared
+        // memory: each step the warp issues one row (every lane copies its
+        // 2 x 16 bytes with cp.async) and sums the row issued kRing - 1 steps
+        // earlier, so kRing - 1 rows are in flight per warp without holding
+        // registers.  A lane reads back only the bytes it copied itself, so its
+        // own cp.async.wait_group orders the copy before the read.  The copying
+        // side walks the warp's buckets (chunk by chunk) ahead of the summing
+        // side; every issued row carries its chunk and sign to the summing side
+        // (meta), which closes a chunk's bucket when a row of a later chunk
+        // arrives (or at the end).
+        const int gi = warp - kGath0;
+        const int n0 = 4 * lane;
+        const bool lv0 = n0 < min(p.hw, p.d);            // columns n0.. of the first half exist
+        const bool lv1 = p.hw + n0 < p.d;                // ... of the second half
+        const bool lb = n0 < p.hw;                       // rows n0.. of the B operands
+        const float* A0 = p.A + n0;
+        const float* A1 = p.A + p.hw + n0;
+        const uint32_t here = tc::smem_u32(stages);
+        const uint32_t tile0 = peer_addr(here, 0);       // the stages of the even CTA (shared::cluster)
+        const uint32_t tile1 = peer_addr(here, 1);       // ... of the odd CTA
+        const uint32_t ring = here + kStages * sbytes + (uint32_t)(gi * kRing * 1024 + 16 * lane);
+        const int kb = 16 * (int)rank + gi;              // this warp's bucket within every chunk
+        auto range_of = [&](int g, uint32_t& bs, uint32_t& be) {
+            bs = be = 0u;
+            if (g < nchunks) {
+                const int64_t b = c_begin + (int64_t)g * kKC + kb;
+                if (b < c_end) {
+                    bs = __ldg(p.off + b);
+                    be = __ldg(p.off + b + 1);
                 }
-                bend = __shfl_sync(0xffffffffu, ends_cur, bb);
             }
+        };
+        auto window = [&](uint32_t t, uint32_t e) -> uint32_t {
+            return (t + lane < e) ? __ldg(p.perm + t + lane) : 0x80000000u;
+        };
+        // ---- copying side: chunk gp, rows [tp, ep) of its bucket, permutation
+        // window [wp, wp + 32) in pwp, the next window (base pnb) in pnp
+        int gp = 0;
+        uint32_t tp, ep, s1, e1, s2, e2;
+        range_of(0, tp, ep);
+        range_of(1, s1, e1);
+        range_of(2, s2, e2);
+        uint32_t wp = tp, pwp = window(tp, ep);
+        uint32_t pnb = tp + 32 < ep ? tp + 32 : s1, pne = tp + 32 < ep ? ep : e1;
+        uint32_t pnp = window(pnb, pne);
+        // window [tp, tp + 32): from pnp when that was loaded for it (the same
+        // base and bucket end), and the next one (this bucket's or the next
+        // bucket's first) into pnp
+        auto open_window = [&]() {
+            wp = tp;
+            pwp = (pnb == tp && pne == ep) ? pnp : window(tp, ep);
+            pnb = tp + 32 < ep ? tp + 32 : s1;
+            pne = tp + 32 < ep ? ep : e1;
+            pnp = window(pnb, pne);
+        };
+        // move to the next row to copy: skip finished (and empty) buckets, open windows
+        auto normalize = [&]() {
+            while (gp < nchunks && tp == ep) {
+                ++gp;
+                tp = s1;
+                ep = e1;
+                s1 = s2;
+                e1 = e2;
+                range_of(gp + 2, s2, e2);
+                if (tp < ep) open_window();
+            }
+            if (gp < nchunks && tp == wp + 32) open_window();
+        };
+        normalize();
+        // ---- summing side: chunk gc, its sums
+        int gc = 0;
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        bool ok = true;
+        // close chunk gc's bucket: its sums into both CTAs' B operands of the chunk
+        auto close = [&]() -> bool {
+            const int st = gc % kStages;
+            int w = 1;
+            if (lane == 0) w = tc::mbar_wait(emptyS + st, ((uint32_t)(gc / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, w, 0)) return false;
+            const uint32_t so = (uint32_t)st * sbytes + a_bytes();
+            if (lb) {
+                store_split4(tile0 + so, bbytes, n0, kb, acc0);
+                store_split4(tile1 + so, bbytes, n0, kb, acc1);
+            }
+            fence_proxy_async_cluster();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_cluster(fullS + st, 0);
+            acc0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            acc1 = acc0;
+            ++gc;
             return true;
         };
-        if (ok) ok = advance();
-        while (ok && t < T) {
-            const uint32_t grp = t / kGroupRows;
-            const int gi = (int)(grp % kGroups);
-            int w = 1;
-            if (lane == 0) w = tc::mbar_wait(fullR + gi, (grp / kGroups) & 1u, abort) ? 1 : 0;
-            if (!__shfl_sync(0xffffffffu, w, 0)) {
-                ok = false;
-                break;
-            }
-            const uint32_t nr = min((uint32_t)kGroupRows, T - t);
-            float v[kGroupRows], sg[kGroupRows];
+        int meta[kRing];   // per slot: chunk << 1 | sign of the row copied there, -1 if none
 #pragma unroll
-            for (int q = 0; q < kGroupRows; ++q) {
-                const uint32_t slot = (t + q) % kRing;
-                v[q] = ((uint32_t)q < nr && colv) ? ring[slot * p.hw + col] : 0.f;
-                sg[q] = ((uint32_t)q < nr) ? sgn[slot] : 0.f;
-            }
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(emptyR + gi);   // the group's slots may be refilled
+        for (int i = 0; i < kRing; ++i) meta[i] = -1;
+        // rounds of kRing steps; the round that starts with nothing left to copy
+        // sums every row still in the ring and is the last
+        for (bool last = false; ok && !last;) {
+            last = gp >= nchunks;
 #pragma unroll
-            for (int q = 0; q < kGroupRows; ++q) {
-                if ((uint32_t)q < nr && ok) {
-                    acc = fmaf(sg[q], v[q], acc);
-                    ++t;
-                    if (t == bend) ok = advance();
-                }
-            }
-        }
-    } else if (warp == kProdWarp) {
-        // ------------------------------------------------------------ producer
-        // lane l copies columns [4 l, 4 l + 4) of the half row (16-byte copies)
-        const bool lanecp = 4 * lane < hv;
-        const float* Ah = p.A + col0 + 4 * lane;
-        const uint32_t* pp = p.perm + T0;
-        uint32_t pf0 = (lane < T) ? __ldg(pp + lane) : 0u;
-        uint32_t pf1 = (32u + lane < T) ? __ldg(pp + 32 + lane) : 0u;
-        uint32_t pf2 = (64u + lane < T) ? __ldg(pp + 64 + lane) : 0u;
-        uint32_t pf3 = (96u + lane < T) ? __ldg(pp + 96 + lane) : 0u;
-        uint32_t issued = 0;   // ring groups armed so far
-        bool ok = true;
-        for (uint32_t t = 0; t < T && ok; t += 32) {
-            const uint32_t mine = pf0;   // perm entry of row t + lane
-            pf0 = pf1;
-            pf1 = pf2;
-            pf2 = pf3;
-            pf3 = (t + 128u + lane < T) ? __ldg(pp + t + 128 + lane) : 0u;
-#pragma unroll
-            for (int q8 = 0; q8 < 4; ++q8) {
-                const uint32_t tg = t + 8u * q8;
-                if (tg >= T) break;
-                const uint32_t grp = tg / kGroupRows;
-                const int gi = (int)(grp % kGroups);
-                const uint32_t nr = min((uint32_t)kGroupRows, T - tg);
-                int w = 1;
-                if (lane == 0) w = tc::mbar_wait(emptyR + gi, ((grp / kGroups) & 1u) ^ 1u, abort) ? 1 : 0;
-                if (!__shfl_sync(0xffffffffu, w, 0)) {
-                    ok = false;
-                    break;
-                }
-#pragma unroll
-                for (int e = 0; e < kGroupRows; ++e) {
-                    const uint32_t pe = __shfl_sync(0xffffffffu, mine, 8 * q8 + e);
-                    if ((uint32_t)e < nr) {
-                        const uint32_t slot = (tg + e) % kRing;
-                        if (lanecp) cp_async16(ring + slot * p.hw + 4 * lane, Ah + (int64_t)(pe & 0x7fffffffu) * p.lda);
-                        if (lane == 0) sgn[slot] = (pe >> 31) ? -1.f : 1.f;
+            for (int i = 0; i < kRing; ++i) {
+                // (1) sum the row copied kRing - 1 steps ago (slot i + 1)
+                const int sl = (i + 1) % kRing;
+                asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 2) : "memory");
+                const int m = meta[sl];
+                if (m >= 0) {
+                    while (ok && gc < (m >> 1)) ok = close();
+                    const uint32_t a = ring + (uint32_t)sl * 1024u;
+                    const float sg = (m & 1) ? -1.0f : 1.0f;
+                    if (lv0) {
+                        float4 v;
+                        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+                        acc0.x = fmaf(sg, v.x, acc0.x);
+                        acc0.y = fmaf(sg, v.y, acc0.y);
+                        acc0.z = fmaf(sg, v.z, acc0.z);
+                        acc0.w = fmaf(sg, v.w, acc0.w);
+                    }
+                    if (lv1) {
+                        float4 v;
+                        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a + 512u));
+                        acc1.x = fmaf(sg, v.x, acc1.x);
+                        acc1.y = fmaf(sg, v.y, acc1.y);
+                        acc1.z = fmaf(sg, v.z, acc1.z);
+                        acc1.w = fmaf(sg, v.w, acc1.w);
                     }
                 }
-                cp_async_arrive(fullR + gi);
-                if (lane == 0) tc::mbar_arrive(fullR + gi);   // the signs (release)
-                issued = grp + 1;
+                // (2) copy the next row into slot i (summed in step i - 1, its
+                //     values already consumed by the FMAs above)
+                meta[i] = -1;
+                if (gp < nchunks) {
+                    const uint32_t pe = __shfl_sync(0xffffffffu, pwp, (int)(tp - wp));
+                    const int64_t ro = (int64_t)(pe & 0x7fffffffu) * p.lda;
+                    const uint32_t a = ring + (uint32_t)i * 1024u;
+                    if (lv0) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(A0 + ro) : "memory");
+                    if (lv1) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a + 512u), "l"(A1 + ro) : "memory");
+                    meta[i] = (gp << 1) | (int)(pe >> 31);
+                    ++tp;
+                    normalize();
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
             }
         }
-        cp_async_wait_all();
-        if (lane == 0) {
-            // the groups still completing (the last kGroups) complete before the CTA leaves
-            volatile int never = 0;
-            const uint32_t first = issued > (uint32_t)kGroups ? issued - kGroups : 0u;
-            for (uint32_t grp = first; grp < issued; ++grp)
-                tc::mbar_wait(fullR + grp % kGroups, (grp / kGroups) & 1u, &never);
-        }
-        __syncwarp();
+        while (ok && gc < nchunks) ok = close();         // trailing (empty) buckets
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
         // ------------------------------------------------------------ MMA issue (even CTA)
         if (lane == 0 && rank == 0) {
@@ -408,23 +434,50 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) count_g
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }
 
-// clusters of two that fit on the device at once (cached per device and size)
-int cg_clusters(size_t smem) {
+// the kernel shapes that can be launched (gather warps, row slots per warp)
+struct Variant {
+    void (*fn)(CgParams);
+    int threads;
+    int ring;          // row slots per gather warp
+};
+template <int NG, int R>
+constexpr Variant variant() {
+    return Variant{count_gauss_kernel<NG, R>, Shape<NG, R>::kThreads, R};
+}
+// 6 slots (5 rows in flight per warp, 80 KB per SM) measured fastest at
+// 4M x 256 (0.70 ms against 0.72 ms for 4 slots and 0.80 ms for 8)
+const Variant kVariants[] = {variant<16, 6>(), variant<16, 4>()};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// LSK_CG_VARIANT=1 selects the 4-slot kernel (a complete kernel; for timing
+// comparisons and tests)
+int variant_index() {
+    static int v = [] {
+        const char* s = getenv("LSK_CG_VARIANT");
+        const int i = s ? atoi(s) : 0;
+        return (i >= 0 && i < kNumVariants) ? i : 0;
+    }();
+    return v;
+}
+
+// clusters of two that fit on the device at once (cached per device, variant and size)
+int cg_clusters(int vi, size_t smem) {
     static std::mutex mu;
-    static std::map<std::tuple<int, size_t>, int> cache;
+    static std::map<std::tuple<int, int, size_t>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(dev, smem);
+    const auto key = std::make_tuple(dev, vi, smem);
     const auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int n = 0;
-    if (allow_dynamic_smem(count_gauss_kernel) == cudaSuccess) {
+    const Variant& v = kVariants[vi];
+    if (allow_dynamic_smem(v.fn) == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2, 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.blockDim = dim3(v.threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void*)count_gauss_kernel, &cfg) != cudaSuccess) n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (const void*)v.fn, &cfg) != cudaSuccess) n = 0;
     }
     cudaGetLastError();
     cache[key] = n;
@@ -463,8 +516,15 @@ void plan(const lsk_mat* A, int64_t r, int64_t k, int clusters, CgParams& p) {
 bool count_gauss_supported(const lsk_mat* A, int64_t r, int64_t k) {
     if (!shape_ok(A, r, k)) return false;
     const int hw = (int)((A->d + 31) / 32) * 16;
-    const size_t smem = smem_bytes(hw);
-    return smem <= kSmemLimit && cg_clusters(smem) > 0;
+    const int vi = variant_index();
+    const size_t smem = smem_bytes(hw, kVariants[vi].ring);
+    return smem <= kSmemLimit && cg_clusters(vi, smem) > 0;
+}
+
+bool count_gauss_preferred(const lsk_mat* A, int64_t r, int64_t k, int sm_count) {
+    const int64_t pairs = sm_count / 2 > 0 ? sm_count / 2 : 1;
+    return A->kind == LSK_DENSE && A->d > 192 && r >= pairs * 8 * kKC && A->n >= 8 * r &&
+           count_gauss_supported(A, r, k);
 }
 
 size_t count_gauss_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int sm_count) {
@@ -479,8 +539,9 @@ cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t 
     if (!shape_ok(A, r, k)) return cudaErrorNotSupported;
     CgParams p{};
     const int hw = (int)((A->d + 31) / 32) * 16;
-    const size_t smem = smem_bytes(hw);
-    const int maxc = cg_clusters(smem);
+    const int vi = variant_index();
+    const size_t smem = smem_bytes(hw, kVariants[vi].ring);
+    const int maxc = cg_clusters(vi, smem);
     if (smem > kSmemLimit || maxc < 1) return cudaErrorNotSupported;
     const int half = sm_count / 2 > 0 ? sm_count / 2 : 1;
     plan(A, r, k, maxc < half ? maxc : half, p);
@@ -499,7 +560,8 @@ cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t 
     p.k1 = (uint32_t)(seed >> 32);
     p.scale = (float)(1.0 / sqrt((double)k));
     p.flag = flag;
-    LSK_PROF("count_gauss", st) count_gauss_kernel<<<2 * p.slices, kThreads, smem, st>>>(p);
+    const Variant& v = kVariants[vi];
+    LSK_PROF("count_gauss", st) v.fn<<<2 * p.slices, v.threads, smem, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return gauss_tc_reduce_launch(p.part, p.slices, k * A->d, GSA, sm_count, st);

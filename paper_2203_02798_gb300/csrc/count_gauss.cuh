@@ -19,6 +19,12 @@ cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, f
 // scaled draws, S * A carried as bf16 hi + lo), one pass over A: supported for
 // 32 <= d <= 256 with d, ld multiples of 4 and A 16-byte aligned, 1 <= k <= 512.
 bool count_gauss_supported(const lsk_mat* A, int64_t r, int64_t k);
+// Whether the fused kernel is expected to beat the two stages for this shape:
+// each gather lane fully used (d > 192), enough buckets to give every CTA pair
+// of the device a slice of >= 8 chunks, and >= 8 rows a bucket on average
+// (measured on GB300: 4M x 256, r = 65,536: 0.70 ms against 0.92 ms; at
+// d <= 200, few buckets or few rows a bucket the two stages are faster).
+bool count_gauss_preferred(const lsk_mat* A, int64_t r, int64_t k, int sm_count);
 size_t count_gauss_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int sm_count);
 cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, float* GSA, void* ws,
                                int* flag, int sm_count, cudaStream_t st);

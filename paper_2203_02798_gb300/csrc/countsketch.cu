@@ -6,9 +6,10 @@
 // is recomputed from Philox whenever it is needed, and row ownership is kept
 // at the finest grain -- one warp owns one bucket (one row of SA):
 //
-//   1. rank:  cnt[h(i)]++ for every row, remembering each row's arrival rank
-//   2. scan:  off = exclusive prefix sum of cnt        (bucket -> first slot)
-//   3. place: perm[off[h(i)] + rank[i]] = i | sigma_bit << 31
+//   1. count: cnt[h(i)]++ for every row (fire-and-forget atomics)
+//   2. scan:  off = exclusive prefix sum of cnt        (bucket -> first slot),
+//             and a copy of it as each bucket's fill cursor
+//   3. place: perm[cursor[h(i)]++] = i | sigma_bit << 31
 //   4. gather (dense): the warp owning bucket b streams the rows listed in
 //      perm[off[b] .. off[b+1]) with 16-byte coalesced loads, accumulates them
 //      (with their signs) in registers and writes row b of SA exactly once.
@@ -17,7 +18,7 @@
 //
 // Every byte of A is read once and every row of SA written once, with no
 // global atomics on floating-point data; the only extra traffic is the
-// 8 bytes per row of rank/perm.  The per-bucket loads are the Y of Lemma 1:
+// 4 bytes per row of perm.  The per-bucket loads are the Y of Lemma 1:
 // expected n/r rows per warp, concentrated as in Lemma 2-3.
 #include "lsk_internal.cuh"
 
@@ -27,24 +28,26 @@ constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanBlock * kScanItems;
 
-__global__ void cs_rank_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
-                               uint32_t* __restrict__ cnt, uint32_t* __restrict__ rank) {
+__global__ void cs_count_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1, uint32_t* __restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t b, neg;
         cs_hash((uint64_t)i, r, k0, k1, b, neg);
-        rank[i] = atomicAdd(&cnt[b], 1u);
+        atomicAdd(&cnt[b], 1u);   // result unused: compiled to a reduction (no round trip)
     }
 }
 
+// The order of the rows inside a bucket is the order in which their atomics
+// reach the cursor (not fixed from run to run); every consumer sums a bucket's
+// rows in that order, so S*A is exact for integer-valued data and agrees to
+// FP32 rounding otherwise.
 __global__ void cs_place_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
-                                const uint32_t* __restrict__ off,
-                                const uint32_t* __restrict__ rank, uint32_t* __restrict__ perm) {
+                                uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t b, neg;
         cs_hash((uint64_t)i, r, k0, k1, b, neg);
-        perm[off[b] + rank[i]] = (uint32_t)i | (neg << 31);
+        perm[atomicAdd(&cursor[b], 1u)] = (uint32_t)i | (neg << 31);
     }
 }
 
@@ -376,7 +379,7 @@ inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 
 }  // namespace
 
 size_t cs_workspace_bytes(int64_t n, int64_t r) {
-    return ws_round((size_t)(r + 1) * 4) * 2 + ws_round((size_t)n * 4) * 2 +
+    return ws_round((size_t)(r + 1) * 4) * 3 + ws_round((size_t)(n > 0 ? n : 1) * 4) +
            ws_round(scan_tmp_words(r) * 4) + 4096;
 }
 
@@ -388,7 +391,7 @@ cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket,
     return cudaGetLastError();
 }
 
-// Steps 1-3 (rank, scan, place): on return *off_out (r + 1 entries, off[r] = n)
+// Steps 1-3 (count, scan, place): on return *off_out (r + 1 entries, off[r] = n)
 // and *perm_out (n entries) point into ws; the launches are queued on st.
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
                            const uint32_t** off_out, const uint32_t** perm_out) {
@@ -396,12 +399,12 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
     WsCarver wc{(char*)ws, 0};
     uint32_t* cnt = wc.take<uint32_t>(r + 1);
     uint32_t* off = wc.take<uint32_t>(r + 1);
-    uint32_t* rank = wc.take<uint32_t>(n > 0 ? n : 1);
+    uint32_t* cursor = wc.take<uint32_t>(r + 1);
     uint32_t* perm = wc.take<uint32_t>(n > 0 ? n : 1);
     uint32_t* tmp = wc.take<uint32_t>(scan_tmp_words(r));
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)r * 4, st);
     if (e != cudaSuccess) return e;
-    if (n > 0) LSK_PROF("cs_rank", st) cs_rank_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cnt, rank);
+    if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cnt);
     if (r <= 16384) {
         LSK_PROF("cs_scan", st) scan_one_block_kernel<<<1, 1024, 0, st>>>(cnt, off, r);
     } else {
@@ -409,8 +412,11 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
         if (e != cudaSuccess) return e;
         write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
     }
-    if (n > 0)
-        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, off, rank, perm);
+    if (n > 0) {
+        e = cudaMemcpyAsync(cursor, off, (size_t)r * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cursor, perm);
+    }
     *off_out = off;
     *perm_out = perm;
     return cudaGetLastError();

@@ -320,3 +320,5 @@ size_t leverage_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int32_t 
 cudaError_t leverage_pipeline(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, float* ell,
                               double* R_out, void* ws, int* flag, int sm, cudaStream_t st);
 int check_leverage_args(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int32_t prec);
+// the process-wide fused-sketch switch (lsk_set_fused_sketch)
+int fused_sketch_on();

@@ -593,12 +593,14 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
     const size_t sh64 = dense ? (size_t)9 * d * 8 : (size_t)2 * d * 8;
     const size_t sh32 = dense ? (size_t)9 * d * 4 : (size_t)2 * d * 4;
     if (sh64 > 48 * 1024) {
-        allow_dynamic_smem(resid64_dense_kernel);
-        allow_dynamic_smem(resid64_csr_kernel);
+        if (allow_dynamic_smem(resid64_dense_kernel) != cudaSuccess ||
+            allow_dynamic_smem(resid64_csr_kernel) != cudaSuccess)
+            return LSK_ERR_CUDA;
     }
     if (sh32 > 48 * 1024) {
-        allow_dynamic_smem(lsqr_pass_dense_kernel);
-        allow_dynamic_smem(lsqr_pass_csr_kernel);
+        if (allow_dynamic_smem(lsqr_pass_dense_kernel) != cudaSuccess ||
+            allow_dynamic_smem(lsqr_pass_csr_kernel) != cudaSuccess)
+            return LSK_ERR_CUDA;
     }
     int total_it = 0, refinements = 0, status = LSK_ERR_NOT_CONVERGED;
     double eta = INFINITY;

@@ -1,14 +1,21 @@
 // noalloc.cu -- a CountSketch entry point that allocates no device memory.
 //
-// lsk_cs_sketch needs scratch space (bucket counts, bucket offsets, a rank
-// per row and the bucket-sorted row permutation) and takes it from a
+// lsk_cs_sketch needs scratch space (bucket counts, bucket offsets and fill
+// cursors, and the bucket-sorted row permutation) and takes it from a
 // context workspace that grows with cudaMallocAsync.  Some callers cannot let
 // a library allocate: applications that hand all device memory to their own
 // pool allocator (so a foreign cudaMalloc can fail or break their budget),
 // and latency-critical loops where cudaMalloc / cudaFree may synchronise the
 // device.  lsk_cs_sketch_noalloc serves them: it runs the same kernels, but
-// its scratch lives in one fixed-size array in device global memory that the
-// library reserves when it is loaded, so a call allocates nothing.
+// its scratch lives in one fixed-size array in device global memory, so a
+// call allocates nothing.
+//
+// The CUDA runtime loads a library's device code lazily: the array (and the
+// CountSketch kernels' code) is placed on a device when the first call on
+// that device looks the array up.  That first call is therefore the one that
+// takes device memory (12 MiB plus the code); a caller that must not see a
+// later allocation makes one call during its set-up, before any stream
+// capture.  Every later call on that device allocates nothing.
 //
 // The array is shared by every call in the process, so calls whose GPU work
 // overlaps (two streams, two host threads) race on it; serialise them.  It
@@ -20,7 +27,7 @@
 
 namespace {
 
-constexpr size_t kNoallocScratchBytes = 12u << 20;  // 12 MiB, held by every device that loads the library
+constexpr size_t kNoallocScratchBytes = 12u << 20;  // 12 MiB on each device that has made a call, until exit
 
 // Device-side scratch.  Host code must not pass this name to a kernel (on the
 // host it is only a stand-in symbol); the device address comes from

@@ -59,10 +59,13 @@ def test_binding_exports_same_names():
 
 
 def test_fused_sketch_switch_is_host_state(lib):
-    """lsk_set_fused_sketch only flips process-wide host state (no CUDA call):
-    off by default, returns the previous setting."""
+    """lsk_set_fused_sketch only sets process-wide host state (no CUDA call):
+    mode 1 (fused where the shape favours it) by default, values clamped to
+    [0, 2], returns the previous mode."""
     lib.lsk_set_fused_sketch.restype = ctypes.c_int
     lib.lsk_set_fused_sketch.argtypes = [ctypes.c_int]
+    assert lib.lsk_set_fused_sketch(2) == 1
+    assert lib.lsk_set_fused_sketch(0) == 2
+    assert lib.lsk_set_fused_sketch(7) == 0
+    assert lib.lsk_set_fused_sketch(-3) == 2
     assert lib.lsk_set_fused_sketch(1) == 0
-    assert lib.lsk_set_fused_sketch(0) == 1
-    assert lib.lsk_set_fused_sketch(0) == 0

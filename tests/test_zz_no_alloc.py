@@ -88,6 +88,28 @@ def test_noalloc_matches_context_entry_point_on_consecutive_calls(lsk):
     assert torch.equal(got3, ref3)
 
 
+def test_noalloc_second_call_leaves_free_memory_unchanged(lsk):
+    """The first call on a device places the scratch array there (lazy module
+    loading); every later call must take no device memory at all."""
+    A = dense(workloads.dense_normal(100_000, 128, seed=4))
+    rc, _ = noalloc(lsk, A, 16_384, 3)                 # warm-up: set-up happens here
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    out = torch.empty((16_384, 128), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()               # after torch's own allocation for the output
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    m, _, _ = lsk._mat(A)
+    for seed in (4, 5):
+        rc = lsk.load_library().lsk_cs_sketch_noalloc(ctypes.byref(m), 16_384, seed,
+                                                      ctypes.c_void_p(out.data_ptr()), stream)
+        assert rc == 0
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 == free1, (free0, free1, free2)
+
+
 def test_noalloc_rejects_sizes_beyond_its_capacity(lsk):
     lib = lsk.load_library()
     too_many_rows = torch.zeros((lsk_max_rows(lib) + 1, 1), dtype=torch.float32, device="cuda")
