@@ -118,7 +118,7 @@ def max_over_ranks(x):
 
 
 def whole_job_rate(bytes_per_rank, world, ms):
-    """GB/s of the whole job: every rank processes bytes_per_rank (replicas,
+    """GB/s of the whole job: every rank processes bytes_per_rank (its block,
     weak scaling), in the time of the slowest rank (ms)."""
     return world * bytes_per_rank / (ms * 1e-3) / 1e9
 
@@ -149,16 +149,20 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args),
+        "data": "synthetic", "config": workload_config(args, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def workload_config(args):
-    return {"workload": "dense_colscaled_leverage", "n": N_ROWS, "d": D, "r": R_SKETCH, "k": K_GAUSS,
-            "prec": args.prec, "input_bytes": N_ROWS * D * 4, "l2_policy": "input 4.1 GB > L2 (no flush)",
-            "parallelism": f"replicas{args.gpus}"}
+def workload_config(args, world=1):
+    cfg = {"workload": "dense_colscaled_leverage", "n": N_ROWS, "d": D, "r": R_SKETCH, "k": K_GAUSS,
+           "prec": args.prec, "input_bytes": N_ROWS * D * 4, "l2_policy": "input 4.1 GB > L2 (no flush)",
+           "parallelism": "single" if world == 1 else f"rows{world}"}
+    if world > 1:
+        cfg["partition"] = (f"one {world * N_ROWS} x {D} matrix split by rows, {N_ROWS} rows per GPU; one sum "
+                            f"all-reduce of the {K_GAUSS} x {D} partial sketches per step (NCCL)")
+    return cfg
 
 
 # ---------------------------------------------------------------- GPU path --
@@ -212,16 +216,23 @@ def main():
 
     hbm, bf16_peak, sm_max, peak_kind = peaks()
     # inputs: pinned host copy (for e2e) and the device copy
+    # With N > 1 GPUs rank g holds rows [g n, (g + 1) n) of one (N n) x d
+    # matrix (its own draws: data seed DATA_SEED + g) and the step is the
+    # row-partitioned path: partial sketch, one all-reduce, R, local scores.
     A_host = torch.empty((N_ROWS, D), dtype=torch.float32, pin_memory=True)
-    workloads.dense_colscaled(n=N_ROWS, d=D, seed=DATA_SEED, out=A_host.numpy())
+    workloads.dense_colscaled(n=N_ROWS, d=D, seed=DATA_SEED + rank, out=A_host.numpy())
     A = A_host.cuda()
     ell = torch.empty(N_ROWS, dtype=torch.float32, device="cuda")
     ctx = lsk.context()
     st = torch.cuda.current_stream()
     lsk.set_fused_sketch(args.fused_sketch)
+    from paper_2203_02798_gb300 import sharded
 
     def step(prec):
-        lsk.leverage_scores(A, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
+        if world == 1:
+            lsk.leverage_scores(A, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
+        else:
+            sharded.leverage_scores_sharded(A, rank * N_ROWS, R_SKETCH, K_GAUSS, SEED, prec, out=ell, ctx=ctx)
 
     def gram_leg(steps):
         """A^T A of the workload's A (csrrk), BF16x3 on tensor cores and FP32 SIMT,
@@ -351,7 +362,7 @@ def main():
     if args.gram_only:
         g = gram_leg(args.steps)
         if rank == 0:
-            print(json.dumps({"gram": g, "config": workload_config(args)}))
+            print(json.dumps({"gram": g, "config": workload_config(args, world)}))
         return
 
     for _ in range(max(3, args.warmup)):
@@ -412,19 +423,21 @@ def main():
 
     # the plain FP32 single-problem path on the same GPU
     plain = None
-    if not args.no_plain and args.prec != "fp32":
+    if not args.no_plain and args.prec != "fp32" and world == 1:
         for _ in range(2):
             step("fp32")
         pms, _, _ = timed(lambda: step("fp32"), max(3, args.steps // 5))
         pms /= max(3, args.steps // 5)
         plain = {"value": whole_job_rate(a_bytes, world, pms), "unit": "GB/s", "ms_per_step": pms}
 
-    gram = None if args.no_gram else gram_leg(max(3, args.steps // 5))
-    jl = None if args.no_jl else jl_leg(max(3, args.steps // 5))
-    sstage = None if args.no_sketch_stage else sketch_stage_leg(max(3, args.steps // 5))
-    nxt = None if args.no_next else next_legs(max(3, args.steps // 5))
-    batched = None if args.no_batch else run_batched(args, lsk, torch, ctx, plain)
-    served = None if args.no_serve else run_served(args, lsk, torch)
+    # the other legs time single-GPU calls: rank 0's GPU alone, and only at N = 1
+    solo = world == 1
+    gram = None if args.no_gram or not solo else gram_leg(max(3, args.steps // 5))
+    jl = None if args.no_jl or not solo else jl_leg(max(3, args.steps // 5))
+    sstage = None if args.no_sketch_stage or not solo else sketch_stage_leg(max(3, args.steps // 5))
+    nxt = None if args.no_next or not solo else next_legs(max(3, args.steps // 5))
+    batched = None if args.no_batch or not solo else run_batched(args, lsk, torch, ctx, plain)
+    served = None if args.no_serve or not solo else run_served(args, lsk, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -438,7 +451,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16+fp32+f64" if args.prec == "bf16" else "f32+f64",
-            "data": "synthetic", "config": workload_config(args),
+            "data": "synthetic", "config": workload_config(args, world),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
             "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,

@@ -182,11 +182,17 @@ int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B,
 
 /* R of the sketch (Alg. 12 step 2 / Alg. 15 step 3 with a QR in place of
  * the SVD): B = GSA (k x d floats, device, row-major, k >= d) -> R (d x d,
- * upper triangular, R_jj > 0) and R^-1, both FP64 row-major on the device.
- * Computed in FP64 as the Cholesky factor of B^T B (identical to the
- * sign-normalised Householder R in exact arithmetic).  Rank deficiency
- * (a pivot <= 0 or min R_jj <= 16 eps64 d max R_jj) sets the deferred
- * LSK_ERR_RANK_DEFICIENT.  Either output may be NULL. */
+ * upper triangular, R_jj > 0) and R^-1, both FP64 row-major on the device:
+ * the Cholesky factor of B^T B (identical to the sign-normalised
+ * Householder R in exact arithmetic), to FP64 accuracy.  B^T B is formed
+ * with FP64-accurate products; for d <= 256 it is equilibrated by powers of
+ * two, factored and inverted in FP32, and the factor and its inverse are
+ * corrected by one Newton step with FP64-accurate triangular products (the
+ * FP32 error squared, far below what FP64 rounding leaves); for d > 256 the
+ * Cholesky factorisation runs in FP64.  Rank deficiency (a pivot <= 0, an
+ * FP32 factor that needs a correction larger than 1/4, or min R_jj <=
+ * 16 eps64 d max R_jj) sets the deferred LSK_ERR_RANK_DEFICIENT.  Either
+ * output may be NULL. */
 int lsk_sketch_qr(lsk_ctx* ctx, const float* B, int64_t k, int64_t d,
                   double* R, double* Rinv);
 
@@ -199,6 +205,32 @@ int lsk_sketch_qr(lsk_ctx* ctx, const float* B, int64_t k, int64_t d,
 int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                         uint64_t seed, int32_t prec, float* ell,
                         double* R_out);
+
+/* ---- row-partitioned (sharded) leverage scores ----------------------------
+ * The sketch is linear in A and Def. 3 hashes each row of A by its index:
+ * for A split by rows into blocks A_g (row offsets row0_g),
+ *     G S A = sum_g G S_g A_g,
+ * where S_g holds the columns row0_g .. of S.  So each holder of a block
+ * forms its partial sketch with lsk_sketch_rows, the partials are summed
+ * (one all-reduce of k*d floats -- the only exchange; Def. 4's reason for a
+ * small sketch), every holder forms R from the sum, and scores its own rows
+ * with lsk_leverage_scores_from_sketch. */
+
+/* The partial sketch of a block of rows: out = S_g A (k == 0: r x d) or
+ * G S_g A (k > 0: k x d), device floats row-major, overwritten.  Row i of A
+ * is row row0 + i of the whole matrix (its CountSketch column).  Same r, k,
+ * seed and prec as lsk_leverage_scores; the BF16 mode uses the fused kernel
+ * as lsk_set_fused_sketch selects.  row0 >= 0, row0 + n < 2^63. */
+int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
+                    uint64_t seed, int32_t prec, int64_t row0, float* out);
+
+/* R (as lsk_sketch_qr) of a given sketch (rows x d floats, device, e.g. the
+ * sum of the partial sketches of all blocks), then ell_i = ||A_i R^-1||^2
+ * for the rows of A (Alg. 8; prec as lsk_rownorms_prod).  ell: device n
+ * floats.  R_out: NULL or device d*d doubles.  rows >= d, d <= 1024. */
+int lsk_leverage_scores_from_sketch(lsk_ctx* ctx, const lsk_mat* A,
+                                    const float* sketch, int64_t rows,
+                                    int32_t prec, float* ell, double* R_out);
 
 /* Leverage-score estimates of Alg. 15 with its right JL projection: R from
  * the sketch exactly as in lsk_leverage_scores (a QR in place of the SVD of

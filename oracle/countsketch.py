@@ -42,6 +42,23 @@ def countsketch_hash(n, r, seed):
     return bucket, sign
 
 
+def countsketch_hash_rows(row0, n, r, seed):
+    """(h, sigma) for columns row0 .. row0 + n - 1 of S (Def. 3): the hash of
+    a block of rows of a larger matrix, which keeps each row's global index
+    (the counter of its Philox draw)."""
+    if r <= 0 or r >= 2**32:
+        raise ValueError("r must be in [1, 2^32)")
+    if row0 < 0:
+        raise ValueError("row0 must be >= 0")
+    i = np.arange(n, dtype=np.uint64) + np.uint64(row0)
+    k0, k1 = split_seed(seed)
+    w0, w1, _, _ = philox4x32_10(i & np.uint64(0xFFFFFFFF), i >> np.uint64(32),
+                                 STREAM_S, 0, k0, k1)
+    bucket = ((w0.astype(np.uint64) * np.uint64(r)) >> np.uint64(32)).astype(np.int64)
+    sign = np.where(w1 >= np.uint32(2**31), -1, 1).astype(np.int8)
+    return bucket, sign
+
+
 def countsketch_matrix(bucket, sign, r):
     """Explicit dense S (r x n, float64) with S[h(i), i] = sigma_i (Def. 3)."""
     n = len(bucket)

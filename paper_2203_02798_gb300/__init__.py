@@ -91,6 +91,8 @@ _SIGS = {
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_leverage_scores_jl": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _I64, _U64, _I32, _P, _P]),
+    "lsk_sketch_rows": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
+    "lsk_leverage_scores_from_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I32, _P, _P]),
     "lsk_sketch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I64, _U64, _I32, _P]),
     "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
     "lsk_column_select": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
@@ -328,6 +330,34 @@ def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=No
     R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
     ctx._call("lsk_leverage_scores", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), _ptr(ell),
               _ptr(R))
+    return (ell, R) if return_R else ell
+
+
+def sketch_rows(A, r, k, seed, prec="fp32", row0=0, out=None, ctx=None):
+    """lsk_sketch_rows: the partial sketch of a block of rows whose first row
+    is row row0 of the whole matrix -- S_g A (r x d) for k == 0, else
+    G S_g A (k x d), float32.  Summed over the blocks of a row partition it
+    is the sketch of the whole matrix."""
+    m, n, d = _mat(A)
+    ctx = ctx or context(_dev(A).index)
+    rows = int(k) if k > 0 else int(r)
+    out = out if out is not None else torch.empty((rows, d), dtype=torch.float32, device=_dev(A))
+    ctx._call("lsk_sketch_rows", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), int(row0), _ptr(out))
+    return out
+
+
+def leverage_scores_from_sketch(A, sketch, prec="fp32", out=None, return_R=False, ctx=None):
+    """lsk_leverage_scores_from_sketch: R of the given sketch (rows x d
+    float32), then ell_i = ||A_i R^-1||^2 for the rows of A (n float32);
+    optionally R."""
+    m, n, d = _mat(A)
+    _check_cuda(sketch)
+    sketch = sketch.contiguous()
+    ctx = ctx or context(_dev(A).index)
+    ell = out if out is not None else torch.empty(n, dtype=torch.float32, device=_dev(A))
+    R = torch.empty((d, d), dtype=torch.float64, device=_dev(A)) if return_R else None
+    ctx._call("lsk_leverage_scores_from_sketch", ctypes.byref(m), _ptr(sketch), int(sketch.shape[0]), _prec(prec),
+              _ptr(ell), _ptr(R))
     return (ell, R) if return_R else ell
 
 

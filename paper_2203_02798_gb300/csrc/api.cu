@@ -317,27 +317,37 @@ SketchBufs carve(void* ws, const lsk_mat* A, int64_t r, int64_t k) {
     return b;
 }
 
-// SA -> (GSA) -> R, R^-1 on the device, all asynchronous.  In the BF16 mode
-// GSA comes from the fused kernel where it applies (SA is then not formed).
-cudaError_t sketch_and_factor_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
-                                 const SketchBufs& b, double* R_out, int* flag, int sm, cudaStream_t st) {
+// S A (k = 0) into b.SA, or G S A into b.GSA; in the BF16 mode G S A comes
+// from the fused kernel where the fused-sketch mode selects it (S A is then
+// not formed).  A's rows are columns row0.. of S.  *sk / *rows: the sketch.
+cudaError_t sketch_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, const SketchBufs& b,
+                      int* flag, int sm, cudaStream_t st, uint64_t row0, const float** sk, int64_t* rows) {
     const int fused = g_fused_sketch.load();
     if (k > 0 && prec == LSK_PREC_BF16 &&
         ((fused == 1 && count_gauss_preferred(A, r, k, sm)) || (fused == 2 && count_gauss_supported(A, r, k)))) {
-        cudaError_t e = count_gauss_launch(A, r, k, seed, b.GSA, b.scratch, flag, sm, st);
-        if (e != cudaSuccess) return e;
-        return qr_launch(b.GSA, k, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, flag, sm, st);
+        *sk = b.GSA;
+        *rows = k;
+        return count_gauss_launch(A, r, k, seed, b.GSA, b.scratch, flag, sm, st, row0);
     }
-    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, flag, sm, st);
+    cudaError_t e = cs_launch(A, r, seed, b.SA, b.scratch, flag, sm, st, row0);
     if (e != cudaSuccess) return e;
-    const float* sk = b.SA;
-    int64_t rows = r;
+    *sk = b.SA;
+    *rows = r;
     if (k > 0) {
         e = gauss_launch(b.SA, r, A->d, k, seed, prec, b.GSA, b.scratch, sm, st);
-        if (e != cudaSuccess) return e;
-        sk = b.GSA;
-        rows = k;
+        *sk = b.GSA;
+        *rows = k;
     }
+    return e;
+}
+
+// SA -> (GSA) -> R, R^-1 on the device, all asynchronous.
+cudaError_t sketch_and_factor_on(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec,
+                                 const SketchBufs& b, double* R_out, int* flag, int sm, cudaStream_t st) {
+    const float* sk = nullptr;
+    int64_t rows = 0;
+    cudaError_t e = sketch_on(A, r, k, seed, prec, b, flag, sm, st, 0, &sk, &rows);
+    if (e != cudaSuccess) return e;
     return qr_launch(sk, rows, A->d, R_out, b.Rinv64, b.Rinv32, b.scratch, flag, sm, st);
 }
 
@@ -398,6 +408,60 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, ui
                         ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (row norms)");
     return finish(ctx, "lsk_leverage_scores");
+}
+
+int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, int64_t row0,
+                    float* out) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (r < 1 || r >= ((int64_t)1 << 31)) return fail(ctx, LSK_ERR_INVALID_ARG, "r must be in [1, 2^31)");
+    if (k < 0 || k >= ((int64_t)1 << 32)) return fail(ctx, LSK_ERR_INVALID_ARG, "k must be in [0, 2^32)");
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (row0 < 0 || A->n > INT64_MAX - row0) return fail(ctx, LSK_ERR_INVALID_ARG, "row0 must be >= 0 and row0 + n < 2^63");
+    if (!out) return fail(ctx, LSK_ERR_INVALID_ARG, "out is NULL");
+    if (A->kind == LSK_CSR && A->d > 51200) return fail(ctx, LSK_ERR_UNSUPPORTED, "CSR sketch needs d <= 51200");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, 0));
+    if (rc) return rc;
+    const SketchBufs b = carve(ctx->ws, A, r, k);
+    const float* sk = nullptr;
+    int64_t rows = 0;
+    cudaError_t e = sketch_on(A, r, k, seed, prec, b, ctx->flag, ctx->sm_count, ctx->stream, (uint64_t)row0, &sk, &rows);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, sk, (size_t)rows * A->d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_rows");
+    return finish(ctx, "lsk_sketch_rows");
+}
+
+int lsk_leverage_scores_from_sketch(lsk_ctx* ctx, const lsk_mat* A, const float* sketch, int64_t rows, int32_t prec,
+                                    float* ell, double* R_out) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    ProfGuard pg(ctx);
+    int rc = check_mat(ctx, A);
+    if (rc) return rc;
+    if (!sketch) return fail(ctx, LSK_ERR_INVALID_ARG, "sketch is NULL");
+    if (rows < A->d) return fail(ctx, LSK_ERR_INVALID_ARG, "the sketch needs at least d rows");
+    if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "d <= 1024 is supported");
+    if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
+        return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
+    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int64_t d = A->d;
+    const size_t q = qr_workspace_bytes(rows, d), rn = rownorms_workspace_bytes(A, d, 1, prec);
+    rc = ws_ensure(ctx, ws_round((size_t)d * d * 8) + ws_round((size_t)d * d * 4) + (q > rn ? q : rn) + 1024);
+    if (rc) return rc;
+    WsCarver wc{(char*)ctx->ws, 0};
+    double* Rinv64 = wc.take<double>((size_t)d * d);
+    float* Rinv32 = wc.take<float>((size_t)d * d);
+    void* scratch = wc.take<char>(1);
+    cudaError_t e = qr_launch(sketch, rows, d, R_out, Rinv64, Rinv32, scratch, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_from_sketch (R)");
+    e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, prec, ell, scratch, ctx->flag, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_from_sketch (row norms)");
+    return finish(ctx, "lsk_leverage_scores_from_sketch");
 }
 
 int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, int64_t m, uint64_t seed,

@@ -535,7 +535,7 @@ size_t count_gauss_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int s
 }
 
 cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, float* GSA, void* ws,
-                               int* flag, int sm_count, cudaStream_t st) {
+                               int* flag, int sm_count, cudaStream_t st, uint64_t row0) {
     if (!shape_ok(A, r, k)) return cudaErrorNotSupported;
     CgParams p{};
     const int hw = (int)((A->d + 31) / 32) * 16;
@@ -547,7 +547,7 @@ cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t 
     plan(A, r, k, maxc < half ? maxc : half, p);
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
-    cudaError_t e = cs_prep_launch(A->n, r, seed, ws, sm_count, st, &off, &perm);
+    cudaError_t e = cs_prep_launch(A->n, r, seed, ws, sm_count, st, &off, &perm, row0);
     if (e != cudaSuccess) return e;
     p.A = (const float*)A->values;
     p.lda = A->ld;

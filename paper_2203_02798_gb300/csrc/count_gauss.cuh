@@ -9,7 +9,7 @@
 // sign bit << 31, grouped by bucket) point into ws when the queued launches
 // have run.
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
-                           const uint32_t** off, const uint32_t** perm);
+                           const uint32_t** off, const uint32_t** perm, uint64_t row0 = 0);
 
 // out[e] = the slice-order compensated sum of part[z * len + e], z < slices.
 cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, float* out, int sm_count,
@@ -26,5 +26,6 @@ bool count_gauss_supported(const lsk_mat* A, int64_t r, int64_t k);
 // d <= 200, few buckets or few rows a bucket the two stages are faster).
 bool count_gauss_preferred(const lsk_mat* A, int64_t r, int64_t k, int sm_count);
 size_t count_gauss_workspace_bytes(const lsk_mat* A, int64_t r, int64_t k, int sm_count);
+// row0: global index of A's first row (A is a block of rows of a larger matrix)
 cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, float* GSA, void* ws,
-                               int* flag, int sm_count, cudaStream_t st);
+                               int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0);

@@ -28,11 +28,14 @@ constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanBlock * kScanItems;
 
-__global__ void cs_count_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1, uint32_t* __restrict__ cnt) {
+// Row i of A is column row0 + i of S: a block of rows of a larger matrix
+// (one shard of a row partition) is hashed by its global row index.
+__global__ void cs_count_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k0, uint32_t k1,
+                                uint32_t* __restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t b, neg;
-        cs_hash((uint64_t)i, r, k0, k1, b, neg);
+        cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
         atomicAdd(&cnt[b], 1u);   // result unused: compiled to a reduction (no round trip)
     }
 }
@@ -41,12 +44,12 @@ __global__ void cs_count_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
 // reach the cursor (not fixed from run to run); every consumer sums a bucket's
 // rows in that order, so S*A is exact for integer-valued data and agrees to
 // FP32 rounding otherwise.
-__global__ void cs_place_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_t k1,
+__global__ void cs_place_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k0, uint32_t k1,
                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t b, neg;
-        cs_hash((uint64_t)i, r, k0, k1, b, neg);
+        cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
         perm[atomicAdd(&cursor[b], 1u)] = (uint32_t)i | (neg << 31);
     }
 }
@@ -392,9 +395,10 @@ cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket,
 }
 
 // Steps 1-3 (count, scan, place): on return *off_out (r + 1 entries, off[r] = n)
-// and *perm_out (n entries) point into ws; the launches are queued on st.
+// and *perm_out (n entries, local row indices) point into ws; the launches
+// are queued on st.  Row i is hashed as column row0 + i of S.
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
-                           const uint32_t** off_out, const uint32_t** perm_out) {
+                           const uint32_t** off_out, const uint32_t** perm_out, uint64_t row0) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     WsCarver wc{(char*)ws, 0};
     uint32_t* cnt = wc.take<uint32_t>(r + 1);
@@ -404,7 +408,7 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
     uint32_t* tmp = wc.take<uint32_t>(scan_tmp_words(r));
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)r * 4, st);
     if (e != cudaSuccess) return e;
-    if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cnt);
+    if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, cnt);
     if (r <= 16384) {
         LSK_PROF("cs_scan", st) scan_one_block_kernel<<<1, 1024, 0, st>>>(cnt, off, r);
     } else {
@@ -415,7 +419,7 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
     if (n > 0) {
         e = cudaMemcpyAsync(cursor, off, (size_t)r * 4, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
-        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, (uint32_t)r, k0, k1, cursor, perm);
+        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, cursor, perm);
     }
     *off_out = off;
     *perm_out = perm;
@@ -423,11 +427,11 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
 }
 
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
-                      int sm_count, cudaStream_t st) {
+                      int sm_count, cudaStream_t st, uint64_t row0) {
     const int64_t n = A->n, d = A->d;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
-    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm);
+    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0);
     if (e != cudaSuccess) return e;
 
     // parts per bucket: enough warps to stream A when there are few buckets,

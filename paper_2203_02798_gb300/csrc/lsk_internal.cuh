@@ -178,8 +178,9 @@ __device__ __forceinline__ void set_flag(int* flag, int bit) {
 // ---------------------------------------------------------------------------
 // countsketch.cu
 size_t cs_workspace_bytes(int64_t n, int64_t r);
+// row0: global index of A's first row (A is a block of rows of a larger matrix)
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws,
-                      int* flag, int sm_count, cudaStream_t st);
+                      int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0);
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
 

@@ -149,3 +149,35 @@ def test_sketch_subspace_embedding_singular_values():
     Q, _ = np.linalg.qr(rng.standard_normal((n, d)))
     sv = np.linalg.svd(cs.cs_sketch_dense(Q, 4000, 5), compute_uv=False)
     assert np.all(np.abs(sv - 1.0) < 0.15)
+
+
+def test_block_hash_keeps_global_row_index():
+    """A block of rows starting at row0 is hashed as columns row0.. of S
+    (Def. 3): the block hash is the slice of the whole matrix's hash,
+    including across the 2^32 boundary of the counter's low word."""
+    r, seed = 1000, 77
+    b, s = cs.countsketch_hash(5000, r, seed)
+    for row0, n in [(0, 5000), (1234, 2000), (4999, 1)]:
+        bb, ss = cs.countsketch_hash_rows(row0, n, r, seed)
+        assert np.array_equal(bb, b[row0:row0 + n]) and np.array_equal(ss, s[row0:row0 + n])
+    # rows 2^32 - 2 .. 2^32 + 1: the counter's high word takes the carry
+    bb, ss = cs.countsketch_hash_rows(2**32 - 2, 4, r, seed)
+    for t, i in enumerate(range(2**32 - 2, 2**32 + 2)):
+        w = philox4x32_10(i & 0xFFFFFFFF, i >> 32, cs.STREAM_S, 0, seed & 0xFFFFFFFF, seed >> 32)
+        assert bb[t] == (int(w[0]) * r) >> 32
+        assert ss[t] == (-1 if int(w[1]) >= 2**31 else 1)
+
+
+def test_row_partition_sketches_sum_to_the_whole():
+    """S A = sum_g S_g A_g for a row partition (the exchange of the sharded
+    path): brute force with the explicit S of the whole matrix."""
+    rng = np.random.default_rng(3)
+    n, d, r, seed = 300, 7, 40, 9
+    A = rng.standard_normal((n, d))
+    b, s = cs.countsketch_hash(n, r, seed)
+    whole = cs.countsketch_matrix(b, s, r) @ A
+    parts = np.zeros((r, d))
+    for row0, rows in [(0, 120), (120, 1), (121, 179)]:
+        bb, ss = cs.countsketch_hash_rows(row0, rows, r, seed)
+        parts += cs.countsketch_apply_dense(A[row0:row0 + rows], bb, ss, r)
+    assert np.allclose(parts, whole, rtol=0, atol=1e-12)
