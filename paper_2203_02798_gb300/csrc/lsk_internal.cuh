@@ -238,11 +238,12 @@ size_t qr_workspace_bytes(int64_t k, int64_t d);
 // the two halves of qr_launch: C = B^T B in FP64 (pair-FP32 products), then
 // R, R^-1 from an FP64 Gram C (d <= 1024; C is overwritten when d > 256)
 size_t sketch_gram64_workspace_bytes(int64_t k, int64_t d);
+// Cp (nullable): the same Gram as FP32 pairs (hi + lo)
 cudaError_t sketch_gram64_launch(const float* B, int64_t k, int64_t d, double* C, void* ws, int sm_count,
-                                 cudaStream_t st);
+                                 cudaStream_t st, float2* Cp = nullptr);
 size_t qr_from_gram_workspace_bytes(int64_t d);
 cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
-                                cudaStream_t st);
+                                cudaStream_t st, const float2* Cp = nullptr);
 cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv,
                       float* Rinv32, void* ws, int* flag, int sm_count, cudaStream_t st);
 

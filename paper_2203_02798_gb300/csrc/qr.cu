@@ -21,8 +21,8 @@
 #include <algorithm>
 
 size_t qr_mixed_workspace_bytes(int64_t d);
-cudaError_t qr_mixed_launch(const double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws,
-                            int* flag, cudaStream_t st);
+cudaError_t qr_mixed_launch(const double* C, const float2* Cp, int64_t d, double* R, double* Rinv, float* Rinv32,
+                            void* ws, int* flag, cudaStream_t st);
 
 namespace {
 
@@ -111,7 +111,8 @@ __device__ __forceinline__ void sketch_gram64_body(const float* __restrict__ B, 
 }
 
 __device__ __forceinline__ void sketch_gram64_reduce_body(const double* __restrict__ part, int64_t nchunks, int64_t d,
-                                                          double* __restrict__ C, const int blk, const int nblk) {
+                                                          double* __restrict__ C, const int blk, const int nblk,
+                                                          float2* __restrict__ Cp = nullptr) {
     const int nt = (int)((d + QT - 1) / QT);
     const int ntiles = nt * (nt + 1) / 2;
     const int64_t len = d * d;
@@ -129,6 +130,10 @@ __device__ __forceinline__ void sketch_gram64_reduce_body(const double* __restri
         double s = 0.0;
         for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * QT * QT + w];
         C[e] = s;
+        if (Cp) {   // the same as an FP32 pair (hi + lo, ~48 bits)
+            const float h = (float)s;
+            Cp[e] = make_float2(h, (float)(s - (double)h));
+        }
     }
 }
 
@@ -137,8 +142,8 @@ __global__ void __launch_bounds__(256) sketch_gram64_kernel(const float* __restr
     sketch_gram64_body(B, k, d, rows_per, part, blockIdx.x, blockIdx.y);
 }
 __global__ void sketch_gram64_reduce_kernel(const double* __restrict__ part, int64_t nchunks, int64_t d,
-                                            double* __restrict__ C) {
-    sketch_gram64_reduce_body(part, nchunks, d, C, blockIdx.x, gridDim.x);
+                                            double* __restrict__ C, float2* __restrict__ Cp) {
+    sketch_gram64_reduce_body(part, nchunks, d, C, blockIdx.x, gridDim.x, Cp);
 }
 // grouped over QrJob tables: local block b of a job = (tile b % ntiles, chunk b / ntiles)
 __global__ void __launch_bounds__(256) sketch_gram64_grouped_kernel(const QrJob* __restrict__ jobs,
@@ -358,14 +363,14 @@ size_t sketch_gram64_workspace_bytes(int64_t k, int64_t d) {
 }
 
 cudaError_t sketch_gram64_launch(const float* B, int64_t k, int64_t d, double* C, void* ws, int sm_count,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, float2* Cp) {
     const QrPlan p = qr_plan(k, d);
     double* part = (double*)ws;
     LSK_PROF("qr_gram64", st) sketch_gram64_kernel<<<dim3((unsigned)p.ntiles, (unsigned)p.nchunks), 256, 0, st>>>(B, k, d, p.rows_per,
                                                                                       part);
     int64_t g = (d * d + 255) / 256;
     if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;
-    LSK_PROF("qr_gram64", st) sketch_gram64_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, p.nchunks, d, C);
+    LSK_PROF("qr_gram64", st) sketch_gram64_reduce_kernel<<<(unsigned)g, 256, 0, st>>>(part, p.nchunks, d, C, Cp);
     return cudaGetLastError();
 }
 
@@ -377,9 +382,9 @@ size_t qr_from_gram_workspace_bytes(int64_t d) {
 }
 
 cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
-                                cudaStream_t st) {
+                                cudaStream_t st, const float2* Cp) {
     if (d > 1024) return cudaErrorInvalidValue;
-    if (d <= 256) return qr_mixed_launch(C, d, R, Rinv, Rinv32, ws, flag, st);
+    if (d <= 256) return qr_mixed_launch(C, Cp, d, R, Rinv, Rinv32, ws, flag, st);
     const int64_t nbk = (d + NB - 1) / NB;
     double* Ldiag = (double*)ws;
     for (int64_t K = 0; K < nbk; ++K) {
@@ -396,7 +401,7 @@ cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, f
 }
 
 size_t qr_workspace_bytes(int64_t k, int64_t d) {
-    return ws_round((size_t)d * d * 8) + sketch_gram64_workspace_bytes(k, d) + qr_from_gram_workspace_bytes(d);
+    return ws_round((size_t)d * d * 8) * 2 + sketch_gram64_workspace_bytes(k, d) + qr_from_gram_workspace_bytes(d);
 }
 
 cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* Rinv, float* Rinv32,
@@ -404,11 +409,12 @@ cudaError_t qr_launch(const float* B, int64_t k, int64_t d, double* R, double* R
     if (d > 1024) return cudaErrorInvalidValue;
     WsCarver wc{(char*)ws, 0};
     double* C = wc.take<double>((size_t)d * d);
+    float2* Cp = wc.take<float2>((size_t)d * d);
     void* part = wc.take<char>(sketch_gram64_workspace_bytes(k, d));
     void* rest = wc.take<char>(qr_from_gram_workspace_bytes(d));
-    cudaError_t e = sketch_gram64_launch(B, k, d, C, part, sm_count, st);
+    cudaError_t e = sketch_gram64_launch(B, k, d, C, part, sm_count, st, d <= 256 ? Cp : nullptr);
     if (e != cudaSuccess) return e;
-    return qr_from_gram_launch(C, d, R, Rinv, Rinv32, rest, flag, st);
+    return qr_from_gram_launch(C, d, R, Rinv, Rinv32, rest, flag, st, d <= 256 ? Cp : nullptr);
 }
 
 bool qr_group_supported(int64_t k, int64_t d) { return d >= 1 && d <= 256 && k >= d; }

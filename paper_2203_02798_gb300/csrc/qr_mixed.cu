@@ -43,10 +43,6 @@ __device__ __forceinline__ void equil_exponents_body(const double* __restrict__ 
         sc[j] = ldexp(1.0, -ex);
     }
 }
-__global__ void equil_exponents_kernel(const double* __restrict__ C, int d, int* __restrict__ e,
-                                       double* __restrict__ sc, int* flag) {
-    equil_exponents_body(C, d, e, sc, flag, blockIdx.x, gridDim.x);
-}
 
 // Ct64 = C 2^{-e_i-e_j} (two exact multiplications), Ct32 = float(Ct64).
 __device__ __forceinline__ void equil_scale_body(const double* __restrict__ C, int d, const double* __restrict__ sc,
@@ -56,10 +52,6 @@ __device__ __forceinline__ void equil_scale_body(const double* __restrict__ C, i
         Ct64[t] = v;
         Ct32[t] = (float)v;
     }
-}
-__global__ void equil_scale_kernel(const double* __restrict__ C, int d, const double* __restrict__ sc,
-                                   double* __restrict__ Ct64, float* __restrict__ Ct32) {
-    equil_scale_body(C, d, sc, Ct64, Ct32, blockIdx.x, gridDim.x);
 }
 
 // FP32 Cholesky of Ct (d <= 256) in one CTA, blocked by 32: the lower
@@ -216,10 +208,6 @@ __device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int 
         for (int i = lane; i <= l; i += 32) dst[i] = ctile(S, l >> 5, i >> 5)[(l & 31) * CP + (i & 31)];
     }
 }
-__global__ void __launch_bounds__(512) chol32_kernel(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
-                                                      float* __restrict__ Lpk, int* flag) {
-    chol32_body(Ct32, d, Rt, Lpk, flag, blockIdx.x, gridDim.x);
-}
 
 // Back substitution steps l = min(j, 32 SL + 31) .. 32 SL of column j: the
 // rows of block SL hold the pivot; rows i < l of blocks <= SL are updated.
@@ -244,7 +232,10 @@ __device__ __forceinline__ void trinv_block(float (&xr)[8], const float* P, cons
 // The packed factor (row l of L = column l of Rt at offset l(l+1)/2) is
 // staged in shared memory (once per block of 4 or 16 columns) so the
 // back-substitution chain sees shared-memory latency.
-__device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int d, double* __restrict__ X, const int blk, const int nblk) {
+__device__ __forceinline__ void store_x(double* X, int64_t at, float v) { X[at] = (double)v; }
+__device__ __forceinline__ void store_x(float2* X, int64_t at, float v) { X[at] = make_float2(v, 0.f); }
+template <class T>
+__device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int d, T* __restrict__ X, const int blk, const int nblk) {
     extern __shared__ float P[];
     __shared__ float rdiag[256];
     {   // stage the packed factor with 16-byte loads, several in flight per thread
@@ -277,10 +268,11 @@ __device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int 
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const int i = lane + 32 * s;
-        if (i < d) X[(int64_t)i * d + j] = (i <= j) ? (double)xr[s] : 0.0;
+        if (i < d) store_x(X, (int64_t)i * d + j, (i <= j) ? xr[s] : 0.f);
     }
 }
-__global__ void __launch_bounds__(512) trinv32_kernel(const float* __restrict__ Lpk, int d, double* __restrict__ X) {
+// X = Rt^-1 as FP32 pairs (the single-sketch chain keeps its matrices in pair form)
+__global__ void __launch_bounds__(512) trinv32_pair_kernel(const float* __restrict__ Lpk, int d, float2* __restrict__ X) {
     trinv32_body(Lpk, d, X, blockIdx.x, gridDim.x);
 }
 
@@ -374,9 +366,6 @@ __device__ __forceinline__ void tri_gemm64_body(const TriGemm g, const int blk, 
     }
     g.Out[(int64_t)i * g.d + j] = r;
 }
-__global__ void __launch_bounds__(256) tri_gemm64_kernel(const TriGemm g) {
-    tri_gemm64_body(g, blockIdx.x, gridDim.x);
-}
 
 // U = strict_upper(M - I) + diag(M - I) / 2, in place.  |M - I| > 1/4
 // anywhere means the FP32 factor was too far off for one correction: the
@@ -395,9 +384,6 @@ __device__ __forceinline__ void correction_body(double* __restrict__ M, int d, i
     }
     if (big) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
 }
-__global__ void correction_kernel(double* __restrict__ M, int d, int* flag) {
-    correction_body(M, d, flag, blockIdx.x, gridDim.x);
-}
 
 // R = Z D, R^-1 = D^-1 Y (exact power-of-two scalings); FP32 copy of R^-1.
 __device__ __forceinline__ void unscale_body(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
@@ -411,10 +397,6 @@ __device__ __forceinline__ void unscale_body(const double* __restrict__ Z, const
         if (Rinv) Rinv[t] = ri;
         if (Rinv32) Rinv32[t] = (float)ri;
     }
-}
-__global__ void unscale_kernel(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
-                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32) {
-    unscale_body(Z, Y, e, d, R, Rinv, Rinv32, blockIdx.x, gridDim.x);
 }
 
 // min_j Rt_jj <= 2^-20 max_j Rt_jj on the equilibrated factor, with
@@ -444,9 +426,6 @@ __device__ __forceinline__ void rank_check_r_body(const double* __restrict__ Y, 
         }
         if (!(mn > 9.5367431640625e-07 * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
     }
-}
-__global__ void rank_check_r_kernel(const double* __restrict__ Y, int d, int* flag) {
-    rank_check_r_body(Y, d, flag, blockIdx.x, gridDim.x);
 }
 
 // ---- grouped: one grid per stage over many sketches (QrJob table) --------
@@ -507,16 +486,347 @@ __global__ void rank_check_r_grouped_kernel(const QrJob* __restrict__ jobs, cons
     rank_check_r_body(j.Y, j.d, j.flag, blk, nblk);
 }
 
+// ---- single-sketch path: fewer launches, no FP64 arithmetic -----------------
+// FP64 runs at 1/64 of the FP32 rate on this part, so the chain of one
+// sketch keeps its matrices as FP32 pairs (x = hi + lo, |lo| <= ulp(hi) / 2,
+// ~48 bits) from the Gram on, and touches FP64 only to write R and R^-1.
+//
+// Pair arithmetic (FP32 throughout): TwoSum for exact sums, one FMA for the
+// rounding error of a product.
+__device__ __forceinline__ void two_sum_acc(float& S, float& E, float s, float c) {
+    const float t = __fadd_rn(S, s);
+    const float z = __fsub_rn(t, S);
+    E = __fadd_rn(E, __fadd_rn(__fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(s, z)), c));
+    S = t;
+}
+__device__ __forceinline__ float2 pair_norm(float S, float E) {
+    const float h = __fadd_rn(S, E);
+    return make_float2(h, __fsub_rn(E, __fsub_rn(h, S)));
+}
+
+// chol_eq: the pair Gram Cp -> exponents e_j = floor(log2 sqrt(C_jj)) (the
+// scaling 2^-e is exact), the equilibrated FP32 tiles, the FP32 Cholesky
+// factorisation, the rank check on its diagonal, and the packed factor (and
+// Rt as pairs when R is wanted).  One CTA of 512 threads; tile rows padded to
+// 36 floats so that a row of a tile is eight aligned 16-byte vectors (the
+// trailing update reads L_IK rows as float4 broadcasts).
+constexpr int QP = 36;
+__device__ __forceinline__ float* qtile(float* S, int I, int J) { return S + (I * (I + 1) / 2 + J) * (CB * QP); }
+
+size_t chol_eq_smem(int d) {
+    const int nt = (d + CB - 1) / CB;
+    return (size_t)nt * (nt + 1) / 2 * CB * QP * 4;
+}
+
+__global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__ Cp, int d, int* __restrict__ e_out,
+                                                      float2* __restrict__ Rt, float* __restrict__ Lpk, int* flag) {
+    extern __shared__ __align__(16) float S[];
+    __shared__ float rdiag[CB];
+    __shared__ int es[256];
+    __shared__ unsigned char tI[36], tJ[36];
+    __shared__ float dmin[32], dmax[32];
+    const int nt = (d + CB - 1) / CB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // (0) equilibration exponents from the diagonal
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float c = Cp[(int64_t)j * d + j].x;
+        int ex = 0;
+        if (c > 0.f && isfinite(c)) {
+            int b2;
+            frexpf(c, &b2);                 // c = m 2^b2, m in [0.5, 1)
+            ex = (b2 - 1) >> 1;
+        } else {
+            set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+        }
+        e_out[j] = ex;
+        es[j] = ex;
+    }
+    const int ntl = nt * (nt + 1) / 2;
+    if (threadIdx.x < ntl) {
+        int I = 0, t = threadIdx.x;
+        while (t > I) t -= ++I;
+        tI[threadIdx.x] = (unsigned char)I;
+        tJ[threadIdx.x] = (unsigned char)t;
+    }
+    __syncthreads();
+    // (1) the lower tiles of Ct = D^-1 C D^-1 in FP32 (beyond d: the identity);
+    //     the FP32 rounding of C scaled by 2^(-e_i - e_j) exactly
+#pragma unroll 8
+    for (int t = threadIdx.x; t < ntl * CB * CB; t += blockDim.x) {
+        const int tl = t >> 10, el = t & 1023;
+        const int r = el >> 5, c = el & 31, i = tI[tl] * CB + r, j = tJ[tl] * CB + c;
+        S[tl * (CB * QP) + r * QP + c] =
+            (i < d && j < d) ? ldexpf(Cp[(int64_t)i * d + j].x, -es[i] - es[j]) : (i == j ? 1.f : 0.f);
+    }
+    __syncthreads();
+    for (int K = 0; K < nt; ++K) {
+        float* D = qtile(S, K, K);
+        if (w == 0) {   // (2) diagonal tile: row `lane` in registers
+            float a[CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) a[k] = D[lane * QP + k];
+            DiagStep<0>::run(a, lane, flag);
+#pragma unroll
+            for (int k = 0; k < CB; ++k) D[lane * QP + k] = a[k];
+            __syncwarp();
+            rdiag[lane] = 1.f / D[lane * QP + lane];
+            __syncwarp();
+        }
+        __syncthreads();
+        // (3) panel: thread per row of T(I, K), I > K (forward substitution with L_KK)
+        {
+            const int rows = (nt - K - 1) * CB;
+            for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+                const int I = K + 1 + t / CB, r = t % CB;
+                float* T = qtile(S, I, K);
+                float x[CB];
+#pragma unroll
+                for (int j = 0; j < CB; ++j) {
+                    float v = T[r * QP + j];
+#pragma unroll
+                    for (int l = 0; l < j; ++l) v -= x[l] * D[j * QP + l];
+                    x[j] = v * rdiag[j];
+                }
+#pragma unroll
+                for (int j = 0; j < CB; ++j) T[r * QP + j] = x[j];
+            }
+        }
+        __syncthreads();
+        // (4) trailing update T(I, J) -= L_IK L_JK^T, K < J <= I, one tile per
+        //     warp: lane = column of the tile, rows of L_IK as float4 broadcasts
+        {
+            const int T0 = nt - K - 1;
+            const int ntile = T0 * (T0 + 1) / 2;
+            for (int t = w; t < ntile; t += nw) {
+                int I = 0, tt = t;
+                while (tt > I) {
+                    tt -= I + 1;
+                    ++I;
+                }
+                const int Jg = tt + K + 1;
+                I += K + 1;
+                const float* LI = qtile(S, I, K);
+                const float* LJ = qtile(S, Jg, K);
+                float* T = qtile(S, I, Jg);
+                float lj[CB];
+#pragma unroll
+                for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * QP + k];
+#pragma unroll 1
+                for (int a = 0; a < CB; ++a) {
+                    const float4* row = reinterpret_cast<const float4*>(LI + a * QP);
+                    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < CB / 4; q += 2) {
+                        const float4 u = row[q], v = row[q + 1];
+                        acc0 = fmaf(u.x, lj[4 * q], acc0);
+                        acc1 = fmaf(u.y, lj[4 * q + 1], acc1);
+                        acc0 = fmaf(u.z, lj[4 * q + 2], acc0);
+                        acc1 = fmaf(u.w, lj[4 * q + 3], acc1);
+                        acc0 = fmaf(v.x, lj[4 * q + 4], acc0);
+                        acc1 = fmaf(v.y, lj[4 * q + 5], acc1);
+                        acc0 = fmaf(v.z, lj[4 * q + 6], acc0);
+                        acc1 = fmaf(v.w, lj[4 * q + 7], acc1);
+                    }
+                    T[a * QP + lane] -= acc0 + acc1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // (5) rank check on the equilibrated FP32 factor: min_j L_jj <= 2^-20 max_j
+    //     L_jj (one correction step resolves no more than that)
+    {
+        float mn = INFINITY, mx = 0.f;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            const float v = qtile(S, j >> 5, j >> 5)[(j & 31) * QP + (j & 31)];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+        for (int o = 16; o; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            dmin[w] = mn;
+            dmax[w] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < nw; ++q) {
+                mn = fminf(mn, dmin[q]);
+                mx = fmaxf(mx, dmax[q]);
+            }
+            if (!(mn > 9.5367431640625e-07f * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
+        }
+    }
+    // (6) Rt[i][j] = L[j][i] for j >= i (only when R is wanted), packed rows of L
+    if (Rt) {
+        for (int i = w; i < d; i += nw)
+            for (int j = lane; j < d; j += 32)
+                Rt[(int64_t)i * d + j] =
+                    make_float2((j >= i) ? qtile(S, j >> 5, i >> 5)[(j & 31) * QP + (i & 31)] : 0.f, 0.f);
+    }
+    for (int l = w; l < d; l += nw) {
+        float* dst = Lpk + l * (l + 1) / 2;
+        for (int i = lane; i <= l; i += 32) dst[i] = qtile(S, l >> 5, i >> 5)[(l & 31) * QP + (i & 31)];
+    }
+}
+
+// Out = alpha op(A) B + beta Cin + diag_add I on the upper triangle (the
+// TriGemm operation on pair matrices), with the whole reduction range of a
+// 16 x 16 output tile staged in shared memory at once and split between two
+// threads per output; A optionally scaled exactly (A_ik 2^(-e_i - e_k)); an
+// epilogue finishes a step of the correction:
+//   kPlain:   Out as above;
+//   kCorrect: Out = U = strict_upper(E) + diag(E) / 2, E = result - I, and
+//             the rank flag when |E| > 1/4 (the correction of the FP32 factor);
+//   kInverse: Out = Y = result, R64 / R32 = 2^-e_i Y (R^-1 in FP64 and FP32);
+//   kFactor:  R64 = 2^e_j result (R; Out unused).
+// R64 and R32 are written whole: an off-diagonal tile also writes the zeros
+// of its mirror below the diagonal (no lower tile is launched).
+enum TriEpi { kPlain = 0, kCorrect = 1, kInverse = 2, kFactor = 3 };
+struct TriGemmP {
+    const float2* A;
+    const float2* B;
+    const float2* Cin;
+    float2* Out;
+    const int* ea;      // nullable: A_ik scaled by 2^(-ea_i - ea_k)
+    int d, transA, a_upper, a_lower, b_upper, epi;
+    float alpha;        // +1 or -1
+    int beta, diag_add; // 0 or 1
+    const int* e;
+    double* R64;
+    float* R32;
+    int* flag;
+};
+constexpr int kTgThreads = 512;
+size_t tri_gemm_pair_smem(int d) {
+    const int kmax = ((d + TT - 1) / TT) * TT;
+    return (size_t)TT * (kmax + 1) * 8 + (size_t)kmax * (TT + 1) * 8 + (size_t)TT * TT * 4 * 4;
+}
+
+__global__ void __launch_bounds__(kTgThreads) tri_gemm_pair_kernel(const TriGemmP g) {
+    extern __shared__ __align__(16) float2 smp[];
+    const int nt = (g.d + TT - 1) / TT;
+    const int kmax = nt * TT;
+    int t = blockIdx.x, I = 0;
+    while (t >= nt - I) {
+        t -= nt - I;
+        ++I;
+    }
+    const int J = I + t;
+    const int i0 = I * TT, j0 = J * TT;
+    int klo = 0, khi = g.d;
+    if (g.a_upper) klo = i0;
+    if (g.a_lower) khi = min(khi, i0 + TT);
+    if (g.b_upper) khi = min(khi, j0 + TT);
+    klo -= klo % TT;
+    // whole 16-wide chunks (entries past d are zero; past khi within the last
+    // chunk the stored zeros of the triangular factors contribute nothing)
+    const int klen = khi > klo ? ((khi - klo + TT - 1) / TT) * TT : 0;
+    float2* As = smp;                                // [TT][kmax + 1]
+    float2* Bs = smp + TT * (kmax + 1);              // [kmax][TT + 1]
+    float* red = reinterpret_cast<float*>(Bs + kmax * (TT + 1));   // [TT * TT][4]
+    // stage A[i0.., klo..) (a row of 16 per pass, lanes along k) and B[klo.., j0..)
+    const int lg = klen > 0 ? klen : 1;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < TT * klen; q += kTgThreads) {
+        const int r = q / lg, c = q - r * lg;
+        const int ia = i0 + r, ka = klo + c;
+        float2 a = make_float2(0.f, 0.f);
+        if (ia < g.d && ka < g.d) {
+            a = g.transA ? g.A[(int64_t)ka * g.d + ia] : g.A[(int64_t)ia * g.d + ka];
+            if (g.ea) {
+                const int sh = -g.ea[ia] - g.ea[ka];
+                a = make_float2(ldexpf(a.x, sh), ldexpf(a.y, sh));
+            }
+        }
+        As[r * (kmax + 1) + c] = a;
+        const int kr = q >> 4, jc = q & 15;
+        const int kb = klo + kr, jb = j0 + jc;
+        Bs[kr * (TT + 1) + jc] = (kb < g.d && jb < g.d) ? g.B[(int64_t)kb * g.d + jb] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int h = threadIdx.x >> 8, o = threadIdx.x & 255, ty = o >> 4, tx = o & 15;
+    const int half = ((klen / 2 + TT - 1) / TT) * TT;
+    const int kb0 = h ? half : 0, kb1 = h ? klen : min(half, klen);
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    for (int k0 = kb0; k0 < kb1; k0 += TT) {
+#pragma unroll
+        for (int kk = 0; kk < TT; kk += 2) {
+            pair_mac(As[ty * (kmax + 1) + k0 + kk], Bs[(k0 + kk) * (TT + 1) + tx], s0, c0);
+            pair_mac(As[ty * (kmax + 1) + k0 + kk + 1], Bs[(k0 + kk + 1) * (TT + 1) + tx], s1, c1);
+        }
+        pair_renorm(s0, c0);
+        pair_renorm(s1, c1);
+    }
+    if (h) {
+        red[o * 4 + 0] = s0;
+        red[o * 4 + 1] = c0;
+        red[o * 4 + 2] = s1;
+        red[o * 4 + 3] = c1;
+    }
+    __syncthreads();
+    if (h) return;
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= g.d || j >= g.d) return;
+    const bool up = j >= i;
+    float2 r = make_float2(0.f, 0.f);
+    if (up) {
+        float S = s0, E = c0;
+        two_sum_acc(S, E, s1, c1);
+        two_sum_acc(S, E, red[o * 4 + 0], red[o * 4 + 1]);
+        two_sum_acc(S, E, red[o * 4 + 2], red[o * 4 + 3]);
+        S *= g.alpha;
+        E *= g.alpha;
+        if (g.beta) {
+            const float2 ci = g.Cin[(int64_t)i * g.d + j];
+            two_sum_acc(S, E, ci.x, ci.y);
+        }
+        if (i == j && g.diag_add) two_sum_acc(S, E, 1.f, 0.f);
+        r = pair_norm(S, E);
+    }
+    const int64_t at = (int64_t)i * g.d + j;
+    const int64_t mirror = (I < J) ? (int64_t)j * g.d + i : -1;
+    if (g.epi == kCorrect) {
+        if (up) {
+            float S = r.x, E = r.y;
+            if (i == j) two_sum_acc(S, E, -1.f, 0.f);
+            r = pair_norm(S, E);
+            if (!(fabsf(r.x) <= 0.25f)) set_flag(g.flag, LSK_FLAG_RANK_DEFICIENT);
+            if (i == j) r = make_float2(0.5f * r.x, 0.5f * r.y);
+        }
+        g.Out[at] = r;
+    } else if (g.epi == kInverse) {
+        g.Out[at] = r;
+        if (g.R64) g.R64[at] = up ? ldexp((double)r.x + (double)r.y, -g.e[i]) : 0.0;
+        if (g.R32) g.R32[at] = up ? ldexpf(r.x, -g.e[i]) : 0.f;
+        if (mirror >= 0) {
+            if (g.R64) g.R64[mirror] = 0.0;
+            if (g.R32) g.R32[mirror] = 0.f;
+        }
+    } else if (g.epi == kFactor) {
+        g.R64[at] = up ? ldexp((double)r.x + (double)r.y, g.e[j]) : 0.0;
+        if (mirror >= 0) g.R64[mirror] = 0.0;
+    } else {
+        g.Out[at] = r;
+    }
+}
+
+// C (FP64, d x d) -> FP32 pairs, for callers that start from an FP64 Gram
+__global__ void to_pair_kernel(const double* __restrict__ C, int64_t len, float2* __restrict__ Cp) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
+        const double x = C[t];
+        const float h = (float)x;
+        Cp[t] = make_float2(h, (float)(x - (double)h));
+    }
+}
+
 size_t chol32_smem(int d) {
     const int nt = (d + CB - 1) / CB;
     return (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
 }
 
-cudaError_t tri_gemm(const TriGemm& g, cudaStream_t st) {
-    const int nt = (g.d + TT - 1) / TT;
-    LSK_PROF("qr_refine64", st) tri_gemm64_kernel<<<nt * (nt + 1) / 2, 256, 0, st>>>(g);
-    return cudaGetLastError();
-}
 
 }  // namespace
 
@@ -579,53 +889,65 @@ cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, 
     return cudaGetLastError();
 }
 
-// C: FP64 Gram of the sketch (d x d, full).  Outputs as qr_launch; R is only
-// formed (one Newton step) when requested.
-cudaError_t qr_mixed_launch(const double* C, int64_t d64, double* R, double* Rinv, float* Rinv32, void* ws, int* flag,
-                            cudaStream_t st) {
+// C: FP64 Gram of the sketch (d x d, full); Cp: the same as FP32 pairs, or
+// NULL (then formed here).  Outputs as qr_launch; R is only formed (one
+// Newton step) when requested.  Launches: chol_eq (equilibration, FP32
+// factor, rank check), trinv32, then W = Ct X, M = X^T W (epilogue: U),
+// Y = X - X U (epilogue: R^-1) and, for R, P = I - Y Rt, Z = Rt + Rt P
+// (epilogue: R).  Every matrix between them is a pair matrix.
+cudaError_t qr_mixed_launch(const double* C, const float2* Cp, int64_t d64, double* R, double* Rinv, float* Rinv32,
+                            void* ws, int* flag, cudaStream_t st) {
     const int d = (int)d64;
+    const size_t dd = (size_t)d * d;
     WsCarver wc{(char*)ws, 0};
-    double* Ct = wc.take<double>((size_t)d * d);
-    float* Ct32 = wc.take<float>((size_t)d * d);
+    float2* Cq = wc.take<float2>(dd);
     float* Lpk = wc.take<float>((size_t)d * (d + 1) / 2);
-    double* Rt = wc.take<double>((size_t)d * d);
-    double* X = wc.take<double>((size_t)d * d);
-    double* W = wc.take<double>((size_t)d * d);
-    double* M = wc.take<double>((size_t)d * d);
-    double* Y = wc.take<double>((size_t)d * d);
+    float2* Rt = wc.take<float2>(dd);
+    float2* X = wc.take<float2>(dd);
+    float2* W = wc.take<float2>(dd);
+    float2* M = wc.take<float2>(dd);
+    float2* Y = wc.take<float2>(dd);
     int* e = wc.take<int>(d);
-    double* sc = wc.take<double>(d);
-    const int zb = (d * d + 255) / 256 < 1024 ? (d * d + 255) / 256 : 1024;
-    LSK_PROF("qr_equil", st) equil_exponents_kernel<<<1, 256, 0, st>>>(C, d, e, sc, flag);
-    LSK_PROF("qr_equil", st) equil_scale_kernel<<<zb, 256, 0, st>>>(C, d, sc, Ct, Ct32);
-    const size_t tiles = chol32_smem(d);
-    cudaError_t err = allow_dynamic_smem(chol32_kernel);
-    if (err != cudaSuccess) return err;
-    LSK_PROF("qr_chol32", st) chol32_kernel<<<1, 512, tiles, st>>>(Ct32, d, R ? Rt : nullptr, Lpk, flag);
-    const size_t pk = (size_t)d * (d + 1) / 2 * 4;
-    err = allow_dynamic_smem(trinv32_kernel);
-    if (err != cudaSuccess) return err;
-    LSK_PROF("qr_trinv32", st) trinv32_kernel<<<(d * 32 + 127) / 128, 128, pk, st>>>(Lpk, d, X);
-    // M = X^T (Ct X): W = Ct X on the upper triangle (only k <= j is needed by M)
-    TriGemm g{Ct, X, nullptr, W, d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
-    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
-    g = TriGemm{X, W, nullptr, M, d, 1, 0, 1, 1, 1.0, 0.0, 0.0};
-    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
-    LSK_PROF("qr_refine64", st) correction_kernel<<<zb, 256, 0, st>>>(M, d, flag);   // M -> U
-    // Y = X - X U
-    g = TriGemm{X, M, X, Y, d, 0, 1, 0, 1, -1.0, 1.0, 0.0};
-    if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
-    double* Z = nullptr;
-    if (R) {
-        // P = I - Y Rt ; Z = Rt + Rt P   (Newton step for Y^-1)
-        double* P = W;
-        Z = M;
-        g = TriGemm{Y, Rt, nullptr, P, d, 0, 1, 0, 1, -1.0, 0.0, 1.0};
-        if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
-        g = TriGemm{Rt, P, Rt, Z, d, 0, 1, 0, 1, 1.0, 1.0, 0.0};
-        if ((err = tri_gemm(g, st)) != cudaSuccess) return err;
+    cudaError_t err;
+    if (!Cp) {
+        const int64_t g = (int64_t)((dd + 255) / 256) < 1024 ? (int64_t)((dd + 255) / 256) : 1024;
+        LSK_PROF("qr_equil", st) to_pair_kernel<<<(unsigned)g, 256, 0, st>>>(C, (int64_t)dd, Cq);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        Cp = Cq;
     }
-    LSK_PROF("qr_finish", st) unscale_kernel<<<zb, 256, 0, st>>>(Z, Y, e, d, R, Rinv, Rinv32);
-    LSK_PROF("qr_finish", st) rank_check_r_kernel<<<1, 256, 0, st>>>(Y, d, flag);
+    if ((err = allow_dynamic_smem(chol_eq_kernel)) != cudaSuccess) return err;
+    LSK_PROF("qr_chol32", st) chol_eq_kernel<<<1, 512, chol_eq_smem(d), st>>>(Cp, d, e, R ? Rt : nullptr, Lpk, flag);
+    const size_t pk = (size_t)d * (d + 1) / 2 * 4;
+    if ((err = allow_dynamic_smem(trinv32_pair_kernel)) != cudaSuccess) return err;
+    LSK_PROF("qr_trinv32", st) trinv32_pair_kernel<<<(d * 32 + 127) / 128, 128, pk, st>>>(Lpk, d, X);
+    if ((err = allow_dynamic_smem(tri_gemm_pair_kernel)) != cudaSuccess) return err;
+    const int nt = (d + TT - 1) / TT;
+    const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
+    const size_t tsm = tri_gemm_pair_smem(d);
+    auto run = [&](const TriGemmP& g) {
+        LSK_PROF("qr_refine64", st) tri_gemm_pair_kernel<<<tiles, kTgThreads, tsm, st>>>(g);
+        return cudaGetLastError();
+    };
+    // W = Ct X on the upper triangle (only k <= j is needed by M); Ct = D^-1 C D^-1 on the fly
+    if ((err = run(TriGemmP{Cp, X, nullptr, W, e, d, 0, 0, 0, 1, kPlain, 1.f, 0, 0, nullptr, nullptr, nullptr, flag})) !=
+        cudaSuccess)
+        return err;
+    // M = X^T W, epilogue U
+    if ((err = run(TriGemmP{X, W, nullptr, M, nullptr, d, 1, 0, 1, 1, kCorrect, 1.f, 0, 0, nullptr, nullptr, nullptr,
+                            flag})) != cudaSuccess)
+        return err;
+    // Y = X - X U, epilogue R^-1 = D^-1 Y
+    if ((err = run(TriGemmP{X, M, X, Y, nullptr, d, 0, 1, 0, 1, kInverse, -1.f, 1, 0, e, Rinv, Rinv32, flag})) !=
+        cudaSuccess)
+        return err;
+    if (R) {
+        // P = I - Y Rt ; Z = Rt + Rt P (Newton step for Y^-1), epilogue R = Z D
+        if ((err = run(TriGemmP{Y, Rt, nullptr, W, nullptr, d, 0, 1, 0, 1, kPlain, -1.f, 0, 1, nullptr, nullptr,
+                                nullptr, flag})) != cudaSuccess)
+            return err;
+        if ((err = run(TriGemmP{Rt, W, Rt, M, nullptr, d, 0, 1, 0, 1, kFactor, 1.f, 1, 0, e, R, nullptr, flag})) !=
+            cudaSuccess)
+            return err;
+    }
     return cudaGetLastError();
 }
