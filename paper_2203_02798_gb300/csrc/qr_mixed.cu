@@ -518,16 +518,59 @@ size_t chol_eq_smem(int d) {
     return (size_t)nt * (nt + 1) / 2 * CB * QP * 4;
 }
 
+// warp-wide FP32 Cholesky of the diagonal tile D (row `lane` in registers)
+__device__ __forceinline__ void chol_diag_tile(float* D, float* rdiag, int lane, int* flag) {
+    float a[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) a[k] = D[lane * QP + k];
+    DiagStep<0>::run(a, lane, flag);
+#pragma unroll
+    for (int k = 0; k < CB; ++k) D[lane * QP + k] = a[k];
+    __syncwarp();
+    rdiag[lane] = 1.f / D[lane * QP + lane];
+    __syncwarp();
+}
+
+// T(I, J) -= L_IK L_JK^T for one 32 x 32 tile by one warp: lane = column of
+// the tile, rows of L_IK read as float4 broadcasts
+__device__ __forceinline__ void chol_tile_update(float* S, int I, int J, int K, int lane) {
+    const float* LI = qtile(S, I, K);
+    const float* LJ = qtile(S, J, K);
+    float* T = qtile(S, I, J);
+    float lj[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * QP + k];
+#pragma unroll 1
+    for (int a = 0; a < CB; ++a) {
+        const float4* row = reinterpret_cast<const float4*>(LI + a * QP);
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < CB / 4; q += 2) {
+            const float4 u = row[q], v = row[q + 1];
+            acc0 = fmaf(u.x, lj[4 * q], acc0);
+            acc1 = fmaf(u.y, lj[4 * q + 1], acc1);
+            acc0 = fmaf(u.z, lj[4 * q + 2], acc0);
+            acc1 = fmaf(u.w, lj[4 * q + 3], acc1);
+            acc0 = fmaf(v.x, lj[4 * q + 4], acc0);
+            acc1 = fmaf(v.y, lj[4 * q + 5], acc1);
+            acc0 = fmaf(v.z, lj[4 * q + 6], acc0);
+            acc1 = fmaf(v.w, lj[4 * q + 7], acc1);
+        }
+        T[a * QP + lane] -= acc0 + acc1;
+    }
+}
+
 __global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__ Cp, int d, int* __restrict__ e_out,
                                                       float2* __restrict__ Rt, float* __restrict__ Lpk, int* flag) {
     extern __shared__ __align__(16) float S[];
     __shared__ float rdiag[CB];
-    __shared__ int es[256];
+    __shared__ float scf[256];
     __shared__ unsigned char tI[36], tJ[36];
     __shared__ float dmin[32], dmax[32];
     const int nt = (d + CB - 1) / CB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // (0) equilibration exponents from the diagonal
+    // (0) equilibration exponents from the diagonal; scf_j = 2^-e_j (a float:
+    //     e_j is in [-75, 64] for a finite positive FP32 C_jj)
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         const float c = Cp[(int64_t)j * d + j].x;
         int ex = 0;
@@ -539,7 +582,7 @@ __global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__
             set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
         }
         e_out[j] = ex;
-        es[j] = ex;
+        scf[j] = ldexpf(1.f, -ex);
     }
     const int ntl = nt * (nt + 1) / 2;
     if (threadIdx.x < ntl) {
@@ -549,32 +592,40 @@ __global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__
         tJ[threadIdx.x] = (unsigned char)t;
     }
     __syncthreads();
-    // (1) the lower tiles of Ct = D^-1 C D^-1 in FP32 (beyond d: the identity);
-    //     the FP32 rounding of C scaled by 2^(-e_i - e_j) exactly
-#pragma unroll 8
-    for (int t = threadIdx.x; t < ntl * CB * CB; t += blockDim.x) {
-        const int tl = t >> 10, el = t & 1023;
-        const int r = el >> 5, c = el & 31, i = tI[tl] * CB + r, j = tJ[tl] * CB + c;
-        S[tl * (CB * QP) + r * QP + c] =
-            (i < d && j < d) ? ldexpf(Cp[(int64_t)i * d + j].x, -es[i] - es[j]) : (i == j ? 1.f : 0.f);
+    // (1) the lower tiles of Ct = D^-1 C D^-1 in FP32 (beyond d: the identity):
+    //     the FP32 rounding of C times two exact powers of two, in rounds of
+    //     24 loads per thread, all issued before any is used
+    {
+        constexpr int kR = 24;
+        const int total = ntl * CB * CB;
+        for (int t0 = 0; t0 < total; t0 += kR * 512) {
+            float v[kR];
+#pragma unroll
+            for (int q = 0; q < kR; ++q) {
+                const int t = t0 + q * 512 + (int)threadIdx.x;
+                const int tl = t >> 10, el = t & 1023;
+                const int i = tI[tl < 36 ? tl : 0] * CB + (el >> 5), j = tJ[tl < 36 ? tl : 0] * CB + (el & 31);
+                v[q] = (t < total && i < d && j < d) ? __ldg(&Cp[(int64_t)i * d + j].x) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < kR; ++q) {
+                const int t = t0 + q * 512 + (int)threadIdx.x;
+                if (t < total) {
+                    const int tl = t >> 10, el = t & 1023;
+                    const int r = el >> 5, c = el & 31, i = tI[tl] * CB + r, j = tJ[tl] * CB + c;
+                    S[tl * (CB * QP) + r * QP + c] = (i < d && j < d) ? v[q] * scf[i] * scf[j] : (i == j ? 1.f : 0.f);
+                }
+            }
+        }
     }
     __syncthreads();
-    for (int K = 0; K < nt; ++K) {
-        float* D = qtile(S, K, K);
-        if (w == 0) {   // (2) diagonal tile: row `lane` in registers
-            float a[CB];
-#pragma unroll
-            for (int k = 0; k < CB; ++k) a[k] = D[lane * QP + k];
-            DiagStep<0>::run(a, lane, flag);
-#pragma unroll
-            for (int k = 0; k < CB; ++k) D[lane * QP + k] = a[k];
-            __syncwarp();
-            rdiag[lane] = 1.f / D[lane * QP + lane];
-            __syncwarp();
-        }
-        __syncthreads();
-        // (3) panel: thread per row of T(I, K), I > K (forward substitution with L_KK)
-        {
+    // K = -1 factors the first diagonal tile only; every later pass: the panel
+    // of K, then the trailing update with the next diagonal tile looked ahead
+    // (one call site of the unrolled diagonal factorisation keeps the code small)
+    for (int K = -1; K < nt; ++K) {
+        const float* D = qtile(S, K < 0 ? 0 : K, K < 0 ? 0 : K);
+        // (2) panel: thread per row of T(I, K), I > K (forward substitution with L_KK)
+        if (K >= 0) {
             const int rows = (nt - K - 1) * CB;
             for (int t = threadIdx.x; t < rows; t += blockDim.x) {
                 const int I = K + 1 + t / CB, r = t % CB;
@@ -592,42 +643,26 @@ __global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__
             }
         }
         __syncthreads();
-        // (4) trailing update T(I, J) -= L_IK L_JK^T, K < J <= I, one tile per
-        //     warp: lane = column of the tile, rows of L_IK as float4 broadcasts
+        // (3) trailing update with look-ahead: warp 0 updates the next diagonal
+        //     tile (K+1, K+1) and factors it at once, while the other warps
+        //     update the rest of the trailing tiles (I, J), K < J <= I
         {
             const int T0 = nt - K - 1;
-            const int ntile = T0 * (T0 + 1) / 2;
-            for (int t = w; t < ntile; t += nw) {
-                int I = 0, tt = t;
-                while (tt > I) {
-                    tt -= I + 1;
-                    ++I;
+            const int ntile = K < 0 ? 0 : T0 * (T0 + 1) / 2;
+            if (w == 0) {
+                if (T0 > 0) {
+                    if (K >= 0) chol_tile_update(S, K + 1, K + 1, K, lane);
+                    __syncwarp();
+                    chol_diag_tile(qtile(S, K + 1, K + 1), rdiag, lane, flag);
                 }
-                const int Jg = tt + K + 1;
-                I += K + 1;
-                const float* LI = qtile(S, I, K);
-                const float* LJ = qtile(S, Jg, K);
-                float* T = qtile(S, I, Jg);
-                float lj[CB];
-#pragma unroll
-                for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * QP + k];
-#pragma unroll 1
-                for (int a = 0; a < CB; ++a) {
-                    const float4* row = reinterpret_cast<const float4*>(LI + a * QP);
-                    float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-                    for (int q = 0; q < CB / 4; q += 2) {
-                        const float4 u = row[q], v = row[q + 1];
-                        acc0 = fmaf(u.x, lj[4 * q], acc0);
-                        acc1 = fmaf(u.y, lj[4 * q + 1], acc1);
-                        acc0 = fmaf(u.z, lj[4 * q + 2], acc0);
-                        acc1 = fmaf(u.w, lj[4 * q + 3], acc1);
-                        acc0 = fmaf(v.x, lj[4 * q + 4], acc0);
-                        acc1 = fmaf(v.y, lj[4 * q + 5], acc1);
-                        acc0 = fmaf(v.z, lj[4 * q + 6], acc0);
-                        acc1 = fmaf(v.w, lj[4 * q + 7], acc1);
+            } else {
+                for (int t = w; t < ntile; t += nw - 1) {   // t = 0 is the diagonal tile
+                    int I = 0, tt = t;
+                    while (tt > I) {
+                        tt -= I + 1;
+                        ++I;
                     }
-                    T[a * QP + lane] -= acc0 + acc1;
+                    chol_tile_update(S, I + K + 1, tt + K + 1, K, lane);
                 }
             }
         }
