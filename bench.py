@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-gram", action="store_true", help="skip the A^T A leg")
     ap.add_argument("--no-jl", action="store_true", help="skip the Alg. 15 right-projection leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the dense 20,000 x 50 and CSR 1M x 200 legs")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the sketch-and-solve (Alg. 11) and csrjlt (Alg. 4) legs")
     ap.add_argument("--jl-m", type=int, default=64, help="columns of the right JL projection Pi")
@@ -340,6 +342,63 @@ def main():
         del b, bvec
         return out
 
+    def configs_leg(steps):
+        """The two smaller workloads the path is specified on, each one step =
+        the whole leverage-score path, with the A^T A of the same A, per-kernel
+        CUDA-event times and each kernel's fraction of the measured HBM
+        bandwidth on its algorithmic bytes (the CountSketch pass: A once + the
+        S A write; the row norms: A once + the scores; the Gram: A once):
+          dense 20,000 x 50 (FP64 input cast to FP32 once; rows 0-4 x 100),
+              r = 2,500, k = 100, FP32 and BF16 stages;
+          CSR 1,000,000 x 200, each entry kept with p = 0.01 (~2M nnz), r = 40,000,
+              k = 400, FP32 throughout."""
+        out = {}
+
+        def run_case(name, Ac, r, k, prec, a_bytes, kernel_bytes):
+            ellc = torch.empty(Ac.n if isinstance(Ac, lsk.CSR) else Ac.shape[0], dtype=torch.float32, device="cuda")
+            fn = lambda: lsk.leverage_scores(Ac, r, k, SEED, prec, out=ellc, ctx=ctx)
+            for _ in range(3):
+                fn()
+            ctx.sync()
+            ctx.profile(True)
+            ctx.profile_reset()
+            ms, _, _ = timed(fn, steps)
+            gfn = lambda: lsk.gram(Ac, prec="fp32", ctx=ctx)
+            gms, _, _ = timed(gfn, steps)         # the Gram's kernels join the same per-kernel record
+            ctx.profile(False)
+            ctx.sync()
+            ms /= steps
+            gms /= steps
+            kern = {}
+            for kn, (launches, tot) in ctx.profile_totals().items():
+                per = tot / max(launches, 1)
+                e = {"launches_per_step": launches / steps, "ms_per_launch": per}
+                if kn in kernel_bytes:
+                    e["algorithmic_bytes"] = kernel_bytes[kn]
+                    e["GB/s"] = kernel_bytes[kn] / (per * 1e-3) / 1e9
+                    e["frac_of_measured_hbm"] = e["GB/s"] / hbm
+                kern[kn] = e
+            out[name] = {"ms_per_step": ms, "value": a_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s of A",
+                         "prec": prec, "kernels": kern,
+                         "gram_fp32": {"ms": gms, "GB/s": a_bytes / (gms * 1e-3) / 1e9}}
+
+        A1 = torch.from_numpy(workloads.dense_outliers().astype(np.float32)).cuda()
+        n1, d1 = A1.shape
+        b1 = n1 * d1 * 4
+        for prec in ("fp32", "bf16"):
+            run_case(f"dense_outliers_20000x50_{prec}", A1, 2500, 100, prec, b1,
+                     {"cs_dense_gather": b1 + 4 * 2500 * d1, "rownorm_dense_simt": b1 + 4 * n1,
+                      "rownorm_dense_tc": b1 + 4 * n1})
+        V, J, I = workloads.csr_bernoulli(1_000_000, 200, 0.01, seed=1)
+        A2 = lsk.csr_from_numpy(V, J, I, 200)
+        nnz, n2 = int(len(V)), 1_000_000
+        b2 = 8 * nnz + 8 * (n2 + 1)
+        run_case("csr_1Mx200_p0.01_fp32", A2, 40_000, 400, "fp32", b2,
+                 {"cs_csr_gather": b2 + 4 * 40_000 * 200, "rownorm_csr": b2 + 4 * n2, "gram_csr": b2})
+        out["csr_1Mx200_p0.01_fp32"]["nnz"] = nnz
+        del A1, A2, V, J, I
+        return out
+
     def barrier():
         if world > 1:
             dist.barrier()
@@ -436,6 +495,7 @@ def main():
     jl = None if args.no_jl or not solo else jl_leg(max(3, args.steps // 5))
     sstage = None if args.no_sketch_stage or not solo else sketch_stage_leg(max(3, args.steps // 5))
     nxt = None if args.no_next or not solo else next_legs(max(3, args.steps // 5))
+    small = None if args.no_configs or not solo else configs_leg(max(5, args.steps // 2))
     batched = None if args.no_batch or not solo else run_batched(args, lsk, torch, ctx, plain)
     served = None if args.no_serve or not solo else run_served(args, lsk, torch)
 
@@ -454,7 +514,8 @@ def main():
             "data": "synthetic", "config": workload_config(args, world),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
+            "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "configs": small,
+            "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
     if world > 1:
@@ -478,6 +539,7 @@ def run_batched(args, lsk, torch, ctx, plain):
     outs = lsk.batch_leverage_scores(probs, prec="bf16", autotune=True, ctx=ctx)
     ctx.sync()
     streams = lsk.batch_streams(probs, prec="bf16", ctx=ctx)
+    _, schedule = lsk.batch_schedule(probs, prec="bf16", ctx=ctx)
     lsk.batch_leverage_scores(probs, prec="bf16", graph=True, outs=outs, ctx=ctx)   # capture
     ctx.sync()
     reps = 3
@@ -492,7 +554,8 @@ def run_batched(args, lsk, torch, ctx, plain):
     ms = e0.elapsed_time(e1) / reps
     value = a_bytes / (ms * 1e-3) / 1e9
     out = {"workload": "batch_512_leverage", "problems": len(probs), "input_bytes": a_bytes,
-           "ms_per_batch": ms, "value": value, "unit": "GB/s", "streams": streams, "graph": True,
+           "ms_per_batch": ms, "value": value, "unit": "GB/s", "streams": streams, "schedule": schedule,
+           "graph": True,
            "vs_plain_fp32_single": (value / plain["value"]) if plain else None}
     del probs, outs
     torch.cuda.empty_cache()

@@ -344,9 +344,10 @@ typedef struct lsk_batch_item {
 #define LSK_BATCH_GRAPH        0x100   /* capture the batch into a CUDA graph  */
                                        /* (cached; replayed when the same      */
                                        /* items come again)                    */
-#define LSK_BATCH_AUTOTUNE     0x200   /* time stream counts on this batch and */
-                                       /* keep the fastest (per signature;     */
-                                       /* file LSK_AUTOTUNE_CACHE if set)      */
+#define LSK_BATCH_AUTOTUNE     0x200   /* tune the schedule on this batch      */
+                                       /* (see lsk_batch_schedule; kept per    */
+                                       /* signature, and in the file named by  */
+                                       /* LSK_AUTOTUNE_CACHE if set)           */
 #define LSK_BATCH_PER_PROBLEM  0x400   /* no grouped stages: every problem's   */
                                        /* whole pipeline on the worker streams */
 
@@ -367,6 +368,14 @@ int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_batch_item*
                               int32_t prec, int32_t flags);
 /* Stream count chosen for this batch signature (0 if none yet). */
 int lsk_batch_streams(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec);
+/* The schedule of this batch signature, out[4] = {worker streams, most waves
+ * of grouped problems, chunks of 32 sketch columns per block of the grouped
+ * Gaussian stage, least 128-row tiles per CTA of the dense row norms}.
+ * LSK_BATCH_AUTOTUNE picks it by coordinate descent over waves {2, 4, 8, 16},
+ * streams {2, 4, 8, 16}, slice {64, 128, 256} and tiles {8, 16, 32}, each
+ * candidate timed on the batch itself.  Returns 1 when a tuned schedule is
+ * known for the signature (0 and the defaults {8, 4, 128, 16} otherwise). */
+int lsk_batch_schedule(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec, int32_t* out);
 
 /* ---- sketch-and-precondition least squares (Alg. 12) ------------------- */
 typedef struct lsk_lsq_opts {

@@ -109,6 +109,7 @@ _SIGS = {
     "lsk_debug_wait_timeout": (ctypes.c_int, [_P, _I64]),
     "lsk_batch_leverage_scores": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32, _I32]),
     "lsk_batch_streams": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32]),
+    "lsk_batch_schedule": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_BatchItem), _I32, _P]),
     "lsk_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "lsk_profile_reset": (ctypes.c_int, [_P]),
     "lsk_profile_count": (ctypes.c_int, [_P]),
@@ -484,6 +485,19 @@ def batch_streams(problems, prec="bf16", ctx=None):
         items[i].r, items[i].k, items[i].seed = int(r), int(k), int(seed)
     ctx = ctx or context()
     return int(ctx._lib.lsk_batch_streams(ctx.h, len(problems), items, _prec(prec)))
+
+
+def batch_schedule(problems, prec="bf16", ctx=None):
+    """lsk_batch_schedule: (known, {"streams", "waves", "slice", "tiles"}) of
+    this batch signature."""
+    items = (_BatchItem * max(len(problems), 1))()
+    for i, (A, r, k, seed) in enumerate(problems):
+        items[i].A = _mat(A)[0]
+        items[i].r, items[i].k, items[i].seed = int(r), int(k), int(seed)
+    ctx = ctx or context()
+    out = (ctypes.c_int32 * 4)()
+    known = int(ctx._lib.lsk_batch_schedule(ctx.h, len(problems), items, _prec(prec), out))
+    return bool(known), {"streams": out[0], "waves": out[1], "slice": out[2], "tiles": out[3]}
 
 
 def lsq_default_opts(d):

@@ -32,6 +32,19 @@
 #include <string>
 #include <vector>
 
+// The schedule knobs of a batch (chosen by the autotuner per batch signature):
+//   S      worker streams;
+//   W      most waves the grouped problems are dealt into (phase 2 of a wave
+//          overlaps phases 1 / 3 of its neighbours; more waves shorten the
+//          head and the tail of that pipeline, fewer make larger grouped grids);
+//   slice  chunks of 32 columns of r per block of the grouped Gaussian stage
+//          (longer slices: fewer partials to add, fewer blocks);
+//   tiles  128-row tiles per CTA, at least, of the dense row norms (more: fewer
+//          CTAs per problem, so problems on other streams share the SMs).
+struct BatchTune {
+    int S = 8, W = 4, slice = 128, tiles = 16;
+};
+
 struct LskBatch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
@@ -43,7 +56,7 @@ struct LskBatch {
     std::vector<size_t> ws_bytes;
     cudaGraphExec_t exec = nullptr;
     uint64_t exec_key = 0;
-    std::map<uint64_t, int> tuned;   // batch signature -> stream count
+    std::map<uint64_t, struct BatchTune> tuned;   // batch signature -> schedule
     // grouped phases
     void* arena = nullptr;           // sketches, factors and scratch of the grouped problems
     size_t arena_bytes = 0;
@@ -145,7 +158,7 @@ int size_workspaces(lsk_ctx* ctx, const std::vector<std::vector<int>>& lanes, co
 // has finished its phase 1 of w.  So the compute-bound grouped stages of one
 // wave overlap the memory-bound passes over A of its neighbours.
 cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vector<int>>& lanes,
-                   const lsk_batch_item* items, int32_t prec) {
+                   const lsk_batch_item* items, int32_t prec, const BatchTune& tune) {
     LskBatch* b = ctx->batch;
     const int S = (int)lanes.size(), W = b->waves;
     auto ev_sketch = [&](int w, int s) { return b->ev[(size_t)w * (S + 1) + s]; };
@@ -180,7 +193,7 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
             if (!b->grouped[i] || b->wave[i] != w) continue;
             const lsk_batch_item& it = items[i];
             er = rownorms_launch(&it.A, b->Rinv32[i], it.A.d, 1.0, 0.0, 1, prec, it.ell, b->ws[s], ctx->flag,
-                                 ctx->sm_count, st);
+                                 ctx->sm_count, st, tune.tiles);
         }
         return er;
     };
@@ -212,8 +225,8 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
     return cudaSuccess;
 }
 
-constexpr int kMaxWaves = 4;           // grouped problems are split into up to 4 waves
-constexpr int kMinWaveProblems = 32;   // of at least 32 problems each
+constexpr int kMaxWaves = 16;          // grouped problems are split into up to 16 waves
+constexpr int kMinWaveProblems = 16;   // of at least 16 problems each
 
 bool groupable(const lsk_batch_item& it, int32_t prec) {
     return prec == LSK_PREC_BF16 && it.k > 0 && it.A.n > 0 && gauss_tc_supported(it.r, it.A.d, it.k) &&
@@ -223,7 +236,8 @@ bool groupable(const lsk_batch_item& it, int32_t prec) {
 // Arena layout of the grouped problems, their launch tables, and the upload
 // of the tables (only when they changed; the previous batch on the context
 // stream is finished first, since it may still read the old table).
-int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t prec, bool allow) {
+int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t prec, bool allow,
+                   const BatchTune& tune) {
     LskBatch* b = ctx->batch;
     b->grouped.assign(count, 0);
     b->SA.assign(count, nullptr);
@@ -233,7 +247,7 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         if (!allow || !groupable(items[i], prec)) continue;
         const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
         b->grouped[i] = 1;
-        bytes += ws_round((size_t)r * d * 4) + ws_round((size_t)k * d * 4) + gauss_group_part_bytes(r, d, k) +
+        bytes += ws_round((size_t)r * d * 4) + ws_round((size_t)k * d * 4) + gauss_group_part_bytes(r, d, k, tune.slice) +
                  ws_round(qr_workspace_bytes(k, d)) + ws_round((size_t)d * d * 4);
     }
     if (bytes > b->arena_bytes) {
@@ -254,7 +268,7 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         if (b->grouped[i]) order.push_back(i);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost_of(items[x]) > cost_of(items[y]); });
     const int ng = (int)order.size();
-    b->waves = ng == 0 ? 0 : std::max(1, std::min(kMaxWaves, ng / kMinWaveProblems));
+    b->waves = ng == 0 ? 0 : std::max(1, std::min(std::min(tune.W, kMaxWaves), ng / kMinWaveProblems));
     b->wave.assign(count, 0);
     for (int q = 0; q < ng; ++q) b->wave[order[q]] = q % std::max(b->waves, 1);
     std::vector<std::vector<GaussJob>> gj(b->waves);
@@ -265,12 +279,12 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
         float* SA = wc.take<float>((size_t)r * d);
         float* GSA = wc.take<float>((size_t)k * d);
-        float* part = (float*)wc.take<char>(gauss_group_part_bytes(r, d, k));
+        float* part = (float*)wc.take<char>(gauss_group_part_bytes(r, d, k, tune.slice));
         void* qws = wc.take<char>(qr_workspace_bytes(k, d));
         float* Ri32 = wc.take<float>((size_t)d * d);
         b->SA[i] = SA;
         b->Rinv32[i] = Ri32;
-        gj[b->wave[i]].push_back(GaussJob{SA, r, d, k, items[i].seed, GSA, part});
+        gj[b->wave[i]].push_back(GaussJob{SA, r, d, k, items[i].seed, GSA, part, tune.slice});
         QrJob q{};
         qr_group_job(q, GSA, k, d, qws, nullptr, Ri32, ctx->flag);
         qj[b->wave[i]].push_back(q);
@@ -316,8 +330,8 @@ uint64_t signature(const lsk_batch_item* items, int count, int32_t prec) {
     return h;
 }
 
-uint64_t exact_key(const LskBatch* b, const lsk_batch_item* items, int count, int32_t prec, int S) {
-    uint64_t h = fnv(signature(items, count, prec), &S, sizeof(S));
+uint64_t exact_key(const LskBatch* b, const lsk_batch_item* items, int count, int32_t prec, const BatchTune& t) {
+    uint64_t h = fnv(signature(items, count, prec), &t, sizeof(t));
     const int fused = fused_sketch_on();   // ungrouped problems' sketch path is recorded in the graph
     h = fnv(h, &fused, sizeof(fused));
     h = fnv(h, &b->arena, sizeof(b->arena));
@@ -326,25 +340,30 @@ uint64_t exact_key(const LskBatch* b, const lsk_batch_item* items, int count, in
     return fnv(h, items, sizeof(lsk_batch_item) * (size_t)count);
 }
 
-int cache_lookup(uint64_t sig) {
+// LSK_AUTOTUNE_CACHE: one line per tuned batch, "signature S W slice tiles"
+bool cache_lookup(uint64_t sig, BatchTune& out) {
     const char* path = getenv("LSK_AUTOTUNE_CACHE");
-    if (!path) return 0;
+    if (!path) return false;
     FILE* f = fopen(path, "r");
-    if (!f) return 0;
+    if (!f) return false;
     unsigned long long k;
-    int s, best = 0;
-    while (fscanf(f, "%llx %d", &k, &s) == 2)
-        if (k == sig) best = s;
+    BatchTune t;
+    bool found = false;
+    while (fscanf(f, "%llx %d %d %d %d", &k, &t.S, &t.W, &t.slice, &t.tiles) == 5)
+        if (k == sig && t.S > 0 && t.W > 0 && t.slice > 0 && t.tiles > 0) {
+            out = t;
+            found = true;
+        }
     fclose(f);
-    return best;
+    return found;
 }
 
-void cache_store(uint64_t sig, int S) {
+void cache_store(uint64_t sig, const BatchTune& t) {
     const char* path = getenv("LSK_AUTOTUNE_CACHE");
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%llx %d\n", (unsigned long long)sig, S);
+    fprintf(f, "%llx %d %d %d %d\n", (unsigned long long)sig, t.S, t.W, t.slice, t.tiles);
     fclose(f);
 }
 
@@ -391,34 +410,44 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
     if (!ctx->batch) ctx->batch = new LskBatch();
     LskBatch* b = ctx->batch;
     const uint64_t sig = signature(items, count, prec);
-    {
-        const int rc = prepare_groups(ctx, items, count, prec, !(flags & LSK_BATCH_PER_PROBLEM));
-        if (rc) return rc;
-    }
+    const bool allow_groups = !(flags & LSK_BATCH_PER_PROBLEM);
+    const int forced_S = flags & LSK_BATCH_STREAMS_MASK;
 
-    int S = (flags & LSK_BATCH_STREAMS_MASK) ? (flags & LSK_BATCH_STREAMS_MASK) : 0;
-    if (!S) {
+    // the schedule: remembered for this signature, else from the cache file,
+    // else tuned (LSK_BATCH_AUTOTUNE), else the defaults
+    BatchTune tune;
+    bool have = false;
+    {
         auto it = b->tuned.find(sig);
-        if (it != b->tuned.end()) S = it->second;
-        else if ((S = cache_lookup(sig)) > 0) b->tuned[sig] = S;
+        if (it != b->tuned.end()) {
+            tune = it->second;
+            have = true;
+        } else if (cache_lookup(sig, tune)) {
+            b->tuned[sig] = tune;
+            have = true;
+        }
     }
-    if (!S && (flags & LSK_BATCH_AUTOTUNE)) {
-        // time each candidate on the batch itself (outside any capture)
-        const int cand[] = {1, 4, 8, 16, 32};
-        float best_ms = 1e30f;
-        int best = 8;
+    // set up streams, arena, tables and workspaces for a schedule
+    auto setup = [&](const BatchTune& t, std::vector<std::vector<int>>& lanes) -> int {
+        int rc = prepare_groups(ctx, items, count, prec, allow_groups, t);
+        if (rc) return rc;
+        if ((rc = ensure_streams(ctx, t.S))) return rc;
+        lanes = plan(items, count, t.S);
+        return size_workspaces(ctx, lanes, items, prec);
+    };
+    if (!have && (flags & LSK_BATCH_AUTOTUNE)) {
+        // coordinate descent over the knobs, each candidate timed on the
+        // batch itself (outside any capture; the first of two passes warms up)
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int c : cand) {
-            if (c > count) continue;
-            int rc = ensure_streams(ctx, c);
+        auto time_of = [&](const BatchTune& t, float& ms) -> int {
+            std::vector<std::vector<int>> lanes;
+            int rc = setup(t, lanes);
             if (rc) return rc;
-            const auto lanes = plan(items, count, c);
-            if ((rc = size_workspaces(ctx, lanes, items, prec))) return rc;
-            for (int rep = 0; rep < 2; ++rep) {   // first pass warms up
+            for (int rep = 0; rep < 2; ++rep) {
                 cudaEventRecord(e0, ctx->stream);
-                cudaError_t e = record(ctx, ctx->stream, lanes, items, prec);
+                const cudaError_t e = record(ctx, ctx->stream, lanes, items, prec, t);
                 if (e != cudaSuccess) {
                     snprintf(ctx->err, sizeof(ctx->err), "batch: %s", cudaGetErrorString(e));
                     return LSK_ERR_CUDA;
@@ -426,35 +455,58 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
                 cudaEventRecord(e1, ctx->stream);
             }
             cudaEventSynchronize(e1);
-            float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
+            return LSK_OK;
+        };
+        BatchTune best;
+        if (forced_S) best.S = forced_S;
+        best.S = std::min(best.S, count);
+        float best_ms = 0.f;
+        int rc = time_of(best, best_ms);
+        if (rc) return rc;
+        const std::vector<int> Ws = {2, 4, 8, 16}, Ss = {2, 4, 8, 16}, slices = {64, 128, 256}, tiles = {8, 16, 32};
+        auto sweep = [&](const std::vector<int>& vals, int BatchTune::*knob) -> int {
+            for (int v : vals) {
+                if (best.*knob == v) continue;
+                BatchTune t = best;
+                t.*knob = v;
+                if (t.S > count) continue;
+                float ms = 0.f;
+                const int r = time_of(t, ms);
+                if (r) return r;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
             }
-        }
+            return LSK_OK;
+        };
+        if ((rc = sweep(Ws, &BatchTune::W))) return rc;
+        if (!forced_S && (rc = sweep(Ss, &BatchTune::S))) return rc;
+        if ((rc = sweep(slices, &BatchTune::slice))) return rc;
+        if ((rc = sweep(tiles, &BatchTune::tiles))) return rc;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        S = best;
-        b->tuned[sig] = S;
-        cache_store(sig, S);
+        tune = best;
+        b->tuned[sig] = tune;
+        cache_store(sig, tune);
     }
-    if (!S) S = count < 8 ? count : 8;
+    if (forced_S) tune.S = forced_S;
+    tune.S = std::max(1, std::min(tune.S, count));
 
-    int rc = ensure_streams(ctx, S);
+    std::vector<std::vector<int>> lanes;
+    int rc = setup(tune, lanes);
     if (rc) return rc;
-    const auto lanes = plan(items, count, S);
-    if ((rc = size_workspaces(ctx, lanes, items, prec))) return rc;
 
     if (!(flags & LSK_BATCH_GRAPH)) {
-        cudaError_t e = record(ctx, ctx->stream, lanes, items, prec);
+        cudaError_t e = record(ctx, ctx->stream, lanes, items, prec, tune);
         if (e != cudaSuccess) {
             snprintf(ctx->err, sizeof(ctx->err), "batch: %s", cudaGetErrorString(e));
             return LSK_ERR_CUDA;
         }
         return LSK_OK;
     }
-    const uint64_t key = exact_key(b, items, count, prec, S);
+    const uint64_t key = exact_key(b, items, count, prec, tune);
     if (!b->exec || b->exec_key != key) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
@@ -465,7 +517,7 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t er = record(ctx, b->cap, lanes, items, prec);
+            const cudaError_t er = record(ctx, b->cap, lanes, items, prec, tune);
             e = cudaStreamEndCapture(b->cap, &g);
             if (er != cudaSuccess) e = er;
         }
@@ -492,5 +544,25 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
 extern "C" int lsk_batch_streams(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec) {
     if (!ctx || !ctx->batch) return 0;
     auto it = ctx->batch->tuned.find(signature(items, count, prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : prec));
-    return it == ctx->batch->tuned.end() ? 0 : it->second;
+    return it == ctx->batch->tuned.end() ? 0 : it->second.S;
+}
+
+extern "C" int lsk_batch_schedule(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec,
+                                  int32_t* out) {
+    BatchTune t;
+    int known = 0;
+    if (ctx && ctx->batch && items) {
+        auto it = ctx->batch->tuned.find(signature(items, count, prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : prec));
+        if (it != ctx->batch->tuned.end()) {
+            t = it->second;
+            known = 1;
+        }
+    }
+    if (out) {
+        out[0] = t.S;
+        out[1] = t.W;
+        out[2] = t.slice;
+        out[3] = t.tiles;
+    }
+    return known;
 }

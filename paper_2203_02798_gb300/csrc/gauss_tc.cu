@@ -327,11 +327,13 @@ __global__ void gauss_tc_reduce_grouped_kernel(const GtParams* __restrict__ ps, 
 }
 
 // Grouped plan: the parallelism comes from the many problems, so a block
-// takes a longer slice (>= 128 chunks) and fewer partials are written.
-void plan_grouped(int64_t r, int64_t d, int64_t k, Plan& P) {
+// takes a longer slice (>= slice_chunks chunks, 128 by default; the batch
+// autotuner may pick another) and fewer partials are written.
+void plan_grouped(int64_t r, int64_t d, int64_t k, Plan& P, int slice_chunks) {
     P.npad = (int)((d + 31) / 32) * 32;
     P.tiles_m = (int)((k + kM - 1) / kM);
-    const int64_t want = (r + 128 * kKC - 1) / (128 * kKC);
+    if (slice_chunks < 1) slice_chunks = 128;
+    const int64_t want = (r + (int64_t)slice_chunks * kKC - 1) / ((int64_t)slice_chunks * kKC);
     int64_t ks = (r + want - 1) / want;
     ks = ((ks + kKC - 1) / kKC) * kKC;
     P.kslice = ks;
@@ -394,9 +396,9 @@ cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, f
     return cudaGetLastError();
 }
 
-size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k) {
+size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k, int slice_chunks) {
     Plan P;
-    plan_grouped(r, d, k, P);
+    plan_grouped(r, d, k, P, slice_chunks);
     return ws_round((size_t)P.slices * k * d * 4);
 }
 
@@ -407,7 +409,7 @@ void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGro
     for (size_t i = 0; i < jobs.size(); ++i) {
         const GaussJob& j = jobs[i];
         Plan P;
-        plan_grouped(j.r, j.d, j.k, P);
+        plan_grouped(j.r, j.d, j.k, P, j.slice_chunks);
         GtParams& p = ps[i];
         p.SA = j.SA;
         p.part = j.part;

@@ -190,7 +190,8 @@ struct GaussJob {
     int64_t r, d, k;
     uint64_t seed;
     float* GSA;
-    float* part;             // gauss_group_part_bytes(r, d, k) bytes
+    float* part;             // gauss_group_part_bytes(r, d, k, slice_chunks) bytes
+    int slice_chunks;        // chunks of 32 columns of r per block (0: the default, 128)
 };
 struct GaussGroup {
     size_t params_off, off_off, roff_off;
@@ -198,7 +199,7 @@ struct GaussGroup {
     size_t smem;
 };
 bool gauss_tc_supported(int64_t r, int64_t d, int64_t k);
-size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k);
+size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k, int slice_chunks = 0);
 void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGroup& g);
 cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, cudaStream_t st);
 
@@ -224,14 +225,17 @@ cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C
 
 // rownorms.cu
 size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec);
+// min_tiles: the dense tensor-core form launches CTAs for at least that many
+// 128-row tiles each (a small problem leaves SMs to concurrent work)
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha,
                             double beta, int upper_tri, int32_t prec, float* x, void* ws, int* flag,
-                            int sm_count, cudaStream_t st);
+                            int sm_count, cudaStream_t st, int min_tiles = 16);
 // rownorms_tc.cu
 bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri);
 size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri);
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta,
-                               int upper_tri, float* x, void* ws, int* flag, int sm_count, cudaStream_t st);
+                               int upper_tri, float* x, void* ws, int* flag, int sm_count, cudaStream_t st,
+                               int min_tiles = 16);
 
 // qr.cu
 size_t qr_workspace_bytes(int64_t k, int64_t d);

@@ -160,11 +160,12 @@ size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int3
 
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha, double beta,
                             int upper_tri, int32_t prec, float* x, void* ws, int* flag, int sm_count,
-                            cudaStream_t st) {
+                            cudaStream_t st, int min_tiles) {
     const int64_t n = A->n, d = A->d;
     if (n == 0) return cudaSuccess;
     if (A->kind == LSK_DENSE && prec == LSK_PREC_BF16 && rownorms_tc_supported(A, c, upper_tri))
-        return rownorms_tc_launch(A, B, c, (float)alpha, (float)beta, upper_tri, x, ws, flag, sm_count, st);
+        return rownorms_tc_launch(A, B, c, (float)alpha, (float)beta, upper_tri, x, ws, flag, sm_count, st,
+                                  min_tiles);
     if (A->kind == LSK_DENSE) {
         const unsigned grid = (unsigned)((n + RM - 1) / RM);
         LSK_PROF("rownorm_dense_simt", st) rownorm_dense_kernel<<<grid, 256, 0, st>>>((const float*)A->values, A->ld, n, d, B, c,

@@ -634,7 +634,7 @@ size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri) {
 }
 
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta, int upper_tri,
-                               float* x, void* ws, int* flag, int sm_count, cudaStream_t st) {
+                               float* x, void* ws, int* flag, int sm_count, cudaStream_t st, int min_tiles) {
     RnParams p{};
     if (!make_plan(A, c, upper_tri, p)) return cudaErrorNotSupported;
     p.A = (const float*)A->values;
@@ -661,9 +661,15 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     if (!p.pair && p.stages < 2) return cudaErrorNotSupported;
     LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
     cudaError_t e;
+    // CTAs (pairs) for at least min_tiles tiles each: a small problem then
+    // leaves SMs to the problems on other streams (its per-CTA set-up -- TMEM,
+    // the B image, the ring -- is paid over several tiles); a large one still
+    // takes one persistent CTA per SM
+    const int kMinTiles = min_tiles > 0 ? min_tiles : 1;
     if (p.pair) {
         const size_t smem2 = smem_bytes2(p);
-        const int grid2 = 2 * (p.ntiles2 < ncl ? p.ntiles2 : ncl);
+        const int want2 = (p.ntiles2 + kMinTiles - 1) / kMinTiles;
+        const int grid2 = 2 * (want2 < ncl ? want2 : ncl);
         if (vec) {
             LSK_PROF("rownorm_dense_tc", st) rownorm_tc2_kernel<true><<<grid2, kThreads, smem2, st>>>(p, img);
         } else {
@@ -672,7 +678,8 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
         return cudaGetLastError();
     }
     const size_t smem = smem_bytes(p);
-    const int grid = p.ntiles < sm_count ? p.ntiles : sm_count;
+    const int want = (p.ntiles + kMinTiles - 1) / kMinTiles;
+    const int grid = want < sm_count ? want : sm_count;
     if (vec) {
         e = allow_dynamic_smem(rownorm_tc_kernel<true>);
         if (e != cudaSuccess) return e;
