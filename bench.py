@@ -104,6 +104,29 @@ def oracle_sample(n_sample):
     return A.nbytes, dt
 
 
+ORACLE_THREADING = ("FP64 numpy oracle: the BLAS products (G S A, the QR, A R^-1) on every host core, "
+                    "the CountSketch scatter and the row sums single-threaded")
+
+
+def cpu_baseline_leg(n2):
+    """The oracle on two row samples of the workload (n2 / 4 and n2 rows): the
+    rate on the larger one (the same sample the reference arm times), and a
+    fit t(n) = fixed + per_row * n -- the fixed part is the Gaussian stage
+    (k r d FP64 flops) and the QR, the per-row part the scatter and the row
+    norms -- extrapolated to the full workload."""
+    n1 = max(1024, n2 // 4)
+    b1, t1 = oracle_sample(n1)
+    b2, t2 = oracle_sample(n2)
+    per_row = max((t2 - t1) / (n2 - n1), 0.0)
+    fixed = max(t2 - per_row * n2, 0.0)
+    full = fixed + per_row * N_ROWS
+    return {"value": b2 / t2 / 1e9, "unit": "GB/s", "cores": cores(), "kind": "oracle",
+            "sample": f"first {n2} rows of the workload (r={R_SKETCH}, k={K_GAUSS}), one run, {t2:.1f} s "
+                      f"(and {n1} rows, {t1:.1f} s, for the fit); {ORACLE_THREADING}",
+            "fit": {"fixed_s": fixed, "per_row_us": per_row * 1e6,
+                    "full_workload_s": full, "full_workload_GB/s": N_ROWS * D * 4 / full / 1e9}}
+
+
 def max_over_ranks(x):
     """The largest x over all ranks (x itself when torch.distributed is not
     initialised): the job takes as long as its slowest rank."""
@@ -144,7 +167,7 @@ def run_reference(args):
     tot = sum(times)
     value = nbytes * len(times) / tot / 1e9
     sample = (f"first {n_s} rows of the {N_ROWS} x {D} workload per step (r={R_SKETCH}, k={K_GAUSS}); "
-              f"FP64 numpy oracle, BLAS steps multithreaded, scatter single-threaded")
+              f"{ORACLE_THREADING}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
@@ -174,8 +197,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
-    ap.add_argument("--ref-rows", type=int, default=65_536)
-    ap.add_argument("--cpu-rows", type=int, default=262_144)
+    ap.add_argument("--ref-rows", type=int, default=262_144,
+                    help="rows of the workload the reference arm's oracle runs per step")
+    ap.add_argument("--cpu-rows", type=int, default=262_144,
+                    help="rows of the larger oracle sample of the cpu_baseline leg (the smaller is a quarter)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller for profiling)")
@@ -468,17 +493,28 @@ def main():
     # end to end through the public API with host buffers
     ell_host = torch.empty(N_ROWS, dtype=torch.float32, pin_memory=True)
 
+    # N = 1: lsk.leverage_scores_host (the copy of row block c + 1 overlaps the
+    # CountSketch of block c); N > 1: the copy, then the row-partitioned step
     def e2e_step():
-        A.copy_(A_host, non_blocking=True)
-        step(args.prec)
-        ell_host.copy_(ell, non_blocking=True)
+        if world == 1:
+            lsk.leverage_scores_host(A_host, R_SKETCH, K_GAUSS, SEED, args.prec, out_host=ell_host, A_dev=A,
+                                     ctx=ctx)
+        else:
+            A.copy_(A_host, non_blocking=True)
+            step(args.prec)
+            ell_host.copy_(ell, non_blocking=True)
 
     e2e_steps = max(3, min(args.steps, 20))
     e2e_step()
     ems, _, _ = timed(e2e_step, e2e_steps)
     ems /= e2e_steps
+    # the copy alone (the floor of any end-to-end step on this host link)
+    cms, _, _ = timed(lambda: A.copy_(A_host, non_blocking=True), e2e_steps)
+    cms /= e2e_steps
     e2e = {"value": whole_job_rate(a_bytes, world, ems), "unit": "GB/s", "ms_per_step": ems,
-           "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": N_ROWS * 4}
+           "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": N_ROWS * 4,
+           "copy_only_ms": cms, "copy_only_GB/s": a_bytes / (cms * 1e-3) / 1e9,
+           "overlapped": world == 1}
 
     # the plain FP32 single-problem path on the same GPU
     plain = None
@@ -501,10 +537,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nb, dt = oracle_sample(args.cpu_rows)
-        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": cores(), "kind": "oracle",
-               "sample": f"first {args.cpu_rows} rows of the workload (r={R_SKETCH}, k={K_GAUSS}), "
-                         f"one run, {dt:.1f} s; FP64 numpy, BLAS multithreaded"}
+        cpu = cpu_baseline_leg(args.cpu_rows)
 
     if rank == 0:
         print(json.dumps({

@@ -216,13 +216,17 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
  * small sketch), every holder forms R from the sum, and scores its own rows
  * with lsk_leverage_scores_from_sketch. */
 
-/* The partial sketch of a block of rows: out = S_g A (k == 0: r x d) or
- * G S_g A (k > 0: k x d), device floats row-major, overwritten.  Row i of A
- * is row row0 + i of the whole matrix (its CountSketch column).  Same r, k,
- * seed and prec as lsk_leverage_scores; the BF16 mode uses the fused kernel
- * as lsk_set_fused_sketch selects.  row0 >= 0, row0 + n < 2^63. */
+/* The partial sketch of a block of rows: S_g A (k == 0: r x d) or G S_g A
+ * (k > 0: k x d), device floats row-major, into out (accumulate == 0: out is
+ * overwritten) or added to it (accumulate != 0: out already holds the sketch
+ * of other blocks -- one device holding several blocks, e.g. while later
+ * blocks are still being copied in).  Row i of A is row row0 + i of the whole
+ * matrix (its CountSketch column).  Same r, k, seed and prec as
+ * lsk_leverage_scores; the BF16 mode uses the fused kernel as
+ * lsk_set_fused_sketch selects.  row0 >= 0, row0 + n < 2^63. */
 int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
-                    uint64_t seed, int32_t prec, int64_t row0, float* out);
+                    uint64_t seed, int32_t prec, int64_t row0, int32_t accumulate,
+                    float* out);
 
 /* R (as lsk_sketch_qr) of a given sketch (rows x d floats, device, e.g. the
  * sum of the partial sketches of all blocks), then ell_i = ||A_i R^-1||^2

@@ -91,7 +91,7 @@ _SIGS = {
     "lsk_sketch_qr": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P]),
     "lsk_leverage_scores": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _P, _P]),
     "lsk_leverage_scores_jl": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _I64, _U64, _I32, _P, _P]),
-    "lsk_sketch_rows": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _P]),
+    "lsk_sketch_rows": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _I64, _U64, _I32, _I64, _I32, _P]),
     "lsk_leverage_scores_from_sketch": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I32, _P, _P]),
     "lsk_sketch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _P, _I64, _I64, _U64, _I32, _P]),
     "lsk_csrjlt": (ctypes.c_int, [_P, ctypes.POINTER(_Mat), _I64, _U64, _I32, _P]),
@@ -334,17 +334,69 @@ def leverage_scores(A, r, k, seed, prec="fp32", out=None, return_R=False, ctx=No
     return (ell, R) if return_R else ell
 
 
-def sketch_rows(A, r, k, seed, prec="fp32", row0=0, out=None, ctx=None):
+def sketch_rows(A, r, k, seed, prec="fp32", row0=0, out=None, accumulate=False, ctx=None):
     """lsk_sketch_rows: the partial sketch of a block of rows whose first row
     is row row0 of the whole matrix -- S_g A (r x d) for k == 0, else
-    G S_g A (k x d), float32.  Summed over the blocks of a row partition it
-    is the sketch of the whole matrix."""
+    G S_g A (k x d), float32, written to out or (accumulate) added to it.
+    Summed over the blocks of a row partition it is the sketch of the whole
+    matrix."""
     m, n, d = _mat(A)
     ctx = ctx or context(_dev(A).index)
     rows = int(k) if k > 0 else int(r)
+    if accumulate and out is None:
+        raise ValueError("accumulate needs out")
     out = out if out is not None else torch.empty((rows, d), dtype=torch.float32, device=_dev(A))
-    ctx._call("lsk_sketch_rows", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), int(row0), _ptr(out))
+    ctx._call("lsk_sketch_rows", ctypes.byref(m), int(r), int(k), int(seed), _prec(prec), int(row0),
+              int(bool(accumulate)), _ptr(out))
     return out
+
+
+def leverage_scores_host(A_host, r, k, seed, prec="bf16", out_host=None, chunk_rows=1 << 19, A_dev=None,
+                         ctx=None):
+    """Leverage scores of a dense matrix in pinned host memory, end to end:
+    the host-to-device copy of row block c + 1 runs (on a side stream) while
+    the CountSketch of block c runs (lsk_sketch_rows, accumulating S A); then
+    the Gaussian stage, R and the row norms of the whole matrix on the device,
+    and the scores copied back to out_host (pinned, n floats).  Same result
+    as leverage_scores on the device copy with the two-stage sketch.  A_dev:
+    the device buffer to copy into (allocated if None).  Returns out_host."""
+    n, d = A_host.shape
+    if not A_host.is_pinned():
+        raise ValueError("A_host must be in pinned memory")
+    ctx = ctx or context()
+    dev = ctx.device   # the context's stream is the device's current stream (as in every call here)
+    A = A_dev if A_dev is not None else torch.empty((n, d), dtype=torch.float32, device=dev)
+    main = torch.cuda.current_stream(dev)
+    copy = _copy_stream(dev)
+    SA = torch.empty((r, d), dtype=torch.float32, device=dev)
+    blocks = [(c0, min(n, c0 + chunk_rows)) for c0 in range(0, n, chunk_rows)] or [(0, 0)]
+    copy.wait_stream(main)
+    events = []
+    with torch.cuda.stream(copy):
+        for c0, c1 in blocks:
+            A[c0:c1].copy_(A_host[c0:c1], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(copy)
+            events.append(ev)
+    for (c0, c1), ev in zip(blocks, events):
+        main.wait_event(ev)
+        sketch_rows(A[c0:c1], r, 0, seed, prec, row0=c0, out=SA, accumulate=c0 > 0, ctx=ctx)
+    sk = SA if k == 0 else gauss_sketch(SA, k, seed, prec, ctx=ctx)
+    ell = leverage_scores_from_sketch(A, sk, prec, ctx=ctx)
+    if out_host is None:
+        out_host = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    out_host.copy_(ell, non_blocking=True)
+    A.record_stream(copy)
+    return out_host
+
+
+_COPY_STREAMS = {}
+
+
+def _copy_stream(dev):
+    if dev.index not in _COPY_STREAMS:
+        _COPY_STREAMS[dev.index] = torch.cuda.Stream(device=dev)
+    return _COPY_STREAMS[dev.index]
 
 
 def leverage_scores_from_sketch(A, sketch, prec="fp32", out=None, return_R=False, ctx=None):

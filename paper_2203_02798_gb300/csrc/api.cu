@@ -411,7 +411,7 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, ui
 }
 
 int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64_t seed, int32_t prec, int64_t row0,
-                    float* out) {
+                    int32_t accumulate, float* out) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     ProfGuard pg(ctx);
     int rc = check_mat(ctx, A);
@@ -424,14 +424,23 @@ int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64
     if (!out) return fail(ctx, LSK_ERR_INVALID_ARG, "out is NULL");
     if (A->kind == LSK_CSR && A->d > 51200) return fail(ctx, LSK_ERR_UNSUPPORTED, "CSR sketch needs d <= 51200");
     if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    cudaError_t e;
+    if (k == 0) {   // S A straight into out (the gather adds into it when accumulating)
+        rc = ws_ensure(ctx, cs_workspace_bytes(A->n, r));
+        if (rc) return rc;
+        e = cs_launch(A, r, seed, out, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream, (uint64_t)row0, accumulate != 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_rows");
+        return finish(ctx, "lsk_sketch_rows");
+    }
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, 0));
     if (rc) return rc;
     const SketchBufs b = carve(ctx->ws, A, r, k);
     const float* sk = nullptr;
     int64_t rows = 0;
-    cudaError_t e = sketch_on(A, r, k, seed, prec, b, ctx->flag, ctx->sm_count, ctx->stream, (uint64_t)row0, &sk, &rows);
+    e = sketch_on(A, r, k, seed, prec, b, ctx->flag, ctx->sm_count, ctx->stream, (uint64_t)row0, &sk, &rows);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out, sk, (size_t)rows * A->d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
+        e = accumulate ? add_into_launch(out, sk, rows * A->d, ctx->stream)
+                       : cudaMemcpyAsync(out, sk, (size_t)rows * A->d * 4, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_sketch_rows");
     return finish(ctx, "lsk_sketch_rows");
 }

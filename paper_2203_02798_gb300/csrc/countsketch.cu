@@ -234,7 +234,8 @@ __device__ __forceinline__ typename VecT<VEC>::T ldg_stream(const float* p) {
 template <int VEC, int U>
 __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
     const float* __restrict__ A, int64_t lda, int64_t d, uint32_t r,
-    const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA, int P) {
+    const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA, int P,
+    int accumulate) {
     using V = typename VecT<VEC>::T;
     constexpr int kCols = 32 * VEC * U;  // columns per pass
     constexpr int kBatch = (VEC * U >= 8) ? 8 : 4;   // rows of loads in flight per warp
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
         const uint32_t s0 = off[b], len = off[b + 1] - s0;
         const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
         const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
-        if (P > 1 && s == e) continue;
+        if ((P > 1 || accumulate) && s == e) continue;
         for (int64_t c0 = 0; c0 < d; c0 += kCols) {
             V acc[U];
 #pragma unroll
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
                 }
             }
             float* out = SA + (int64_t)b * d + c0;
-            if (P == 1) {
+            if (P == 1 && !accumulate) {
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     if (colok[u]) *reinterpret_cast<V*>(out + (u * 32 + lane) * VEC) = acc[u];
@@ -312,7 +313,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
                                      const int64_t* __restrict__ I, int64_t nnz, int64_t d,
                                      uint32_t r, const uint32_t* __restrict__ off,
                                      const uint32_t* __restrict__ perm, float* __restrict__ SA,
-                                     int* flag, int P) {
+                                     int* flag, int P, int accumulate) {
     extern __shared__ float srow[];
     const int lane = threadIdx.x & 31;
     float* acc = srow + (int64_t)(threadIdx.x >> 5) * d;
@@ -325,7 +326,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
         const uint32_t s0 = off[b], len = off[b + 1] - s0;
         const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
         const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
-        if (P > 1 && s == e) continue;
+        if ((P > 1 || accumulate) && s == e) continue;
         for (int64_t c = lane; c < d; c += 32) acc[c] = 0.0f;
         __syncwarp();
         bool bad = false;
@@ -350,7 +351,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
         if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
         __syncwarp();
         float* out = SA + (int64_t)b * d;
-        if (P == 1) {
+        if (P == 1 && !accumulate) {
             for (int64_t c = lane; c < d; c += 32) out[c] = acc[c];
         } else {
             for (int64_t c = lane; c < d; c += 32)
@@ -427,7 +428,7 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
 }
 
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
-                      int sm_count, cudaStream_t st, uint64_t row0) {
+                      int sm_count, cudaStream_t st, uint64_t row0, bool accumulate) {
     const int64_t n = A->n, d = A->d;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
@@ -438,7 +439,8 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
     // while each part keeps several rows
     int P = 1;
     while (P < 32 && r * P < 16384 && n >= (int64_t)r * P * 8) P *= 2;
-    if (P > 1 && (e = cudaMemsetAsync(SA, 0, (size_t)r * d * 4, st)) != cudaSuccess) return e;
+    if (P > 1 && !accumulate && (e = cudaMemsetAsync(SA, 0, (size_t)r * d * 4, st)) != cudaSuccess) return e;
+    const int acc = accumulate ? 1 : 0;   // add into SA (the parts add atomically either way)
     const int64_t warps_needed = r * P;
     if (A->kind == LSK_DENSE) {
         const float* Av = (const float*)A->values;
@@ -447,14 +449,14 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         const unsigned grid = grid_for(warps_needed * 32, 256, sm_count, 8);
         if (vec4) {
             if (d <= 128)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
         } else {
             if (d <= 32)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
         }
     } else {
         // shared-memory row per warp: pick warps per block to fit 200 KB
@@ -472,7 +474,7 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         if (g > cap) g = cap;
         if (g < 1) g = 1;
         LSK_PROF("cs_csr_gather", st) cs_csr_gather_kernel<<<(unsigned)g, threads, smem, st>>>(
-            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P);
+            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P, acc);
     }
     return cudaGetLastError();
 }

@@ -188,3 +188,17 @@ cudaError_t gauss_debug_launch(int64_t k, int64_t r, uint64_t seed, int32_t prec
                                                    scale, prec == LSK_PREC_BF16 ? 1 : 0, G);
     return cudaGetLastError();
 }
+
+// dst[i] += src[i] (the sum of the partial sketches of row blocks)
+namespace {
+__global__ void add_into_kernel(float* __restrict__ dst, const float* __restrict__ src, int64_t len) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+}  // namespace
+cudaError_t add_into_launch(float* dst, const float* src, int64_t len, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    const int64_t g = (len + 255) / 256 < 1024 ? (len + 255) / 256 : 1024;
+    LSK_PROF("sketch_add", st) add_into_kernel<<<(unsigned)g, 256, 0, st>>>(dst, src, len);
+    return cudaGetLastError();
+}

@@ -178,9 +178,10 @@ __device__ __forceinline__ void set_flag(int* flag, int bit) {
 // ---------------------------------------------------------------------------
 // countsketch.cu
 size_t cs_workspace_bytes(int64_t n, int64_t r);
-// row0: global index of A's first row (A is a block of rows of a larger matrix)
+// row0: global index of A's first row (A is a block of rows of a larger matrix);
+// accumulate: SA += S A (SA holds a previous block's sketch) instead of SA = S A
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws,
-                      int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0);
+                      int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0, bool accumulate = false);
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
 
@@ -207,6 +208,7 @@ cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, 
 size_t gauss_workspace_bytes(int64_t r, int64_t d, int64_t k, int32_t prec, int sm_count);
 cudaError_t gauss_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
                          int32_t prec, float* GSA, void* ws, int sm_count, cudaStream_t st);
+cudaError_t add_into_launch(float* dst, const float* src, int64_t len, cudaStream_t st);
 cudaError_t gauss_debug_launch(int64_t k, int64_t r, uint64_t seed, int32_t prec, float* G,
                                cudaStream_t st);
 

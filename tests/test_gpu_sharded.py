@@ -128,3 +128,42 @@ def test_sketch_rows_rejects_bad_arguments(lsk):
         lsk.sketch_rows(A, 0, 0, 1, "fp32")
     with pytest.raises(lsk.LskError):
         lsk.leverage_scores_from_sketch(A, torch.zeros((4, 8), dtype=torch.float32, device="cuda"))
+
+
+def test_accumulated_blocks_equal_the_whole_sketch(lsk):
+    """lsk_sketch_rows with accumulate: one buffer summing the blocks' sketches
+    (integer data: exact), for k = 0 (added by the gather itself) and k > 0."""
+    n, d, r, k, seed = 40_000, 48, 2000, 96, 13
+    A = workloads.integer_dense(n, d, seed=8)
+    Ad = dev(A)
+    whole = lsk.cs_sketch(Ad, r, seed)
+    acc = torch.full_like(whole, float("nan"))
+    for i, (c0, c1) in enumerate([(0, 7_000), (7_000, 7_001), (7_001, 40_000)]):
+        lsk.sketch_rows(Ad[c0:c1], r, 0, seed, "fp32", row0=c0, out=acc, accumulate=i > 0)
+    lsk.context().sync()
+    assert torch.equal(acc, whole)
+    g_whole = lsk.sketch_rows(Ad, r, k, seed, "fp32")
+    g_acc = torch.zeros_like(g_whole)
+    for c0, c1 in [(0, 25_000), (25_000, 40_000)]:
+        lsk.sketch_rows(Ad[c0:c1], r, k, seed, "fp32", row0=c0, out=g_acc, accumulate=True)
+    lsk.context().sync()
+    assert rel_fro(g_acc.cpu().numpy().astype(np.float64), g_whole.cpu().numpy().astype(np.float64)) <= 1e-6
+
+
+@pytest.mark.parametrize("n,chunk", [(300_001, 65_536), (50_000, 1 << 19)])
+def test_leverage_scores_from_host_memory(lsk, n, chunk):
+    """The end-to-end call (copy of block c + 1 overlapping the sketch of block
+    c) gives the scores of the device call with the two-stage sketch, to FP32
+    summation order."""
+    d, r, k, seed = 64, 4096, 128, 3
+    A = workloads.dense_normal(n, d, seed=12)
+    A[:2] *= 30.0
+    A_host = torch.from_numpy(A).pin_memory()
+    got = lsk.leverage_scores_host(A_host, r, k, seed, "bf16", chunk_rows=chunk)
+    torch.cuda.synchronize()
+    prev = lsk.set_fused_sketch(0)
+    try:
+        ref = lsk.leverage_scores(dev(A), r, k, seed, "bf16").cpu()
+    finally:
+        lsk.set_fused_sketch(prev)
+    assert torch.allclose(got, ref, rtol=2e-5, atol=0)
