@@ -153,16 +153,21 @@ int lsk_set_fused_sketch(int mode);
 
 /* Gram matrix C <- alpha * A^T A + beta * C (csrrk, Sec. 5; Alg. 5 and
  * Alg. 7 for CSR A; the same operation for dense A).  C: device d*d floats
- * row-major, read when beta != 0 and overwritten.  Products are FP32,
- * partial sums are folded into FP64 before the final FP32 store. */
+ * row-major, read when beta != 0 and overwritten.  Dense A with d <= 256
+ * (d, ld multiples of 4, 16-byte aligned values) runs on the tensor cores as
+ * lsk_gram_prec(LSK_PREC_BF16) (about 1e-5 relative Frobenius error: 7e-6 at
+ * 4M x 256 with column scales 1e-3 .. 1e3); CSR A and other dense A run in
+ * FP32 on the CUDA cores, partial sums folded into FP64 before the final
+ * FP32 store (lsk_gram_prec(LSK_PREC_FP32) always takes this path). */
 int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
              float* C);
-/* lsk_gram with a precision: LSK_PREC_FP32 / LSK_PREC_TF32 as lsk_gram;
- * LSK_PREC_BF16 forms the products of dense A with d <= 256 on the tensor
+/* lsk_gram with a precision: LSK_PREC_FP32 / LSK_PREC_TF32 on the CUDA cores
+ * in FP32 (as lsk_gram for CSR A); LSK_PREC_BF16 forms the products of dense
+ * A with d <= 256 on the tensor
  * cores from a bfloat16 split of A (a = hi + lo; hi^T hi + hi^T lo + lo^T hi,
  * about 2^-16 relative per product), accumulating at most 1024 rows in FP32
  * before the slices are added (compensated FP32, alpha and beta in FP64).
- * CSR A or d > 256 take the lsk_gram path.  Workspace: ceil(n / 1024) d*d
+ * CSR A or d > 256 take the FP32 path.  Workspace: ceil(n / 1024) d*d
  * floats for the BF16 path. */
 int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
                   int32_t prec, float* C);

@@ -284,14 +284,16 @@ def set_fused_sketch(mode):
 
 
 def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):
-    """lsk_gram / lsk_gram_prec: alpha A^T A + beta C (d x d float32, C updated
-    in place if given); prec="bf16": tensor-core products of a bf16 split."""
+    """alpha A^T A + beta C (d x d float32, C updated in place if given).
+    prec: "fp32" (lsk_gram_prec FP32: CUDA-core FP32), "bf16" (lsk_gram_prec
+    BF16: tensor-core products of a bf16 split), None (lsk_gram: the tensor
+    cores for dense d <= 256, else FP32)."""
     m, n, d = _mat(A)
     ctx = ctx or context(_dev(A).index)
     if C is None:
         C = torch.empty((d, d), dtype=torch.float32, device=_dev(A))
         beta = 0.0
-    if prec == "fp32":
+    if prec is None:
         ctx._call("lsk_gram", ctypes.byref(m), float(alpha), float(beta), _ptr(C))
     else:
         ctx._call("lsk_gram_prec", ctypes.byref(m), float(alpha), float(beta), _prec(prec), _ptr(C))

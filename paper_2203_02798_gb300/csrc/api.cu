@@ -206,8 +206,10 @@ int lsk_count_gauss(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64
 
 int lsk_set_fused_sketch(int mode) { return g_fused_sketch.exchange(mode < 0 ? 0 : mode > 2 ? 2 : mode); }
 
-int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
-    if (!ctx) return LSK_ERR_INVALID_ARG;
+}  // extern "C"
+namespace {
+// A^T A on the CUDA cores in FP32 (partials folded in FP64); CSR: Alg. 7
+int gram_fp32(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
     ProfGuard pg(ctx);
     int rc = check_mat(ctx, A);
     if (rc) return rc;
@@ -218,17 +220,27 @@ int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_gram");
     return finish(ctx, "lsk_gram");
 }
+}  // namespace
+extern "C" {
+
+int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, float* C) {
+    if (!ctx) return LSK_ERR_INVALID_ARG;
+    // dense, d <= 256: the tensor cores (BF16x3, ~1e-5 relative); else FP32
+    if (A && A->kind == LSK_DENSE && A->dtype == LSK_F32 && gram_tc_supported(A))
+        return lsk_gram_prec(ctx, A, alpha, beta, LSK_PREC_BF16, C);
+    return gram_fp32(ctx, A, alpha, beta, C);
+}
 
 int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, int32_t prec, float* C) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
-    if (prec != LSK_PREC_BF16) return lsk_gram(ctx, A, alpha, beta, C);
+    if (prec != LSK_PREC_BF16) return gram_fp32(ctx, A, alpha, beta, C);
     ProfGuard pg(ctx);
     int rc = check_mat(ctx, A);
     if (rc) return rc;
     if (!C) return fail(ctx, LSK_ERR_INVALID_ARG, "C is NULL");
-    if (!gram_tc_supported(A)) return lsk_gram(ctx, A, alpha, beta, C);   // CSR or d > 256: the FP32 path
+    if (!gram_tc_supported(A)) return gram_fp32(ctx, A, alpha, beta, C);   // CSR or d > 256: the FP32 path
     rc = ws_ensure(ctx, gram_tc_workspace_bytes(A, ctx->sm_count));
     if (rc) return rc;
     cudaError_t e = gram_tc_launch(A, alpha, beta, C, ctx->ws, ctx->flag, ctx->sm_count, ctx->stream);

@@ -478,3 +478,25 @@ def test_sketch_precondition_lsq_large_residual(lsk, kind):
     x_ls = olsq.least_squares_qr(A64, b)
     x = host(x)
     assert np.linalg.norm(x - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
+
+
+@pytest.mark.parametrize("n,d", [(50_000, 256), (7_000, 36)])
+def test_gram_default_runs_on_the_tensor_cores(lsk, n, d):
+    """lsk_gram on dense A with d <= 256 takes the BF16x3 tensor-core kernel
+    (within the 1e-5 relative bound); CSR A keeps the FP32 path."""
+    A = workloads.dense_normal(n, d, seed=d + 1) * (10.0 ** np.linspace(-2, 2, d)).astype(np.float32)
+    ctx = lsk.context()
+    ctx.sync()
+    ctx.profile(True)
+    ctx.profile_reset()
+    try:
+        C = host(lsk.gram(dev(A), prec=None)).astype(np.float64)
+        ctx.sync()
+        names = set(ctx.profile_totals())
+    finally:
+        ctx.profile(False)
+    assert "gram_tc" in names and "gram_dense" not in names
+    assert rel_fro(C, ogr.gram_dense(A.astype(np.float64))) <= 1e-5
+    V, J, I = workloads.csr_bernoulli(20_000, 40, 0.05, seed=2)
+    Cc = host(lsk.gram(csr_dev(lsk, V, J, I, 40), prec=None)).astype(np.float64)
+    assert rel_fro(Cc, ogr.gram_csr(V, J, I, 40)) <= 1e-6
