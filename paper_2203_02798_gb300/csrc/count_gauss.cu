@@ -56,7 +56,7 @@ constexpr size_t kSmemLimit = 232448;
 static_assert(2 * kMaxSets * kWorkerThreads == kMaxSets * 32 * 16, "two G items per thread and set");
 
 // gather warps and rows in flight per gather warp
-template <int NG, int kRing>
+template <int NG, int kRing, bool kUnroll = true>
 struct Shape {
     static constexpr int kMmaWarp = kGath0 + NG;
     static constexpr int kThreads = (kMmaWarp + 1) * 32;
@@ -123,7 +123,7 @@ __device__ __forceinline__ void store_split4(uint32_t bh, uint32_t bbytes, int n
     st_cluster_u16(bh + bbytes + o3, l23 >> 16);
 }
 
-template <int NG, int kRing>
+template <int NG, int kRing, bool kUnroll>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Shape<NG, kRing>::kThreads, 1)
     count_gauss_kernel(const CgParams p) {
     constexpr int kMmaWarp = Shape<NG, kRing>::kMmaWarp;
@@ -334,14 +334,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Shape<NG, kRing>::kT
             ++gc;
             return true;
         };
-        int meta[kRing];   // per slot: chunk << 1 | sign of the row copied there, -1 if none
+        // per slot: chunk << 1 | sign of the row copied there, -1 if none (in
+        // registers when the steps of a round are unrolled, else in the
+        // thread's local memory: a smaller loop body for the instruction cache)
+        int meta[kRing];
 #pragma unroll
         for (int i = 0; i < kRing; ++i) meta[i] = -1;
         // rounds of kRing steps; the round that starts with nothing left to copy
         // sums every row still in the ring and is the last
         for (bool last = false; ok && !last;) {
             last = gp >= nchunks;
-#pragma unroll
+#pragma unroll(kUnroll ? kRing : 1)
             for (int i = 0; i < kRing; ++i) {
                 // (1) sum the row copied kRing - 1 steps ago (slot i + 1)
                 const int sl = (i + 1) % kRing;
@@ -440,13 +443,14 @@ struct Variant {
     int threads;
     int ring;          // row slots per gather warp
 };
-template <int NG, int R>
+template <int NG, int R, bool U>
 constexpr Variant variant() {
-    return Variant{count_gauss_kernel<NG, R>, Shape<NG, R>::kThreads, R};
+    return Variant{count_gauss_kernel<NG, R, U>, Shape<NG, R>::kThreads, R};
 }
 // 6 slots (5 rows in flight per warp, 80 KB per SM) measured fastest at
-// 4M x 256 (0.70 ms against 0.72 ms for 4 slots and 0.80 ms for 8)
-const Variant kVariants[] = {variant<16, 6>(), variant<16, 4>()};
+// 4M x 256 (0.70 ms against 0.72 ms for 4 slots and 0.80 ms for 8; the
+// 6-slot steps not unrolled, with the slot metadata in local memory: 0.73)
+const Variant kVariants[] = {variant<16, 6, true>(), variant<16, 4, true>()};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 // LSK_CG_VARIANT=1 selects the 4-slot kernel (a complete kernel; for timing

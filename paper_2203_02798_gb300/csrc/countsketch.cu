@@ -29,14 +29,24 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanBlock * kScanItems;
 
 // Row i of A is column row0 + i of S: a block of rows of a larger matrix
-// (one shard of a row partition) is hashed by its global row index.
+// (one shard of a row partition) is hashed by its global row index.  Each
+// thread takes kPrepRows rows per pass with their atomics independent, so
+// several round trips to L2 are in flight per thread.
+constexpr int kPrepRows = 4;
+
 __global__ void cs_count_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k0, uint32_t k1,
                                 uint32_t* __restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint32_t b, neg;
-        cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
-        atomicAdd(&cnt[b], 1u);   // result unused: compiled to a reduction (no round trip)
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kPrepRows) {
+#pragma unroll
+        for (int q = 0; q < kPrepRows; ++q) {
+            const int64_t i = i0 + q * stride;
+            if (i < n) {
+                uint32_t b, neg;
+                cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
+                atomicAdd(&cnt[b], 1u);   // result unused: compiled to a reduction (no round trip)
+            }
+        }
     }
 }
 
@@ -47,10 +57,21 @@ __global__ void cs_count_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k
 __global__ void cs_place_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k0, uint32_t k1,
                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint32_t b, neg;
-        cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
-        perm[atomicAdd(&cursor[b], 1u)] = (uint32_t)i | (neg << 31);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kPrepRows) {
+        uint32_t slot[kPrepRows], val[kPrepRows];
+#pragma unroll
+        for (int q = 0; q < kPrepRows; ++q) {
+            const int64_t i = i0 + q * stride;
+            if (i < n) {
+                uint32_t b, neg;
+                cs_hash(row0 + (uint64_t)i, r, k0, k1, b, neg);
+                slot[q] = atomicAdd(&cursor[b], 1u);
+                val[q] = (uint32_t)i | (neg << 31);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPrepRows; ++q)
+            if (i0 + q * stride < n) perm[slot[q]] = val[q];
     }
 }
 
