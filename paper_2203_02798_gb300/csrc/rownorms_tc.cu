@@ -33,6 +33,7 @@
 // the epilogue of one tile overlaps the MMAs of the next.
 #include "tc_common.cuh"
 
+#include <cuda.h>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -113,17 +114,18 @@ __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnPara
 // Lane l loads float4 number f = l + 32 i of the piece (row f / 8 of the
 // piece, columns 4 (f % 8) .. +3): consecutive lanes read consecutive
 // 16-byte pieces, four 128-byte row segments per warp instruction.
-template <bool VEC>
+template <bool VEC, int PR = kPieceRows>
 __device__ __forceinline__ void load_piece(const RnParams& p, int64_t rowbase, int q, int half, int lane,
-                                           float4 (&v)[kF4]) {
-    const int64_t row0 = rowbase + half * kPieceRows + (lane >> 3);
+                                           float4 (&v)[PR / 4]) {
+    constexpr int F4 = PR / 4;
+    const int64_t row0 = rowbase + half * PR + (lane >> 3);
     const int k0 = kKC * q + 4 * (lane & 7);
-    if (VEC && row0 - (lane >> 3) + kPieceRows <= p.n && kKC * q + kKC <= p.d) {
+    if (VEC && row0 - (lane >> 3) + PR <= p.n && kKC * q + kKC <= p.d) {
         // interior piece: no bounds checks, rows 4 apart per step
         const float* src = p.A + row0 * p.lda + k0;
         const int64_t step = 4 * p.lda;
 #pragma unroll
-        for (int i = 0; i < kF4; ++i) {
+        for (int i = 0; i < F4; ++i) {
             asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
                          : "=f"(v[i].x), "=f"(v[i].y), "=f"(v[i].z), "=f"(v[i].w)
                          : "l"(src));
@@ -132,9 +134,9 @@ __device__ __forceinline__ void load_piece(const RnParams& p, int64_t rowbase, i
         return;
     }
 #pragma unroll
-    for (int i = 0; i < kF4; ++i) {
+    for (int i = 0; i < F4; ++i) {
         const int f = lane + 32 * i;
-        const int m = half * kPieceRows + (f >> 3), c4 = f & 7;
+        const int m = half * PR + (f >> 3), c4 = f & 7;
         const int64_t row = rowbase + m;
         const int k = kKC * q + 4 * c4;
         v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -155,22 +157,23 @@ __device__ __forceinline__ void load_piece(const RnParams& p, int64_t rowbase, i
     }
 }
 
-// Element (m, 4 c4) of the piece, m = 64 half + 4 i + l8 (l8 = lane / 8,
+// Element (m, 4 c4) of the piece, m = PR half + 4 i + l8 (l8 = lane / 8,
 // c4 = lane % 8), sits at tc::sw64_offset(m, 4 c4).  Because l8 < 4, the row
-// atom (m / 8 = 8 half + i / 2), the row in the atom (4 (i % 2) + l8) and the
-// swizzle phase ((m / 2) % 4 = 2 (i % 2) + l8 / 2) split into a per-lane part
-// that depends only on the parity of i and a constant 512 (i / 2): two base
-// offsets per lane, and every store takes an immediate offset.
-__device__ __forceinline__ void store_piece(uint8_t* stage, int half, int lane, const float4 (&v)[kF4]) {
+// atom (m / 8 = (PR / 8) half + i / 2), the row in the atom (4 (i % 2) + l8)
+// and the swizzle phase ((m / 2) % 4 = 2 (i % 2) + l8 / 2) split into a
+// per-lane part that depends only on the parity of i and a constant 512 (i /
+// 2): two base offsets per lane, and every store takes an immediate offset.
+template <int PR = kPieceRows>
+__device__ __forceinline__ void store_piece(uint8_t* stage, int half, int lane, const float4 (&v)[PR / 4]) {
     const uint32_t l8 = (uint32_t)lane >> 3, c4 = (uint32_t)lane & 7u;
     const uint32_t lane_part = l8 * 64u + (c4 & 1u) * 8u;
-    const uint32_t b_even = (uint32_t)half * (kPieceRows * 64u) + lane_part + ((((c4 >> 1) ^ (l8 >> 1)) & 3u) << 4);
-    const uint32_t b_odd = (uint32_t)half * (kPieceRows * 64u) + 256u + lane_part +
+    const uint32_t b_even = (uint32_t)half * (PR * 64u) + lane_part + ((((c4 >> 1) ^ (l8 >> 1)) & 3u) << 4);
+    const uint32_t b_odd = (uint32_t)half * (PR * 64u) + 256u + lane_part +
                            ((((c4 >> 1) ^ (2u + (l8 >> 1))) & 3u) << 4);
     uint8_t* const s_even = stage + b_even;
     uint8_t* const s_odd = stage + b_odd;
 #pragma unroll
-    for (int i = 0; i < kF4; ++i) {
+    for (int i = 0; i < PR / 4; ++i) {
         uint2 hi, lo;
         tc::split_bf16x2(v[i].x, v[i].y, hi.x, lo.x);
         tc::split_bf16x2(v[i].z, v[i].w, hi.y, lo.y);
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) rownorm_tc_kernel(const RnParams 
 // the converters of both CTAs arrive on its stage barriers and its commits
 // are multicast to both CTAs' barriers; each CTA's epilogue reads its own
 // TMEM rows and reports to the even CTA.
-template <bool VEC>
+template <bool VEC, int PR>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     rownorm_tc2_kernel(const RnParams p, const uint8_t* __restrict__ img) {
     extern __shared__ uint8_t smem_raw[];
@@ -375,7 +378,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint8_t* sA = smem;                                  // S stages of (hi, lo), this CTA's 128 rows
     uint8_t* sB = smem + S * kStageBytes;                // this CTA's half of B: hi image, then lo image
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * p.hb_bytes + 1024);
-    uint64_t* full = bars;                       // [S] even CTA: stage filled in both CTAs (2 kPieces arrivals)
+    constexpr int NP = kRows / PR;               // pieces per chunk
+    uint64_t* full = bars;                       // [S] even CTA: stage filled in both CTAs (2 NP arrivals)
     uint64_t* empty = bars + kMaxStages2;        // [S] stage consumed (multicast commit)
     uint64_t* tfull = bars + 2 * kMaxStages2;    // [2] accumulator done (multicast commit)
     uint64_t* tempty = tfull + 2;                // [2] even CTA: accumulator read in both (2 kEpiWarps arrivals)
@@ -387,7 +391,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            tc::mbar_init(full + s, 2 * kPieces);
+            tc::mbar_init(full + s, 2 * NP);
             tc::mbar_init(empty + s, 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -499,33 +503,302 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ converters
+        // piece number pc = NP * g + part goes to converter warp pc % kConvWarps;
+        // the uses of each stage are claimed in piece order (stored[s])
         const int cw = warp - kConvWarp0;
         const int G = my_tiles * p.nq;
-        float4 buf[kF4];
-        int pc = cw, g = pc / kPieces, t = g / p.nq, q = g % p.nq, s = g % S, u = g / S;
-        for (; g < G;) {
-            const int half = pc % kPieces;
-            const int64_t rowbase = ((int64_t)cid + (int64_t)t * ncl) * (2 * kRows) + rank * kRows;
-            load_piece<VEC>(p, rowbase, q, half, lane, buf);
+        struct Piece {
+            int pc, g, t, q, s, u;
+        };
+        const auto first = [&](int pc) {
+            const int g = pc / NP;
+            return Piece{pc, g, g / p.nq, g % p.nq, g % S, g / S};
+        };
+        const auto advance = [&](Piece& x) {
+            x.pc += kConvWarps;
+            const int dg = x.pc / NP - x.g;
+            x.g += dg;
+            for (x.q += dg; x.q >= p.nq; x.q -= p.nq) ++x.t;
+            for (x.s += dg; x.s >= S; x.s -= S) ++x.u;
+        };
+        const auto rowbase = [&](const Piece& x) {
+            return ((int64_t)cid + (int64_t)x.t * ncl) * (2 * kRows) + rank * kRows;
+        };
+        // claim the stage for piece x (in order), split and store it, arrive
+        const auto put = [&](const Piece& x, const float4 (&v)[PR / 4]) -> bool {
             int ok = 1;
             if (lane == 0) {
-                ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + s), kPieces * u, abort) &&
-                     tc::mbar_wait(empty + s, ((uint32_t)u & 1u) ^ 1u, abort);
+                ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + x.s), NP * x.u, abort) &&
+                     tc::mbar_wait(empty + x.s, ((uint32_t)x.u & 1u) ^ 1u, abort);
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            store_piece(sA + s * kStageBytes, half, lane, buf);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+            store_piece<PR>(sA + x.s * kStageBytes, x.pc % NP, lane, v);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) tc::mbar_arrive(full + x.s);
+                else tc::mbar_arrive_cluster(full + x.s, 0);
+                atomicAdd(stored + x.s, 1);
+            }
+            return true;
+        };
+        // one piece in registers: load it, claim its stage, store it.  (Two
+        // 32-row pieces in flight per warp measured slower: twice the claims,
+        // fences and arrivals per byte, and the loads were not the limit.)
+        float4 buf[PR / 4];
+        for (Piece a = first(cw); a.g < G; advance(a)) {
+            load_piece<VEC, PR>(p, rowbase(a), a.q, a.pc % NP, lane, buf);
+            if (!put(a, buf)) break;
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::cluster_sync();   // no CTA leaves while its peer may still arrive on its barriers
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc_pair(tmem, kTmemCols);
+    }
+    if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
+}
+
+// CTA-pair form fed by TMA (A row-major FP32 with 16-byte aligned rows).
+// One thread per CTA streams the CTA's 128 rows of every K-chunk (128 x 32
+// FP32 = 16 KB, 128-byte swizzle) into the stage ring as soon as the MMAs
+// have released the stage, so the ring itself is the data in flight (9
+// stages = 144 KB per SM at d = c = 256) and no thread holds loads in
+// registers.  The converters split a landed chunk into bf16 hi / lo in
+// place: a warp owns whole 8-row blocks, and the 1 KB of FP32 of one block is
+// exactly the room of its 512-byte hi atom (at +0) and 512-byte lo atom (at
+// +512), so the split needs no barrier beyond the warp; the MMAs read the hi
+// and lo operands with 8-row atoms 1024 bytes apart.  Converter group i of
+// G takes chunks i, i + G, ...; the ring is a multiple of G stages, so each
+// stage belongs to one group, which waits on its uses in order (never a
+// phase ahead of the barrier).  The MMA issue, the accumulators and
+// the epilogue are those of rownorm_tc2_kernel.
+constexpr int kTmaWarp = 5;
+constexpr int kCvtWarp0 = 6;
+template <int GROUPS, int WARPS>
+struct TmaShape {
+    static constexpr int kGroups = GROUPS;                          // converter groups
+    static constexpr int kWarps = WARPS;                            // warps per group
+    static constexpr int kBlocks = kRows / 8 / WARPS;               // 8-row blocks per warp
+    static constexpr int kThreads = (kCvtWarp0 + GROUPS * WARPS) * 32;
+};
+constexpr uint32_t kChunkBytes = kRows * kKC * 4;              // one FP32 chunk = one stage
+static_assert(kChunkBytes == kStageBytes, "a landed FP32 chunk becomes its own hi / lo stage");
+
+// Lane l splits row l / 4 of the block, K-elements 8 (l % 4) .. +7: two
+// 16-byte reads of the FP32 rows (chunk c of row r at 128 r + 16 (c ^ r) under
+// the 128-byte swizzle), one 16-byte write each to the hi and lo atoms (chunk
+// kc of row r at 64 r + 16 (kc ^ (r / 2)) under the 64-byte swizzle).  All
+// reads of the warp's blocks precede the warp barrier, all writes follow it.
+template <int NB>
+__device__ __forceinline__ void split_blocks_in_place(uint8_t* first_block, int lane) {
+    const uint32_t r = (uint32_t)lane >> 2, kc = (uint32_t)lane & 3u;
+    const uint32_t rd0 = 128u * r + 16u * ((2u * kc) ^ r), rd1 = 128u * r + 16u * ((2u * kc + 1u) ^ r);
+    const uint32_t wr = 64u * r + 16u * ((kc ^ (r >> 1)) & 3u);
+    constexpr int kPass = NB < 4 ? NB : 4;   // blocks held in registers at once
+#pragma unroll
+    for (int b0 = 0; b0 < NB; b0 += kPass) {
+        uint4 hi[kPass], lo[kPass];
+#pragma unroll
+        for (int b = 0; b < kPass; ++b) {
+            const uint8_t* blk = first_block + (b0 + b) * 1024;
+            const float4 v0 = *reinterpret_cast<const float4*>(blk + rd0);
+            const float4 v1 = *reinterpret_cast<const float4*>(blk + rd1);
+            tc::split_bf16x2(v0.x, v0.y, hi[b].x, lo[b].x);
+            tc::split_bf16x2(v0.z, v0.w, hi[b].y, lo[b].y);
+            tc::split_bf16x2(v1.x, v1.y, hi[b].z, lo[b].z);
+            tc::split_bf16x2(v1.z, v1.w, hi[b].w, lo[b].w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < kPass; ++b) {
+            uint8_t* blk = first_block + (b0 + b) * 1024;
+            *reinterpret_cast<uint4*>(blk + wr) = hi[b];
+            *reinterpret_cast<uint4*>(blk + 512 + wr) = lo[b];
+        }
+    }
+}
+
+template <class T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(T::kThreads, 1)
+    rownorm_tma2_kernel(const RnParams p, const uint8_t* __restrict__ img, const __grid_constant__ CUtensorMap tmA) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int S = p.stages2;
+    const uint32_t rank = tc::cluster_ctarank();
+    const int cid = (int)tc::cluster_id_x(), ncl = (int)tc::nclusters_x();
+    uint8_t* sA = smem;                                  // S stages: FP32 chunk, then its hi / lo blocks
+    uint8_t* sB = smem + S * kStageBytes;                // this CTA's half of B: hi image, then lo image
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * p.hb_bytes + 1024);
+    uint64_t* full = bars;                       // [S] even CTA: chunk split in both CTAs (2 kWarps arrivals)
+    uint64_t* empty = bars + kMaxStages2;        // [S] stage consumed (multicast commit)
+    uint64_t* landed = bars + 2 * kMaxStages2;   // [S] this CTA's chunk has landed (TMA bytes)
+    uint64_t* tfull = bars + 3 * kMaxStages2;    // [2] accumulator done (multicast commit)
+    uint64_t* tempty = tfull + 2;                // [2] even CTA: accumulator read in both (2 kEpiWarps arrivals)
+    uint64_t* fin = tfull + 4;                   // all MMAs complete (multicast commit)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full + s, 2 * T::kWarps);
+            tc::mbar_init(empty + s, 1);
+            tc::mbar_init(landed + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(tfull + a, 1);
+            tc::mbar_init(tempty + a, 2 * kEpiWarps);
+        }
+        tc::mbar_init(fin, 1);
+        *abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc_pair(tmem_slot, kTmemCols);
+        tc::tmem_relinquish_pair();
+    }
+    if (warp == kTmaWarp && lane == 0) tc::prefetch_tmap(&tmA);
+    {   // this CTA's half of B (hi and lo images), 16-byte copies
+        const uint4* src = reinterpret_cast<const uint4*>(img + (size_t)rank * 2 * p.hb_bytes);
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        const uint32_t n16 = (2 * p.hb_bytes) >> 4;
+        for (uint32_t i = threadIdx.x; i < n16; i += T::kThreads) dst[i] = __ldg(src + i);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    tc::cluster_sync();   // barriers of both CTAs initialised, B halves in place
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const int my_tiles = (cid < p.ntiles2) ? (p.ntiles2 - 1 - cid) / ncl + 1 : 0;
+    const int G = my_tiles * p.nq;
+
+    if (warp < kEpiWarps) {
+        // ------------------------------------------------------------ epilogue
+        for (int i = 0; i < my_tiles; ++i) {
+            const int acc = i & 1;
+            if (!warp_wait(tfull + acc, (uint32_t)(i >> 1) & 1u, abort)) break;
+            tc::fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * kAccCols;
+            float sum = 0.f;
+            for (int col = 0; col < p.npad; col += 64) {
+                uint32_t v0[32], v1[32];
+                tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col, v0);
+                const bool two = col + 32 < p.npad;
+                if (two) tc::tmem_ld_32x32b_x32(taddr + (uint32_t)col + 32u, v1);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v0[e]), __uint_as_float(v0[e]), sum);
+                if (two) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) sum = fmaf(__uint_as_float(v1[e]), __uint_as_float(v1[e]), sum);
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) tc::mbar_arrive(tempty + acc);
+                else tc::mbar_arrive_cluster(tempty + acc, 0);
+            }
+            const int64_t row = ((int64_t)cid + (int64_t)i * ncl) * (2 * kRows) + rank * kRows + warp * 32 + lane;
+            if (row < p.n) p.x[row] = (p.beta != 0.f) ? fmaf(p.alpha, sum, p.beta * p.x[row]) : p.alpha * sum;
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------ MMA issue (even CTA)
+        if (lane == 0 && rank == 0) {
+            const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
+            bool ok = true;
+            int s = 0;
+            uint32_t ph = 0;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int acc = i & 1;
+                if (!tc::mbar_wait_cluster(tempty + acc, ((uint32_t)(i >> 1) & 1u) ^ 1u, abort)) break;
+                tc::fence_after_sync();
+                const uint32_t d_base = tmem + (uint32_t)acc * kAccCols;
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) {
+                    if (q >= p.nq) break;
+                    if (!tc::mbar_wait_cluster(full + s, ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_hi = sA_u32 + (uint32_t)s * kStageBytes, a_lo = a_hi + 512u;
+                    const uint32_t b_hi = sB_u32 + p.hoff[q], b_lo = b_hi + p.hb_bytes;
+                    const uint32_t idesc = tc::idesc_bf16_f32(2 * kRows, p.nn[q]);
+                    const uint32_t d_tmem = d_base + p.n0[q];
+#pragma unroll
+                    for (int kk = 0; kk < kKC / 16; ++kk) {
+                        const uint32_t ko = 32u * kk;
+                        const uint64_t ah = tc::desc_sw64_kmajor_sbo(a_hi + ko, 1024u);
+                        const uint64_t al = tc::desc_sw64_kmajor_sbo(a_lo + ko, 1024u);
+                        tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_hi + ko), idesc, (q | kk) != 0);
+                        tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_lo + ko), idesc, 1);
+                        tc::mma_bf16_pair(d_tmem, al, tc::desc_sw64_kmajor(b_hi + ko), idesc, 1);
+                    }
+                    tc::mma_commit_pair(empty + s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) tc::mma_commit_pair(tfull + acc);
+            }
+            tc::mma_commit_pair(fin);
+        }
+        if (lane == 0) {
+            volatile int never = 0;
+            tc::mbar_wait(fin, 0, &never);
+        }
+        __syncwarp();
+    } else if (warp == kTmaWarp) {
+        // ------------------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            int issued = 0, t = 0, q = 0, s = 0;
+            uint32_t u = 0;
+            for (int g = 0; g < G; ++g) {
+                if (!tc::mbar_wait(empty + s, (u & 1u) ^ 1u, abort)) break;
+                tc::mbar_arrive_expect_tx(landed + s, kChunkBytes);
+                const int64_t y = ((int64_t)cid + (int64_t)t * ncl) * (2 * kRows) + rank * kRows;
+                tc::tma_load_2d(sA + s * kStageBytes, &tmA, kKC * q, (int32_t)y, landed + s);
+                ++issued;
+                if (++q == p.nq) {
+                    q = 0;
+                    ++t;
+                }
+                if (++s == S) {
+                    s = 0;
+                    ++u;
+                }
+            }
+            // no copy may still be landing when the CTA leaves (only possible
+            // after a wait gave up): wait for the last use issued on each stage
+            volatile int never = 0;
+            for (int st = 0; st < S && st < issued; ++st) {
+                const int uses = (issued - 1 - st) / S + 1;
+                tc::mbar_wait(landed + st, (uint32_t)(uses - 1) & 1u, &never);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ converters
+        const int cw = warp - kCvtWarp0, grp = cw / T::kWarps, wi = cw % T::kWarps;
+        int s = grp % S;
+        uint32_t u = (uint32_t)(grp / S);
+        for (int g = grp; g < G; g += T::kGroups) {
+            if (!warp_wait(landed + s, u & 1u, abort)) break;
+            tc::mbar_try_wait(landed + s, u & 1u);   // every lane acquires the landed bytes
+            split_blocks_in_place<T::kBlocks>(sA + s * kStageBytes + wi * T::kBlocks * 1024, lane);
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 if (rank == 0) tc::mbar_arrive(full + s);
                 else tc::mbar_arrive_cluster(full + s, 0);
-                atomicAdd(stored + s, 1);
             }
-            pc += kConvWarps;
-            const int dg = pc / kPieces - g;
-            g += dg;
-            for (q += dg; q >= p.nq; q -= p.nq) ++t;
-            for (s += dg; s >= S; s -= S) ++u;
+            for (s += T::kGroups; s >= S; s -= S) ++u;
         }
     }
 
@@ -590,30 +863,96 @@ bool make_plan(const lsk_mat* A, int64_t c, int upper_tri, RnParams& p) {
     return p.stages >= 2 || p.stages2 >= 2;
 }
 
-// clusters of two that fit on the device at once with this shared memory (0:
-// none; cached per device, variant and size)
-int pair_clusters(bool vec, size_t smem) {
+// clusters of two of `fn` (`threads` a CTA) that fit on the device at once
+// with this shared memory (0: none; cached per device, kernel and size)
+int pair_clusters(const void* fn, int threads, size_t smem) {
     static std::mutex mu;
-    static std::map<std::tuple<int, bool, size_t>, int> cache;
+    static std::map<std::tuple<int, const void*, size_t>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(dev, vec, smem);
+    const auto key = std::make_tuple(dev, fn, smem);
     const auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    const void* fn = vec ? (const void*)rownorm_tc2_kernel<true> : (const void*)rownorm_tc2_kernel<false>;
-    cudaError_t e = vec ? allow_dynamic_smem(rownorm_tc2_kernel<true>) : allow_dynamic_smem(rownorm_tc2_kernel<false>);
+    cudaError_t e = allow_dynamic_smem(fn);
     int n = 0;
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2, 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
     }
     cudaGetLastError();
     cache[key] = n;
     return n;
+}
+
+const void* pair_kernel(bool vec) {
+    return vec ? (const void*)rownorm_tc2_kernel<true, kPieceRows> : (const void*)rownorm_tc2_kernel<false, kPieceRows>;
+}
+
+// The TMA-fed kernel's converter layouts (groups x warps a group); the
+// first is the default, LSK_ROWNORM_TMA_VARIANT=i selects another.
+struct TmaVariant {
+    const void* fn;
+    int threads, groups;
+    void (*launch)(int grid, size_t smem, cudaStream_t st, const RnParams& p, const uint8_t* img,
+                   const CUtensorMap& tmA);
+};
+template <int G, int W>
+TmaVariant tma_variant_of() {
+    using T = TmaShape<G, W>;
+    return {(const void*)rownorm_tma2_kernel<T>, T::kThreads, T::kGroups,
+            [](int grid, size_t smem, cudaStream_t st, const RnParams& p, const uint8_t* img, const CUtensorMap& tmA) {
+                rownorm_tma2_kernel<T><<<grid, T::kThreads, smem, st>>>(p, img, tmA);
+            }};
+}
+const TmaVariant& tma_variant() {
+    static const TmaVariant kVariants[] = {tma_variant_of<4, 4>(), tma_variant_of<8, 2>(), tma_variant_of<2, 4>(),
+                                           tma_variant_of<3, 4>(), tma_variant_of<4, 2>(), tma_variant_of<3, 2>()};
+    const char* v = getenv("LSK_ROWNORM_TMA_VARIANT");
+    const int i = v ? atoi(v) : 0;
+    return kVariants[(i >= 0 && i < (int)(sizeof(kVariants) / sizeof(kVariants[0]))) ? i : 0];
+}
+
+// cuTensorMapEncodeTiled from the driver (looked up once; null if absent)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// The TMA-fed pair form reads A through a tensor map of boxes 32 columns x
+// 128 rows: rows must start on 16-byte boundaries, and the row count must
+// fit the map's 32-bit coordinates.
+bool tma_ok(const lsk_mat* A) {
+    return A->d >= kKC && A->n >= 2 * kRows && A->n < ((int64_t)1 << 31) - 4 * kRows && A->ld % 4 == 0 &&
+           ((uintptr_t)A->values & 15) == 0 && encode_tiled() != nullptr;
+}
+
+bool make_tmap(const RnParams& p, CUtensorMap* m) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)p.d, (cuuint64_t)p.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.lda * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kRows};
+    const cuuint32_t elem[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.A), dims, strides, box, elem,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -624,7 +963,7 @@ bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri) {
     if (p.stages >= 2) return true;
     // only the CTA-pair form fits: it needs clusters of two on this device
     const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
-    return pair_clusters(vec, smem_bytes2(p)) > 0;
+    return pair_clusters(pair_kernel(vec), kThreads, smem_bytes2(p)) > 0;
 }
 
 size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri) {
@@ -656,7 +995,19 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     // single-CTA ring short of its full depth
     const bool want_pair = p.stages2 >= 2 && (p.stages < 2 || (allow_pair && p.stages < kMaxStages &&
                                                                p.stages2 > p.stages));
-    const int ncl = want_pair ? pair_clusters(vec, smem_bytes2(p)) : 0;
+    // LSK_ROWNORM_TMA=1 feeds the pair form by TMA (measured slower at d = c =
+    // 256: its in-place ring of 8 stages caps the bytes in flight)
+    const char* tma_env = getenv("LSK_ROWNORM_TMA");
+    bool use_tma = want_pair && (tma_env && tma_env[0] == '1') && tma_ok(A);
+    const TmaVariant& tv = tma_variant();
+    // converter group i takes the chunks (and so the stages) i mod groups: with
+    // the ring a multiple of the group count, each stage belongs to one group,
+    // which then sees every use of it in order (no wait a phase ahead)
+    const int stages_tma = (p.stages2 / tv.groups) * tv.groups;
+    use_tma = use_tma && stages_tma >= 2;
+    if (use_tma) p.stages2 = stages_tma;
+    const void* pfn = use_tma ? tv.fn : pair_kernel(vec);
+    const int ncl = want_pair ? pair_clusters(pfn, use_tma ? tv.threads : kThreads, smem_bytes2(p)) : 0;
     p.pair = ncl > 0 ? 1 : 0;
     if (!p.pair && p.stages < 2) return cudaErrorNotSupported;
     LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
@@ -670,10 +1021,16 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
         const size_t smem2 = smem_bytes2(p);
         const int want2 = (p.ntiles2 + kMinTiles - 1) / kMinTiles;
         const int grid2 = 2 * (want2 < ncl ? want2 : ncl);
-        if (vec) {
-            LSK_PROF("rownorm_dense_tc", st) rownorm_tc2_kernel<true><<<grid2, kThreads, smem2, st>>>(p, img);
+        if (use_tma) {
+            CUtensorMap tmA;
+            if (!make_tmap(p, &tmA)) return cudaErrorNotSupported;
+            LSK_PROF("rownorm_dense_tc", st) tv.launch(grid2, smem2, st, p, img, tmA);
+        } else if (vec) {
+            LSK_PROF("rownorm_dense_tc", st)
+                rownorm_tc2_kernel<true, kPieceRows><<<grid2, kThreads, smem2, st>>>(p, img);
         } else {
-            LSK_PROF("rownorm_dense_tc", st) rownorm_tc2_kernel<false><<<grid2, kThreads, smem2, st>>>(p, img);
+            LSK_PROF("rownorm_dense_tc", st)
+                rownorm_tc2_kernel<false, kPieceRows><<<grid2, kThreads, smem2, st>>>(p, img);
         }
         return cudaGetLastError();
     }

@@ -137,6 +137,27 @@ __device__ __forceinline__ bool counter_wait(volatile int* ctr, int target, vola
     return true;
 }
 
+// ---- TMA (tensor-map bulk copies) ------------------------------------------
+// Arrive on a local barrier and raise its expected transaction bytes: the
+// phase completes once the arrivals are in and `bytes` have landed.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Load the box at coordinates (x, y) of a 2-D tensor map into this CTA's
+// shared memory at `dst` (1024-byte aligned for the 128-byte swizzle),
+// completing `bytes` on `bar`.  x times the element size must be a multiple
+// of 16 bytes; out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -197,6 +218,19 @@ __device__ __forceinline__ uint64_t desc_sw64_kmajor(uint32_t smem_addr) {
     d |= (uint64_t)(512u >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)4 << 61;                              // 64-byte swizzle
+    return d;
+}
+
+// Same, with the 8-row atoms `sbo` bytes apart (a multiple of 512): two
+// operands can then interleave atom by atom (the hi / lo halves of a split
+// tile at +0 and +512 of every 1024-byte block).
+__device__ __forceinline__ uint64_t desc_sw64_kmajor_sbo(uint32_t smem_addr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 

@@ -274,6 +274,30 @@ def test_rownorms_dense_bf16_single_cta_form(lsk, monkeypatch, n, d, c, tri):
     assert np.max(np.abs(single - pair) / ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n,d,c,tri,ld", [(10_000, 256, 256, True, 256), (2_000, 256, 256, False, 256),
+                                            (1_000, 256, 160, False, 256), (5_003, 200, 200, True, 200),
+                                            (300, 232, 232, True, 236), (70_001, 256, 256, True, 260)])
+def test_rownorms_dense_bf16_tma_form(lsk, monkeypatch, n, d, c, tri, ld):
+    """The CTA-pair kernel in its two feeds: register-staged loads (default)
+    and the TMA stage ring with in-place hi / lo split (LSK_ROWNORM_TMA=1).
+    Both split and multiply identically, so the scores agree bit for bit;
+    ragged row tails, K-chunks past d (zero-filled by the copy) and row
+    strides above d included."""
+    W = workloads.dense_normal(n, ld, seed=c) * (10.0 ** np.linspace(-2, 2, ld)).astype(np.float32)
+    B = workloads.dense_normal(d, c, seed=d + 1)
+    if tri:
+        B = np.triu(B)
+    Ad = dev(W)[:, :d]
+    regs = host(lsk.rownorms_prod(Ad, dev(B), upper_triangular=tri, prec="bf16")).astype(np.float64)
+    monkeypatch.setenv("LSK_ROWNORM_TMA", "1")
+    tma = host(lsk.rownorms_prod(Ad, dev(B), upper_triangular=tri, prec="bf16")).astype(np.float64)
+    lsk.context().sync()
+    A64 = W[:, :d].astype(np.float64)
+    ref = orn.rownorms_prod_dense(A64, B.astype(np.float64))
+    assert np.max(np.abs(tma - ref) / ref) <= 1e-3
+    assert np.array_equal(tma, regs)
+
+
 def test_rownorms_alpha_beta(lsk):
     A = workloads.dense_normal(1000, 20, seed=1)
     B = workloads.dense_normal(20, 7, seed=2)
