@@ -10,20 +10,26 @@
 // of kSliceRows = 1024 rows each, so no FP32 accumulator sums more than
 // 3 x 1024 products (the tensor cores' FP32 accumulation biases long
 // all-positive sums, such as the diagonal, at the 1e-5 level by 2048 rows).
-// After each slice the epilogue warps add the accumulator into the CTA's
-// running FP32 partial in global memory (upper triangle; all CTAs' partials
-// together stay in L2), and a second kernel adds the CTAs' partials in order
-// with a compensated FP32 sum, then forms alpha * sum + beta * C.
-//   warps 0-15  workers: per chunk of 32 rows, load the rows (16-byte loads)
-//               into a padded FP32 staging buffer and transpose them into one
-//               K-major bf16 hi / lo tile pair (row a of the tile = column a of
-//               A, 32 consecutive rows along K) in a 4-stage ring;
-//   warp 16     lane 0 issues, for each 128-row M tile t, the products with
-//               the tile's rows 128 t .. npad - 1 as the N operand (the same
+// After each slice the epilogue warps read the accumulator out of TMEM, hand
+// it back to the MMAs at once, and add it into the CTA's running FP32 partial
+// in global memory with fire-and-forget vector reductions (one writer per
+// address, in program order, so the sums are deterministic); a second kernel
+// adds the CTAs' partials in order with a compensated FP32 sum, then forms
+// alpha * sum + beta * C.  Warps:
+//   0 .. kWorkers-1
+//               workers: each owns every kWorkers-th piece of 8 rows (a
+//               quarter of a 32-row chunk) and works alone: 16-byte loads of
+//               whole rows, a bf16 hi / lo split, and 8-byte stores into the
+//               stage's MN-major tiles (no transpose: a row-major chunk of A
+//               is MN-major for both operands of A^T A, the instruction
+//               descriptor's transpose bits say so).  The uses of each ring
+//               stage are claimed in piece order;
+//   kWorkers    lane 0 issues, for each 128-column M tile t, the products
+//               with columns 128 t .. npad - 1 as the N operand (the same
 //               shared-memory tile is both operands; only the upper block
 //               triangle is computed);
-//   warps 17-24 epilogue: accumulator t is read by the warps whose TMEM lane
-//               quarter covers it, added into the running partial, released.
+//   then 8      epilogue: accumulator t is read by the warps whose TMEM lane
+//               quarter covers it.
 // TMEM holds the two accumulators (N = npad and npad - 128 columns).  Waits
 // are bounded; a timeout sets the TIMEOUT flag.
 #include "tc_common.cuh"
@@ -32,53 +38,93 @@ namespace {
 
 constexpr int kKC = 32;            // rows of A per chunk (the K of the MMAs)
 constexpr int kMT = 128;           // rows of an MMA tile (columns of A)
-constexpr int kWorkers = 16;
+constexpr int kWorkers = 11;
 constexpr int kMmaWarp = kWorkers;
 constexpr int kEpi0 = kWorkers + 1;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (kWorkers + 1 + kEpiWarps) * 32;
-constexpr int kWorkerThreads = kWorkers * 32;
-constexpr int kStagePad = 4;
-constexpr int kStages = 4;
+constexpr int kPieceRows = 8;                  // rows of one worker piece
+constexpr int kPieces = kKC / kPieceRows;      // pieces per chunk (4)
+constexpr int kMaxStages = 8;
 constexpr int kSliceRows = 1024;   // rows per slice (FP32 accumulation length bound)
 constexpr size_t kSmemLimit = 232448;
 
 struct GrParams {
     const float* A;
     int64_t lda, n;
-    int d, npad, slices, vec;
-    float* part;       // [gridDim][d][d] running partials (upper triangle), zeroed before the launch
+    int d, npad, slices, vec;   // vec: 16-byte loads
+    float* part;       // [gridDim][npad][npad] running partials, zeroed before the launch
     int* flag;
 };
 
-__host__ __device__ inline uint32_t half_bytes(int npad) { return (uint32_t)npad * kKC * 2; }   // one bf16 tile
-__host__ __device__ inline uint32_t stage_bytes(int npad) { return 2 * half_bytes(npad); }     // hi + lo
+// Stage layout, per bf16 tile (hi, then lo): MN-major 128-byte-swizzled atoms
+// of 8 rows of A (K) x 64 columns of A (M / N), atom (column block mb, row
+// group kg) at mb x 1024 + kg x kSbo(npad).  The column blocks run to a whole
+// number of 128-column MMA tiles, so an M = 128 operand never reads past its
+// tile (columns past d hold zeros, past npad they feed accumulator rows that
+// are never read).
+__host__ __device__ constexpr uint32_t mn_blocks(int npad) { return 2u * (uint32_t)((npad + kMT - 1) / kMT); }
+__host__ __device__ constexpr uint32_t kSbo(int npad) { return mn_blocks(npad) * 1024u; }   // next 8 rows
+__host__ __device__ constexpr uint32_t half_bytes(int npad) { return kSbo(npad) * (kKC / 8); }  // one bf16 tile
+__host__ __device__ constexpr uint32_t stage_bytes(int npad) { return 2 * half_bytes(npad); }   // hi + lo
+// ring depth that fits next to the barriers
+__host__ __device__ constexpr int stages_of(int npad) {
+    return (int)((232448 - 2048) / stage_bytes(npad)) < kMaxStages ? (int)((232448 - 2048) / stage_bytes(npad))
+                                                                     : kMaxStages;
+}
 
-__device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkerThreads) : "memory"); }
-
-// Rows i0 .. i0+31 (clipped to r_end) of A into registers: float4 f = wt + 512 j
-// -> row f / q4, columns 4 (f % q4).
+// Rows row0 .. row0 + 7 of A (zeros at and past r_end or d), lane t: float4
+// number t + 32 h of each row (columns 4 t + 128 h .. + 3): 512 contiguous
+// bytes a row per warp instruction.
 template <int NPAD>
-__device__ __forceinline__ void load_rows(const GrParams& p, int64_t i0, int64_t r_end, int wt, float4 (&a)[4]) {
-    constexpr int q4 = NPAD / 4, nf4 = kKC * q4;
+__device__ __forceinline__ void load_piece(const GrParams& p, int64_t row0, int64_t r_end, int lane,
+                                           float4 (&v)[kPieceRows][(NPAD + kMT - 1) / kMT]) {
+    constexpr int H = (NPAD + kMT - 1) / kMT;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int f = wt + kWorkerThreads * j;
-        if (f < nf4) {
-            const int rr = f / q4, c = 4 * (f % q4);
-            const int64_t i = i0 + rr;
-            if (i < r_end) {
-                const float* src = p.A + i * p.lda + c;
-                if (p.vec && c < p.d) {
-                    a[j] = __ldg(reinterpret_cast<const float4*>(src));
+    for (int r = 0; r < kPieceRows; ++r) {
+        const int64_t row = row0 + r;
+        const float* src = p.A + row * p.lda;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int c = 4 * lane + kMT * h;
+            v[r][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < r_end && c < p.d) {
+                if (p.vec && c + 3 < p.d) {
+                    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(v[r][h].x), "=f"(v[r][h].y), "=f"(v[r][h].z), "=f"(v[r][h].w)
+                                 : "l"(src + c));
                 } else {
-                    a[j].x = c < p.d ? __ldg(src) : 0.f;
-                    a[j].y = c + 1 < p.d ? __ldg(src + 1) : 0.f;
-                    a[j].z = c + 2 < p.d ? __ldg(src + 2) : 0.f;
-                    a[j].w = c + 3 < p.d ? __ldg(src + 3) : 0.f;
+                    v[r][h].x = __ldg(src + c);
+                    v[r][h].y = c + 1 < p.d ? __ldg(src + c + 1) : 0.f;
+                    v[r][h].z = c + 2 < p.d ? __ldg(src + c + 2) : 0.f;
+                    v[r][h].w = c + 3 < p.d ? __ldg(src + c + 3) : 0.f;
                 }
             }
+        }
+    }
+}
+
+// Split the piece into bf16 hi / lo and store it as row group `part` of the
+// stage: columns 4 t .. 4 t + 3 of row r go to atom (c / 64, part), row r,
+// 16-byte chunk ((c % 64) / 8) ^ r, bytes 8 (t % 2) .. +7.  Sixteen lanes
+// fill one 128-byte atom row: two wavefronts a warp instruction.
+template <int NPAD>
+__device__ __forceinline__ void store_piece(uint8_t* th, uint8_t* tl, int part, int lane,
+                                            const float4 (&v)[kPieceRows][(NPAD + kMT - 1) / kMT]) {
+    constexpr int H = (NPAD + kMT - 1) / kMT;
+    const uint32_t c0 = 4u * (uint32_t)lane;
+#pragma unroll
+    for (int r = 0; r < kPieceRows; ++r) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const uint32_t c = c0 + kMT * h;
+            const uint32_t off = (c >> 6) * 1024u + (uint32_t)part * kSbo(NPAD) + (uint32_t)r * 128u +
+                                 (((((c & 63u) >> 3) ^ (uint32_t)r) & 7u) << 4) + (c & 7u) * 2u;
+            uint2 hi, lo;
+            tc::split_bf16x2(v[r][h].x, v[r][h].y, hi.x, lo.x);
+            tc::split_bf16x2(v[r][h].z, v[r][h].w, hi.y, lo.y);
+            *reinterpret_cast<uint2*>(th + off) = hi;
+            *reinterpret_cast<uint2*>(tl + off) = lo;
         }
     }
 }
@@ -89,19 +135,18 @@ template <int NPAD>
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    constexpr int kStages = stages_of(NPAD);
     const uint32_t sbytes = stage_bytes(NPAD);
     uint8_t* stages = smem;
-    float* stagef = reinterpret_cast<float*>(smem + kStages * sbytes);   // kKC x (npad + pad)
-    constexpr int ldf = NPAD + kStagePad;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stagef + kKC * ldf);
-    uint64_t* full = bars;                 // [kStages] (kWorkers arrivals)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
+    uint64_t* full = bars;                 // [kStages] (kPieces arrivals)
     uint64_t* empty = bars + kStages;      // [kStages] (MMA commit)
     uint64_t* done = bars + 2 * kStages;   // slice accumulated       (MMA commit)
     uint64_t* drained = done + 1;          // accumulator read        (epilogue warp arrivals)
     uint64_t* fin = done + 2;              // every MMA complete      (MMA commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* go_on = abort + 1;
+    int* stored = const_cast<int*>(abort) + 1;   // [kStages] pieces stored per stage (in use order)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int ntiles = (NPAD + kMT - 1) / kMT;   // 1 or 2 M tiles
@@ -110,8 +155,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(full + s, kWorkers);
+            tc::mbar_init(full + s, kPieces);
             tc::mbar_init(empty + s, 1);
+            stored[s] = 0;
         }
         tc::mbar_init(done, 1);
         tc::mbar_init(drained, nepi);
@@ -131,67 +177,36 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kWorkers) {
-        const int wt = threadIdx.x;
-        constexpr int q4 = NPAD / 4;
-        constexpr int nf4 = kKC * q4;   // float4 in a chunk (<= 4 per thread)
-        int s = 0;
-        uint32_t ph = 0;
-        for (int z = 0; z < my_slices; ++z) {
+        // the CTA's chunks in order: slice z (rows from (blockIdx.x + z grid)
+        // 1024) holds chunks 32 z .. 32 z + 31; only the matrix's last slice
+        // is short
+        int my_chunks = my_slices * (kSliceRows / kKC);
+        if (my_slices > 0 && (int)blockIdx.x + (my_slices - 1) * (int)gridDim.x == p.slices - 1) {
+            const int64_t last_rows = p.n - (int64_t)(p.slices - 1) * kSliceRows;
+            my_chunks -= kSliceRows / kKC - (int)((last_rows + kKC - 1) / kKC);
+        }
+        float4 v[kPieceRows][(NPAD + kMT - 1) / kMT];
+        for (int pc = warp; pc < my_chunks * kPieces; pc += kWorkers) {
+            const int h = pc / kPieces, part = pc % kPieces;
+            const int z = h / (kSliceRows / kKC), cz = h % (kSliceRows / kKC);
             const int64_t r_begin = ((int64_t)blockIdx.x + (int64_t)z * gridDim.x) * kSliceRows;
             const int64_t r_end = min(p.n, r_begin + kSliceRows);
-            const int nchunks = (int)((r_end - r_begin + kKC - 1) / kKC);
-            bool ok = true;
-            // chunk g's rows are loaded while chunk g-1 is staged and transposed
-            float4 a[4], nx[4];
-            load_rows<NPAD>(p, r_begin, r_end, wt, a);
-            for (int g = 0; g < nchunks; ++g) {
-                if (g + 1 < nchunks) load_rows<NPAD>(p, r_begin + (int64_t)(g + 1) * kKC, r_end, wt, nx);
-                // (2) wait for the stage (one thread decides for all workers)
-                if (wt == 0) *go_on = tc::mbar_wait(empty + s, ph ^ 1u, abort) ? 1 : 0;
-                named_sync();
-                if (!*go_on) {
-                    ok = false;
-                    break;
-                }
-                // (3) rows into the FP32 staging buffer
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int f = wt + kWorkerThreads * j;
-                    if (f < nf4) {
-                        const int rr = f / q4, c = 4 * (f % q4);
-                        *reinterpret_cast<float4*>(stagef + rr * ldf + c) = a[j];
-                    }
-                }
-                named_sync();
-                // (4) transpose + split: item (column c, row group r8) -> 8 consecutive rows of column c
-                uint8_t* th = stages + s * sbytes;
-                uint8_t* tl = th + half_bytes(NPAD);
-                #pragma unroll
-                for (int item = wt; item < NPAD * (kKC / 8); item += kWorkerThreads) {
-                    const int c = item % NPAD, r8 = item / NPAD;
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = stagef[(8 * r8 + e) * ldf + c];
-                    uint4 hi, lo;
-                    tc::split_bf16x2(v[0], v[1], hi.x, lo.x);
-                    tc::split_bf16x2(v[2], v[3], hi.y, lo.y);
-                    tc::split_bf16x2(v[4], v[5], hi.z, lo.z);
-                    tc::split_bf16x2(v[6], v[7], hi.w, lo.w);
-                    const uint32_t off = tc::sw64_offset(c, 8 * r8);
-                    *reinterpret_cast<uint4*>(th + off) = hi;
-                    *reinterpret_cast<uint4*>(tl + off) = lo;
-                }
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(full + s);
-                if (++s == kStages) {
-                    s = 0;
-                    ph ^= 1u;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) a[j] = nx[j];
+            load_piece<NPAD>(p, r_begin + (int64_t)cz * kKC + part * kPieceRows, r_end, lane, v);
+            const int s = h % kStages, u = h / kStages;
+            int ok = 1;
+            if (lane == 0) {
+                ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + s), kPieces * u, abort) &&
+                     tc::mbar_wait(empty + s, ((uint32_t)u & 1u) ^ 1u, abort);
             }
-            if (!ok) break;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            uint8_t* th = stages + (size_t)s * sbytes;
+            store_piece<NPAD>(th, th + half_bytes(NPAD), part, lane, v);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(full + s);
+                atomicAdd(stored + s, 1);
+            }
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -215,15 +230,16 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
                     const uint32_t hi = base + (uint32_t)s * sbytes, lo = hi + half_bytes(NPAD);
 #pragma unroll
                     for (int kk = 0; kk < kKC / 16; ++kk) {
-                        const uint32_t ko = 32u * kk;   // 16 bf16 = 32 bytes along the swizzled row
+                        const uint32_t ko = 2u * kSbo(NPAD) * kk;   // 16 rows = two 8-row groups
                         for (int t = 0; t < ntiles; ++t) {
-                            const uint32_t off = (uint32_t)t * (kMT * kKC * 2) + ko;   // tile rows from 128 t
-                            const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)(NPAD - t * kMT));
+                            const uint32_t off = (uint32_t)t * 2048u + ko;   // columns from 128 t
+                            const uint32_t idesc = tc::idesc_bf16_f32_mn(128, (uint32_t)(NPAD - t * kMT));
                             const uint32_t dt = tmem + 256u * t;
-                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(hi + off), tc::desc_sw64_kmajor(hi + off), idesc,
-                                         (g | kk) != 0);
-                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(hi + off), tc::desc_sw64_kmajor(lo + off), idesc, 1);
-                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(lo + off), tc::desc_sw64_kmajor(hi + off), idesc, 1);
+                            const uint64_t dh = tc::desc_sw128_mnmajor(hi + off, 1024u, kSbo(NPAD));
+                            const uint64_t dl = tc::desc_sw128_mnmajor(lo + off, 1024u, kSbo(NPAD));
+                            tc::mma_bf16(dt, dh, dh, idesc, (g | kk) != 0);
+                            tc::mma_bf16(dt, dh, dl, idesc, 1);
+                            tc::mma_bf16(dt, dl, dh, idesc, 1);
                         }
                     }
                     tc::mma_commit(empty + s);
@@ -244,27 +260,34 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
         const int e = warp - kEpi0, t = e >> 2, q = warp & 3;
         const int row = t * kMT + q * 32 + lane;   // column a of A
         const int ncols = NPAD - t * kMT;        // columns b = t*128 .. npad-1
-        float* dst = p.part + ((int64_t)blockIdx.x * p.d + row) * p.d + t * kMT;
+        float* dst = p.part + ((int64_t)blockIdx.x * NPAD + row) * NPAD + t * kMT;
         for (int z = 0; z < my_slices; ++z) {
             int okw = 0;
             if (lane == 0) okw = tc::mbar_wait(done, (uint32_t)z & 1u, abort) ? 1 : 0;
             if (!__shfl_sync(0xffffffffu, okw, 0)) break;
             tc::fence_after_sync();
+            // the accumulator is handed back as soon as it is in registers; the
+            // adds into the running partial are fire-and-forget reductions (one
+            // writer per address, in program order: deterministic)
             for (int col = 0; col < ncols; col += 32) {
                 uint32_t v[32];
                 tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(256 * t + col), v);
                 tc::tmem_ld_wait();
+                if (col + 32 >= ncols) {
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(drained);
+                }
                 if (row < p.d) {
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const int b = t * kMT + col + k;
-                        if (b < p.d && b >= row) dst[col + k] += __uint_as_float(v[k]);
+                    for (int k = 0; k < 32; k += 4) {
+                        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + col + k),
+                                     "f"(__uint_as_float(v[k])), "f"(__uint_as_float(v[k + 1])),
+                                     "f"(__uint_as_float(v[k + 2])), "f"(__uint_as_float(v[k + 3]))
+                                     : "memory");
                     }
                 }
             }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(drained);
         }
     }
     tc::fence_before_sync();
@@ -278,9 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
 
 // C[a][b] = alpha * sum_c part[c][min][max] + beta * C[a][b]: the CTAs'
 // partials in order, compensated FP32 sum (Neumaier), alpha and beta in FP64.
-__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int slices, int d, double alpha, double beta,
-                                      float* __restrict__ C) {
-    const int64_t len = (int64_t)d * d;
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int slices, int d, int npad, double alpha,
+                                      double beta, float* __restrict__ C) {
+    const int64_t len = (int64_t)d * d, plen = (int64_t)npad * npad;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
         int a = (int)(e / d), b = (int)(e % d);
@@ -289,10 +312,10 @@ __global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int slices
             a = b;
             b = t;
         }
-        const int64_t idx = (int64_t)a * d + b;
+        const int64_t idx = (int64_t)a * npad + b;
         float s = 0.f, c = 0.f;
         for (int z = 0; z < slices; ++z) {
-            const float x = part[(int64_t)z * len + idx];
+            const float x = part[(int64_t)z * plen + idx];
             const float t = s + x;
             c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
             s = t;
@@ -304,7 +327,7 @@ __global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int slices
 }
 
 size_t smem_bytes(int npad) {
-    return (size_t)kStages * stage_bytes(npad) + (size_t)kKC * (npad + kStagePad) * 4 + 1024 + 128;
+    return (size_t)stages_of(npad) * stage_bytes(npad) + 1024 + 256;
 }
 
 }  // namespace
@@ -330,7 +353,8 @@ int grid_of(const lsk_mat* A, int sm_count) {
 
 size_t gram_tc_workspace_bytes(const lsk_mat* A, int sm_count) {
     const int g = grid_of(A, sm_count);
-    return ws_round((size_t)(g > 0 ? g : 1) * A->d * A->d * 4);
+    const size_t npad = (size_t)((A->d + 31) / 32) * 32;
+    return ws_round((size_t)(g > 0 ? g : 1) * npad * npad * 4);
 }
 
 cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag, int sm_count,
@@ -343,7 +367,7 @@ cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C
     p.d = (int)A->d;
     p.npad = (int)((A->d + 31) / 32) * 32;
     p.slices = (int)((A->n + kSliceRows - 1) / kSliceRows);
-    p.vec = (A->d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
+    p.vec = (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
     p.part = (float*)ws;
     p.flag = flag;
     const int grid = grid_of(A, sm_count);
@@ -352,7 +376,7 @@ cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C
     if (rg > 8 * (int64_t)sm_count) rg = 8 * (int64_t)sm_count;
     cudaError_t e;
     if (grid > 0) {
-        e = cudaMemsetAsync(p.part, 0, (size_t)grid * len * 4, st);
+        e = cudaMemsetAsync(p.part, 0, (size_t)grid * p.npad * p.npad * 4, st);
         if (e != cudaSuccess) return e;
         switch (p.npad) {
             case 32: e = launch_npad<32>(p, grid, st); break;
@@ -366,6 +390,6 @@ cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C
         }
         if (e != cudaSuccess) return e;
     }
-    LSK_PROF("gram_reduce", st) gram_tc_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(p.part, grid, p.d, alpha, beta, C);
+    LSK_PROF("gram_reduce", st) gram_tc_reduce_kernel<<<(unsigned)rg, 256, 0, st>>>(p.part, grid, p.d, p.npad, alpha, beta, C);
     return cudaGetLastError();
 }

@@ -234,6 +234,20 @@ __device__ __forceinline__ uint64_t desc_sw64_kmajor_sbo(uint32_t smem_addr, uin
     return d;
 }
 
+// MN-major operand, 128-byte swizzle: atoms of 8 K-rows x 128 bytes (64 bf16
+// along M/N, the row of K-index k at 128 k within the atom), atoms `lbo`
+// bytes apart along M/N and `sbo` bytes apart along K (the next 8 rows).
+// Atom bases must be 1024-byte aligned.
+__device__ __forceinline__ uint64_t desc_sw128_mnmajor(uint32_t smem_addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
     return (1u << 4)            // D format F32
@@ -241,6 +255,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
            | (1u << 10)         // B format BF16
            | ((N >> 3) << 17)   // N / 8
            | ((M >> 4) << 24);  // M / 16
+}
+// Same with both operands MN-major (the transpose bits of A and B).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(uint32_t M, uint32_t N) {
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
