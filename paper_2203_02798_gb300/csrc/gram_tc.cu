@@ -38,13 +38,17 @@ namespace {
 
 constexpr int kKC = 32;            // rows of A per chunk (the K of the MMAs)
 constexpr int kMT = 128;           // rows of an MMA tile (columns of A)
-constexpr int kWorkers = 11;
-constexpr int kMmaWarp = kWorkers;
-constexpr int kEpi0 = kWorkers + 1;
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = (kWorkers + 1 + kEpiWarps) * 32;
-constexpr int kPieceRows = 8;                  // rows of one worker piece
-constexpr int kPieces = kKC / kPieceRows;      // pieces per chunk (4)
+// warp roles: kWorkers workers, one MMA warp, kEpiWarps epilogue warps
+template <int W, int E, int PR = 8>
+struct GramShape {
+    static constexpr int kPieceRows = PR;   // rows of one worker piece
+    static constexpr int kPieces = 32 / PR; // pieces per 32-row chunk
+    static constexpr int kWorkers = W;
+    static constexpr int kMmaWarp = W;
+    static constexpr int kEpi0 = W + 1;
+    static constexpr int kEpiWarps = E;   // 4 (both accumulators each) or 8 (one each)
+    static constexpr int kThreads = (W + 1 + E) * 32;
+};
 constexpr int kMaxStages = 8;
 constexpr int kSliceRows = 1024;   // rows per slice (FP32 accumulation length bound)
 constexpr size_t kSmemLimit = 232448;
@@ -76,12 +80,12 @@ __host__ __device__ constexpr int stages_of(int npad) {
 // Rows row0 .. row0 + 7 of A (zeros at and past r_end or d), lane t: float4
 // number t + 32 h of each row (columns 4 t + 128 h .. + 3): 512 contiguous
 // bytes a row per warp instruction.
-template <int NPAD>
+template <int NPAD, int PR>
 __device__ __forceinline__ void load_piece(const GrParams& p, int64_t row0, int64_t r_end, int lane,
-                                           float4 (&v)[kPieceRows][(NPAD + kMT - 1) / kMT]) {
+                                           float4 (&v)[PR][(NPAD + kMT - 1) / kMT]) {
     constexpr int H = (NPAD + kMT - 1) / kMT;
 #pragma unroll
-    for (int r = 0; r < kPieceRows; ++r) {
+    for (int r = 0; r < PR; ++r) {
         const int64_t row = row0 + r;
         const float* src = p.A + row * p.lda;
 #pragma unroll
@@ -104,35 +108,41 @@ __device__ __forceinline__ void load_piece(const GrParams& p, int64_t row0, int6
     }
 }
 
-// Split the piece into bf16 hi / lo and store it as row group `part` of the
-// stage: columns 4 t .. 4 t + 3 of row r go to atom (c / 64, part), row r,
-// 16-byte chunk ((c % 64) / 8) ^ r, bytes 8 (t % 2) .. +7.  Sixteen lanes
-// fill one 128-byte atom row: two wavefronts a warp instruction.
-template <int NPAD>
+// Split the piece into bf16 hi / lo and store it as rows PR part .. PR part +
+// PR - 1 of the chunk: row k of the chunk is row k % 8 of the atoms of row
+// group k / 8; columns 4 t .. 4 t + 3 go to atom (c / 64, k / 8), 16-byte
+// chunk ((c % 64) / 8) ^ (k % 8), bytes 8 (t % 2) .. +7.  Sixteen lanes fill
+// one 128-byte atom row: two wavefronts a warp instruction.
+template <int NPAD, int PR>
 __device__ __forceinline__ void store_piece(uint8_t* th, uint8_t* tl, int part, int lane,
-                                            const float4 (&v)[kPieceRows][(NPAD + kMT - 1) / kMT]) {
+                                            const float4 (&v)[PR][(NPAD + kMT - 1) / kMT]) {
     constexpr int H = (NPAD + kMT - 1) / kMT;
     const uint32_t c0 = 4u * (uint32_t)lane;
+    const uint32_t k0 = (uint32_t)(PR * part);
+    uint8_t* const bh = th + (k0 >> 3) * kSbo(NPAD);
+    uint8_t* const bl = tl + (k0 >> 3) * kSbo(NPAD);
 #pragma unroll
-    for (int r = 0; r < kPieceRows; ++r) {
+    for (int r = 0; r < PR; ++r) {
+        const uint32_t rr = (k0 & 7u) + (uint32_t)r;   // row in the atom
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             const uint32_t c = c0 + kMT * h;
-            const uint32_t off = (c >> 6) * 1024u + (uint32_t)part * kSbo(NPAD) + (uint32_t)r * 128u +
-                                 (((((c & 63u) >> 3) ^ (uint32_t)r) & 7u) << 4) + (c & 7u) * 2u;
+            const uint32_t off = (c >> 6) * 1024u + rr * 128u + (((((c & 63u) >> 3) ^ rr) & 7u) << 4) + (c & 7u) * 2u;
             uint2 hi, lo;
             tc::split_bf16x2(v[r][h].x, v[r][h].y, hi.x, lo.x);
             tc::split_bf16x2(v[r][h].z, v[r][h].w, hi.y, lo.y);
-            *reinterpret_cast<uint2*>(th + off) = hi;
-            *reinterpret_cast<uint2*>(tl + off) = lo;
+            *reinterpret_cast<uint2*>(bh + off) = hi;
+            *reinterpret_cast<uint2*>(bl + off) = lo;
         }
     }
 }
 
 // NPAD (d rounded up to 32) is a template parameter: every index split below
 // is then a division by a constant.
-template <int NPAD>
-__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) {
+template <int NPAD, class SH>
+__global__ void __launch_bounds__(SH::kThreads, 1) gram_tc_kernel(const GrParams p) {
+    constexpr int kWorkers = SH::kWorkers, kMmaWarp = SH::kMmaWarp, kEpi0 = SH::kEpi0, kEpiWarps = SH::kEpiWarps;
+    constexpr int kPieceRows = SH::kPieceRows, kPieces = SH::kPieces;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr int kStages = stages_of(NPAD);
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int ntiles = (NPAD + kMT - 1) / kMT;   // 1 or 2 M tiles
-    const int nepi = 4 * ntiles;                   // epilogue warps in use
+    const int nepi = 4 * (ntiles < kEpiWarps / 4 ? ntiles : kEpiWarps / 4);   // epilogue warps in use
     const int my_slices = ((int)blockIdx.x < p.slices) ? (p.slices - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
@@ -185,28 +195,44 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
             const int64_t last_rows = p.n - (int64_t)(p.slices - 1) * kSliceRows;
             my_chunks -= kSliceRows / kKC - (int)((last_rows + kKC - 1) / kKC);
         }
-        float4 v[kPieceRows][(NPAD + kMT - 1) / kMT];
-        for (int pc = warp; pc < my_chunks * kPieces; pc += kWorkers) {
-            const int h = pc / kPieces, part = pc % kPieces;
+        constexpr int H = (NPAD + kMT - 1) / kMT;
+        const int npieces = my_chunks * kPieces;
+        // piece pc: chunk h = pc / kPieces of the CTA's sequence, rows
+        // kPieceRows (pc % kPieces) .. of it
+        const auto rows_of = [&](int pc, int64_t& row0, int64_t& r_end) {
+            const int h = pc / kPieces;
             const int z = h / (kSliceRows / kKC), cz = h % (kSliceRows / kKC);
             const int64_t r_begin = ((int64_t)blockIdx.x + (int64_t)z * gridDim.x) * kSliceRows;
-            const int64_t r_end = min(p.n, r_begin + kSliceRows);
-            load_piece<NPAD>(p, r_begin + (int64_t)cz * kKC + part * kPieceRows, r_end, lane, v);
-            const int s = h % kStages, u = h / kStages;
+            r_end = min(p.n, r_begin + kSliceRows);
+            row0 = r_begin + (int64_t)cz * kKC + (pc % kPieces) * kPieceRows;
+        };
+        // claim piece pc's stage (in piece order), store it, arrive
+        const auto put = [&](int pc, const float4 (&v)[kPieceRows][H]) -> bool {
+            const int h = pc / kPieces, s = h % kStages, u = h / kStages;
             int ok = 1;
             if (lane == 0) {
                 ok = tc::counter_wait(reinterpret_cast<volatile int*>(stored + s), kPieces * u, abort) &&
                      tc::mbar_wait(empty + s, ((uint32_t)u & 1u) ^ 1u, abort);
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
             uint8_t* th = stages + (size_t)s * sbytes;
-            store_piece<NPAD>(th, th + half_bytes(NPAD), part, lane, v);
+            store_piece<NPAD, kPieceRows>(th, th + half_bytes(NPAD), pc % kPieces, lane, v);
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 tc::mbar_arrive(full + s);
                 atomicAdd(stored + s, 1);
             }
+            return true;
+        };
+        // one piece in registers: load it, claim its stage, store it (two
+        // 4-row pieces in flight a warp measured no faster)
+        int64_t row0, r_end;
+        float4 v[kPieceRows][H];
+        for (int pc = warp; pc < npieces; pc += kWorkers) {
+            rows_of(pc, row0, r_end);
+            load_piece<NPAD, kPieceRows>(p, row0, r_end, lane, v);
+            if (!put(pc, v)) break;
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -256,11 +282,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
         }
         __syncwarp();
     } else if (warp - kEpi0 < nepi) {
-        // epilogue warp e: accumulator t = e / 4, TMEM lanes of its quarter q = warp % 4
-        const int e = warp - kEpi0, t = e >> 2, q = warp & 3;
-        const int row = t * kMT + q * 32 + lane;   // column a of A
-        const int ncols = NPAD - t * kMT;        // columns b = t*128 .. npad-1
-        float* dst = p.part + ((int64_t)blockIdx.x * NPAD + row) * NPAD + t * kMT;
+        // epilogue warp e: TMEM lane quarter q = warp % 4, accumulators
+        // t = e / 4, e / 4 + nepi / 4, ...
+        const int e = warp - kEpi0, q = warp & 3;
         for (int z = 0; z < my_slices; ++z) {
             int okw = 0;
             if (lane == 0) okw = tc::mbar_wait(done, (uint32_t)z & 1u, abort) ? 1 : 0;
@@ -269,22 +293,33 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const GrParams p) 
             // the accumulator is handed back as soon as it is in registers; the
             // adds into the running partial are fire-and-forget reductions (one
             // writer per address, in program order: deterministic)
-            for (int col = 0; col < ncols; col += 32) {
-                uint32_t v[32];
-                tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(256 * t + col), v);
-                tc::tmem_ld_wait();
-                if (col + 32 >= ncols) {
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(drained);
-                }
-                if (row < p.d) {
+            for (int t = e >> 2; t < ntiles; t += nepi >> 2) {
+                const int row = t * kMT + q * 32 + lane;   // column a of A
+                const int ncols = NPAD - t * kMT;        // columns b = t*128 .. npad-1
+                float* dst = p.part + ((int64_t)blockIdx.x * NPAD + row) * NPAD + t * kMT;
+                // 64 columns per TMEM round trip (ncols is a multiple of 32)
+                for (int col = 0; col < ncols; col += 64) {
+                    uint32_t va[32], vb[32];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(256 * t + col);
+                    const bool two = col + 32 < ncols;
+                    tc::tmem_ld_32x32b_x32(ta, va);
+                    if (two) tc::tmem_ld_32x32b_x32(ta + 32u, vb);
+                    tc::tmem_ld_wait();
+                    if (t + (nepi >> 2) >= ntiles && col + 64 >= ncols) {
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(drained);
+                    }
+                    if (row < p.d) {
 #pragma unroll
-                    for (int k = 0; k < 32; k += 4) {
-                        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + col + k),
-                                     "f"(__uint_as_float(v[k])), "f"(__uint_as_float(v[k + 1])),
-                                     "f"(__uint_as_float(v[k + 2])), "f"(__uint_as_float(v[k + 3]))
-                                     : "memory");
+                        for (int k = 0; k < 64; k += 4) {
+                            const uint32_t* w = k < 32 ? va + k : vb + (k - 32);
+                            if (k < 32 || two)
+                                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + col + k),
+                                             "f"(__uint_as_float(w[0])), "f"(__uint_as_float(w[1])),
+                                             "f"(__uint_as_float(w[2])), "f"(__uint_as_float(w[3]))
+                                             : "memory");
+                        }
                     }
                 }
             }
@@ -336,13 +371,20 @@ bool gram_tc_supported(const lsk_mat* A) {
     return A->kind == LSK_DENSE && A->d >= 1 && A->d <= 256 && smem_bytes((int)((A->d + 31) / 32) * 32) <= kSmemLimit;
 }
 
+template <int NPAD, class SH>
+cudaError_t launch_shape(const GrParams& p, int grid, cudaStream_t st) {
+    const size_t smem = smem_bytes(NPAD);
+    cudaError_t e = allow_dynamic_smem(gram_tc_kernel<NPAD, SH>);
+    if (e != cudaSuccess) return e;
+    LSK_PROF("gram_tc", st) gram_tc_kernel<NPAD, SH><<<grid, SH::kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+// 15 workers and 4 epilogue warps (each reading both accumulators): 640
+// threads, 96 registers a thread (11 workers with 8 epilogue warps measured
+// 1.3% slower at 4M x 256)
 template <int NPAD>
 cudaError_t launch_npad(const GrParams& p, int grid, cudaStream_t st) {
-    const size_t smem = smem_bytes(NPAD);
-    cudaError_t e = allow_dynamic_smem(gram_tc_kernel<NPAD>);
-    if (e != cudaSuccess) return e;
-    LSK_PROF("gram_tc", st) gram_tc_kernel<NPAD><<<grid, kThreads, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_shape<NPAD, GramShape<15, 4>>(p, grid, st);
 }
 
 // one running partial per CTA of the persistent grid
