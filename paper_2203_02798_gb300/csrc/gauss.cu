@@ -20,7 +20,7 @@ constexpr int BK = 16;    // reduction step
 
 // Thread (ty, tx) = (tid / 16, tid % 16) owns rows 4*ty..4*ty+3 and columns
 // {4*tx..4*tx+3} U {64+4*tx..64+4*tx+3} of the block tile.
-__global__ void __launch_bounds__(256) gauss_simt_kernel(
+__global__ void __launch_bounds__(256, 2) gauss_simt_kernel(
     const float* __restrict__ SA, int64_t r, int64_t d, int64_t k, uint32_t k0, uint32_t k1,
     float scale, int bf16, int64_t kc, float* __restrict__ part) {
     __shared__ __align__(16) float Gs[BK][BM];
@@ -42,6 +42,19 @@ __global__ void __launch_bounds__(256) gauss_simt_kernel(
     const int gl_c = tid >> 4;   // 0..15
     const int gl_q = tid & 15;   // rows 4*gl_q .. 4*gl_q+3 of the tile
 
+    // the SA tile of the next step is loaded into registers while the current
+    // one is multiplied (thread: elements tid + 256 t of the BK x BN tile)
+    float sa[(BK * BN) / 256];
+    const auto load_sa = [&](int64_t c0) {
+#pragma unroll
+        for (int t = 0; t < (BK * BN) / 256; ++t) {
+            const int idx = tid + 256 * t;
+            const int kr = idx / BN, cc = idx % BN;
+            const int64_t c = c0 + kr, n = n0 + cc;
+            sa[t] = (c < c_end && n < d) ? __ldg(SA + c * d + n) : 0.f;
+        }
+    };
+    if (c_begin < c_end) load_sa(c_begin);
     for (int64_t c0 = c_begin; c0 < c_end; c0 += BK) {
         {   // G tile (transposed: Gs[c][j])
             const int64_t c = c0 + gl_c;
@@ -68,11 +81,10 @@ __global__ void __launch_bounds__(256) gauss_simt_kernel(
 #pragma unroll
         for (int t = 0; t < (BK * BN) / 256; ++t) {  // SA tile
             const int idx = tid + 256 * t;
-            const int kr = idx / BN, cc = idx % BN;
-            const int64_t c = c0 + kr, n = n0 + cc;
-            Ss[kr][cc] = (c < c_end && n < d) ? __ldg(SA + c * d + n) : 0.f;
+            Ss[idx / BN][idx % BN] = sa[t];
         }
         __syncthreads();
+        if (c0 + BK < c_end) load_sa(c0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             const float4 gv = *reinterpret_cast<const float4*>(&Gs[kk][4 * ty]);
@@ -137,7 +149,10 @@ Plan make_plan(int64_t r, int64_t d, int64_t k, int sm_count) {
     p.tiles_n = (d + BN - 1) / BN;
     p.tiles_m = (k + BM - 1) / BM;
     const int64_t tiles = p.tiles_n * p.tiles_m;
-    int64_t want = (4 * (int64_t)sm_count + tiles - 1) / tiles;
+    // r-slices so that the grid fills whole waves of 2 blocks per SM (a
+    // partial last wave costs a whole block time), at least 128 columns each
+    int64_t want = 2 * (int64_t)sm_count / tiles;
+    if (want > (r + 127) / 128) want = (r + 127) / 128;
     if (want < 1) want = 1;
     int64_t kc = (r + want - 1) / want;
     kc = ((kc + BK - 1) / BK) * BK;

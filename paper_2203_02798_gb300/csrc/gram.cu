@@ -9,9 +9,10 @@
 //         FP64 partials of the chunks are added in a fixed order.
 //  CSR:   a block owns a slice of rows of C held in shared memory (the
 //         "private d x d" of Alg. 7, sliced so it fits) and a range of rows
-//         of A; each thread runs Alg. 5 on its rows (outer products of the
-//         row's nonzeros, shared-memory atomics), the FP32 slices of all
-//         blocks are then summed in FP64 in a fixed order.
+//         of A; each thread runs Alg. 5 on its rows (the upper-triangle
+//         outer products of the row's nonzeros, shared-memory atomics), the
+//         FP32 slices of all blocks are then summed in FP64 in a fixed order
+//         and mirrored.
 #include "lsk_internal.cuh"
 
 namespace {
@@ -93,37 +94,59 @@ __global__ void __launch_bounds__(256) gram_dense_kernel(const float* __restrict
         for (int b = 0; b < 4; ++b) P[(4 * ty + a) * GT + 4 * tx + b] = acc64[a][b] + (double)acc[a][b];
 }
 
+// C[a][b] = C[b][a] = alpha sum_z part[z][tile(a, b)][w] + beta C (a <= b):
+// a block takes 32 consecutive entries; thread (g, x) adds the chunks z = g,
+// g + 8, ... of entry x, then the 8 group sums are added in order
+// (deterministic).
 template <typename OutT>
-__global__ void gram_dense_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
-                                         int64_t d, double alpha, double beta,
-                                         OutT* __restrict__ C) {
+__global__ void __launch_bounds__(256) gram_dense_reduce_kernel(const double* __restrict__ part, int64_t nchunks,
+                                                                 int64_t d, double alpha, double beta,
+                                                                 OutT* __restrict__ C) {
+    __shared__ double acc[8][33];
     const int nt = (int)((d + GT - 1) / GT);
     const int ntiles = nt * (nt + 1) / 2;
-    const int64_t len = d * d;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-        int64_t a = e / d, b = e % d;
-        if (a > b) {
-            const int64_t t = a;
-            a = b;
-            b = t;
-        }
+    const int x = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + x;
+    const int64_t a = e / d, b = e % d;
+    const bool upper = e < d * d && a <= b;
+    double s = 0.0;
+    if (upper) {
         const int ta = (int)(a / GT), tb = (int)(b / GT);
         const int tile = ta * nt - ta * (ta - 1) / 2 + (tb - ta);
-        const int64_t w = (a % GT) * GT + (b % GT);
-        double s = 0.0;
-        for (int64_t z = 0; z < nchunks; ++z) s += part[(z * ntiles + tile) * GT * GT + w];
-        double v = alpha * s;
-        if (beta != 0.0) v += beta * (double)C[e];
-        C[e] = (OutT)v;
+        const double* src = part + (int64_t)tile * GT * GT + (a % GT) * GT + (b % GT);
+        const int64_t zs = (int64_t)ntiles * GT * GT;   // one chunk
+        int64_t z = g;
+        for (; z + 24 < nchunks; z += 32) {   // four loads in flight
+            const double x0 = src[z * zs], x1 = src[(z + 8) * zs], x2 = src[(z + 16) * zs], x3 = src[(z + 24) * zs];
+            s += x0;
+            s += x1;
+            s += x2;
+            s += x3;
+        }
+        for (; z < nchunks; z += 8) s += src[z * zs];
+    }
+    acc[g][x] = s;
+    __syncthreads();
+    if (g == 0 && upper) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += acc[k][x];
+        const double ab = alpha * t;
+        C[a * d + b] = (OutT)(beta != 0.0 ? ab + beta * (double)C[a * d + b] : ab);
+        if (a != b) C[b * d + a] = (OutT)(beta != 0.0 ? ab + beta * (double)C[b * d + a] : ab);
     }
 }
 
 // ---- CSR ------------------------------------------------------------------
-__global__ void gram_csr_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
-                                const int64_t* __restrict__ I, int64_t n, int64_t nnz, int64_t d,
-                                int64_t slice_rows, int64_t rows_per, float* __restrict__ part,
-                                int* flag) {
+// Alg. 5 on the rows of one block: for each pair of nonzeros p <= q of a row
+// (positions in the row), v_p v_q is added to the upper-triangle entry
+// (min(j_p, j_q), max(j_p, j_q)) of the block's shared-memory slice -- twice
+// when p < q share a column, once on the diagonal -- so each off-diagonal
+// product is formed once.  1024 threads a block (one block per SM: the slice
+// is up to 192 KB), one row a thread.
+__global__ void __launch_bounds__(1024) gram_csr_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
+                                                       const int64_t* __restrict__ I, int64_t n, int64_t nnz,
+                                                       int64_t d, int64_t slice_rows, int64_t rows_per,
+                                                       float* __restrict__ part, int* flag) {
     extern __shared__ float S[];
     const int64_t j0 = (int64_t)blockIdx.y * slice_rows;
     const int64_t j1 = min(d, j0 + slice_rows);
@@ -139,19 +162,20 @@ __global__ void gram_csr_kernel(const float* __restrict__ V, const int32_t* __re
             bad = true;
             continue;
         }
-        for (int64_t p = k0; p < k1; ++p) {
-            const int32_t jp = __ldg(J + p);
+        for (int64_t pp = k0; pp < k1; ++pp) {
+            const int32_t jp = __ldg(J + pp);
             if (jp < 0 || jp >= d) {
                 bad = true;
                 continue;
             }
-            if (jp < j0 || jp >= j1) continue;
-            const float vp = __ldg(V + p);
-            float* Srow = S + (jp - j0) * d;
-            for (int64_t q = k0; q < k1; ++q) {
-                const int32_t jq = __ldg(J + q);
+            const float vp = __ldg(V + pp);
+            for (int64_t qq = pp; qq < k1; ++qq) {
+                const int32_t jq = __ldg(J + qq);
                 if (jq < 0 || jq >= d) continue;
-                atomicAdd(&Srow[jq], vp * __ldg(V + q));
+                const int32_t a = jp < jq ? jp : jq, b = jp < jq ? jq : jp;
+                if (a < j0 || a >= j1) continue;
+                const float w = vp * __ldg(V + qq);
+                atomicAdd(&S[(a - j0) * d + b], (qq != pp && jp == jq) ? 2.f * w : w);
             }
         }
     }
@@ -161,17 +185,41 @@ __global__ void gram_csr_kernel(const float* __restrict__ V, const int32_t* __re
     for (int64_t e = threadIdx.x; e < sl * d; e += blockDim.x) P[e] = S[e];
 }
 
+// C[a][b] = C[b][a] = alpha sum_z part[z][a][b] + beta C (a <= b): a block
+// takes 32 consecutive entries; thread (g, x) adds the partials z = g, g + 8,
+// ... of entry x in FP64, then the 8 group sums are added in order
+// (deterministic).
 template <typename OutT>
-__global__ void gram_csr_reduce_kernel(const float* __restrict__ part, int64_t nblocks, int64_t d,
-                                       double alpha, double beta, OutT* __restrict__ C) {
+__global__ void __launch_bounds__(256) gram_csr_reduce_kernel(const float* __restrict__ part, int64_t nblocks,
+                                                               int64_t d, double alpha, double beta,
+                                                               OutT* __restrict__ C) {
+    __shared__ double acc[8][33];
+    const int x = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int64_t len = d * d;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-        double s = 0.0;
-        for (int64_t z = 0; z < nblocks; ++z) s += (double)part[z * len + e];
-        double v = alpha * s;
-        if (beta != 0.0) v += beta * (double)C[e];
-        C[e] = (OutT)v;
+    const int64_t e = (int64_t)blockIdx.x * 32 + x;
+    const int64_t a = e / d, b = e % d;
+    const bool upper = e < len && a <= b;
+    double s = 0.0;
+    if (upper) {
+        int64_t z = g;
+        for (; z + 24 < nblocks; z += 32) {   // four loads in flight
+            const float x0 = part[z * len + e], x1 = part[(z + 8) * len + e];
+            const float x2 = part[(z + 16) * len + e], x3 = part[(z + 24) * len + e];
+            s += (double)x0;
+            s += (double)x1;
+            s += (double)x2;
+            s += (double)x3;
+        }
+        for (; z < nblocks; z += 8) s += (double)part[z * len + e];
+    }
+    acc[g][x] = s;
+    __syncthreads();
+    if (g == 0 && upper) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += acc[k][x];
+        const double ab = alpha * t;
+        C[a * d + b] = (OutT)(beta != 0.0 ? ab + beta * (double)C[a * d + b] : ab);
+        if (a != b) C[b * d + a] = (OutT)(beta != 0.0 ? ab + beta * (double)C[b * d + a] : ab);
     }
 }
 
@@ -204,7 +252,8 @@ CsrPlan csr_plan(int64_t n, int64_t d, int sm_count) {
     if (p.slice_rows > d) p.slice_rows = d;
     if (p.slice_rows < 1) p.slice_rows = 1;
     p.nslices = (d + p.slice_rows - 1) / p.slice_rows;
-    int64_t nb = (2 * (int64_t)sm_count + p.nslices - 1) / p.nslices;
+    // one 1024-thread block per SM
+    int64_t nb = ((int64_t)sm_count + p.nslices - 1) / p.nslices;
     if (nb < 1) nb = 1;
     p.rows_per = (n + nb - 1) / nb;
     if (p.rows_per < 1) p.rows_per = 1;
@@ -230,14 +279,13 @@ cudaError_t gram_launch_t(const lsk_mat* A, double alpha, double beta, OutT* C, 
                           int sm_count, cudaStream_t st) {
     const int64_t n = A->n, d = A->d;
     const int64_t len = d * d;
-    int64_t rg = (len + 255) / 256;
-    if (rg > 8 * (int64_t)sm_count) rg = 8 * (int64_t)sm_count;
     if (A->kind == LSK_DENSE) {
         const DensePlan p = dense_plan(n, d, sm_count);
         double* part = (double*)ws;
         dim3 grid((unsigned)p.ntiles, (unsigned)p.nchunks);
         LSK_PROF("gram_dense", st) gram_dense_kernel<<<grid, 256, 0, st>>>((const float*)A->values, A->ld, n, d, p.rows_per, part);
-        LSK_PROF("gram_reduce", st) gram_dense_reduce_kernel<OutT><<<(unsigned)rg, 256, 0, st>>>(part, p.nchunks, d, alpha, beta, C);
+        LSK_PROF("gram_reduce", st) gram_dense_reduce_kernel<OutT>
+            <<<(unsigned)((len + 31) / 32), 256, 0, st>>>(part, p.nchunks, d, alpha, beta, C);
     } else {
         const CsrPlan p = csr_plan(n, d, sm_count);
         if (p.smem > 48 * 1024) {
@@ -246,9 +294,11 @@ cudaError_t gram_launch_t(const lsk_mat* A, double alpha, double beta, OutT* C, 
         }
         float* part = (float*)ws;
         dim3 grid((unsigned)p.nblocks, (unsigned)p.nslices);
-        LSK_PROF("gram_csr", st) gram_csr_kernel<<<grid, 256, p.smem, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
-                                                   A->nnz, d, p.slice_rows, p.rows_per, part, flag);
-        LSK_PROF("gram_reduce", st) gram_csr_reduce_kernel<OutT><<<(unsigned)rg, 256, 0, st>>>(part, p.nblocks, d, alpha, beta, C);
+        LSK_PROF("gram_csr", st) gram_csr_kernel<<<grid, 1024, p.smem, st>>>((const float*)A->values, A->colidx,
+                                                                            A->rowptr, n, A->nnz, d, p.slice_rows,
+                                                                            p.rows_per, part, flag);
+        LSK_PROF("gram_reduce", st) gram_csr_reduce_kernel<OutT>
+            <<<(unsigned)((len + 31) / 32), 256, 0, st>>>(part, p.nblocks, d, alpha, beta, C);
     }
     return cudaGetLastError();
 }
