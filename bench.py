@@ -273,7 +273,14 @@ def main():
             gms, _, _ = timed(lambda: lsk.gram(A, C=C, prec=prec, ctx=ctx), steps)
             gms /= steps
             err = float(torch.linalg.norm(C.double() - ref) / torch.linalg.norm(ref))
-            out[prec] = {"ms": gms, "GB/s": N_ROWS * D * 4 / (gms * 1e-3) / 1e9, "rel_fro_err": err}
+            gbs = N_ROWS * D * 4 / (gms * 1e-3) / 1e9
+            out[prec] = {"ms": gms, "GB/s": gbs, "rel_fro_err": err,
+                         "algorithmic_bytes": N_ROWS * D * 4, "frac_of_measured_hbm": gbs / hbm}
+            if prec == "bf16":
+                # BF16x3 products of the upper triangle: 3 n d (d + 1) flops
+                tf = 3 * N_ROWS * D * (D + 1) / (gms * 1e-3) / 1e12
+                out[prec].update({"TFLOP/s": tf, "frac_of_measured_bf16": tf / bf16_peak,
+                                  "traffic": measured_traffic("gram_tc", N_ROWS)})
         del ref
         return out
 
