@@ -145,12 +145,12 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint3
     if (len <= 0) return cudaSuccess;
     const int64_t tiles = (len + kScanTile - 1) / kScanTile;
     uint32_t* sums = tmp;
-    scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, out, sums, len);
+    LSK_PROF("cs_scan", st) scan_tiles_kernel<<<(unsigned)tiles, kScanBlock, 0, st>>>(in, out, sums, len);
     if (tiles > 1) {
         uint32_t* sums_off = tmp + tiles + 32;
         cudaError_t e = exclusive_scan(sums, sums_off, tiles, sums_off + tiles + 32, st);
         if (e != cudaSuccess) return e;
-        scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(out, sums_off, len);
+        LSK_PROF("cs_scan", st) scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(out, sums_off, len);
     }
     return cudaGetLastError();
 }
@@ -434,9 +434,9 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
     if (r <= 16384) {
         LSK_PROF("cs_scan", st) scan_one_block_kernel<<<1, 1024, 0, st>>>(cnt, off, r);
     } else {
-        LSK_PROF("cs_scan", st) e = exclusive_scan(cnt, off, r, tmp, st);
+        e = exclusive_scan(cnt, off, r, tmp, st);   // its launches are profiled one by one
         if (e != cudaSuccess) return e;
-        write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
+        LSK_PROF("cs_scan", st) write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
     }
     if (n > 0) {
         e = cudaMemcpyAsync(cursor, off, (size_t)r * 4, cudaMemcpyDeviceToDevice, st);

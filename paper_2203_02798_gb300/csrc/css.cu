@@ -151,19 +151,19 @@ cudaError_t pivchol_launch(const double* C, int64_t d, int64_t c, double rcond, 
 
 cudaError_t gather_sub_gram_launch(const double* C, int64_t d, const int32_t* cols, int64_t c, double* Csub,
                                    cudaStream_t st) {
-    gather_sub_gram_kernel<<<grid_of(c * c), 256, 0, st>>>(C, d, cols, c, Csub);
+    LSK_PROF("css_gather", st) gather_sub_gram_kernel<<<grid_of(c * c), 256, 0, st>>>(C, d, cols, c, Csub);
     return cudaGetLastError();
 }
 
 cudaError_t gather_cols_launch(const float* B, int64_t rows, int64_t d, const int32_t* cols, int64_t c, float* Bk,
                                cudaStream_t st) {
-    gather_cols_kernel<<<grid_of(rows * c), 256, 0, st>>>(B, rows, d, cols, c, Bk);
+    LSK_PROF("css_gather", st) gather_cols_kernel<<<grid_of(rows * c), 256, 0, st>>>(B, rows, d, cols, c, Bk);
     return cudaGetLastError();
 }
 
 cudaError_t embed_rows_launch(const float* X, int64_t c, const int32_t* cols, int64_t d, float* Bf, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(Bf, 0, (size_t)d * c * 4, st);
     if (e != cudaSuccess) return e;
-    embed_rows_kernel<<<grid_of(c * c), 256, 0, st>>>(X, c, cols, d, Bf);
+    LSK_PROF("css_gather", st) embed_rows_kernel<<<grid_of(c * c), 256, 0, st>>>(X, c, cols, d, Bf);
     return cudaGetLastError();
 }

@@ -555,7 +555,7 @@ cudaError_t atr64_launch(const lsk_mat* A, const double* b, const double* x, dou
     else
         LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr,
                                                                                         n, A->nnz, d, b, x, u, qpart, sspart, flag);
-    sum_qpart_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(qpart, nb, d, atr);
+    LSK_PROF("lsq_small", st) sum_qpart_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(qpart, nb, d, atr);
     return cudaGetLastError();
 }
 
@@ -611,7 +611,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         else
             LSK_PROF("lsq_resid64", st) resid64_csr_kernel<<<nb, kPassThreads, sh64, st>>>((const float*)A->values, A->colidx, A->rowptr, n,
                                                                A->nnz, d, b, x, u, qpart64, sspart, ctx->flag);
-        cg_start_kernel<<<1, 256, 0, st>>>(qpart64, nb, d, Rinv64, t == 0 ? 1 : 0, S, cg_s, cg_p, y, atr, p);
+        LSK_PROF("lsq_small", st) cg_start_kernel<<<1, 256, 0, st>>>(qpart64, nb, d, Rinv64, t == 0 ? 1 : 0, S, cg_s, cg_p, y, atr, p);
         e = cudaMemcpyAsync(&h, S, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return LSK_ERR_CUDA;
@@ -630,7 +630,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         int it = 0;
         while (!h.done && it < o->max_iter) {
             lsqr_pass(A, nb, sh32, p, S, u, qpart32, sspart, st);
-            cg_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv64, S, cg_s, cg_p, y, qtmp,
+            LSK_PROF("lsq_small", st) cg_step_kernel<<<1, 1024, 0, st>>>(qpart32, sspart, nb, d, Rinv64, S, cg_s, cg_p, y, qtmp,
                                                stop_rel, p);
             ++it;
             if ((it & 3) == 0 || it >= o->max_iter) {   // stopping test every 4 iterations
@@ -643,7 +643,7 @@ int lsq_run(lsk_ctx* ctx, const lsk_mat* A, const double* b, double* x, const ls
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return LSK_ERR_CUDA;
         total_it += h.it;
-        update_x_kernel<<<1, 256, 0, st>>>(Rinv64, d, y, x);
+        LSK_PROF("lsq_small", st) update_x_kernel<<<1, 256, 0, st>>>(Rinv64, d, y, x);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return LSK_ERR_CUDA;

@@ -394,7 +394,7 @@ cudaError_t qr_from_gram_launch(double* C, int64_t d, double* R, double* Rinv, f
         if (T > 0) LSK_PROF("qr_cholesky", st) chol_update_kernel<<<(unsigned)(T * (T + 1) / 2), NB * NB, 0, st>>>(C, d, K);
     }
     LSK_PROF("qr_cholesky", st) copy_diag_kernel<<<(unsigned)nbk, NB * NB, 0, st>>>(C, d, Ldiag);
-    rank_check_kernel<<<1, 256, 0, st>>>(C, d, flag);
+    LSK_PROF("qr_rank", st) rank_check_kernel<<<1, 256, 0, st>>>(C, d, flag);
     const unsigned tg = (unsigned)((d * 32 + 127) / 128);
     LSK_PROF("qr_trinv", st) trinv_kernel<32><<<tg, 128, 0, st>>>(C, d, Rinv, Rinv32, R);
     return cudaGetLastError();

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(1024) seminormal_kernel(const double* __restri
 
 cudaError_t seminormal_launch(const double* c, const double* Rinv64, int64_t d, int add, double* x, cudaStream_t st) {
     if (d > 1024) return cudaErrorInvalidValue;
-    seminormal_kernel<<<1, 1024, 0, st>>>(c, Rinv64, (int)d, add, x);
+    LSK_PROF("solve_small", st) seminormal_kernel<<<1, 1024, 0, st>>>(c, Rinv64, (int)d, add, x);
     return cudaGetLastError();
 }
 
@@ -147,7 +147,7 @@ cudaError_t solve_launch(const lsk_mat* A, const double* b, int64_t r, int64_t k
         const float scale = (float)(1.0 / sqrt((double)k));
         LSK_PROF("solve_gauss_b", st) gauss_vec_kernel<<<(unsigned)gblk, 128, 0, st>>>(
             Sb, r, (int)k, k0, k1, scale, prec == LSK_PREC_BF16 ? 1 : 0, gpart);
-        sum_parts_kernel<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(gpart, (int)gblk, (int)k, bt);
+        LSK_PROF("solve_small", st) sum_parts_kernel<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(gpart, (int)gblk, (int)k, bt);
     } else {
         e = cudaMemcpyAsync(bt, Sb, (size_t)r * 8, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
@@ -156,12 +156,12 @@ cudaError_t solve_launch(const lsk_mat* A, const double* b, int64_t r, int64_t k
     for (int step = 0; step < 2; ++step) {
         const double* v = bt;
         if (step == 1) {
-            residual_kernel<<<grid_for(rows, 256, sm_count), 256, 0, st>>>(At, rows, (int)d, bt, x, res);
+            LSK_PROF("solve_small", st) residual_kernel<<<grid_for(rows, 256, sm_count), 256, 0, st>>>(At, rows, (int)d, bt, x, res);
             v = res;
         }
         LSK_PROF("solve_atv", st) atv_kernel<<<(unsigned)ablk, 256, 0, st>>>(At, rows, (int)d, v, apart);
-        sum_parts_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(apart, (int)ablk, (int)d, c);
-        seminormal_kernel<<<1, 1024, 0, st>>>(c, Rinv64, (int)d, step, x);
+        LSK_PROF("solve_small", st) sum_parts_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(apart, (int)ablk, (int)d, c);
+        LSK_PROF("solve_small", st) seminormal_kernel<<<1, 1024, 0, st>>>(c, Rinv64, (int)d, step, x);
     }
     return cudaGetLastError();
 }
