@@ -635,7 +635,7 @@ def run_served(args, lsk, torch):
         p = reqs[s].payload
         server.solve(s, p["A"], p["b"], **p["opts"])
     done, rejected = server.run(reqs, hbm_budget=150 * 10**9)
-    summ = latency_summary(done)
+    summ = latency_summary(done, slots=server.slots)
     etas = [c.result[1]["eta"] for c in done if c.error is None]
     errors = sorted({c.error for c in done if c.error is not None})
     summ.update({"workload": "served_lsq_poisson200", "requests": len(reqs), "rejected": len(rejected),

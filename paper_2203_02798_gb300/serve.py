@@ -133,16 +133,27 @@ def run_trace(requests, execute, slots, hbm_budget, time_scale=1.0, clock=time.p
     return done, sched.rejected
 
 
-def latency_summary(completions):
-    lat = np.array([c.latency for c in completions if c.error is None])
+def latency_summary(completions, slots=None):
+    """Latency percentiles, split into the wait for admission (arrival to
+    start: queueing behind busy slots or the HBM budget) and the service time
+    (start to finish: the solve, sharing the GPU with the other slots)."""
+    ok = [c for c in completions if c.error is None]
+    lat = np.array([c.latency for c in ok])
     if lat.size == 0:
         return {"count": 0}
+    queue = np.array([c.start - c.arrival for c in ok])
+    service = np.array([c.finish - c.start for c in ok])
     span = max(c.finish for c in completions) - min(c.arrival for c in completions)
-    return {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "max_ms": float(lat.max() * 1e3), "span_s": float(span),
-            "throughput_rps": float(lat.size / span) if span > 0 else None,
-            "errors": sum(1 for c in completions if c.error is not None)}
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3)
+    out = {"count": int(lat.size), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+           "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3), "span_s": float(span),
+           "throughput_rps": float(lat.size / span) if span > 0 else None,
+           "errors": sum(1 for c in completions if c.error is not None),
+           "queue_p50_ms": pct(queue, 50), "queue_p99_ms": pct(queue, 99),
+           "service_p50_ms": pct(service, 50), "service_p99_ms": pct(service, 99)}
+    if slots and span > 0:
+        out["slot_busy_frac"] = float(service.sum() / (span * slots))   # mean fraction of the slots in use
+    return out
 
 
 class Server:

@@ -58,8 +58,15 @@ def test_run_trace_overlap_and_limits():
     # continuous batching: some request started while an earlier one was running
     by_id = {c.rid: c for c in done}
     assert any(by_id[i + 1].start < by_id[i].finish for i in range(23))
-    summ = latency_summary(done)
+    summ = latency_summary(done, slots=3)
     assert summ["count"] == 24 and summ["p99_ms"] >= summ["p50_ms"] > 0
+    # latency = admission wait + service, request by request
+    for c in done:
+        assert c.start >= c.arrival - 1e-9 and c.finish >= c.start
+    assert summ["queue_p99_ms"] >= summ["queue_p50_ms"] >= 0
+    assert summ["service_p99_ms"] >= summ["service_p50_ms"] > 0
+    assert summ["max_ms"] <= 1e3 * max(c.start - c.arrival for c in done) + 1e3 * max(c.finish - c.start for c in done) + 1e-6
+    assert 0 < summ["slot_busy_frac"] <= 1.0
 
 
 def test_run_trace_reports_errors():
