@@ -4,7 +4,8 @@
 // takes the mixed-precision path (d <= 256) are run in three phases:
 //   1. CountSketch of each problem on the worker streams (memory-bound
 //      passes over A, concurrent across problems), into a batch arena that
-//      holds every such problem's sketch;
+//      holds every such problem's sketch -- compacted to its non-empty
+//      buckets where n < 4r, so that phase 2 draws G only for those columns;
 //   2. the Gaussian stage and the whole R^-1 computation as grouped
 //      launches: one grid per stage over all problems (qr.cu, qr_mixed.cu,
 //      gauss_tc.cu), so the latency-bound small stages of hundreds of
@@ -66,6 +67,7 @@ struct LskBatch {
     std::vector<char> grouped;       // per item: takes the grouped path
     std::vector<int> wave;           // per grouped item: its wave
     std::vector<float*> SA, Rinv32;  // per grouped item: its sketch and FP32 R^-1 in the arena
+    std::vector<uint32_t*> cidx;     // per compacted item: the buckets of its sketch's rows, then their count
     int waves = 0;
     std::vector<GaussGroup> gg;      // per wave
     std::vector<QrGroup> qg;
@@ -78,6 +80,12 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
     for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
     return h;
 }
+
+// A grouped problem's sketch is compacted to its non-empty buckets when more
+// than ~2% of the r buckets are expected empty (e^(-n/r) > e^-4): its
+// Gaussian stage then draws G only for the columns that meet a row of A.
+bool compacts(const lsk_batch_item& it) { return it.A.n < 4 * it.r; }
+int64_t sketch_rows(const lsk_batch_item& it) { return compacts(it) ? std::min<int64_t>(it.r, it.A.n) : it.r; }
 
 double cost_of(const lsk_batch_item& it) {
     const lsk_mat& A = it.A;
@@ -175,8 +183,11 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
             const lsk_batch_item& it = items[i];
             cudaError_t er = cudaSuccess;
             if (b->grouped[i]) {
-                if (b->wave[i] == w)
-                    er = cs_launch(&it.A, it.r, it.seed, b->SA[i], b->ws[s], ctx->flag, ctx->sm_count, st);
+                if (b->wave[i] == w) {
+                    uint32_t* ci = b->cidx[i];
+                    er = cs_launch(&it.A, it.r, it.seed, b->SA[i], b->ws[s], ctx->flag, ctx->sm_count, st, 0, false,
+                                   ci, ci ? ci + sketch_rows(it) : nullptr);
+                }
             } else if (w == 0) {
                 er = leverage_pipeline(&it.A, it.r, it.k, it.seed, prec, it.ell, nullptr, b->ws[s], ctx->flag,
                                        ctx->sm_count, st);
@@ -242,13 +253,15 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     b->grouped.assign(count, 0);
     b->SA.assign(count, nullptr);
     b->Rinv32.assign(count, nullptr);
+    b->cidx.assign(count, nullptr);
     size_t bytes = 0;
     for (int i = 0; i < count; ++i) {
         if (!allow || !groupable(items[i], prec)) continue;
-        const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
+        const int64_t rs = sketch_rows(items[i]), k = items[i].k, d = items[i].A.d;
         b->grouped[i] = 1;
-        bytes += ws_round((size_t)r * d * 4) + ws_round((size_t)k * d * 4) + gauss_group_part_bytes(r, d, k, tune.slice) +
-                 ws_round(qr_workspace_bytes(k, d)) + ws_round((size_t)d * d * 4);
+        bytes += ws_round((size_t)rs * d * 4) + ws_round((size_t)k * d * 4) +
+                 gauss_group_part_bytes(rs, d, k, tune.slice) + ws_round(qr_workspace_bytes(k, d)) +
+                 ws_round((size_t)d * d * 4) + (compacts(items[i]) ? ws_round((size_t)(rs + 1) * 4) : 0);
     }
     if (bytes > b->arena_bytes) {
         cudaStreamSynchronize(ctx->stream);
@@ -276,15 +289,22 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     WsCarver wc{(char*)b->arena, 0};
     for (int i = 0; i < count; ++i) {
         if (!b->grouped[i]) continue;
-        const int64_t r = items[i].r, k = items[i].k, d = items[i].A.d;
-        float* SA = wc.take<float>((size_t)r * d);
+        const int64_t rs = sketch_rows(items[i]), k = items[i].k, d = items[i].A.d;
+        float* SA = wc.take<float>((size_t)rs * d);
         float* GSA = wc.take<float>((size_t)k * d);
-        float* part = (float*)wc.take<char>(gauss_group_part_bytes(r, d, k, tune.slice));
+        float* part = (float*)wc.take<char>(gauss_group_part_bytes(rs, d, k, tune.slice));
         void* qws = wc.take<char>(qr_workspace_bytes(k, d));
         float* Ri32 = wc.take<float>((size_t)d * d);
+        uint32_t* cidx = compacts(items[i]) ? wc.take<uint32_t>((size_t)rs + 1) : nullptr;
         b->SA[i] = SA;
         b->Rinv32[i] = Ri32;
-        gj[b->wave[i]].push_back(GaussJob{SA, r, d, k, items[i].seed, GSA, part, tune.slice});
+        b->cidx[i] = cidx;
+        GaussJob gjob{SA, rs, d, k, items[i].seed, GSA, part, tune.slice};
+        if (cidx) {
+            gjob.idx = cidx;
+            gjob.rcount = cidx + rs;
+        }
+        gj[b->wave[i]].push_back(gjob);
         QrJob q{};
         qr_group_job(q, GSA, k, d, qws, nullptr, Ri32, ctx->flag);
         qj[b->wave[i]].push_back(q);

@@ -256,7 +256,7 @@ template <int VEC, int U>
 __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
     const float* __restrict__ A, int64_t lda, int64_t d, uint32_t r,
     const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm, float* __restrict__ SA, int P,
-    int accumulate) {
+    int accumulate, const uint32_t* __restrict__ cpos) {
     using V = typename VecT<VEC>::T;
     constexpr int kCols = 32 * VEC * U;  // columns per pass
     constexpr int kBatch = (VEC * U >= 8) ? 8 : 4;   // rows of loads in flight per warp
@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
         const uint32_t s0 = off[b], len = off[b + 1] - s0;
         const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
         const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
-        if ((P > 1 || accumulate) && s == e) continue;
+        if ((P > 1 || accumulate || cpos) && s == e) continue;
+        const int64_t orow = cpos ? (int64_t)cpos[b] : b;   // compacted: the bucket's rank among the non-empty
         for (int64_t c0 = 0; c0 < d; c0 += kCols) {
             V acc[U];
 #pragma unroll
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(256) cs_dense_gather_kernel(
                         if (colok[u]) vadd(acc[u], ldg_stream<VEC>(row + (u * 32 + lane) * VEC), sg);
                 }
             }
-            float* out = SA + (int64_t)b * d + c0;
+            float* out = SA + orow * d + c0;
             if (P == 1 && !accumulate) {
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -334,7 +335,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
                                      const int64_t* __restrict__ I, int64_t nnz, int64_t d,
                                      uint32_t r, const uint32_t* __restrict__ off,
                                      const uint32_t* __restrict__ perm, float* __restrict__ SA,
-                                     int* flag, int P, int accumulate) {
+                                     int* flag, int P, int accumulate, const uint32_t* __restrict__ cpos) {
     extern __shared__ float srow[];
     const int lane = threadIdx.x & 31;
     float* acc = srow + (int64_t)(threadIdx.x >> 5) * d;
@@ -347,7 +348,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
         const uint32_t s0 = off[b], len = off[b + 1] - s0;
         const uint32_t s = s0 + (uint32_t)(((uint64_t)len * part) / P);
         const uint32_t e = s0 + (uint32_t)(((uint64_t)len * (part + 1)) / P);
-        if ((P > 1 || accumulate) && s == e) continue;
+        if ((P > 1 || accumulate || cpos) && s == e) continue;
         for (int64_t c = lane; c < d; c += 32) acc[c] = 0.0f;
         __syncwarp();
         bool bad = false;
@@ -371,7 +372,7 @@ __global__ void cs_csr_gather_kernel(const float* __restrict__ V, const int32_t*
         }
         if (bad) set_flag(flag, LSK_FLAG_BAD_CSR);
         __syncwarp();
-        float* out = SA + (int64_t)b * d;
+        float* out = SA + (cpos ? (int64_t)cpos[b] : b) * d;
         if (P == 1 && !accumulate) {
             for (int64_t c = lane; c < d; c += 32) out[c] = acc[c];
         } else {
@@ -393,6 +394,58 @@ __global__ void cs_hash_debug_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_
     }
 }
 
+// Compaction of the sketch's rows to the non-empty buckets (off[b + 1] >
+// off[b]), in bucket order: cpos[b] = the number of non-empty buckets before b,
+// cidx[cpos[b]] = b for each non-empty b, *ccount = their number.  One block
+// of 1024 threads, rounds of 4096 buckets (4 consecutive a thread) with the
+// running total carried across rounds.
+__global__ void __launch_bounds__(1024) cs_compact_kernel(const uint32_t* __restrict__ off, int64_t r,
+                                                          uint32_t* __restrict__ cpos, uint32_t* __restrict__ cidx,
+                                                          uint32_t* __restrict__ ccount) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t r0 = 0; r0 < r; r0 += 4096) {
+        const int64_t b0 = r0 + 4 * (int64_t)threadIdx.x;
+        uint32_t f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = (b0 + q < r && off[b0 + q + 1] > off[b0 + q]) ? 1u : 0u;
+        const uint32_t run = f[0] + f[1] + f[2] + f[3];
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t v = wsum[lane], vi = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+                if (lane >= o) vi += y;
+            }
+            wsum[lane] = vi - v;   // exclusive warp offsets
+            if (lane == 31) carry_s = vi;
+        }
+        __syncthreads();
+        uint32_t pos = carry + wsum[w] + incl - run;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (b0 + q < r) {
+                cpos[b0 + q] = pos;
+                if (f[q]) cidx[pos] = (uint32_t)(b0 + q);
+            }
+            pos += f[q];
+        }
+        carry += carry_s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ccount = carry;
+}
+
 inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 8) {
     int64_t g = (items + threads - 1) / threads;
     const int64_t cap = (int64_t)sm_count * per_sm;
@@ -404,7 +457,7 @@ inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 
 }  // namespace
 
 size_t cs_workspace_bytes(int64_t n, int64_t r) {
-    return ws_round((size_t)(r + 1) * 4) * 3 + ws_round((size_t)(n > 0 ? n : 1) * 4) +
+    return ws_round((size_t)(r + 1) * 4) * 4 + ws_round((size_t)(n > 0 ? n : 1) * 4) +
            ws_round(scan_tmp_words(r) * 4) + 4096;
 }
 
@@ -449,17 +502,31 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
 }
 
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
-                      int sm_count, cudaStream_t st, uint64_t row0, bool accumulate) {
+                      int sm_count, cudaStream_t st, uint64_t row0, bool accumulate, uint32_t* cidx,
+                      uint32_t* ccount) {
     const int64_t n = A->n, d = A->d;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
     cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0);
     if (e != cudaSuccess) return e;
+    const bool compact = cidx != nullptr && ccount != nullptr && !accumulate;
+    uint32_t* cpos = nullptr;
+    if (compact) {
+        // after cs_prep_launch's carve: cnt, off, cursor, perm, scan tmp
+        WsCarver wc{(char*)ws, 0};
+        wc.take<uint32_t>(r + 1);
+        wc.take<uint32_t>(r + 1);
+        wc.take<uint32_t>(r + 1);
+        wc.take<uint32_t>(n > 0 ? n : 1);
+        wc.take<uint32_t>(scan_tmp_words(r));
+        cpos = wc.take<uint32_t>(r + 1);
+        LSK_PROF("cs_compact", st) cs_compact_kernel<<<1, 1024, 0, st>>>(off, r, cpos, cidx, ccount);
+    }
 
     // parts per bucket: enough warps to stream A when there are few buckets,
-    // while each part keeps several rows
+    // while each part keeps several rows (one part a bucket when compacting)
     int P = 1;
-    while (P < 32 && r * P < 16384 && n >= (int64_t)r * P * 8) P *= 2;
+    while (!compact && P < 32 && r * P < 16384 && n >= (int64_t)r * P * 8) P *= 2;
     if (P > 1 && !accumulate && (e = cudaMemsetAsync(SA, 0, (size_t)r * d * 4, st)) != cudaSuccess) return e;
     const int acc = accumulate ? 1 : 0;   // add into SA (the parts add atomically either way)
     const int64_t warps_needed = r * P;
@@ -470,14 +537,14 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         const unsigned grid = grid_for(warps_needed * 32, 256, sm_count, 8);
         if (vec4) {
             if (d <= 128)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc, cpos);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<4, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc, cpos);
         } else {
             if (d <= 32)
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 1><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc, cpos);
             else
-                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc);
+                LSK_PROF("cs_dense_gather", st) cs_dense_gather_kernel<1, 2><<<grid, 256, 0, st>>>(Av, A->ld, d, (uint32_t)r, off, perm, SA, P, acc, cpos);
         }
     } else {
         // shared-memory row per warp: pick warps per block to fit 200 KB
@@ -495,7 +562,7 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         if (g > cap) g = cap;
         if (g < 1) g = 1;
         LSK_PROF("cs_csr_gather", st) cs_csr_gather_kernel<<<(unsigned)g, threads, smem, st>>>(
-            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P, acc);
+            (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P, acc, cpos);
     }
     return cudaGetLastError();
 }

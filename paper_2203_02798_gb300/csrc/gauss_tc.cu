@@ -46,6 +46,10 @@ struct GtParams {
     float scale;
     int* flag;
     float* out;        // GSA, k x d (read by the reduction)
+    // compacted sketch: SA's row c is bucket idx[c] (its column of G), *rcount
+    // rows in all; r bounds *rcount (null: rows are buckets 0 .. r - 1)
+    const uint32_t* idx;
+    const uint32_t* rcount;
 };
 
 __host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 16 KB (two tiles)
@@ -75,8 +79,9 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     const int mt = blk % p.tiles_m, slice = blk / p.tiles_m;
     const int64_t j0 = (int64_t)mt * kM;
     const int64_t c_begin = (int64_t)slice * p.kslice;
-    const int64_t c_end = min(p.r, c_begin + p.kslice);
-    const int nchunks = (int)((c_end - c_begin + kKC - 1) / kKC);
+    const int64_t r_rows = p.rcount ? min(p.r, (int64_t)__ldg(p.rcount)) : p.r;   // rows of SA
+    const int64_t c_end = min(r_rows, c_begin + p.kslice);
+    const int nchunks = c_end > c_begin ? (int)((c_end - c_begin + kKC - 1) / kKC) : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -141,8 +146,12 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                 const int64_t c = c0 + 2 * cp;
                 float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
                 if (jq < p.k) {
-                    if (c < c_end) z0 = gauss4((uint64_t)c, (uint32_t)(jq >> 2), p.k0, p.k1);
-                    if (c + 1 < c_end) z1 = gauss4((uint64_t)(c + 1), (uint32_t)(jq >> 2), p.k0, p.k1);
+                    // column of G = the row's bucket
+                    if (c < c_end)
+                        z0 = gauss4((uint64_t)(p.idx ? __ldg(p.idx + c) : c), (uint32_t)(jq >> 2), p.k0, p.k1);
+                    if (c + 1 < c_end)
+                        z1 = gauss4((uint64_t)(p.idx ? __ldg(p.idx + c + 1) : c + 1), (uint32_t)(jq >> 2), p.k0,
+                                    p.k1);
                 }
                 const float a0[4] = {z0.x, z0.y, z0.z, z0.w}, a1[4] = {z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
@@ -204,7 +213,15 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
         }
         // epilogue: warps 0-3 read tile 0 (columns 0..npad), warps 4-7 tile 1 (columns npad..2 npad);
         // a warp may only read the TMEM lanes 32 (warp % 4) .. + 31
-        if (warp < 8) {
+        if (warp < 8 && nchunks == 0) {
+            // a slice past the compacted sketch's rows: its partial is zero
+            const int tile = warp >> 2, wq = warp & 3;
+            const int64_t j = j0 + tile * kMT + wq * 32 + lane;
+            if (j < p.k) {
+                float* dst = p.part + ((int64_t)slice * p.k + j) * p.d;
+                for (int col = 0; col < p.d; ++col) dst[col] = 0.f;
+            }
+        } else if (warp < 8) {
             int okw = 0;
             if (lane == 0) okw = (ok && tc::mbar_wait(done, 0, abort)) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -375,6 +392,8 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     p.scale = (float)(1.0 / sqrt((double)k));
     p.flag = nullptr;
     p.out = GSA;
+    p.idx = nullptr;
+    p.rcount = nullptr;
     cudaError_t e = allow_dynamic_smem(gauss_tc_kernel);
     if (e != cudaSuccess) return e;
     LSK_PROF("gauss_tc", st) gauss_tc_kernel<<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
@@ -425,6 +444,8 @@ void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGro
         p.scale = (float)(1.0 / sqrt((double)j.k));
         p.flag = nullptr;
         p.out = j.GSA;
+        p.idx = j.idx;
+        p.rcount = j.rcount;
         blocks[i] = P.tiles_m * P.slices;
         const int64_t rb = (j.k * j.d + 255) / 256;
         rblocks[i] = (int)(rb < kReduceBlockCap ? rb : kReduceBlockCap);

@@ -180,8 +180,12 @@ __device__ __forceinline__ void set_flag(int* flag, int bit) {
 size_t cs_workspace_bytes(int64_t n, int64_t r);
 // row0: global index of A's first row (A is a block of rows of a larger matrix);
 // accumulate: SA += S A (SA holds a previous block's sketch) instead of SA = S A
+// cidx / ccount (both or neither): compact SA to the non-empty buckets in
+// bucket order -- row j of SA is bucket cidx[j], *ccount rows in all (the rows
+// past it are left as they were); not with accumulate
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws,
-                      int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0, bool accumulate = false);
+                      int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0, bool accumulate = false,
+                      uint32_t* cidx = nullptr, uint32_t* ccount = nullptr);
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
 
@@ -193,6 +197,10 @@ struct GaussJob {
     float* GSA;
     float* part;             // gauss_group_part_bytes(r, d, k, slice_chunks) bytes
     int slice_chunks;        // chunks of 32 columns of r per block (0: the default, 128)
+    // compacted sketch (cs_launch's cidx / ccount): SA's row j is bucket idx[j]
+    // of *rcount rows; r is then an upper bound (the slices are planned on it)
+    const uint32_t* idx = nullptr;
+    const uint32_t* rcount = nullptr;
 };
 struct GaussGroup {
     size_t params_off, off_off, roff_off;

@@ -131,6 +131,47 @@ def test_grouped_stages_match_per_problem_pipelines(lsk):
         assert np.max(np.abs(got[nz] - o[nz]) / o[nz]) <= 1e-3
 
 
+def test_grouped_compacted_sketches_match_per_problem_pipelines(lsk):
+    """Problems with n < 4r take a sketch compacted to their non-empty buckets
+    (most buckets empty here: n / r from 0.05 to 0.5), and the grouped
+    Gaussian stage draws G only for those columns; each result equals the
+    problem's own uncompacted pipeline to rounding and the oracle's estimate
+    to 1e-3."""
+    specs = [("dense", 3000, 128, 16384), ("csr", 5000, 128, 16384), ("dense", 9000, 256, 65536),
+             ("dense", 33000, 256, 65536), ("csr", 2000, 64, 4096), ("dense", 1500, 32, 1024)]
+    probs, host = [], []
+    for i, (kind, n, d, r) in enumerate(specs):
+        k = 2 * d
+        if kind == "dense":
+            A = workloads.dense_normal(n, d, seed=300 + i)
+            A[: 2] *= 20.0
+            probs.append((torch.from_numpy(A).cuda(), r, k, 500 + i))
+            host.append((kind, A, n, d, r, k, 500 + i))
+        else:
+            V, J, I = workloads.csr_bernoulli(n, d, 0.1, seed=300 + i)
+            probs.append((lsk.csr_from_numpy(V, J, I, d), r, k, 500 + i))
+            host.append((kind, (V, J, I), n, d, r, k, 500 + i))
+    grouped = lsk.batch_leverage_scores(probs, prec="bf16", streams=3)
+    lsk.context().sync()
+    ref = lsk.batch_leverage_scores(probs, prec="bf16", streams=3, per_problem=True)
+    lsk.context().sync()
+    for a, b in zip(grouped, ref):
+        nz = b > 0
+        assert torch.all(a[~nz] == 0)
+        assert torch.max(torch.abs(a[nz] - b[nz]) / b[nz]).item() <= CONSISTENT
+    for ell, h in list(zip(grouped, host))[:3]:
+        kind, data, n, d, r, k, seed = h
+        if kind == "dense":
+            o, _ = olev.leverage_scores_dense(data.astype(np.float64), r, k, seed, oga.PREC_BF16)
+        else:
+            V, J, I = data
+            o, _ = olev.leverage_scores_csr(V, J, I, n, d, r, k, seed, oga.PREC_BF16)
+        got = ell.cpu().numpy().astype(np.float64)
+        nz = o > 0
+        assert np.all(got[~nz] == 0)
+        assert np.max(np.abs(got[nz] - o[nz]) / o[nz]) <= 1e-3
+
+
 def test_grouped_batch_graph_replay_and_rank_deficiency(lsk):
     """A graph-captured grouped batch replays to the same answer; a rank-
     deficient member raises the context's deferred error."""
