@@ -51,6 +51,7 @@ struct LskBatch {
     std::vector<cudaEvent_t> done;
     cudaEvent_t fork = nullptr;
     cudaStream_t gstream = nullptr;  // grouped launches
+    cudaStream_t pstream = nullptr;  // grouped CountSketch preparation of the waves
     std::vector<cudaEvent_t> ev;     // wave events: [wave][stream] sketch done, then [wave] grouped done
     cudaStream_t cap = nullptr;      // capture stream (the caller's may be the legacy stream)
     std::vector<void*> ws;
@@ -68,6 +69,8 @@ struct LskBatch {
     std::vector<int> wave;           // per grouped item: its wave
     std::vector<float*> SA, Rinv32;  // per grouped item: its sketch and FP32 R^-1 in the arena
     std::vector<uint32_t*> cidx;     // per compacted item: the buckets of its sketch's rows, then their count
+    std::vector<CsGroup> cg;         // per wave: the grouped CountSketch preparation
+    std::vector<int64_t> cnt_base;   // per grouped item: its counters' offset in its wave's preparation
     int waves = 0;
     std::vector<GaussGroup> gg;      // per wave
     std::vector<QrGroup> qg;
@@ -107,7 +110,8 @@ int ensure_streams(lsk_ctx* ctx, int S) {
     }
     if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
     if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
-    const size_t nev = (size_t)std::max(b->waves, 1) * (S + 1);
+    if (!b->pstream && cudaStreamCreateWithFlags(&b->pstream, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
+    const size_t nev = (size_t)std::max(b->waves, 1) * (S + 2);
     while (b->ev.size() < nev) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
@@ -169,24 +173,37 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
                    const lsk_batch_item* items, int32_t prec, const BatchTune& tune) {
     LskBatch* b = ctx->batch;
     const int S = (int)lanes.size(), W = b->waves;
-    auto ev_sketch = [&](int w, int s) { return b->ev[(size_t)w * (S + 1) + s]; };
-    auto ev_group = [&](int w) { return b->ev[(size_t)w * (S + 1) + S]; };
+    auto ev_sketch = [&](int w, int s) { return b->ev[(size_t)w * (S + 2) + s]; };
+    auto ev_group = [&](int w) { return b->ev[(size_t)w * (S + 2) + S]; };
+    auto ev_prep = [&](int w) { return b->ev[(size_t)w * (S + 2) + S + 1]; };
     cudaError_t e = cudaEventRecord(b->fork, main);
     if (e != cudaSuccess) return e;
     for (int s = 0; s < S; ++s)
         if ((e = cudaStreamWaitEvent(b->streams[s], b->fork, 0)) != cudaSuccess) return e;
     if (W > 0 && (e = cudaStreamWaitEvent(b->gstream, b->fork, 0)) != cudaSuccess) return e;
+    // phase 0: the CountSketch permutations of every wave, grouped, ahead of the gathers
+    if (W > 0) {
+        if ((e = cudaStreamWaitEvent(b->pstream, b->fork, 0)) != cudaSuccess) return e;
+        for (int w = 0; w < W; ++w) {
+            if ((e = cs_group_launch(b->cg[w], b->table, ctx->sm_count, b->pstream)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(ev_prep(w), b->pstream)) != cudaSuccess) return e;
+        }
+    }
 
     auto phase1 = [&](int s, int w) -> cudaError_t {
         cudaStream_t st = b->streams[s];
+        bool prepared = false;   // this stream waits for wave w's permutations before its first gather
         for (int i : lanes[s]) {
             const lsk_batch_item& it = items[i];
             cudaError_t er = cudaSuccess;
             if (b->grouped[i]) {
                 if (b->wave[i] == w) {
-                    uint32_t* ci = b->cidx[i];
-                    er = cs_launch(&it.A, it.r, it.seed, b->SA[i], b->ws[s], ctx->flag, ctx->sm_count, st, 0, false,
-                                   ci, ci ? ci + sketch_rows(it) : nullptr);
+                    if (!prepared && (er = cudaStreamWaitEvent(st, ev_prep(w), 0)) != cudaSuccess) return er;
+                    prepared = true;
+                    const CsGroup& g = b->cg[w];
+                    er = cs_gather_launch(&it.A, it.r, g.off + b->cnt_base[i], g.perm,
+                                          b->cidx[i] ? g.cpos + b->cnt_base[i] : nullptr, b->SA[i], ctx->flag,
+                                          ctx->sm_count, st);
                 }
             } else if (w == 0) {
                 er = leverage_pipeline(&it.A, it.r, it.k, it.seed, prec, it.ell, nullptr, b->ws[s], ctx->flag,
@@ -233,6 +250,7 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
         if ((e = cudaStreamWaitEvent(main, b->done[s], 0)) != cudaSuccess) return e;
     }
     if (W > 0 && (e = cudaStreamWaitEvent(main, ev_group(W - 1), 0)) != cudaSuccess) return e;
+    if (W > 0 && (e = cudaStreamWaitEvent(main, ev_prep(W - 1), 0)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -254,15 +272,29 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     b->SA.assign(count, nullptr);
     b->Rinv32.assign(count, nullptr);
     b->cidx.assign(count, nullptr);
+    b->cnt_base.assign(count, 0);
+    for (int i = 0; i < count; ++i) b->grouped[i] = (allow && groupable(items[i], prec)) ? 1 : 0;
+    // waves: grouped problems by decreasing cost, dealt round-robin
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i)
+        if (b->grouped[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost_of(items[x]) > cost_of(items[y]); });
+    const int ng = (int)order.size();
+    b->waves = ng == 0 ? 0 : std::max(1, std::min(std::min(tune.W, kMaxWaves), ng / kMinWaveProblems));
+    b->wave.assign(count, 0);
+    for (int q = 0; q < ng; ++q) b->wave[order[q]] = q % std::max(b->waves, 1);
+    std::vector<int64_t> wrows(b->waves, 0), wcnt(b->waves, 0);
     size_t bytes = 0;
     for (int i = 0; i < count; ++i) {
-        if (!allow || !groupable(items[i], prec)) continue;
+        if (!b->grouped[i]) continue;
         const int64_t rs = sketch_rows(items[i]), k = items[i].k, d = items[i].A.d;
-        b->grouped[i] = 1;
         bytes += ws_round((size_t)rs * d * 4) + ws_round((size_t)k * d * 4) +
                  gauss_group_part_bytes(rs, d, k, tune.slice) + ws_round(qr_workspace_bytes(k, d)) +
                  ws_round((size_t)d * d * 4) + (compacts(items[i]) ? ws_round((size_t)(rs + 1) * 4) : 0);
+        wrows[b->wave[i]] += items[i].A.n;
+        wcnt[b->wave[i]] += items[i].r + 1;
     }
+    for (int w = 0; w < b->waves; ++w) bytes += cs_group_ws_bytes(wrows[w], wcnt[w]);
     if (bytes > b->arena_bytes) {
         cudaStreamSynchronize(ctx->stream);
         if (b->arena) cudaFree(b->arena);
@@ -275,17 +307,10 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         }
         b->arena_bytes = bytes;
     }
-    // waves: grouped problems by decreasing cost, dealt round-robin
-    std::vector<int> order;
-    for (int i = 0; i < count; ++i)
-        if (b->grouped[i]) order.push_back(i);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost_of(items[x]) > cost_of(items[y]); });
-    const int ng = (int)order.size();
-    b->waves = ng == 0 ? 0 : std::max(1, std::min(std::min(tune.W, kMaxWaves), ng / kMinWaveProblems));
-    b->wave.assign(count, 0);
-    for (int q = 0; q < ng; ++q) b->wave[order[q]] = q % std::max(b->waves, 1);
     std::vector<std::vector<GaussJob>> gj(b->waves);
     std::vector<std::vector<QrJob>> qj(b->waves);
+    std::vector<std::vector<CsJob>> cj(b->waves);
+    std::vector<std::vector<int>> cj_item(b->waves);
     WsCarver wc{(char*)b->arena, 0};
     for (int i = 0; i < count; ++i) {
         if (!b->grouped[i]) continue;
@@ -305,6 +330,8 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
             gjob.rcount = cidx + rs;
         }
         gj[b->wave[i]].push_back(gjob);
+        cj[b->wave[i]].push_back(CsJob{items[i].A.n, items[i].r, items[i].seed, cidx, cidx ? cidx + rs : nullptr, 0});
+        cj_item[b->wave[i]].push_back(i);
         QrJob q{};
         qr_group_job(q, GSA, k, d, qws, nullptr, Ri32, ctx->flag);
         qj[b->wave[i]].push_back(q);
@@ -312,9 +339,13 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     HostTable t;
     b->gg.assign(b->waves, GaussGroup{});
     b->qg.assign(b->waves, QrGroup{});
+    b->cg.assign(b->waves, CsGroup{});
     for (int w = 0; w < b->waves; ++w) {
         gauss_group_build(gj[w], t, b->gg[w]);
         qr_group_build(qj[w], t, b->qg[w]);
+        void* cws = wc.take<char>(cs_group_ws_bytes(wrows[w], wcnt[w]));
+        cs_group_build(cj[w], cws, t, b->cg[w]);
+        for (size_t q = 0; q < cj[w].size(); ++q) b->cnt_base[cj_item[w][q]] = cj[w][q].cnt_base;
     }
     if (t.bytes.empty()) return LSK_OK;
     if (t.bytes != b->table_host || !b->table) {
@@ -401,6 +432,7 @@ void lsk_batch_free(lsk_ctx* ctx) {
     }
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->pstream) cudaStreamDestroy(b->pstream);
     if (b->arena) cudaFree(b->arena);
     if (b->table) cudaFree(b->table);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -399,9 +399,8 @@ __global__ void cs_hash_debug_kernel(int64_t n, uint32_t r, uint32_t k0, uint32_
 // cidx[cpos[b]] = b for each non-empty b, *ccount = their number.  One block
 // of 1024 threads, rounds of 4096 buckets (4 consecutive a thread) with the
 // running total carried across rounds.
-__global__ void __launch_bounds__(1024) cs_compact_kernel(const uint32_t* __restrict__ off, int64_t r,
-                                                          uint32_t* __restrict__ cpos, uint32_t* __restrict__ cidx,
-                                                          uint32_t* __restrict__ ccount) {
+__device__ __forceinline__ void compact_body(const uint32_t* __restrict__ off, int64_t r, uint32_t* __restrict__ cpos,
+                                             uint32_t* __restrict__ cidx, uint32_t* __restrict__ ccount) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry_s;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -444,6 +443,69 @@ __global__ void __launch_bounds__(1024) cs_compact_kernel(const uint32_t* __rest
         __syncthreads();
     }
     if (threadIdx.x == 0) *ccount = carry;
+}
+__global__ void __launch_bounds__(1024) cs_compact_kernel(const uint32_t* __restrict__ off, int64_t r,
+                                                          uint32_t* __restrict__ cpos, uint32_t* __restrict__ cidx,
+                                                          uint32_t* __restrict__ ccount) {
+    compact_body(off, r, cpos, cidx, ccount);
+}
+
+// ---- grouped preparation: the permutations of many problems, three launches
+// The problems' rows are numbered consecutively (problem p owns rows
+// rowoff[p] .. rowoff[p + 1] - 1) and their counters too (problem p's r + 1
+// counters from cnt_base); one exclusive scan over all the counters then
+// gives each bucket its range of the shared permutation, so the problems'
+// rows land in consecutive blocks of it and each problem's off[] (its slice
+// of the scanned counters) indexes that shared permutation directly.
+struct CsGp {
+    int64_t n, r, cnt_base;
+    uint32_t k0, k1;
+    uint32_t* cidx;     // compaction (or null)
+    uint32_t* ccount;
+};
+
+__device__ __forceinline__ int job_of(const int64_t* __restrict__ rowoff, int count, int64_t g) {
+    int lo = 0, hi = count - 1;   // largest p with rowoff[p] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(rowoff + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void cs_count_grouped_kernel(const CsGp* __restrict__ ps, const int64_t* __restrict__ rowoff, int count,
+                                        int64_t rows, uint32_t* __restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += stride) {
+        const int p = job_of(rowoff, count, g);
+        const CsGp& j = ps[p];
+        uint32_t b, neg;
+        cs_hash((uint64_t)(g - __ldg(rowoff + p)), (uint32_t)j.r, j.k0, j.k1, b, neg);
+        atomicAdd(&cnt[j.cnt_base + b], 1u);
+    }
+}
+
+__global__ void cs_place_grouped_kernel(const CsGp* __restrict__ ps, const int64_t* __restrict__ rowoff, int count,
+                                        int64_t rows, uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < rows; g += stride) {
+        const int p = job_of(rowoff, count, g);
+        const CsGp& j = ps[p];
+        const uint32_t i = (uint32_t)(g - __ldg(rowoff + p));
+        uint32_t b, neg;
+        cs_hash((uint64_t)i, (uint32_t)j.r, j.k0, j.k1, b, neg);
+        perm[atomicAdd(&cursor[j.cnt_base + b], 1u)] = i | (neg << 31);
+    }
+}
+
+// block p: problem p's compaction (if it has one)
+__global__ void __launch_bounds__(1024) cs_compact_grouped_kernel(const CsGp* __restrict__ ps,
+                                                                  const uint32_t* __restrict__ off,
+                                                                  uint32_t* __restrict__ cpos) {
+    const CsGp& j = ps[blockIdx.x];
+    if (!j.cidx) return;
+    compact_body(off + j.cnt_base, j.r, cpos + j.cnt_base, j.cidx, j.ccount);
 }
 
 inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 8) {
@@ -504,7 +566,7 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
                       int sm_count, cudaStream_t st, uint64_t row0, bool accumulate, uint32_t* cidx,
                       uint32_t* ccount) {
-    const int64_t n = A->n, d = A->d;
+    const int64_t n = A->n;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
     cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0);
@@ -522,7 +584,15 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         cpos = wc.take<uint32_t>(r + 1);
         LSK_PROF("cs_compact", st) cs_compact_kernel<<<1, 1024, 0, st>>>(off, r, cpos, cidx, ccount);
     }
+    return cs_gather_launch(A, r, off, perm, cpos, SA, flag, sm_count, st, accumulate);
+}
 
+cudaError_t cs_gather_launch(const lsk_mat* A, int64_t r, const uint32_t* off, const uint32_t* perm,
+                             const uint32_t* cpos, float* SA, int* flag, int sm_count, cudaStream_t st,
+                             bool accumulate) {
+    const int64_t n = A->n, d = A->d;
+    cudaError_t e = cudaSuccess;
+    const bool compact = cpos != nullptr;
     // parts per bucket: enough warps to stream A when there are few buckets,
     // while each part keeps several rows (one part a bucket when compacting)
     int P = 1;
@@ -564,5 +634,59 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
         LSK_PROF("cs_csr_gather", st) cs_csr_gather_kernel<<<(unsigned)g, threads, smem, st>>>(
             (const float*)A->values, A->colidx, A->rowptr, A->nnz, d, (uint32_t)r, off, perm, SA, flag, P, acc, cpos);
     }
+    return cudaGetLastError();
+}
+
+size_t cs_group_ws_bytes(int64_t rows, int64_t counters) {
+    return ws_round((size_t)counters * 4) * 4 + ws_round((size_t)(rows > 0 ? rows : 1) * 4) +
+           ws_round(scan_tmp_words(counters) * 4) + 2048;
+}
+
+void cs_group_build(std::vector<CsJob>& jobs, void* ws, HostTable& t, CsGroup& g) {
+    std::vector<CsGp> ps(jobs.size());
+    std::vector<int64_t> rowoff(jobs.size() + 1, 0);
+    int64_t cb = 0;
+    g.any_compact = false;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        CsJob& j = jobs[i];
+        j.cnt_base = cb;
+        ps[i] = CsGp{j.n, j.r, cb, (uint32_t)j.seed, (uint32_t)(j.seed >> 32), j.cidx, j.ccount};
+        rowoff[i + 1] = rowoff[i] + j.n;
+        cb += j.r + 1;
+        g.any_compact = g.any_compact || j.cidx != nullptr;
+    }
+    g.count = (int)jobs.size();
+    g.rows = rowoff.back();
+    g.counters = cb;
+    WsCarver wc{(char*)ws, 0};
+    g.cnt = wc.take<uint32_t>((size_t)g.counters);
+    g.off = wc.take<uint32_t>((size_t)g.counters);
+    g.cursor = wc.take<uint32_t>((size_t)g.counters);
+    g.cpos = wc.take<uint32_t>((size_t)g.counters);
+    g.perm = wc.take<uint32_t>((size_t)(g.rows > 0 ? g.rows : 1));
+    g.tmp = wc.take<uint32_t>(scan_tmp_words(g.counters));
+    g.params_off = t.put(ps.data(), ps.size());
+    g.rowoff_off = t.put(rowoff.data(), rowoff.size());
+}
+
+cudaError_t cs_group_launch(const CsGroup& g, const unsigned char* table, int sm_count, cudaStream_t st) {
+    if (g.count == 0) return cudaSuccess;
+    const CsGp* ps = reinterpret_cast<const CsGp*>(table + g.params_off);
+    const int64_t* rowoff = reinterpret_cast<const int64_t*>(table + g.rowoff_off);
+    cudaError_t e = cudaMemsetAsync(g.cnt, 0, (size_t)g.counters * 4, st);
+    if (e != cudaSuccess) return e;
+    if (g.rows > 0)
+        LSK_PROF("cs_count", st) cs_count_grouped_kernel<<<grid_for(g.rows, 256, sm_count), 256, 0, st>>>(
+            ps, rowoff, g.count, g.rows, g.cnt);
+    e = exclusive_scan(g.cnt, g.off, g.counters, g.tmp, st);
+    if (e != cudaSuccess) return e;
+    if (g.rows > 0) {
+        e = cudaMemcpyAsync(g.cursor, g.off, (size_t)g.counters * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        LSK_PROF("cs_place", st) cs_place_grouped_kernel<<<grid_for(g.rows, 256, sm_count), 256, 0, st>>>(
+            ps, rowoff, g.count, g.rows, g.cursor, g.perm);
+    }
+    if (g.any_compact)
+        LSK_PROF("cs_compact", st) cs_compact_grouped_kernel<<<g.count, 1024, 0, st>>>(ps, g.off, g.cpos);
     return cudaGetLastError();
 }

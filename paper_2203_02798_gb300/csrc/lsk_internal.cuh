@@ -188,6 +188,33 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
                       uint32_t* cidx = nullptr, uint32_t* ccount = nullptr);
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
+// The gather step alone (S A from a prepared permutation: off[b] .. off[b+1]
+// of perm are bucket b's rows, local row index | sign << 31; cpos: compact to
+// the non-empty buckets' ranks).
+cudaError_t cs_gather_launch(const lsk_mat* A, int64_t r, const uint32_t* off, const uint32_t* perm,
+                             const uint32_t* cpos, float* SA, int* flag, int sm_count, cudaStream_t st,
+                             bool accumulate = false);
+// Grouped preparation of many problems' CountSketch permutations (count, one
+// scan, place, compaction) in a handful of launches; problem j then gathers
+// with off = g.off + jobs[j].cnt_base, perm = g.perm, cpos = g.cpos +
+// jobs[j].cnt_base when it compacts.
+struct CsJob {
+    int64_t n, r;
+    uint64_t seed;
+    uint32_t* cidx;       // cs_launch's compaction outputs (or null)
+    uint32_t* ccount;
+    int64_t cnt_base;     // set by cs_group_build
+};
+struct CsGroup {
+    size_t params_off = 0, rowoff_off = 0;
+    int count = 0;
+    int64_t rows = 0, counters = 0;
+    bool any_compact = false;
+    uint32_t *cnt = nullptr, *off = nullptr, *cursor = nullptr, *cpos = nullptr, *perm = nullptr, *tmp = nullptr;
+};
+size_t cs_group_ws_bytes(int64_t rows, int64_t counters);
+void cs_group_build(std::vector<CsJob>& jobs, void* ws, HostTable& t, CsGroup& g);
+cudaError_t cs_group_launch(const CsGroup& g, const unsigned char* table, int sm_count, cudaStream_t st);
 
 // gauss_tc.cu: grouped Gaussian stage (BF16) over many sketches
 struct GaussJob {
