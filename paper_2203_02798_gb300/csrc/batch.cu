@@ -6,12 +6,16 @@
 //      passes over A, concurrent across problems), into a batch arena that
 //      holds every such problem's sketch -- compacted to its non-empty
 //      buckets where n < 4r, so that phase 2 draws G only for those columns;
-//   2. the Gaussian stage and the whole R^-1 computation as grouped
-//      launches: one grid per stage over all problems (qr.cu, qr_mixed.cu,
-//      gauss_tc.cu), so the latency-bound small stages of hundreds of
-//      problems run side by side instead of one after another;
+//   2. the Gaussian stage, the whole R^-1 computation and the row norms'
+//      operand built from R^-1 as grouped launches: one grid per stage over
+//      all problems (qr.cu, qr_mixed.cu, gauss_tc.cu, rownorms*.cu), so the
+//      latency-bound small stages of hundreds of problems run side by side
+//      instead of one after another;
 //   3. row norms of each problem on the worker streams.
 // Other problems run their whole pipeline on the worker streams in phase 1.
+// The CountSketch permutations of each wave's grouped problems (count, scan,
+// place, compaction) are grouped launches too, on a stream of their own
+// ahead of the gathers (phase 0).
 // The problems are sorted by estimated cost (longest first) and assigned
 // greedily to the least-loaded of S worker streams; each stream owns a
 // workspace sized for the largest of its problems, so problems on different
@@ -70,6 +74,9 @@ struct LskBatch {
     std::vector<float*> SA, Rinv32;  // per grouped item: its sketch and FP32 R^-1 in the arena
     std::vector<uint32_t*> cidx;     // per compacted item: the buckets of its sketch's rows, then their count
     std::vector<CsGroup> cg;         // per wave: the grouped CountSketch preparation
+    std::vector<RnImageGroup> ig;    // per wave: the row norms' B images (dense) ...
+    std::vector<BbtGroup> mg;        // ... and B B^T (CSR), built after the wave's R^-1
+    std::vector<void*> prepared;     // per grouped item: that operand
     std::vector<int64_t> cnt_base;   // per grouped item: its counters' offset in its wave's preparation
     int waves = 0;
     std::vector<GaussGroup> gg;      // per wave
@@ -88,6 +95,15 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
 // than ~2% of the r buckets are expected empty (e^(-n/r) > e^-4): its
 // Gaussian stage then draws G only for the columns that meet a row of A.
 bool compacts(const lsk_batch_item& it) { return it.A.n < 4 * it.r; }
+// The row norms' operand built for a grouped problem in phase 2: the
+// tensor-core image of R^-1 (dense BF16) or R^-1 R^-T (CSR); 0: none.
+size_t prepared_bytes(const lsk_batch_item& it, int32_t prec) {
+    const lsk_mat* A = &it.A;
+    if (A->kind == LSK_DENSE)
+        return (prec == LSK_PREC_BF16 && rownorms_tc_supported(A, A->d, 1)) ? rownorms_tc_workspace_bytes(A, A->d, 1)
+                                                                          : 0;
+    return (size_t)A->d * A->d * 4;
+}
 int64_t sketch_rows(const lsk_batch_item& it) { return compacts(it) ? std::min<int64_t>(it.r, it.A.n) : it.r; }
 
 double cost_of(const lsk_batch_item& it) {
@@ -221,7 +237,7 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
             if (!b->grouped[i] || b->wave[i] != w) continue;
             const lsk_batch_item& it = items[i];
             er = rownorms_launch(&it.A, b->Rinv32[i], it.A.d, 1.0, 0.0, 1, prec, it.ell, b->ws[s], ctx->flag,
-                                 ctx->sm_count, st, tune.tiles);
+                                 ctx->sm_count, st, tune.tiles, b->prepared[i]);
         }
         return er;
     };
@@ -231,6 +247,8 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
             if ((er = cudaStreamWaitEvent(b->gstream, ev_sketch(w, s), 0)) != cudaSuccess) return er;
         if ((er = gauss_group_launch(b->gg[w], b->table, b->gstream)) != cudaSuccess) return er;
         if ((er = qr_group_launch(b->qg[w], b->table, b->gstream)) != cudaSuccess) return er;
+        if ((er = rownorms_image_group_launch(b->ig[w], b->table, b->gstream)) != cudaSuccess) return er;
+        if ((er = bbt_group_launch(b->mg[w], b->table, b->gstream)) != cudaSuccess) return er;
         return cudaEventRecord(ev_group(w), b->gstream);
     };
 
@@ -273,6 +291,7 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     b->Rinv32.assign(count, nullptr);
     b->cidx.assign(count, nullptr);
     b->cnt_base.assign(count, 0);
+    b->prepared.assign(count, nullptr);
     for (int i = 0; i < count; ++i) b->grouped[i] = (allow && groupable(items[i], prec)) ? 1 : 0;
     // waves: grouped problems by decreasing cost, dealt round-robin
     std::vector<int> order;
@@ -290,7 +309,8 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         const int64_t rs = sketch_rows(items[i]), k = items[i].k, d = items[i].A.d;
         bytes += ws_round((size_t)rs * d * 4) + ws_round((size_t)k * d * 4) +
                  gauss_group_part_bytes(rs, d, k, tune.slice) + ws_round(qr_workspace_bytes(k, d)) +
-                 ws_round((size_t)d * d * 4) + (compacts(items[i]) ? ws_round((size_t)(rs + 1) * 4) : 0);
+                 ws_round((size_t)d * d * 4) + (compacts(items[i]) ? ws_round((size_t)(rs + 1) * 4) : 0) +
+                 ws_round(prepared_bytes(items[i], prec));
         wrows[b->wave[i]] += items[i].A.n;
         wcnt[b->wave[i]] += items[i].r + 1;
     }
@@ -310,6 +330,8 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     std::vector<std::vector<GaussJob>> gj(b->waves);
     std::vector<std::vector<QrJob>> qj(b->waves);
     std::vector<std::vector<CsJob>> cj(b->waves);
+    std::vector<std::vector<RnImageJob>> imj(b->waves);
+    std::vector<std::vector<BbtJob>> bbj(b->waves);
     std::vector<std::vector<int>> cj_item(b->waves);
     WsCarver wc{(char*)b->arena, 0};
     for (int i = 0; i < count; ++i) {
@@ -321,6 +343,13 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
         void* qws = wc.take<char>(qr_workspace_bytes(k, d));
         float* Ri32 = wc.take<float>((size_t)d * d);
         uint32_t* cidx = compacts(items[i]) ? wc.take<uint32_t>((size_t)rs + 1) : nullptr;
+        const size_t pb = prepared_bytes(items[i], prec);
+        void* prep = pb ? (void*)wc.take<char>(pb) : nullptr;
+        b->prepared[i] = prep;
+        if (prep && items[i].A.kind == LSK_DENSE)
+            imj[b->wave[i]].push_back(RnImageJob{items[i].A, Ri32, d, 1, (uint8_t*)prep});
+        else if (prep)
+            bbj[b->wave[i]].push_back(BbtJob{Ri32, d, d, (float*)prep});
         b->SA[i] = SA;
         b->Rinv32[i] = Ri32;
         b->cidx[i] = cidx;
@@ -340,12 +369,16 @@ int prepare_groups(lsk_ctx* ctx, const lsk_batch_item* items, int count, int32_t
     b->gg.assign(b->waves, GaussGroup{});
     b->qg.assign(b->waves, QrGroup{});
     b->cg.assign(b->waves, CsGroup{});
+    b->ig.assign(b->waves, RnImageGroup{});
+    b->mg.assign(b->waves, BbtGroup{});
     for (int w = 0; w < b->waves; ++w) {
         gauss_group_build(gj[w], t, b->gg[w]);
         qr_group_build(qj[w], t, b->qg[w]);
         void* cws = wc.take<char>(cs_group_ws_bytes(wrows[w], wcnt[w]));
         cs_group_build(cj[w], cws, t, b->cg[w]);
         for (size_t q = 0; q < cj[w].size(); ++q) b->cnt_base[cj_item[w][q]] = cj[w][q].cnt_base;
+        rownorms_image_group_build(imj[w], t, b->ig[w]);
+        bbt_group_build(bbj[w], t, b->mg[w]);
     }
     if (t.bytes.empty()) return LSK_OK;
     if (t.bytes != b->table_host || !b->table) {

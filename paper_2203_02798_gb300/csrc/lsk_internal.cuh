@@ -264,15 +264,43 @@ cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C
 size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec);
 // min_tiles: the dense tensor-core form launches CTAs for at least that many
 // 128-row tiles each (a small problem leaves SMs to concurrent work)
+// prepared (nullable): B's operand built beforehand by a grouped launch -- the
+// tensor-core image (rownorms_image_group_launch) for dense BF16, B B^T
+// (bbt_group_launch) for CSR -- so this launch skips building it
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha,
                             double beta, int upper_tri, int32_t prec, float* x, void* ws, int* flag,
-                            int sm_count, cudaStream_t st, int min_tiles = 16);
+                            int sm_count, cudaStream_t st, int min_tiles = 16, const void* prepared = nullptr);
+struct BbtJob {
+    const float* B;
+    int64_t d, c;
+    float* M;            // d x d
+};
+struct BbtGroup {
+    size_t params_off = 0, off_off = 0;
+    int count = 0, blocks = 0;
+};
+void bbt_group_build(const std::vector<BbtJob>& jobs, HostTable& t, BbtGroup& g);
+cudaError_t bbt_group_launch(const BbtGroup& g, const unsigned char* table, cudaStream_t st);
 // rownorms_tc.cu
 bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri);
 size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri);
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta,
                                int upper_tri, float* x, void* ws, int* flag, int sm_count, cudaStream_t st,
-                               int min_tiles = 16);
+                               int min_tiles = 16, const uint8_t* img_ready = nullptr);
+// the tensor-core images of many problems' B (rownorms_tc_workspace_bytes each)
+struct RnImageJob {
+    lsk_mat A;
+    const float* B;
+    int64_t c;
+    int upper_tri;
+    uint8_t* img;
+};
+struct RnImageGroup {
+    size_t params_off = 0, off_off = 0;
+    int count = 0, blocks = 0;
+};
+void rownorms_image_group_build(const std::vector<RnImageJob>& jobs, HostTable& t, RnImageGroup& g);
+cudaError_t rownorms_image_group_launch(const RnImageGroup& g, const unsigned char* table, cudaStream_t st);
 
 // qr.cu
 size_t qr_workspace_bytes(int64_t k, int64_t d);

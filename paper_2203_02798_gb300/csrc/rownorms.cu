@@ -92,11 +92,10 @@ __global__ void __launch_bounds__(256) rownorm_dense_kernel(
 
 // Btilde[a][b] = sum_j B[a][j] B[b][j], FP32, 16 x 16 output tiles (one
 // output per thread, two accumulation chains).
-__global__ void __launch_bounds__(256) bbt_kernel(const float* __restrict__ B, int64_t d, int64_t c,
-                                                  float* __restrict__ M) {
+__device__ __forceinline__ void bbt_body(const float* __restrict__ B, int64_t d, int64_t c, float* __restrict__ M,
+                                         int64_t a0, int64_t b0) {
     __shared__ float Ba[16][17], Bb[16][17];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t a0 = (int64_t)blockIdx.y * 16, b0 = (int64_t)blockIdx.x * 16;
     float acc0 = 0.f, acc1 = 0.f;
     for (int64_t j0 = 0; j0 < c; j0 += 16) {
         const int64_t ja = j0 + tx;
@@ -111,6 +110,19 @@ __global__ void __launch_bounds__(256) bbt_kernel(const float* __restrict__ B, i
         __syncthreads();
     }
     if (a0 + ty < d && b0 + tx < d) M[(a0 + ty) * d + b0 + tx] = acc0 + acc1;
+}
+__global__ void __launch_bounds__(256) bbt_kernel(const float* __restrict__ B, int64_t d, int64_t c,
+                                                  float* __restrict__ M) {
+    bbt_body(B, d, c, M, (int64_t)blockIdx.y * 16, (int64_t)blockIdx.x * 16);
+}
+// B B^T of many problems in one launch: problem g's 16 x 16 tiles are blocks
+// off[g] .. off[g + 1] - 1, row-major over the tile grid
+__global__ void __launch_bounds__(256) bbt_grouped_kernel(const BbtJob* __restrict__ jobs, const int* __restrict__ off,
+                                                          int count) {
+    const int g = group_of(off, count, blockIdx.x);
+    const BbtJob& j = jobs[g];
+    const int64_t tiles = (j.d + 15) / 16, t = (int64_t)blockIdx.x - __ldg(off + g);
+    bbt_body(j.B, j.d, j.c, j.M, (t / tiles) * 16, (t % tiles) * 16);
 }
 
 __global__ void rownorm_csr_kernel(const float* __restrict__ V, const int32_t* __restrict__ J,
@@ -160,25 +172,45 @@ size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int3
 
 cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double alpha, double beta,
                             int upper_tri, int32_t prec, float* x, void* ws, int* flag, int sm_count,
-                            cudaStream_t st, int min_tiles) {
+                            cudaStream_t st, int min_tiles, const void* prepared) {
     const int64_t n = A->n, d = A->d;
     if (n == 0) return cudaSuccess;
     if (A->kind == LSK_DENSE && prec == LSK_PREC_BF16 && rownorms_tc_supported(A, c, upper_tri))
         return rownorms_tc_launch(A, B, c, (float)alpha, (float)beta, upper_tri, x, ws, flag, sm_count, st,
-                                  min_tiles);
+                                  min_tiles, (const uint8_t*)prepared);
     if (A->kind == LSK_DENSE) {
         const unsigned grid = (unsigned)((n + RM - 1) / RM);
         LSK_PROF("rownorm_dense_simt", st) rownorm_dense_kernel<<<grid, 256, 0, st>>>((const float*)A->values, A->ld, n, d, B, c,
                                                    upper_tri ? 1 : 0, (float)alpha, (float)beta, x);
     } else {
-        float* M = (float*)ws;
+        float* M = prepared ? (float*)prepared : (float*)ws;   // prepared: built by bbt_group_launch
         const dim3 bg((unsigned)((d + 15) / 16), (unsigned)((d + 15) / 16));
-        LSK_PROF("rownorm_bbt", st) bbt_kernel<<<bg, 256, 0, st>>>(B, d, c, M);
+        if (!prepared) LSK_PROF("rownorm_bbt", st) bbt_kernel<<<bg, 256, 0, st>>>(B, d, c, M);
         int64_t gr = (n + 255) / 256;
         if (gr > 16 * (int64_t)sm_count) gr = 16 * (int64_t)sm_count;
         LSK_PROF("rownorm_csr", st) rownorm_csr_kernel<<<(unsigned)gr, 256, 0, st>>>((const float*)A->values, A->colidx, A->rowptr,
                                                          n, A->nnz, d, M, (float)alpha, (float)beta, x,
                                                          flag);
     }
+    return cudaGetLastError();
+}
+
+void bbt_group_build(const std::vector<BbtJob>& jobs, HostTable& t, BbtGroup& g) {
+    std::vector<int> blocks, off;
+    for (const BbtJob& j : jobs) {
+        const int tiles = (int)((j.d + 15) / 16);
+        blocks.push_back(tiles * tiles);
+    }
+    g.count = (int)jobs.size();
+    g.blocks = group_offsets(blocks, off);
+    g.params_off = t.put(jobs.data(), jobs.size());
+    g.off_off = t.put(off.data(), off.size());
+}
+
+cudaError_t bbt_group_launch(const BbtGroup& g, const unsigned char* table, cudaStream_t st) {
+    if (g.count == 0) return cudaSuccess;
+    LSK_PROF("rownorm_bbt", st) bbt_grouped_kernel<<<g.blocks, 256, 0, st>>>(
+        reinterpret_cast<const BbtJob*>(table + g.params_off), reinterpret_cast<const int*>(table + g.off_off),
+        g.count);
     return cudaGetLastError();
 }

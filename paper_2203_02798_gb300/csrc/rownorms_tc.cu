@@ -81,10 +81,11 @@ struct RnParams {
 
 // B (d x c, row-major) -> the shared-memory image of its bf16 hi / lo parts:
 // per K-chunk q, an (nn[q] x 32) K-major tile whose row r is column n0[q]+r.
-__global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnParams p, uint8_t* __restrict__ img) {
+__device__ __forceinline__ void prep_body(const float* __restrict__ B, const RnParams& p, uint8_t* __restrict__ img,
+                                          uint32_t blk, uint32_t nblk) {
     uint32_t total = 0;
     for (int q = 0; q < p.nq; ++q) total += p.nn[q] * (kKC / 2);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    for (uint32_t e = blk * blockDim.x + threadIdx.x; e < total; e += nblk * blockDim.x) {
         int q = 0;
         uint32_t el = e;
         while (el >= p.nn[q] * (kKC / 2)) {
@@ -109,6 +110,22 @@ __global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnPara
             *reinterpret_cast<uint32_t*>(img + p.b_bytes + off) = lo;
         }
     }
+}
+__global__ void rownorm_tc_prep_kernel(const float* __restrict__ B, const RnParams p, uint8_t* __restrict__ img) {
+    prep_body(B, p, img, blockIdx.x, gridDim.x);
+}
+// the images of many problems' B in one launch (kPrepBlocks blocks a problem)
+struct RnPrepJob {
+    const float* B;
+    RnParams p;
+    uint8_t* img;
+};
+constexpr int kPrepBlocks = 16;
+__global__ void rownorm_tc_prep_grouped_kernel(const RnPrepJob* __restrict__ jobs, const int* __restrict__ off,
+                                               int count) {
+    const int g = group_of(off, count, blockIdx.x);
+    const int b0 = __ldg(off + g), b1 = __ldg(off + g + 1);
+    prep_body(jobs[g].B, jobs[g].p, jobs[g].img, (uint32_t)((int)blockIdx.x - b0), (uint32_t)(b1 - b0));
 }
 
 // Lane l loads float4 number f = l + 32 i of the piece (row f / 8 of the
@@ -955,6 +972,43 @@ bool make_tmap(const RnParams& p, CUtensorMap* m) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The form a launch takes: the CTA-pair form where B leaves the single-CTA
+// ring short of its full depth and clusters of two fit (TMA-fed behind
+// LSK_ROWNORM_TMA=1), else the single-CTA form.  The B image's layout follows
+// from it, so the grouped image build asks the same question.
+struct PairChoice {
+    int ncl = 0;        // clusters of two (0: single-CTA form)
+    bool tma = false;
+    int stages2 = 0;    // the TMA form's ring (a multiple of its converter groups)
+};
+PairChoice choose_form(const lsk_mat* A, const RnParams& p, bool vec) {
+    PairChoice pc;
+    // LSK_ROWNORM_SINGLE_CTA=1 selects the single-CTA form (for testing it)
+    const char* single = getenv("LSK_ROWNORM_SINGLE_CTA");
+    const bool allow_pair = !(single && single[0] == '1');
+    // the pair form pays for its cross-SM hand-offs only where B leaves the
+    // single-CTA ring short of its full depth
+    const bool want_pair = p.stages2 >= 2 && (p.stages < 2 || (allow_pair && p.stages < kMaxStages &&
+                                                               p.stages2 > p.stages));
+    // LSK_ROWNORM_TMA=1 feeds the pair form by TMA (measured slower at d = c =
+    // 256: its in-place ring of 8 stages caps the bytes in flight)
+    const char* tma_env = getenv("LSK_ROWNORM_TMA");
+    bool use_tma = want_pair && (tma_env && tma_env[0] == '1') && tma_ok(A);
+    const TmaVariant& tv = tma_variant();
+    // converter group i takes the chunks (and so the stages) i mod groups: with
+    // the ring a multiple of the group count, each stage belongs to one group,
+    // which then sees every use of it in order (no wait a phase ahead)
+    const int stages_tma = (p.stages2 / tv.groups) * tv.groups;
+    use_tma = use_tma && stages_tma >= 2;
+    RnParams q = p;
+    if (use_tma) q.stages2 = stages_tma;
+    const void* pfn = use_tma ? tv.fn : pair_kernel(vec);
+    pc.ncl = want_pair ? pair_clusters(pfn, use_tma ? tv.threads : kThreads, smem_bytes2(q)) : 0;
+    pc.tma = use_tma && pc.ncl > 0;
+    pc.stages2 = q.stages2;
+    return pc;
+}
+
 }  // namespace
 
 bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri) {
@@ -973,7 +1027,8 @@ size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri) {
 }
 
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta, int upper_tri,
-                               float* x, void* ws, int* flag, int sm_count, cudaStream_t st, int min_tiles) {
+                               float* x, void* ws, int* flag, int sm_count, cudaStream_t st, int min_tiles,
+                               const uint8_t* img_ready) {
     RnParams p{};
     if (!make_plan(A, c, upper_tri, p)) return cudaErrorNotSupported;
     p.A = (const float*)A->values;
@@ -988,29 +1043,15 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     uint8_t* img = (uint8_t*)ws;
     const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
     p.ntiles2 = (int)((A->n + 2 * kRows - 1) / (2 * kRows));
-    // LSK_ROWNORM_SINGLE_CTA=1 selects the single-CTA form (for testing it)
-    const char* single = getenv("LSK_ROWNORM_SINGLE_CTA");
-    const bool allow_pair = !(single && single[0] == '1');
-    // the pair form pays for its cross-SM hand-offs only where B leaves the
-    // single-CTA ring short of its full depth
-    const bool want_pair = p.stages2 >= 2 && (p.stages < 2 || (allow_pair && p.stages < kMaxStages &&
-                                                               p.stages2 > p.stages));
-    // LSK_ROWNORM_TMA=1 feeds the pair form by TMA (measured slower at d = c =
-    // 256: its in-place ring of 8 stages caps the bytes in flight)
-    const char* tma_env = getenv("LSK_ROWNORM_TMA");
-    bool use_tma = want_pair && (tma_env && tma_env[0] == '1') && tma_ok(A);
+    const PairChoice pc = choose_form(A, p, vec);
+    const bool use_tma = pc.tma;
     const TmaVariant& tv = tma_variant();
-    // converter group i takes the chunks (and so the stages) i mod groups: with
-    // the ring a multiple of the group count, each stage belongs to one group,
-    // which then sees every use of it in order (no wait a phase ahead)
-    const int stages_tma = (p.stages2 / tv.groups) * tv.groups;
-    use_tma = use_tma && stages_tma >= 2;
-    if (use_tma) p.stages2 = stages_tma;
-    const void* pfn = use_tma ? tv.fn : pair_kernel(vec);
-    const int ncl = want_pair ? pair_clusters(pfn, use_tma ? tv.threads : kThreads, smem_bytes2(p)) : 0;
+    const int ncl = pc.ncl;
+    if (use_tma) p.stages2 = pc.stages2;
     p.pair = ncl > 0 ? 1 : 0;
     if (!p.pair && p.stages < 2) return cudaErrorNotSupported;
-    LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
+    if (img_ready) img = const_cast<uint8_t*>(img_ready);   // built by rownorms_image_group_launch
+    else LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
     cudaError_t e;
     // CTAs (pairs) for at least min_tiles tiles each: a small problem then
     // leaves SMs to the problems on other streams (its per-CTA set-up -- TMEM,
@@ -1046,5 +1087,32 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
         if (e != cudaSuccess) return e;
         LSK_PROF("rownorm_dense_tc", st) rownorm_tc_kernel<false><<<grid, kThreads, smem, st>>>(p, img);
     }
+    return cudaGetLastError();
+}
+
+void rownorms_image_group_build(const std::vector<RnImageJob>& jobs, HostTable& t, RnImageGroup& g) {
+    std::vector<RnPrepJob> js;
+    std::vector<int> blocks, off;
+    for (const RnImageJob& j : jobs) {
+        RnPrepJob r{};
+        if (!make_plan(&j.A, j.c, j.upper_tri, r.p)) continue;
+        const bool vec = (r.p.d % 4 == 0) && (j.A.ld % 4 == 0) && (((uintptr_t)j.A.values & 15) == 0);
+        r.p.pair = choose_form(&j.A, r.p, vec).ncl > 0 ? 1 : 0;
+        r.B = j.B;
+        r.img = j.img;
+        js.push_back(r);
+        blocks.push_back(kPrepBlocks);
+    }
+    g.count = (int)js.size();
+    g.blocks = group_offsets(blocks, off);
+    g.params_off = t.put(js.data(), js.size());
+    g.off_off = t.put(off.data(), off.size());
+}
+
+cudaError_t rownorms_image_group_launch(const RnImageGroup& g, const unsigned char* table, cudaStream_t st) {
+    if (g.count == 0) return cudaSuccess;
+    LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_grouped_kernel<<<g.blocks, 256, 0, st>>>(
+        reinterpret_cast<const RnPrepJob*>(table + g.params_off), reinterpret_cast<const int*>(table + g.off_off),
+        g.count);
     return cudaGetLastError();
 }
