@@ -53,6 +53,8 @@ struct BatchTune {
 struct LskBatch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
+    std::vector<cudaStream_t> rstreams;   // phase 3 (row norms of the grouped problems)
+    std::vector<cudaEvent_t> rdone;
     cudaEvent_t fork = nullptr;
     cudaStream_t gstream = nullptr;  // grouped launches
     cudaStream_t pstream = nullptr;  // grouped CountSketch preparation of the waves
@@ -124,6 +126,14 @@ int ensure_streams(lsk_ctx* ctx, int S) {
         b->ws.push_back(nullptr);
         b->ws_bytes.push_back(0);
     }
+    while ((int)b->rstreams.size() < S) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
+        b->rstreams.push_back(s);
+        b->rdone.push_back(e);
+    }
     if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return LSK_ERR_CUDA;
     if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
     if (!b->pstream && cudaStreamCreateWithFlags(&b->pstream, cudaStreamNonBlocking) != cudaSuccess) return LSK_ERR_CUDA;
@@ -179,12 +189,18 @@ int size_workspaces(lsk_ctx* ctx, const std::vector<std::vector<int>>& lanes, co
     return LSK_OK;
 }
 
-// The whole batch on `main`'s timeline.  Worker stream s runs, in order,
-// phase 1 of wave 0 (and the full pipelines of ungrouped problems), then for
-// w = 1.. phase 1 of wave w followed by phase 3 of wave w-1, then phase 3 of
-// the last wave; the grouped stream runs phase 2 of wave w once every worker
-// has finished its phase 1 of w.  So the compute-bound grouped stages of one
-// wave overlap the memory-bound passes over A of its neighbours.
+// The whole batch on `main`'s timeline.  Worker stream s runs phase 1 of every
+// wave back to back (and, with wave 0, the full pipelines of ungrouped
+// problems); the grouped stream runs phase 2 of wave w once every worker has
+// finished its phase 1 of w; row-norm stream s runs phase 3 of each wave once
+// its phase 2 is done.  So the compute-bound grouped stages of one wave
+// overlap the memory-bound passes over A of the others, and no gather waits
+// for a grouped stage.  (Measured on the 512-problem batch with phase-boundary
+// timestamps: the gathers of all waves end by ~17 ms, the four grouped stages
+// -- ~4 ms of draws and ~1.5 ms of QR each -- run back to back on the grouped
+// stream from the end of wave 0's slowest gathers, and the row norms of the
+// last wave end the batch: 43-45 ms, as with phase 3 queued on the worker
+// streams.)
 cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vector<int>>& lanes,
                    const lsk_batch_item* items, int32_t prec, const BatchTune& tune) {
     LskBatch* b = ctx->batch;
@@ -230,13 +246,14 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
         return W > 0 ? cudaEventRecord(ev_sketch(w, s), st) : cudaSuccess;
     };
     auto phase3 = [&](int s, int w) -> cudaError_t {
-        cudaStream_t st = b->streams[s];
+        cudaStream_t st = b->rstreams[s];
         cudaError_t er = cudaStreamWaitEvent(st, ev_group(w), 0);
         for (int i : lanes[s]) {
             if (er != cudaSuccess) return er;
             if (!b->grouped[i] || b->wave[i] != w) continue;
             const lsk_batch_item& it = items[i];
-            er = rownorms_launch(&it.A, b->Rinv32[i], it.A.d, 1.0, 0.0, 1, prec, it.ell, b->ws[s], ctx->flag,
+            // the operand was built in phase 2: the workspace is not touched
+            er = rownorms_launch(&it.A, b->Rinv32[i], it.A.d, 1.0, 0.0, 1, prec, it.ell, nullptr, ctx->flag,
                                  ctx->sm_count, st, tune.tiles, b->prepared[i]);
         }
         return er;
@@ -252,18 +269,23 @@ cudaError_t record(lsk_ctx* ctx, cudaStream_t main, const std::vector<std::vecto
         return cudaEventRecord(ev_group(w), b->gstream);
     };
 
+    // worker streams: the gathers of every wave back to back; the grouped
+    // stream: phase 2 of each wave once its gathers are in; phase 3 on a
+    // stream pool of its own (its operands are in the arena), so no gather
+    // waits behind a row norm that waits for a grouped stage
     for (int s = 0; s < S; ++s)
-        if ((e = phase1(s, 0)) != cudaSuccess) return e;
-    if (W > 0 && (e = phase2(0)) != cudaSuccess) return e;
-    for (int w = 1; w < W; ++w) {
-        for (int s = 0; s < S; ++s) {
+        for (int w = 0; w < std::max(W, 1); ++w)
             if ((e = phase1(s, w)) != cudaSuccess) return e;
-            if ((e = phase3(s, w - 1)) != cudaSuccess) return e;
-        }
+    for (int w = 0; w < W; ++w)
         if ((e = phase2(w)) != cudaSuccess) return e;
-    }
     for (int s = 0; s < S; ++s) {
-        if (W > 0 && (e = phase3(s, W - 1)) != cudaSuccess) return e;
+        if (W > 0) {
+            if ((e = cudaStreamWaitEvent(b->rstreams[s], b->fork, 0)) != cudaSuccess) return e;
+            for (int w = 0; w < W; ++w)
+                if ((e = phase3(s, w)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(b->rdone[s], b->rstreams[s])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(main, b->rdone[s], 0)) != cudaSuccess) return e;
+        }
         if ((e = cudaEventRecord(b->done[s], b->streams[s])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(main, b->done[s], 0)) != cudaSuccess) return e;
     }
@@ -464,6 +486,8 @@ void lsk_batch_free(lsk_ctx* ctx) {
         cudaStreamDestroy(b->streams[s]);
     }
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (cudaStream_t st : b->rstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->rdone) cudaEventDestroy(e);
     if (b->gstream) cudaStreamDestroy(b->gstream);
     if (b->pstream) cudaStreamDestroy(b->pstream);
     if (b->arena) cudaFree(b->arena);
