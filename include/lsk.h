@@ -78,7 +78,10 @@ typedef struct lsk_mat {
 } lsk_mat;
 
 /* precision of the contractions (Gaussian stage, row-norm GEMM) */
-#define LSK_PREC_FP32 0     /* plain FP32 on CUDA cores                     */
+#define LSK_PREC_FP32 0     /* FP32 accuracy: CUDA cores, or (the Gaussian  */
+                            /* stage of a sketch with r >= 8192) the BF16   */
+                            /* tensor pipe on three-term bf16 splits of G   */
+                            /* and SA with FP32 accumulation                */
 #define LSK_PREC_TF32 1     /* reserved (accepted, runs as LSK_PREC_FP32)    */
 #define LSK_PREC_BF16 2     /* tensor cores: BF16 G, split-BF16 operands,   */
                             /* FP32 accumulation                            */
@@ -118,7 +121,10 @@ int lsk_cs_sketch(lsk_ctx* ctx, const lsk_mat* A, int64_t r, uint64_t seed,
  * GSA = G * SA with G k x r, N(0,1) entries scaled by 1/sqrt(k) (header
  * comment).  SA: device r*d floats row-major; GSA: device k*d floats
  * row-major, overwritten.  prec: LSK_PREC_FP32 or LSK_PREC_BF16 (G exact in
- * bfloat16, SA split into two bfloat16 terms, FP32 accumulation). */
+ * bfloat16, SA split into two bfloat16 terms, FP32 accumulation).  In the
+ * FP32 mode a sketch with r >= 8192 runs on the tensor cores with G and SA
+ * each split into three bfloat16 terms (24 significant bits, exact) and the
+ * six products down to order 2^-16 accumulated in FP32. */
 int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d,
                      int64_t k, uint64_t seed, int32_t prec, float* GSA);
 

@@ -165,13 +165,20 @@ Plan make_plan(int64_t r, int64_t d, int64_t k, int sm_count) {
 }  // namespace
 
 cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
-                            float* GSA, void* ws, int sm_count, cudaStream_t st);
-size_t gauss_tc_workspace_bytes(int64_t r, int64_t d, int64_t k, int sm_count);
-bool gauss_tc_supported(int64_t r, int64_t d, int64_t k);
+                            float* GSA, void* ws, int sm_count, cudaStream_t st, int terms);
+size_t gauss_tc_workspace_bytes(int64_t r, int64_t d, int64_t k, int sm_count, int terms);
+
+// The FP32 mode (and TF32, which runs as FP32) on the tensor cores -- G and
+// SA as three bf16 terms each -- where the shape fits and the sketch is long
+// enough for its slices to fill the GPU; the SIMT tiles otherwise.
+bool fp32_on_tensor_cores(int64_t r, int64_t d, int64_t k, int32_t prec) {
+    return (prec == LSK_PREC_FP32 || prec == LSK_PREC_TF32) && r >= 8192 && gauss_tc_supported(r, d, k, 3);
+}
 
 size_t gauss_workspace_bytes(int64_t r, int64_t d, int64_t k, int32_t prec, int sm_count) {
     if (prec == LSK_PREC_BF16 && gauss_tc_supported(r, d, k))
-        return gauss_tc_workspace_bytes(r, d, k, sm_count);
+        return gauss_tc_workspace_bytes(r, d, k, sm_count, 1);
+    if (fp32_on_tensor_cores(r, d, k, prec)) return gauss_tc_workspace_bytes(r, d, k, sm_count, 3);
     const Plan p = make_plan(r, d, k, sm_count);
     return ws_round((size_t)p.nz * k * d * 4);
 }
@@ -179,7 +186,8 @@ size_t gauss_workspace_bytes(int64_t r, int64_t d, int64_t k, int32_t prec, int 
 cudaError_t gauss_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed,
                          int32_t prec, float* GSA, void* ws, int sm_count, cudaStream_t st) {
     if (prec == LSK_PREC_BF16 && gauss_tc_supported(r, d, k))
-        return gauss_tc_launch(SA, r, d, k, seed, GSA, ws, sm_count, st);
+        return gauss_tc_launch(SA, r, d, k, seed, GSA, ws, sm_count, st, 1);
+    if (fp32_on_tensor_cores(r, d, k, prec)) return gauss_tc_launch(SA, r, d, k, seed, GSA, ws, sm_count, st, 3);
     const Plan p = make_plan(r, d, k, sm_count);
     const float scale = (float)(1.0 / sqrt((double)k));
     dim3 grid((unsigned)p.tiles_n, (unsigned)p.tiles_m, (unsigned)p.nz);

@@ -32,7 +32,19 @@ constexpr int kThreads = (kWorkers + 1) * 32;
 constexpr int kWorkerThreads = kWorkers * 32;
 constexpr int kMaxN = 256;
 constexpr int kStagePad = 4;       // FP32 staging row padding (floats)
-constexpr int kStages = 3;
+constexpr int kMaxStages = 3;
+// T = 1: the BF16 mode (G exact in bf16, SA as bf16 hi + lo; 2 products a
+// K-step).  T = 3: the FP32 mode -- G and SA each split into three bf16 terms
+// (x = x1 + x2 + x3 exactly: 3 x 8 significant bits), and the six products
+// of order down to 2^-16 accumulated in FP32 (the dropped G2 S3, G3 S2, G3 S3
+// are below 2^-23 of |G||SA|): FP32 accuracy on the BF16 tensor pipe.
+template <int T>
+struct Terms {
+    static constexpr int kA = T;                    // G terms
+    static constexpr int kB = T == 1 ? 2 : 3;       // SA terms
+    static constexpr int kStages = T == 1 ? 3 : 2;
+    static constexpr int kProducts = T == 1 ? 2 : 6;
+};
 constexpr size_t kSmemLimit = 232448;
 
 struct GtParams {
@@ -52,17 +64,42 @@ struct GtParams {
     const uint32_t* rcount;
 };
 
-__host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 16 KB (two tiles)
-__host__ __device__ inline uint32_t b_bytes(int npad) { return (uint32_t)npad * kKC * 2; }  // per hi / lo
-__host__ __device__ inline uint32_t stage_bytes(int npad) { return a_bytes() + 2 * b_bytes(npad); }
+__host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 16 KB (two tiles) a term
+__host__ __device__ inline uint32_t b_bytes(int npad) { return (uint32_t)npad * kKC * 2; }  // a term
+template <int T>
+__host__ __device__ inline uint32_t stage_bytes(int npad) {
+    return Terms<T>::kA * a_bytes() + Terms<T>::kB * b_bytes(npad);
+}
+template <int T>
+__host__ __device__ inline size_t smem_of(int npad) {
+    return (size_t)Terms<T>::kStages * stage_bytes<T>(npad) + (size_t)kKC * (npad + kStagePad) * 4 + 1024 + 128;
+}
+
+// x = t1 + t2 + t3 to 24 significant bits (each term the bf16 rounding of the
+// remainder): three bf16x2 words for the pair (a, b), a in the low halves.
+__device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t& w1, uint32_t& w2, uint32_t& w3) {
+    uint32_t h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(b), "f"(a));
+    const float ra = a - __uint_as_float(h << 16), rb = b - __uint_as_float(h & 0xFFFF0000u);
+    uint32_t m;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(m) : "f"(rb), "f"(ra));
+    const float sa = ra - __uint_as_float(m << 16), sb = rb - __uint_as_float(m & 0xFFFF0000u);
+    uint32_t l;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(sb), "f"(sa));
+    w1 = h;
+    w2 = m;
+    w3 = l;
+}
 
 __device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkerThreads) : "memory"); }
 
 // One block: row tile and r-slice number `blk` of problem p.
+template <int T>
 __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) {
+    constexpr int kStages = Terms<T>::kStages, kA = Terms<T>::kA, kB = Terms<T>::kB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-    const uint32_t sbytes = stage_bytes(p.npad);
+    const uint32_t sbytes = stage_bytes<T>(p.npad);
     uint8_t* stages = smem;
     float* stagef = reinterpret_cast<float*>(smem + kStages * sbytes);        // kKC x (npad + pad)
     const int ldf = p.npad + kStagePad;
@@ -137,7 +174,7 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
             // (2) G chunk: item = wt + 512 i -> (row quad gq = item / 16, column pair cp = item % 16),
             //     64 x 16 items = the 256 x 32 chunk, two independent draws per worker thread
             static_assert(2 * kWorkerThreads == (kM / 4) * (kKC / 2), "two G items per worker thread");
-            uint32_t gw[2][4];
+            uint32_t gw[2][4][kA];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int item = wt + kWorkerThreads * i;
@@ -157,9 +194,13 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const bool rowok = jq + t < p.k;
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(rowok ? a0[t] * p.scale : 0.f,
-                                                                   rowok ? a1[t] * p.scale : 0.f);
-                    gw[i][t] = *reinterpret_cast<const uint32_t*>(&h);
+                    const float g0 = rowok ? a0[t] * p.scale : 0.f, g1 = rowok ? a1[t] * p.scale : 0.f;
+                    if constexpr (kA == 1) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
+                        gw[i][t][0] = *reinterpret_cast<const uint32_t*>(&h);
+                    } else {
+                        split3_bf16x2(g0, g1, gw[i][t][0], gw[i][t][1], gw[i][t][2]);
+                    }
                 }
             }
             // (3) wait for the stage (one thread decides for all workers)
@@ -178,7 +219,10 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                 const int gq = item >> 4, cp = item & 15;
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    *reinterpret_cast<uint32_t*>(st + tc::sw64_offset(4 * gq + t, 2 * cp)) = gw[i][t];
+#pragma unroll
+                    for (int a = 0; a < kA; ++a)
+                        *reinterpret_cast<uint32_t*>(st + a * a_bytes() + tc::sw64_offset(4 * gq + t, 2 * cp)) =
+                            gw[i][t][a];
             }
             // (5) SA into the FP32 staging buffer
 #pragma unroll
@@ -191,21 +235,31 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
             }
             named_sync();
             // (6) transpose + split: item (n, c8) -> 8 consecutive c of column n
-            uint8_t* bh = st + a_bytes();
-            uint8_t* bl = bh + b_bytes(p.npad);
+            uint8_t* b0 = st + kA * a_bytes();   // SA term tiles, b_bytes apart
             for (int item = wt; item < p.npad * (kKC / 8); item += kWorkerThreads) {
                 const int n = item % p.npad, c8 = item / p.npad;
                 float v[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] = stagef[(8 * c8 + e) * ldf + n];
-                uint4 hi, lo;
-                tc::split_bf16x2(v[0], v[1], hi.x, lo.x);
-                tc::split_bf16x2(v[2], v[3], hi.y, lo.y);
-                tc::split_bf16x2(v[4], v[5], hi.z, lo.z);
-                tc::split_bf16x2(v[6], v[7], hi.w, lo.w);
                 const uint32_t off = tc::sw64_offset(n, 8 * c8);
-                *reinterpret_cast<uint4*>(bh + off) = hi;
-                *reinterpret_cast<uint4*>(bl + off) = lo;
+                if constexpr (kB == 2) {
+                    uint4 hi, lo;
+                    tc::split_bf16x2(v[0], v[1], hi.x, lo.x);
+                    tc::split_bf16x2(v[2], v[3], hi.y, lo.y);
+                    tc::split_bf16x2(v[4], v[5], hi.z, lo.z);
+                    tc::split_bf16x2(v[6], v[7], hi.w, lo.w);
+                    *reinterpret_cast<uint4*>(b0 + off) = hi;
+                    *reinterpret_cast<uint4*>(b0 + b_bytes(p.npad) + off) = lo;
+                } else {
+                    uint4 w1, w2, w3;
+                    split3_bf16x2(v[0], v[1], w1.x, w2.x, w3.x);
+                    split3_bf16x2(v[2], v[3], w1.y, w2.y, w3.y);
+                    split3_bf16x2(v[4], v[5], w1.z, w2.z, w3.z);
+                    split3_bf16x2(v[6], v[7], w1.w, w2.w, w3.w);
+                    *reinterpret_cast<uint4*>(b0 + off) = w1;
+                    *reinterpret_cast<uint4*>(b0 + b_bytes(p.npad) + off) = w2;
+                    *reinterpret_cast<uint4*>(b0 + 2 * b_bytes(p.npad) + off) = w3;
+                }
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -254,16 +308,23 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t a = base + s * sbytes, bh = a + a_bytes(), bl = bh + b_bytes(p.npad);
+                const uint32_t a = base + s * sbytes, b = a + kA * a_bytes();
+                // (A term, SA term) of each product: BF16 mode G (SA_hi + SA_lo);
+                // FP32 mode the six products of order down to 2^-16
+                constexpr int kPA[6] = {0, 0, 1, 0, 1, 2}, kPB[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
                 for (int kk = 0; kk < kKC / 16; ++kk) {
                     const uint32_t ko = 32u * kk;
 #pragma unroll
                     for (int t = 0; t < kM / kMT; ++t) {
-                        const uint32_t at = a + (uint32_t)t * (kMT * kKC * 2) + ko;
                         const uint32_t dt = tmem + (uint32_t)(t * p.npad);
-                        tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bh + ko), idesc, (g | kk) != 0);
-                        tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bl + ko), idesc, 1);
+#pragma unroll
+                        for (int q = 0; q < Terms<T>::kProducts; ++q) {
+                            const uint32_t at = a + (uint32_t)kPA[q] * a_bytes() + (uint32_t)t * (kMT * kKC * 2) + ko;
+                            const uint32_t bt = b + (uint32_t)kPB[q] * b_bytes(p.npad) + ko;
+                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bt), idesc,
+                                         (g | kk | q) != 0);
+                        }
                     }
                 }
                 tc::mma_commit(empty + s);
@@ -284,13 +345,14 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     if (threadIdx.x == 0 && *abort) set_flag(p.flag, LSK_FLAG_TIMEOUT);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p) { gauss_tc_body(p, blockIdx.x); }
+template <int T>
+__global__ void __launch_bounds__(kThreads, 1) gauss_tc_kernel(const GtParams p) { gauss_tc_body<T>(p, blockIdx.x); }
 
 // Grouped: the blocks of many problems in one grid.
 __global__ void __launch_bounds__(kThreads, 1) gauss_tc_grouped_kernel(const GtParams* __restrict__ ps,
                                                                        const int* __restrict__ off, int count) {
     const int g = group_of(off, count, blockIdx.x);
-    gauss_tc_body(ps[g], (int)blockIdx.x - __ldg(off + g));
+    gauss_tc_body<1>(ps[g], (int)blockIdx.x - __ldg(off + g));
 }
 
 struct Plan {
@@ -299,7 +361,7 @@ struct Plan {
     size_t smem;
 };
 
-bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
+bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P, int terms = 1) {
     if (d < 1 || d > kMaxN || k < 1 || r < 1) return false;
     P.npad = (int)((d + 31) / 32) * 32;
     P.tiles_m = (int)((k + kM - 1) / kM);
@@ -311,7 +373,7 @@ bool make_plan(int64_t r, int64_t d, int64_t k, int sm_count, Plan& P) {
     ks = ((ks + kKC - 1) / kKC) * kKC;
     P.kslice = ks;
     P.slices = (int)((r + ks - 1) / ks);
-    P.smem = (size_t)kStages * stage_bytes(P.npad) + (size_t)kKC * (P.npad + kStagePad) * 4 + 1024 + 128;
+    P.smem = terms == 3 ? smem_of<3>(P.npad) : smem_of<1>(P.npad);
     return P.smem <= kSmemLimit;
 }
 
@@ -355,28 +417,28 @@ void plan_grouped(int64_t r, int64_t d, int64_t k, Plan& P, int slice_chunks) {
     ks = ((ks + kKC - 1) / kKC) * kKC;
     P.kslice = ks;
     P.slices = (int)((r + ks - 1) / ks);
-    P.smem = (size_t)kStages * stage_bytes(P.npad) + (size_t)kKC * (P.npad + kStagePad) * 4 + 1024 + 128;
+    P.smem = smem_of<1>(P.npad);
 }
 
 constexpr int kReduceBlockCap = 64;
 
 }  // namespace
 
-bool gauss_tc_supported(int64_t r, int64_t d, int64_t k) {
+bool gauss_tc_supported(int64_t r, int64_t d, int64_t k, int terms) {
     Plan P;
-    return make_plan(r, d, k, 152, P);
+    return make_plan(r, d, k, 152, P, terms);
 }
 
-size_t gauss_tc_workspace_bytes(int64_t r, int64_t d, int64_t k, int sm_count) {
+size_t gauss_tc_workspace_bytes(int64_t r, int64_t d, int64_t k, int sm_count, int terms) {
     Plan P;
-    if (!make_plan(r, d, k, sm_count, P)) return 0;
+    if (!make_plan(r, d, k, sm_count, P, terms)) return 0;
     return ws_round((size_t)P.slices * k * d * 4);
 }
 
 cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, uint64_t seed, float* GSA, void* ws,
-                            int sm_count, cudaStream_t st) {
+                            int sm_count, cudaStream_t st, int terms) {
     Plan P;
-    if (!make_plan(r, d, k, sm_count, P)) return cudaErrorNotSupported;
+    if (!make_plan(r, d, k, sm_count, P, terms)) return cudaErrorNotSupported;
     GtParams p;
     p.SA = SA;
     p.part = (float*)ws;
@@ -394,9 +456,16 @@ cudaError_t gauss_tc_launch(const float* SA, int64_t r, int64_t d, int64_t k, ui
     p.out = GSA;
     p.idx = nullptr;
     p.rcount = nullptr;
-    cudaError_t e = allow_dynamic_smem(gauss_tc_kernel);
-    if (e != cudaSuccess) return e;
-    LSK_PROF("gauss_tc", st) gauss_tc_kernel<<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
+    cudaError_t e;
+    if (terms == 3) {
+        e = allow_dynamic_smem(gauss_tc_kernel<3>);
+        if (e != cudaSuccess) return e;
+        LSK_PROF("gauss_tc_fp32", st) gauss_tc_kernel<3><<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
+    } else {
+        e = allow_dynamic_smem(gauss_tc_kernel<1>);
+        if (e != cudaSuccess) return e;
+        LSK_PROF("gauss_tc", st) gauss_tc_kernel<1><<<P.tiles_m * P.slices, kThreads, P.smem, st>>>(p);
+    }
     const int64_t len = k * d;
     int64_t g = (len + 255) / 256;
     if (g > 8 * (int64_t)sm_count) g = 8 * (int64_t)sm_count;

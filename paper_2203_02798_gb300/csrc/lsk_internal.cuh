@@ -234,7 +234,8 @@ struct GaussGroup {
     int count, blocks, rblocks;
     size_t smem;
 };
-bool gauss_tc_supported(int64_t r, int64_t d, int64_t k);
+// terms = 1: the BF16 mode; 3: the FP32 mode on the tensor cores
+bool gauss_tc_supported(int64_t r, int64_t d, int64_t k, int terms = 1);
 size_t gauss_group_part_bytes(int64_t r, int64_t d, int64_t k, int slice_chunks = 0);
 void gauss_group_build(const std::vector<GaussJob>& jobs, HostTable& t, GaussGroup& g);
 cudaError_t gauss_group_launch(const GaussGroup& g, const unsigned char* table, cudaStream_t st);

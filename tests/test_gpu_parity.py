@@ -149,7 +149,9 @@ def test_cs_sketch_bad_csr_reported(lsk):
 
 
 # ---------------------------------------------------------------- G * SA ---
+# fp32 with r >= 8192 runs on the tensor cores (three bf16 terms of G and SA)
 @pytest.mark.parametrize("r,d,k,prec", [(2500, 50, 100, "fp32"), (40_000, 200, 400, "fp32"),
+                                        (8192, 256, 512, "fp32"), (20_011, 64, 100, "fp32"), (9000, 130, 257, "fp32"),
                                         (3000, 256, 512, "bf16"), (777, 3, 5, "fp32"), (1000, 129, 70, "bf16"),
                                         (65_536, 256, 512, "bf16"), (40_000, 200, 400, "bf16"), (31, 7, 3, "bf16"),
                                         (2500, 50, 100, "bf16")])
@@ -174,6 +176,36 @@ def test_gram_dense(lsk, n, d):
     ref = ogr.gram_dense(A)
     assert rel_fro(C, ref) <= 1e-5
     assert np.array_equal(C, C.T)
+
+
+def test_gauss_fp32_runs_on_the_tensor_cores(lsk):
+    """The FP32 Gaussian stage of a long sketch takes the three-term tensor-core
+    kernel (checked by its profile name), and its result is as close to the
+    FP64 product as the SIMT FP32 kernel's is on a short sketch."""
+    r, d, k = 16_384, 200, 400
+    SA = workloads.dense_normal(r, d, seed=4) * (10.0 ** np.linspace(-3, 3, d)).astype(np.float32)
+    ctx = lsk.context()
+    ctx.profile(True)
+    ctx.profile_reset()
+    got = host(lsk.gauss_sketch(dev(SA), k, 5, "fp32")).astype(np.float64)
+    ctx.sync()
+    names = set(ctx.profile_totals())
+    ctx.profile(False)
+    assert "gauss_tc_fp32" in names and "gauss_simt" not in names
+    # against the oracle: the FP32 tolerance (G's float32 evaluation differs
+    # from the oracle's by a few ulp, as on the SIMT path)
+    G = oga.gaussian_matrix(k, r, 5, oga.PREC_FP32)
+    assert rel_fro(got, G @ SA.astype(np.float64)) <= 1e-5
+    # the tensor-core arithmetic alone: against the FP64 product of the
+    # device's own G -- products of three-term splits (below 2^-22 |G||SA|
+    # each) and FP32 sums; the tensor pipe's FP32 accumulation rounds toward
+    # zero, ~2^-25 of the running sum per accumulation (96 a slice here), so
+    # the entries come out ~2e-6 small in magnitude: bounded by 4e-6 relative
+    Gd = host(lsk.debug_gauss(k, r, 5, "fp32")).astype(np.float64)
+    ref = Gd @ SA.astype(np.float64)
+    bound = np.abs(Gd) @ np.abs(SA.astype(np.float64))
+    assert np.all(np.abs(got - ref) <= (2 * (r + 16) * U32 + 2.0**-21) * bound)
+    assert rel_fro(got, ref) <= 4e-6
 
 
 def test_gram_dense_integer_exact_and_alpha_beta(lsk):
