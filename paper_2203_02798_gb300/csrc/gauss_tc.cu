@@ -1,24 +1,24 @@
-// gauss_tc.cu -- Gaussian stage GSA = G * SA on tcgen05 tensor cores (BF16).
+// gauss_tc.cu -- Gaussian stage GSA = G * SA on tcgen05 tensor cores.
 //
-// G (k x r) is exactly representable in bfloat16 by definition of the BF16
-// mode (the bf16 rounding of z / sqrt(k)); SA is split into bf16 hi + lo.
+// BF16 mode: G (k x r) is exactly representable in bfloat16 by definition of
+// the mode (the bf16 rounding of z / sqrt(k)); SA is split into bf16 hi + lo.
 //     GSA = G SA_hi + G SA_lo       (FP32 accumulation in tensor memory)
+// FP32 mode (Terms<3>): G and SA each as three bf16 terms, six products.
 // A block owns one 256-row band of G (two 128-row MMA tiles) and one slice
 // of the r dimension; the k x d partials of the slices are added afterwards
-// in a fixed order with a compensated FP32 sum (deterministic).  Per 32-column chunk of the slice:
-//   - the 16 worker warps draw the 256 x 32 G chunk (Philox + Box-Muller, 4
-//     rows per draw, two independent draws per thread) straight into the
-//     bf16 K-major operand tiles, and load the 32 rows of SA (row-major, N
-//     contiguous) into a padded FP32 staging buffer, then transpose it into
-//     the K-major bf16 hi / lo tiles, which both MMA tiles share;
-//   - lane 0 of warp 16 issues the 8 MMAs (2 K-steps x {hi, lo} x 2 tiles).
-// Drawing G is the bulk of the work (about 60 instructions per entry, with
-// long dependent chains), so the block runs 16 worker warps with two draws
-// each to keep every scheduler supplied; SA staging is split thin.
-// The draws of the next chunk overlap the loads of SA; the loads are always
-// consumed before the stage barrier is arrived on.  All workers move through
-// the chunks in lockstep (one thread waits on a stage and broadcasts the
-// result through a named barrier), so a timeout exits every worker alike.
+// in a fixed order with a compensated FP32 sum (deterministic).  Per 32-column
+// chunk of the slice, each of the 16 worker warps, on its own:
+//   - loads rows 2w, 2w+1 of the chunk's 32 rows of SA (16-byte loads);
+//   - draws its 64 items of the 256 x 32 G chunk (Philox + Box-Muller, 4 rows
+//     per draw, two independent draws per thread) into bf16 words;
+//   - claims the ring stage (the MMAs of its previous use are done), writes
+//     its G words into the K-major operand tiles and its SA rows, split, into
+//     MN-major tiles (SA's rows are the MMA's K, its columns N: no transpose),
+//     and arrives;
+// lane 0 of warp 16 issues the MMAs (2 K-steps x products x 2 tiles) once all
+// 16 warps have arrived.  Drawing G (~90 instructions per entry) is the bound,
+// so the workers share no barrier: a warp still drawing does not hold the
+// others up, and a warp may run a whole ring ahead.
 #include "tc_common.cuh"
 
 namespace {
@@ -31,8 +31,6 @@ constexpr int kMmaWarp = kWorkers;
 constexpr int kThreads = (kWorkers + 1) * 32;
 constexpr int kWorkerThreads = kWorkers * 32;
 constexpr int kMaxN = 256;
-constexpr int kStagePad = 4;       // FP32 staging row padding (floats)
-constexpr int kMaxStages = 3;
 // T = 1: the BF16 mode (G exact in bf16, SA as bf16 hi + lo; 2 products a
 // K-step).  T = 3: the FP32 mode -- G and SA each split into three bf16 terms
 // (x = x1 + x2 + x3 exactly: 3 x 8 significant bits), and the six products
@@ -42,7 +40,7 @@ template <int T>
 struct Terms {
     static constexpr int kA = T;                    // G terms
     static constexpr int kB = T == 1 ? 2 : 3;       // SA terms
-    static constexpr int kStages = T == 1 ? 3 : 2;
+    static constexpr int kStages = T == 1 ? 4 : 2;
     static constexpr int kProducts = T == 1 ? 2 : 6;
 };
 constexpr size_t kSmemLimit = 232448;
@@ -65,14 +63,19 @@ struct GtParams {
 };
 
 __host__ __device__ constexpr uint32_t a_bytes() { return kM * kKC * 2; }               // 16 KB (two tiles) a term
-__host__ __device__ inline uint32_t b_bytes(int npad) { return (uint32_t)npad * kKC * 2; }  // a term
+// SA's terms are MN-major (SA's rows are K, its columns N): 128-byte-swizzled
+// atoms of 8 rows x 64 columns, 1 KB apart along the columns (nbn of them)
+// and nbn KB apart along the rows
+__host__ __device__ inline uint32_t b_atoms(int npad) { return (uint32_t)(npad + 63) / 64; }
+__host__ __device__ inline uint32_t b_sbo(int npad) { return b_atoms(npad) * 1024u; }
+__host__ __device__ inline uint32_t b_bytes(int npad) { return b_sbo(npad) * (kKC / 8); }   // a term
 template <int T>
 __host__ __device__ inline uint32_t stage_bytes(int npad) {
     return Terms<T>::kA * a_bytes() + Terms<T>::kB * b_bytes(npad);
 }
 template <int T>
 __host__ __device__ inline size_t smem_of(int npad) {
-    return (size_t)Terms<T>::kStages * stage_bytes<T>(npad) + (size_t)kKC * (npad + kStagePad) * 4 + 1024 + 128;
+    return (size_t)Terms<T>::kStages * stage_bytes<T>(npad) + 1024 + 128;
 }
 
 // x = t1 + t2 + t3 to 24 significant bits (each term the bf16 rounding of the
@@ -91,7 +94,6 @@ __device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t& w1, ui
     w3 = l;
 }
 
-__device__ __forceinline__ void named_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkerThreads) : "memory"); }
 
 // One block: row tile and r-slice number `blk` of problem p.
 template <int T>
@@ -101,16 +103,13 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbytes = stage_bytes<T>(p.npad);
     uint8_t* stages = smem;
-    float* stagef = reinterpret_cast<float*>(smem + kStages * sbytes);        // kKC x (npad + pad)
-    const int ldf = p.npad + kStagePad;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stagef + kKC * ldf);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
     uint64_t* full = bars;              // [kStages] (kWorkers arrivals)
     uint64_t* empty = bars + kStages;   // [kStages] (MMA commit)
     uint64_t* done = bars + 2 * kStages;  // accumulator complete   (MMA commit)
     uint64_t* fin = done + 1;             // every MMA complete     (MMA commit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* go_on = abort + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blk % p.tiles_m, slice = blk / p.tiles_m;
@@ -142,31 +141,35 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kWorkers) {
+        // Each worker warp works alone: per chunk it loads SA rows 2 w, 2 w + 1
+        // of the chunk, draws its 64 items of G, claims the stage, writes both
+        // and arrives; the warps are held together only by the stage ring.
         const int wt = threadIdx.x;   // 0 .. kWorkerThreads - 1
+        constexpr int H = (kMaxN + 127) / 128;          // 128-column halves of a row of SA
+        const int nh = (p.npad + 127) / 128;
+        const bool vec = (p.d % 4) == 0;
         bool ok = true;
         for (int g = 0; g < nchunks; ++g) {
             const int s = g % kStages;
             const int64_t c0 = c_begin + (int64_t)g * kKC;
-            // (1) SA rows c0 .. c0+31 into registers: float4 f = wt + 512 i,
-            //     row f / (npad/4), columns 4 (f % (npad/4))
-            const int q4 = p.npad / 4;
-            const int nf4 = kKC * q4;                     // float4 in the chunk (<= 4 per thread)
-            float4 sa[4];
+            // (1) SA rows c0 + 2 w + e, lane: columns 4 lane + 128 h .. + 3
+            float4 sa[2][H];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                sa[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const int f = wt + kWorkerThreads * i;
-                if (f < nf4) {
-                    const int rr = f / q4, n = 4 * (f % q4);
-                    const int64_t c = c0 + rr;
-                    if (c < c_end) {
+            for (int e = 0; e < 2; ++e) {
+                const int64_t c = c0 + 2 * warp + e;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    sa[e][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int n = 4 * lane + 128 * h;
+                    if (h < nh && c < c_end && n < p.d) {
                         const float* src = p.SA + c * p.d + n;
-                        if (n + 3 < p.d) {
-                            sa[i] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+                        if (vec) {
+                            sa[e][h] = __ldg(reinterpret_cast<const float4*>(src));
                         } else {
-                            sa[i].x = n < p.d ? __ldg(src) : 0.f;
-                            sa[i].y = n + 1 < p.d ? __ldg(src + 1) : 0.f;
-                            sa[i].z = n + 2 < p.d ? __ldg(src + 2) : 0.f;
+                            sa[e][h].x = __ldg(src);
+                            sa[e][h].y = n + 1 < p.d ? __ldg(src + 1) : 0.f;
+                            sa[e][h].z = n + 2 < p.d ? __ldg(src + 2) : 0.f;
+                            sa[e][h].w = n + 3 < p.d ? __ldg(src + 3) : 0.f;
                         }
                     }
                 }
@@ -203,10 +206,10 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                     }
                 }
             }
-            // (3) wait for the stage (one thread decides for all workers)
-            if (wt == 0) *go_on = tc::mbar_wait(empty + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
-            named_sync();
-            if (!*go_on) {
+            // (3) claim the stage (the MMAs of its previous use are done)
+            int okw = 1;
+            if (lane == 0) okw = tc::mbar_wait(empty + s, ((uint32_t)(g / kStages) & 1u) ^ 1u, abort) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, okw, 0)) {
                 ok = false;
                 break;
             }
@@ -224,41 +227,35 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
                         *reinterpret_cast<uint32_t*>(st + a * a_bytes() + tc::sw64_offset(4 * gq + t, 2 * cp)) =
                             gw[i][t][a];
             }
-            // (5) SA into the FP32 staging buffer
+            // (5) SA rows split into the kB MN-major terms: columns 4 lane .. + 3 of
+            //     K-row kr go to atom (col / 64, kr / 8), row kr % 8, 16-byte chunk
+            //     ((col % 64) / 8) ^ (kr % 8), bytes 8 (lane % 2) .. + 7
+            uint8_t* b0 = st + kA * a_bytes();
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int f = wt + kWorkerThreads * i;
-                if (f < nf4) {
-                    const int rr = f / q4, n = 4 * (f % q4);
-                    *reinterpret_cast<float4*>(stagef + rr * ldf + n) = sa[i];
-                }
-            }
-            named_sync();
-            // (6) transpose + split: item (n, c8) -> 8 consecutive c of column n
-            uint8_t* b0 = st + kA * a_bytes();   // SA term tiles, b_bytes apart
-            for (int item = wt; item < p.npad * (kKC / 8); item += kWorkerThreads) {
-                const int n = item % p.npad, c8 = item / p.npad;
-                float v[8];
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t kr = 2u * (uint32_t)warp + (uint32_t)e, rr = kr & 7u;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = stagef[(8 * c8 + e) * ldf + n];
-                const uint32_t off = tc::sw64_offset(n, 8 * c8);
-                if constexpr (kB == 2) {
-                    uint4 hi, lo;
-                    tc::split_bf16x2(v[0], v[1], hi.x, lo.x);
-                    tc::split_bf16x2(v[2], v[3], hi.y, lo.y);
-                    tc::split_bf16x2(v[4], v[5], hi.z, lo.z);
-                    tc::split_bf16x2(v[6], v[7], hi.w, lo.w);
-                    *reinterpret_cast<uint4*>(b0 + off) = hi;
-                    *reinterpret_cast<uint4*>(b0 + b_bytes(p.npad) + off) = lo;
-                } else {
-                    uint4 w1, w2, w3;
-                    split3_bf16x2(v[0], v[1], w1.x, w2.x, w3.x);
-                    split3_bf16x2(v[2], v[3], w1.y, w2.y, w3.y);
-                    split3_bf16x2(v[4], v[5], w1.z, w2.z, w3.z);
-                    split3_bf16x2(v[6], v[7], w1.w, w2.w, w3.w);
-                    *reinterpret_cast<uint4*>(b0 + off) = w1;
-                    *reinterpret_cast<uint4*>(b0 + b_bytes(p.npad) + off) = w2;
-                    *reinterpret_cast<uint4*>(b0 + 2 * b_bytes(p.npad) + off) = w3;
+                for (int h = 0; h < H; ++h) {
+                    if (h >= nh) break;
+                    const uint32_t col = 4u * (uint32_t)lane + 128u * h;
+                    if (col >= 64u * b_atoms(p.npad)) continue;   // past the term's atoms (zeros)
+                    const uint32_t off = (col >> 6) * 1024u + (kr >> 3) * b_sbo(p.npad) + rr * 128u +
+                                         (((((col & 63u) >> 3) ^ rr) & 7u) << 4) + (col & 7u) * 2u;
+                    const float4 v = sa[e][h];
+                    if constexpr (kB == 2) {
+                        uint2 hi, lo;
+                        tc::split_bf16x2(v.x, v.y, hi.x, lo.x);
+                        tc::split_bf16x2(v.z, v.w, hi.y, lo.y);
+                        *reinterpret_cast<uint2*>(b0 + off) = hi;
+                        *reinterpret_cast<uint2*>(b0 + b_bytes(p.npad) + off) = lo;
+                    } else {
+                        uint2 w1, w2, w3;
+                        split3_bf16x2(v.x, v.y, w1.x, w2.x, w3.x);
+                        split3_bf16x2(v.z, v.w, w1.y, w2.y, w3.y);
+                        *reinterpret_cast<uint2*>(b0 + off) = w1;
+                        *reinterpret_cast<uint2*>(b0 + b_bytes(p.npad) + off) = w2;
+                        *reinterpret_cast<uint2*>(b0 + 2 * b_bytes(p.npad) + off) = w3;
+                    }
                 }
             }
             tc::fence_proxy_async_smem();
@@ -299,7 +296,8 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
             const uint32_t base = tc::smem_u32(stages);
-            const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)p.npad);
+            // A (G) K-major, B (SA) MN-major
+            const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)p.npad) | (1u << 16);
             bool okm = true;
             for (int g = 0; g < nchunks; ++g) {
                 const int s = g % kStages;
@@ -321,9 +319,9 @@ __device__ __forceinline__ void gauss_tc_body(const GtParams& p, const int blk) 
 #pragma unroll
                         for (int q = 0; q < Terms<T>::kProducts; ++q) {
                             const uint32_t at = a + (uint32_t)kPA[q] * a_bytes() + (uint32_t)t * (kMT * kKC * 2) + ko;
-                            const uint32_t bt = b + (uint32_t)kPB[q] * b_bytes(p.npad) + ko;
-                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw64_kmajor(bt), idesc,
-                                         (g | kk | q) != 0);
+                            const uint32_t bt = b + (uint32_t)kPB[q] * b_bytes(p.npad) + 2u * b_sbo(p.npad) * kk;
+                            tc::mma_bf16(dt, tc::desc_sw64_kmajor(at), tc::desc_sw128_mnmajor(bt, 1024u, b_sbo(p.npad)),
+                                         idesc, (g | kk | q) != 0);
                         }
                     }
                 }
