@@ -196,7 +196,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16"],
+                    help="tf32: BF16 Gaussian stage + TF32 row norms (the workload's own recipe); "
+                         "bf16: BF16x3 row norms; fp32: CUDA-core FP32")
     ap.add_argument("--ref-rows", type=int, default=262_144,
                     help="rows of the workload the reference arm's oracle runs per step")
     ap.add_argument("--cpu-rows", type=int, default=262_144,
@@ -523,6 +525,17 @@ def main():
            "copy_only_ms": cms, "copy_only_GB/s": a_bytes / (cms * 1e-3) / 1e9,
            "overlapped": world == 1}
 
+    # the same step with the other tensor-core row-norm arithmetic (BF16x3
+    # against TF32), for comparison
+    other = None
+    if args.prec in ("tf32", "bf16") and world == 1:
+        op = "bf16" if args.prec == "tf32" else "tf32"
+        for _ in range(2):
+            step(op)
+        oms, _, _ = timed(lambda: step(op), max(3, args.steps // 5))
+        oms /= max(3, args.steps // 5)
+        other = {"prec": op, "value": whole_job_rate(a_bytes, world, oms), "unit": "GB/s", "ms_per_step": oms}
+
     # the plain FP32 single-problem path on the same GPU
     plain = None
     if not args.no_plain and args.prec != "fp32" and world == 1:
@@ -550,11 +563,11 @@ def main():
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16+fp32+f64" if args.prec == "bf16" else "f32+f64",
+            "vs_baseline": None, "dtype": {"tf32": "bf16+tf32+fp32+f64", "bf16": "bf16+fp32+f64"}.get(args.prec, "f32+f64"),
             "data": "synthetic", "config": workload_config(args, world),
             "hbm_frac_of_step": (a_bytes * 2 + 4 * N_ROWS) / (ms_step * 1e-3) / 1e9 / hbm,
             "roofline": roofline, "kernels": kernels, "gpu_launches": gpu_launches,
-            "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "configs": small,
+            "other_prec": other, "plain_fp32": plain, "gram": gram, "jl": jl, "sketch_stage": sstage, "next": nxt, "configs": small,
             "batched": batched, "served": served, "e2e": e2e, "clocks": clk,
             "cpu_baseline": cpu,
         }))
@@ -687,6 +700,7 @@ def algorithmic_work(kernel):
     table = {
         "cs_dense_gather": {"bound": "hbm", "bytes": a_bytes + 4 * r * d},
         "rownorm_dense_simt": {"bound": "alu", "flops": n * d * (d + 1)},
+        "rownorm_dense_tf32": {"bound": "hbm", "bytes": a_bytes + 4 * n, "flops": n * d * (d + 1)},
         "rownorm_dense_tc": {"bound": "hbm", "bytes": a_bytes + 4 * n,
                              "flops": 3 * n * d * (d + 1)},
         "gauss_simt": {"bound": "alu", "flops": 2 * k * r * d},

@@ -82,7 +82,10 @@ typedef struct lsk_mat {
                             /* stage of a sketch with r >= 8192) the BF16   */
                             /* tensor pipe on three-term bf16 splits of G   */
                             /* and SA with FP32 accumulation                */
-#define LSK_PREC_TF32 1     /* reserved (accepted, runs as LSK_PREC_FP32)    */
+#define LSK_PREC_TF32 1     /* LSK_PREC_BF16 with the row-norm GEMM A B in  */
+                            /* TF32: one product of A and B each rounded to */
+                            /* the nearest TF32 (10 mantissa bits), FP32    */
+                            /* accumulation; every other stage as BF16      */
 #define LSK_PREC_BF16 2     /* tensor cores: BF16 G, split-BF16 operands,   */
                             /* FP32 accumulation                            */
 
@@ -121,7 +124,8 @@ int lsk_cs_sketch(lsk_ctx* ctx, const lsk_mat* A, int64_t r, uint64_t seed,
  * GSA = G * SA with G k x r, N(0,1) entries scaled by 1/sqrt(k) (header
  * comment).  SA: device r*d floats row-major; GSA: device k*d floats
  * row-major, overwritten.  prec: LSK_PREC_FP32 or LSK_PREC_BF16 (G exact in
- * bfloat16, SA split into two bfloat16 terms, FP32 accumulation).  In the
+ * bfloat16, SA split into two bfloat16 terms, FP32 accumulation;
+ * LSK_PREC_TF32 runs this stage as LSK_PREC_BF16).  In the
  * FP32 mode a sketch with r >= 8192 runs on the tensor cores with G and SA
  * each split into three bfloat16 terms (24 significant bits, exact) and the
  * six products down to order 2^-16 accumulated in FP32. */
@@ -167,8 +171,8 @@ int lsk_set_fused_sketch(int mode);
  * FP32 store (lsk_gram_prec(LSK_PREC_FP32) always takes this path). */
 int lsk_gram(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
              float* C);
-/* lsk_gram with a precision: LSK_PREC_FP32 / LSK_PREC_TF32 on the CUDA cores
- * in FP32 (as lsk_gram for CSR A); LSK_PREC_BF16 forms the products of dense
+/* lsk_gram with a precision: LSK_PREC_FP32 on the CUDA cores in FP32 (as
+ * lsk_gram for CSR A); LSK_PREC_BF16 (and LSK_PREC_TF32) forms the products of dense
  * A with d <= 256 on the tensor
  * cores from a bfloat16 split of A (a = hi + lo; hi^T hi + hi^T lo + lo^T hi,
  * about 2^-16 relative per product), accumulating at most 1024 rows in FP32
@@ -185,8 +189,16 @@ int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta,
  * lets the dense kernels skip the zero blocks.  prec (dense A):
  * LSK_PREC_FP32 = CUDA-core FP32; LSK_PREC_BF16 = tensor cores with A and B
  * split into bf16 hi + lo, A B ~ AhBh + AhBl + AlBh, FP32 accumulation, for
- * d, c <= 256 (other shapes run the FP32 kernel).  CSR A always runs Alg. 8
- * in FP32. */
+ * d, c <= 256 (other shapes run the FP32 kernel); LSK_PREC_TF32 = one TF32
+ * product on the tensor cores, A streamed by the copy engine (TMA), which
+ * rounds each entry to the nearest TF32 on the way (relative error <= 2^-11
+ * per entry of A and B; about 3e-4 on the leverage scores of 4M x 256 with
+ * column scales 1e-3 .. 1e3; more where a row's score is far below
+ * ||A_i|| ||B||, e.g. 1.6e-3 on rows scaled x100 among 4096 x 32 -- the
+ * BF16 form keeps ~1e-5 there), for 32 <= d <= 256, c <= 256, n >= 256, ld a
+ * multiple of 4 and 16-byte aligned values (other dense shapes run the
+ * BF16 form where it applies, else FP32).  CSR A always runs Alg. 8 in
+ * FP32. */
 int lsk_rownorms_prod(lsk_ctx* ctx, const lsk_mat* A, const float* B,
                       int64_t c, double alpha, double beta,
                       int32_t upper_triangular, int32_t prec, float* x);
@@ -212,7 +224,9 @@ int lsk_sketch_qr(lsk_ctx* ctx, const float* B, int64_t k, int64_t d,
  * the r x d CountSketch alone, as m = 0 in csrcgs), R from the sketch as in
  * lsk_sketch_qr, then ell_i = ||A_i R^-1||^2 (Alg. 8).  ell: device n
  * floats.  R_out: NULL or device d*d doubles receiving R.  Requires the
- * sketch to have at least d rows. */
+ * sketch to have at least d rows.  prec: the Gaussian stage as
+ * lsk_gauss_sketch (LSK_PREC_TF32: as LSK_PREC_BF16) and the row norms as
+ * lsk_rownorms_prod with B = R^-1. */
 int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
                         uint64_t seed, int32_t prec, float* ell,
                         double* R_out);
@@ -375,7 +389,9 @@ typedef struct lsk_batch_item {
  * problems run their whole pipeline on the worker streams.  The streams
  * fork from and join back into the context stream (asynchronous; deferred
  * errors as usual).  The grouped phases keep every grouped problem's sketch
- * resident at once (sum of r d 4 bytes plus small buffers).
+ * resident at once (sum of r d 4 bytes plus small buffers).  A batch runs
+ * LSK_PREC_TF32 as LSK_PREC_BF16 (its row norms use operands prepared for
+ * all problems at once in the BF16x3 layout).
  * Batching is not in the paper: it applies the same per-problem method to
  * many problems at once.  The batch's internal workspaces are owned by the
  * context.  The items array is read during the call only. */

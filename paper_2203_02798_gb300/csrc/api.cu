@@ -178,7 +178,7 @@ int lsk_gauss_sketch(lsk_ctx* ctx, const float* SA, int64_t r, int64_t d, int64_
     if (k >= ((int64_t)1 << 32)) return fail(ctx, LSK_ERR_INVALID_ARG, "k too large");
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);
     int rc = ws_ensure(ctx, gauss_workspace_bytes(r, d, k, prec, ctx->sm_count));
     if (rc) return rc;
     cudaError_t e = gauss_launch(SA, r, d, k, seed, prec, GSA, ctx->ws, ctx->sm_count, ctx->stream);
@@ -235,6 +235,7 @@ int lsk_gram_prec(lsk_ctx* ctx, const lsk_mat* A, double alpha, double beta, int
     if (!ctx) return LSK_ERR_INVALID_ARG;
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    prec = sketch_prec(prec);   // TF32: the BF16x3 tensor-core Gram
     if (prec != LSK_PREC_BF16) return gram_fp32(ctx, A, alpha, beta, C);
     ProfGuard pg(ctx);
     int rc = check_mat(ctx, A);
@@ -410,13 +411,14 @@ int lsk_leverage_scores(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, ui
     rc = check_sketch_args(ctx, A, r, k, prec);
     if (rc) return rc;
     if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, 0));
     if (rc) return rc;
     const SketchBufs b = carve(ctx->ws, A, r, k);
     cudaError_t e = sketch_and_factor(ctx, A, r, k, seed, prec, b, R_out);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (sketch)");
-    e = rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, prec, ell, b.scratch, ctx->flag, ctx->sm_count,
+    e = rownorms_launch(A, b.Rinv32, A->d, 1.0, 0.0, 1, rn_prec, ell, b.scratch, ctx->flag, ctx->sm_count,
                         ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores (row norms)");
     return finish(ctx, "lsk_leverage_scores");
@@ -435,7 +437,7 @@ int lsk_sketch_rows(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint64
     if (row0 < 0 || A->n > INT64_MAX - row0) return fail(ctx, LSK_ERR_INVALID_ARG, "row0 must be >= 0 and row0 + n < 2^63");
     if (!out) return fail(ctx, LSK_ERR_INVALID_ARG, "out is NULL");
     if (A->kind == LSK_CSR && A->d > 51200) return fail(ctx, LSK_ERR_UNSUPPORTED, "CSR sketch needs d <= 51200");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);
     cudaError_t e;
     if (k == 0) {   // S A straight into out (the gather adds into it when accumulating)
         rc = ws_ensure(ctx, cs_workspace_bytes(A->n, r));
@@ -469,9 +471,10 @@ int lsk_leverage_scores_from_sketch(lsk_ctx* ctx, const lsk_mat* A, const float*
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_TF32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     const int64_t d = A->d;
-    const size_t q = qr_workspace_bytes(rows, d), rn = rownorms_workspace_bytes(A, d, 1, prec);
+    const size_t q = qr_workspace_bytes(rows, d), rn = rownorms_workspace_bytes(A, d, 1, rn_prec);
     rc = ws_ensure(ctx, ws_round((size_t)d * d * 8) + ws_round((size_t)d * d * 4) + (q > rn ? q : rn) + 1024);
     if (rc) return rc;
     WsCarver wc{(char*)ctx->ws, 0};
@@ -480,7 +483,7 @@ int lsk_leverage_scores_from_sketch(lsk_ctx* ctx, const lsk_mat* A, const float*
     void* scratch = wc.take<char>(1);
     cudaError_t e = qr_launch(sketch, rows, d, R_out, Rinv64, Rinv32, scratch, ctx->flag, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_from_sketch (R)");
-    e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, prec, ell, scratch, ctx->flag, ctx->sm_count, ctx->stream);
+    e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, rn_prec, ell, scratch, ctx->flag, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_from_sketch (row norms)");
     return finish(ctx, "lsk_leverage_scores_from_sketch");
 }
@@ -495,11 +498,12 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
     if (rc) return rc;
     if (m < 1 || m > 4096) return fail(ctx, LSK_ERR_INVALID_ARG, "m must be in [1, 4096]");
     if (!ell && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "ell is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     // stage scratch after the factorisation: [X = R^-1 Pi, d*m f32][Pi | row-norm workspace]
     const size_t xb = ws_round((size_t)A->d * m * 4);
     const size_t jw = jl_workspace_bytes(A->d, m);
-    const size_t rw = rownorms_workspace_bytes(A, m, 0, prec);
+    const size_t rw = rownorms_workspace_bytes(A, m, 0, rn_prec);
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, xb + (jw > rw ? jw : rw)));
     if (rc) return rc;
     const SketchBufs b = carve(ctx->ws, A, r, k);
@@ -509,7 +513,7 @@ int lsk_leverage_scores_jl(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k,
     void* rest = (char*)b.scratch + xb;
     e = jl_launch(b.Rinv64, A->d, m, seed, X, rest, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_jl (R^-1 Pi)");
-    e = rownorms_launch(A, X, m, 1.0, 0.0, 0, prec, ell, rest, ctx->flag, ctx->sm_count, ctx->stream);
+    e = rownorms_launch(A, X, m, 1.0, 0.0, 0, rn_prec, ell, rest, ctx->flag, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_jl (row norms)");
     return finish(ctx, "lsk_leverage_scores_jl");
 }
@@ -521,7 +525,7 @@ int lsk_csrjlt(lsk_ctx* ctx, const lsk_mat* A, int64_t m, uint64_t seed, int32_t
     if (rc) return rc;
     if (A->kind != LSK_CSR) return fail(ctx, LSK_ERR_UNSUPPORTED, "lsk_csrjlt takes a CSR matrix");
     if (!C) return fail(ctx, LSK_ERR_INVALID_ARG, "C is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     if (m < 1 || !jlt_supported(A->d, m)) return fail(ctx, LSK_ERR_UNSUPPORTED, "m in [1, 2^20], d <= 1280");
@@ -541,7 +545,7 @@ int lsk_sketch_solve(lsk_ctx* ctx, const lsk_mat* A, const double* b, int64_t r,
     rc = check_sketch_args(ctx, A, r, k, prec);
     if (rc) return rc;
     if (!x || (!b && A->n > 0)) return fail(ctx, LSK_ERR_INVALID_ARG, "b / x is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, solve_workspace_bytes(r, k, A->d)));
     if (rc) return rc;
     const SketchBufs bufs = carve(ctx->ws, A, r, k);
@@ -626,10 +630,11 @@ int lsk_leverage_scores_truncated(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int
     if (rc) return rc;
     if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
     if (!(rcond >= 0.0 && rcond < 1.0)) return fail(ctx, LSK_ERR_INVALID_ARG, "rcond must be in [0, 1)");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     const int64_t rows = k > 0 ? k : r;
     const size_t tail = ws_round((size_t)rows * d * 4) + ws_round(qr_workspace_bytes(rows, d)) +
-                        ws_round((size_t)d * d * 4) + ws_round(rownorms_workspace_bytes(A, d, 0, prec)) +
+                        ws_round((size_t)d * d * 4) + ws_round(rownorms_workspace_bytes(A, d, 0, rn_prec)) +
                         ws_round(4) + 4096;
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, d, d) + tail));
     if (rc) return rc;
@@ -655,13 +660,13 @@ int lsk_leverage_scores_truncated(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int
     float* Bk = wc.take<float>((size_t)rows * c);
     void* qw = wc.take<char>(qr_workspace_bytes(rows, c));
     float* Bf = wc.take<float>((size_t)d * c);
-    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, prec));
+    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, rn_prec));
     e = gather_cols_launch(sk, rows, d, cb.cols, c, Bk, ctx->stream);
     if (e == cudaSuccess)
         e = qr_launch(Bk, rows, c, nullptr, b.Rinv64, b.Rinv32, qw, ctx->flag, ctx->sm_count, ctx->stream);
     if (e == cudaSuccess) e = embed_rows_launch(b.Rinv32, c, cb.cols, d, Bf, ctx->stream);
     if (e == cudaSuccess)
-        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
+        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, rn_prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_truncated (row norms)");
     return finish(ctx, "lsk_leverage_scores_truncated");
 }
@@ -673,7 +678,7 @@ int lsk_column_select(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k, uint
     int rc = css_checks(ctx, A, r, k, prec, c);
     if (rc) return rc;
     if (!cols) return fail(ctx, LSK_ERR_INVALID_ARG, "cols is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);
     const int64_t rows = k > 0 ? k : r;
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, A->d, c)));
     if (rc) return rc;
@@ -694,13 +699,14 @@ int lsk_leverage_scores_hrn(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k
     int rc = css_checks(ctx, A, r, k, prec, c);
     if (rc) return rc;
     if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     const int64_t d = A->d, rows = k > 0 ? k : r;
     // after the selection: [Gram of A or B[:, K]][its workspace][C_KK][factor ws][E_K R^-1][row-norm ws]
     const size_t gws = exact ? ws_round(gram_workspace_bytes(A, ctx->sm_count)) + ws_round((size_t)d * d * 8)
                              : ws_round((size_t)rows * c * 4) + ws_round(qr_workspace_bytes(rows, c));
     const size_t tail = gws + ws_round((size_t)c * c * 8) + ws_round(qr_from_gram_workspace_bytes(c)) +
-                        ws_round((size_t)d * c * 4) + ws_round(rownorms_workspace_bytes(A, c, 0, prec)) + 4096;
+                        ws_round((size_t)d * c * 4) + ws_round(rownorms_workspace_bytes(A, c, 0, rn_prec)) + 4096;
     rc = ws_ensure(ctx, sketch_bytes(A, r, k, prec, ctx->sm_count, css_bytes(rows, d, c) + tail));
     if (rc) return rc;
     const SketchBufs b = carve(ctx->ws, A, r, k);
@@ -730,10 +736,10 @@ int lsk_leverage_scores_hrn(lsk_ctx* ctx, const lsk_mat* A, int64_t r, int64_t k
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_hrn (factor)");
     float* Bf = wc.take<float>((size_t)d * c);
-    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, prec));
+    void* rw = wc.take<char>(rownorms_workspace_bytes(A, c, 0, rn_prec));
     e = embed_rows_launch(b.Rinv32, c, cb.cols, d, Bf, ctx->stream);
     if (e == cudaSuccess)
-        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
+        e = rownorms_launch(A, Bf, c, 1.0, 0.0, 0, rn_prec, theta, rw, ctx->flag, ctx->sm_count, ctx->stream);
     if (e == cudaSuccess && cols)
         e = cudaMemcpyAsync(cols, cb.cols, (size_t)c * 4, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_hrn (row norms)");
@@ -762,11 +768,12 @@ int lsk_leverage_scores_exact(lsk_ctx* ctx, const lsk_mat* A, int32_t prec, floa
     if (rc) return rc;
     if (A->d > 1024) return fail(ctx, LSK_ERR_UNSUPPORTED, "d <= 1024");
     if (!theta && A->n > 0) return fail(ctx, LSK_ERR_INVALID_ARG, "theta is NULL");
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    const int32_t rn_prec = prec;   // the row norms keep TF32
+    prec = sketch_prec(prec);
     if (prec != LSK_PREC_FP32 && prec != LSK_PREC_BF16)
         return fail(ctx, LSK_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     const int64_t d = A->d;
-    rc = ws_ensure(ctx, gram_factor_bytes(A, ctx->sm_count) + ws_round(rownorms_workspace_bytes(A, d, 1, prec)));
+    rc = ws_ensure(ctx, gram_factor_bytes(A, ctx->sm_count) + ws_round(rownorms_workspace_bytes(A, d, 1, rn_prec)));
     if (rc) return rc;
     WsCarver wc{(char*)ctx->ws, 0};
     double* G = wc.take<double>((size_t)d * d);
@@ -774,10 +781,10 @@ int lsk_leverage_scores_exact(lsk_ctx* ctx, const lsk_mat* A, int32_t prec, floa
     float* Rinv32 = wc.take<float>((size_t)d * d);
     void* gws = wc.take<char>(gram_workspace_bytes(A, ctx->sm_count));
     void* qws = wc.take<char>(qr_from_gram_workspace_bytes(d));
-    void* rws = wc.take<char>(rownorms_workspace_bytes(A, d, 1, prec));
+    void* rws = wc.take<char>(rownorms_workspace_bytes(A, d, 1, rn_prec));
     cudaError_t e = gram_factor(ctx, A, G, gws, qws, R_out, Rinv64, Rinv32);
     if (e == cudaSuccess)
-        e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, prec, theta, rws, ctx->flag, ctx->sm_count, ctx->stream);
+        e = rownorms_launch(A, Rinv32, d, 1.0, 0.0, 1, rn_prec, theta, rws, ctx->flag, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_leverage_scores_exact");
     return finish(ctx, "lsk_leverage_scores_exact");
 }
@@ -833,7 +840,7 @@ int lsk_sketch_precondition_lsq(lsk_ctx* ctx, const lsk_mat* A, const double* b,
     if (rc) return rc;
     if (!opts) return fail(ctx, LSK_ERR_INVALID_ARG, "opts is NULL");
     if (!x || (!b && A->n > 0)) return fail(ctx, LSK_ERR_INVALID_ARG, "b / x is NULL");
-    int32_t prec = opts->prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : opts->prec;
+    int32_t prec = sketch_prec(opts->prec);
     rc = check_sketch_args(ctx, A, opts->r, opts->k, prec);
     if (rc) return rc;
     if (opts->max_iter < 1 || opts->max_refine < 0 || !(opts->tol > 0.0))
@@ -885,7 +892,7 @@ int lsk_debug_wait_timeout(lsk_ctx* ctx, int64_t limit_us) {
 int lsk_debug_gauss(lsk_ctx* ctx, int64_t k, int64_t r, uint64_t seed, int32_t prec, float* G) {
     if (!ctx) return LSK_ERR_INVALID_ARG;
     if (k < 1 || r < 1 || !G) return fail(ctx, LSK_ERR_INVALID_ARG, "bad k / r / G");
-    cudaError_t e = gauss_debug_launch(k, r, seed, prec == LSK_PREC_BF16 ? LSK_PREC_BF16 : LSK_PREC_FP32, G,
+    cudaError_t e = gauss_debug_launch(k, r, seed, sketch_prec(prec) == LSK_PREC_BF16 ? LSK_PREC_BF16 : LSK_PREC_FP32, G,
                                        ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lsk_debug_gauss");
     return finish(ctx, "lsk_debug_gauss");

@@ -506,7 +506,7 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
         snprintf(ctx->err, sizeof(ctx->err), "bad batch");
         return LSK_ERR_INVALID_ARG;
     }
-    if (prec == LSK_PREC_TF32) prec = LSK_PREC_FP32;
+    prec = sketch_prec(prec);   // a batch's row norms take the prepared BF16x3 images
     for (int i = 0; i < count; ++i) {
         const int rc = check_leverage_args(ctx, &items[i].A, items[i].r, items[i].k, prec);
         if (rc) return rc;
@@ -652,7 +652,7 @@ extern "C" int lsk_batch_leverage_scores(lsk_ctx* ctx, int32_t count, const lsk_
 
 extern "C" int lsk_batch_streams(lsk_ctx* ctx, int32_t count, const lsk_batch_item* items, int32_t prec) {
     if (!ctx || !ctx->batch) return 0;
-    auto it = ctx->batch->tuned.find(signature(items, count, prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : prec));
+    auto it = ctx->batch->tuned.find(signature(items, count, sketch_prec(prec)));
     return it == ctx->batch->tuned.end() ? 0 : it->second.S;
 }
 
@@ -661,7 +661,7 @@ extern "C" int lsk_batch_schedule(lsk_ctx* ctx, int32_t count, const lsk_batch_i
     BatchTune t;
     int known = 0;
     if (ctx && ctx->batch && items) {
-        auto it = ctx->batch->tuned.find(signature(items, count, prec == LSK_PREC_TF32 ? LSK_PREC_FP32 : prec));
+        auto it = ctx->batch->tuned.find(signature(items, count, sketch_prec(prec)));
         if (it != ctx->batch->tuned.end()) {
             t = it->second;
             known = 1;

@@ -261,6 +261,10 @@ size_t gram_tc_workspace_bytes(const lsk_mat* A, int sm_count);
 cudaError_t gram_tc_launch(const lsk_mat* A, double alpha, double beta, float* C, void* ws, int* flag,
                            int sm_count, cudaStream_t st);
 
+// LSK_PREC_TF32 is the BF16 mode with the row-norm GEMM A B in TF32: every
+// stage other than the row norms takes the BF16 arithmetic
+inline int32_t sketch_prec(int32_t prec) { return prec == LSK_PREC_TF32 ? LSK_PREC_BF16 : prec; }
+
 // rownorms.cu
 size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec);
 // min_tiles: the dense tensor-core form launches CTAs for at least that many
@@ -282,12 +286,14 @@ struct BbtGroup {
 };
 void bbt_group_build(const std::vector<BbtJob>& jobs, HostTable& t, BbtGroup& g);
 cudaError_t bbt_group_launch(const BbtGroup& g, const unsigned char* table, cudaStream_t st);
-// rownorms_tc.cu
-bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri);
+// rownorms_tc.cu; tf32: the TMA-fed CTA-pair kernel with one TF32 product
+// (A rounded to the nearest TF32 in shared memory) instead of BF16x3 (the
+// same workspace; img_ready is for the BF16x3 form only)
+bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri, bool tf32 = false);
 size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri);
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta,
                                int upper_tri, float* x, void* ws, int* flag, int sm_count, cudaStream_t st,
-                               int min_tiles = 16, const uint8_t* img_ready = nullptr);
+                               int min_tiles = 16, const uint8_t* img_ready = nullptr, bool tf32 = false);
 // the tensor-core images of many problems' B (rownorms_tc_workspace_bytes each)
 struct RnImageJob {
     lsk_mat A;

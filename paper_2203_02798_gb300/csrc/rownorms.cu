@@ -163,7 +163,9 @@ __global__ void rownorm_csr_kernel(const float* __restrict__ V, const int32_t* _
 
 size_t rownorms_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri, int32_t prec) {
     if (A->kind == LSK_DENSE) {
-        if (prec == LSK_PREC_BF16 && rownorms_tc_supported(A, c, upper_tri))
+        // the BF16x3 and TF32 images have the same size
+        if ((prec == LSK_PREC_BF16 || prec == LSK_PREC_TF32) &&
+            (rownorms_tc_supported(A, c, upper_tri) || rownorms_tc_supported(A, c, upper_tri, true)))
             return rownorms_tc_workspace_bytes(A, c, upper_tri);
         return 0;
     }
@@ -175,7 +177,14 @@ cudaError_t rownorms_launch(const lsk_mat* A, const float* B, int64_t c, double 
                             cudaStream_t st, int min_tiles, const void* prepared) {
     const int64_t n = A->n, d = A->d;
     if (n == 0) return cudaSuccess;
-    if (A->kind == LSK_DENSE && prec == LSK_PREC_BF16 && rownorms_tc_supported(A, c, upper_tri))
+    // TF32: the one-product TF32 kernel where A suits TMA, else BF16x3 (more
+    // accurate), else FP32 on the CUDA cores (an operand prepared by a grouped
+    // launch is a BF16x3 image)
+    if (A->kind == LSK_DENSE && prec == LSK_PREC_TF32 && !prepared && rownorms_tc_supported(A, c, upper_tri, true))
+        return rownorms_tc_launch(A, B, c, (float)alpha, (float)beta, upper_tri, x, ws, flag, sm_count, st,
+                                  min_tiles, nullptr, true);
+    if (A->kind == LSK_DENSE && (prec == LSK_PREC_BF16 || prec == LSK_PREC_TF32) &&
+        rownorms_tc_supported(A, c, upper_tri))
         return rownorms_tc_launch(A, B, c, (float)alpha, (float)beta, upper_tri, x, ws, flag, sm_count, st,
                                   min_tiles, (const uint8_t*)prepared);
     if (A->kind == LSK_DENSE) {

@@ -77,12 +77,41 @@ struct RnParams {
     uint32_t hoff[kMaxQ];
     uint32_t hb_bytes;
     int pair, stages2, ntiles2;
+    // TF32 form (pair only): each CTA's half of B is one TF32 image of
+    // 2 hb_bytes, chunk q at 2 hoff[q] (128-byte rows of 32 FP32 words)
+    int tf32;
 };
 
 // B (d x c, row-major) -> the shared-memory image of its bf16 hi / lo parts:
 // per K-chunk q, an (nn[q] x 32) K-major tile whose row r is column n0[q]+r.
 __device__ __forceinline__ void prep_body(const float* __restrict__ B, const RnParams& p, uint8_t* __restrict__ img,
                                           uint32_t blk, uint32_t nblk) {
+    if (p.tf32) {
+        // B rounded to the nearest TF32 (ties away from zero: half a unit of
+        // the 13 dropped bits added to the magnitude, then those bits
+        // cleared), in 128-byte-swizzled K-major tiles: element (r, k) of
+        // the half tile at 1024 (r / 8) + 128 (r % 8) + 16 ((k / 4) ^ (r % 8))
+        // + 4 (k % 4)
+        uint32_t total = 0;
+        for (int q = 0; q < p.nq; ++q) total += p.nn[q] * kKC;
+        for (uint32_t e = blk * blockDim.x + threadIdx.x; e < total; e += nblk * blockDim.x) {
+            int q = 0;
+            uint32_t el = e;
+            while (el >= p.nn[q] * kKC) {
+                el -= p.nn[q] * kKC;
+                ++q;
+            }
+            const uint32_t r = el / kKC, kl = el % kKC;
+            const int j = (int)(p.n0[q] + r), k = kKC * q + (int)kl;
+            const float b = (k < p.d && j < p.c) ? B[(int64_t)k * p.c + j] : 0.f;
+            const uint32_t u = (__float_as_uint(b) + 0x1000u) & 0xFFFFE000u;
+            const uint32_t hn = p.nn[q] / 2, h = r / hn, rr = r - h * hn;
+            const uint32_t off = h * 2 * p.hb_bytes + 2 * p.hoff[q] + (rr >> 3) * 1024u + (rr & 7u) * 128u +
+                                 (((kl >> 2) ^ (rr & 7u)) << 4) + (kl & 3u) * 4u;
+            *reinterpret_cast<uint32_t*>(img + off) = u;
+        }
+        return;
+    }
     uint32_t total = 0;
     for (int q = 0; q < p.nq; ++q) total += p.nn[q] * (kKC / 2);
     for (uint32_t e = blk * blockDim.x + threadIdx.x; e < total; e += nblk * blockDim.x) {
@@ -639,7 +668,15 @@ __device__ __forceinline__ void split_blocks_in_place(uint8_t* first_block, int 
     }
 }
 
-template <class T>
+// TF32 = false: the BF16x3 products of the converters' hi / lo split.
+// TF32 = true: one kind::tf32 product per K-step straight from the landed
+// chunk (A operand) and the TF32 image of B.  The tensor map then has the
+// TF32 element type, so the copy engine rounds every FP32 word of A to the
+// nearest TF32 on its way into shared memory (the MMA itself would drop the
+// 13 low mantissa bits: rounding toward zero, a -3.5e-4 relative bias on
+// A's entries on average); the converter warps only pass each landed chunk
+// on to the even CTA's MMA thread, group i of G taking chunks i, i + G, ...
+template <class T, bool TF32 = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(T::kThreads, 1)
     rownorm_tma2_kernel(const RnParams p, const uint8_t* __restrict__ img, const __grid_constant__ CUtensorMap tmA) {
     extern __shared__ uint8_t smem_raw[];
@@ -743,18 +780,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(T::kThreads, 1)
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t a_hi = sA_u32 + (uint32_t)s * kStageBytes, a_lo = a_hi + 512u;
-                    const uint32_t b_hi = sB_u32 + p.hoff[q], b_lo = b_hi + p.hb_bytes;
-                    const uint32_t idesc = tc::idesc_bf16_f32(2 * kRows, p.nn[q]);
                     const uint32_t d_tmem = d_base + p.n0[q];
+                    if constexpr (TF32) {
+                        // A: the 128 x 32 FP32 chunk as TMA left it (128-byte
+                        // swizzle, 8-row atoms 1024 bytes apart); B: chunk q of
+                        // the TF32 image; K = 8 (32 bytes) per MMA
+                        const uint32_t a0 = sA_u32 + (uint32_t)s * kStageBytes;
+                        const uint32_t b0 = sB_u32 + 2u * p.hoff[q];
+                        const uint32_t idesc = tc::idesc_tf32_f32(2 * kRows, p.nn[q]);
 #pragma unroll
-                    for (int kk = 0; kk < kKC / 16; ++kk) {
-                        const uint32_t ko = 32u * kk;
-                        const uint64_t ah = tc::desc_sw64_kmajor_sbo(a_hi + ko, 1024u);
-                        const uint64_t al = tc::desc_sw64_kmajor_sbo(a_lo + ko, 1024u);
-                        tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_hi + ko), idesc, (q | kk) != 0);
-                        tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_lo + ko), idesc, 1);
-                        tc::mma_bf16_pair(d_tmem, al, tc::desc_sw64_kmajor(b_hi + ko), idesc, 1);
+                        for (int kk = 0; kk < kKC / 8; ++kk)
+                            tc::mma_tf32_pair(d_tmem, tc::desc_sw128_kmajor(a0 + 32u * kk),
+                                              tc::desc_sw128_kmajor(b0 + 32u * kk), idesc, (q | kk) != 0);
+                    } else {
+                        const uint32_t a_hi = sA_u32 + (uint32_t)s * kStageBytes, a_lo = a_hi + 512u;
+                        const uint32_t b_hi = sB_u32 + p.hoff[q], b_lo = b_hi + p.hb_bytes;
+                        const uint32_t idesc = tc::idesc_bf16_f32(2 * kRows, p.nn[q]);
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; ++kk) {
+                            const uint32_t ko = 32u * kk;
+                            const uint64_t ah = tc::desc_sw64_kmajor_sbo(a_hi + ko, 1024u);
+                            const uint64_t al = tc::desc_sw64_kmajor_sbo(a_lo + ko, 1024u);
+                            tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_hi + ko), idesc, (q | kk) != 0);
+                            tc::mma_bf16_pair(d_tmem, ah, tc::desc_sw64_kmajor(b_lo + ko), idesc, 1);
+                            tc::mma_bf16_pair(d_tmem, al, tc::desc_sw64_kmajor(b_hi + ko), idesc, 1);
+                        }
                     }
                     tc::mma_commit_pair(empty + s);
                     if (++s == S) {
@@ -807,9 +857,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(T::kThreads, 1)
         uint32_t u = (uint32_t)(grp / S);
         for (int g = grp; g < G; g += T::kGroups) {
             if (!warp_wait(landed + s, u & 1u, abort)) break;
-            tc::mbar_try_wait(landed + s, u & 1u);   // every lane acquires the landed bytes
-            split_blocks_in_place<T::kBlocks>(sA + s * kStageBytes + wi * T::kBlocks * 1024, lane);
-            tc::fence_proxy_async_smem();
+            static_assert(T::kBlocks * T::kWarps * 8 == kRows, "the converter warps cover the chunk's rows");
+            if constexpr (!TF32) {
+                tc::mbar_try_wait(landed + s, u & 1u);   // every lane acquires the landed bytes
+                split_blocks_in_place<T::kBlocks>(sA + s * kStageBytes + wi * T::kBlocks * 1024, lane);
+                tc::fence_proxy_async_smem();
+            }
             __syncwarp();
             if (lane == 0) {
                 if (rank == 0) tc::mbar_arrive(full + s);
@@ -933,6 +986,25 @@ const TmaVariant& tma_variant() {
     return kVariants[(i >= 0 && i < (int)(sizeof(kVariants) / sizeof(kVariants[0]))) ? i : 0];
 }
 
+// The TF32 kernel: G one-warp relay groups, the ring G stages deep (the
+// deepest of these that fits beside B; one group per stage, so a landed
+// chunk never waits behind another chunk's hand-off).
+template <int G>
+TmaVariant tf32_variant_of() {
+    using T = TmaShape<G, 1>;
+    return {(const void*)rownorm_tma2_kernel<T, true>, T::kThreads, T::kGroups,
+            [](int grid, size_t smem, cudaStream_t st, const RnParams& p, const uint8_t* img, const CUtensorMap& tmA) {
+                rownorm_tma2_kernel<T, true><<<grid, T::kThreads, smem, st>>>(p, img, tmA);
+            }};
+}
+const TmaVariant* tf32_variant(int stages2) {
+    static const TmaVariant kByDepth[] = {tf32_variant_of<12>(), tf32_variant_of<9>(), tf32_variant_of<6>(),
+                                          tf32_variant_of<4>(), tf32_variant_of<2>()};
+    for (const TmaVariant& v : kByDepth)
+        if (v.groups <= stages2) return &v;
+    return nullptr;
+}
+
 // cuTensorMapEncodeTiled from the driver (looked up once; null if absent)
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -967,7 +1039,9 @@ bool make_tmap(const RnParams& p, CUtensorMap* m) {
     const cuuint64_t strides[1] = {(cuuint64_t)p.lda * 4};
     const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kRows};
     const cuuint32_t elem[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.A), dims, strides, box, elem,
+    // TF32 form: the copy engine rounds FP32 to the nearest TF32
+    const CUtensorMapDataType ty = p.tf32 ? CU_TENSOR_MAP_DATA_TYPE_TFLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return fn(m, ty, 2, const_cast<float*>(p.A), dims, strides, box, elem,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -1009,11 +1083,32 @@ PairChoice choose_form(const lsk_mat* A, const RnParams& p, bool vec) {
     return pc;
 }
 
+// The TF32 form: TMA-fed CTA pairs only, the ring a multiple of the
+// converter groups; fills p (stages2, pair, tf32) and the clusters that fit.
+bool tf32_plan(const lsk_mat* A, RnParams& p, int& ncl, const TmaVariant** tv_out = nullptr) {
+    if (!tma_ok(A) || p.stages2 < 2) return false;
+    const TmaVariant* tv = tf32_variant(p.stages2);
+    if (!tv) return false;
+    RnParams q = p;
+    q.stages2 = tv->groups;
+    q.pair = 1;
+    q.tf32 = 1;
+    ncl = pair_clusters(tv->fn, tv->threads, smem_bytes2(q));
+    if (ncl <= 0) return false;
+    p = q;
+    if (tv_out) *tv_out = tv;
+    return true;
+}
+
 }  // namespace
 
-bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri) {
+bool rownorms_tc_supported(const lsk_mat* A, int64_t c, int upper_tri, bool tf32) {
     RnParams p{};
     if (!make_plan(A, c, upper_tri, p)) return false;
+    if (tf32) {
+        int ncl = 0;
+        return tf32_plan(A, p, ncl);
+    }
     if (p.stages >= 2) return true;
     // only the CTA-pair form fits: it needs clusters of two on this device
     const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
@@ -1028,7 +1123,7 @@ size_t rownorms_tc_workspace_bytes(const lsk_mat* A, int64_t c, int upper_tri) {
 
 cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, float alpha, float beta, int upper_tri,
                                float* x, void* ws, int* flag, int sm_count, cudaStream_t st, int min_tiles,
-                               const uint8_t* img_ready) {
+                               const uint8_t* img_ready, bool tf32) {
     RnParams p{};
     if (!make_plan(A, c, upper_tri, p)) return cudaErrorNotSupported;
     p.A = (const float*)A->values;
@@ -1043,6 +1138,19 @@ cudaError_t rownorms_tc_launch(const lsk_mat* A, const float* B, int64_t c, floa
     uint8_t* img = (uint8_t*)ws;
     const bool vec = (p.d % 4 == 0) && (A->ld % 4 == 0) && (((uintptr_t)A->values & 15) == 0);
     p.ntiles2 = (int)((A->n + 2 * kRows - 1) / (2 * kRows));
+    const int kMinTiles0 = min_tiles > 0 ? min_tiles : 1;
+    if (tf32) {
+        int ncl = 0;
+        const TmaVariant* tv = nullptr;
+        if (!tf32_plan(A, p, ncl, &tv)) return cudaErrorNotSupported;
+        LSK_PROF("rownorm_tc_prep", st) rownorm_tc_prep_kernel<<<64, 256, 0, st>>>(B, p, img);
+        CUtensorMap tmA;
+        if (!make_tmap(p, &tmA)) return cudaErrorNotSupported;
+        const int want2 = (p.ntiles2 + kMinTiles0 - 1) / kMinTiles0;
+        const int grid2 = 2 * (want2 < ncl ? want2 : ncl);
+        LSK_PROF("rownorm_dense_tf32", st) tv->launch(grid2, smem_bytes2(p), st, p, img, tmA);
+        return cudaGetLastError();
+    }
     const PairChoice pc = choose_form(A, p, vec);
     const bool use_tma = pc.tma;
     const TmaVariant& tv = tma_variant();

@@ -84,6 +84,30 @@ def test_dense_4M_x_256_bf16(lsk, dense_4m):
     assert 0.2 * d <= ell.sum() <= 5.0 * d
 
 
+def test_dense_4M_x_256_tf32(lsk, dense_4m):
+    """Config 3 as it names its arithmetic: the BF16 Gaussian stage and the
+    fused TF32 row-norm kernel (the bench's headline step), against the
+    oracle's scores on sampled rows."""
+    c3 = dense_4m
+    A, n, d = c3["A"], c3["n"], c3["d"]
+    Ad = torch.from_numpy(A).cuda()
+    ctx = lsk.context()
+    ctx.profile(True)
+    ctx.profile_reset()
+    ell = lsk.leverage_scores(Ad, c3["r"], c3["k"], c3["seed"], "tf32")
+    ctx.sync()
+    names = set(ctx.profile_totals())
+    ctx.profile(False)
+    ell = ell.cpu().numpy().astype(np.float64)
+    del Ad
+    torch.cuda.empty_cache()
+    assert "rownorm_dense_tf32" in names
+    rows = sample_rows(n, 997, 3)
+    ref = sampled_scores(A[rows], c3["R"])
+    assert np.max(np.abs(ell[rows] - ref) / ref) <= 1e-3
+    assert np.all(ell >= 0) and np.all(np.isfinite(ell))
+
+
 def test_dense_4M_x_256_count_gauss(lsk, dense_4m):
     """The fused CountSketch + Gaussian stage (S A kept on chip) at the bench's
     size against the oracle's FP64 G (S A) on the same seeds."""

@@ -330,6 +330,55 @@ def test_rownorms_dense_bf16_tma_form(lsk, monkeypatch, n, d, c, tri, ld):
     assert np.array_equal(tma, regs)
 
 
+TF32_CASES = [(10_000, 256, 256, True, 256), (2_000, 256, 256, False, 256), (1_000, 256, 160, False, 256),
+              (5_003, 200, 200, True, 200), (300, 232, 232, True, 236), (70_001, 256, 256, True, 260),
+              (20_011, 52, 52, True, 52), (4_096, 32, 32, True, 32), (777, 96, 40, False, 100)]
+
+
+@pytest.mark.parametrize("n,d,c,tri,ld", TF32_CASES)
+def test_rownorms_dense_tf32(lsk, n, d, c, tri, ld):
+    """The one-product TF32 kernel (checked by its profile name): A and B each
+    rounded to the nearest TF32 (11 significant bits, relative error <= 2^-11
+    an entry), products exact in FP32, FP32 sums of d products and of the c
+    squares.  Ragged row tails, K-chunks past d (zero-filled by the copy),
+    row strides above d and general B included.  Rounding to nearest leaves
+    no systematic bias (dropping the low mantissa bits instead shrinks the
+    scores by ~1.4e-3 here)."""
+    W = workloads.dense_normal(n, ld, seed=c) * (10.0 ** np.linspace(-2, 2, ld)).astype(np.float32)
+    B = workloads.dense_normal(d, c, seed=d + 1)
+    if tri:
+        B = np.triu(B)
+    ctx = lsk.context()
+    ctx.profile(True)
+    ctx.profile_reset()
+    x = host(lsk.rownorms_prod(dev(W)[:, :d], dev(B), upper_triangular=tri, prec="tf32")).astype(np.float64)
+    ctx.sync()
+    names = set(ctx.profile_totals())
+    ctx.profile(False)
+    assert "rownorm_dense_tf32" in names
+    A64, B64 = W[:, :d].astype(np.float64), B.astype(np.float64)
+    ref = orn.rownorms_prod_dense(A64, B64)
+    y = A64 @ B64
+    absy = np.abs(A64) @ np.abs(B64)
+    E = (2.0**-10 + 2.0**-21 + 2.05 * (d + 2) * U32) * absy
+    bound = np.sum(2 * np.abs(y) * E + E * E, axis=1) + 2 * U32 * ref * c
+    assert np.all(np.abs(x - ref) <= bound)
+    # no systematic bias: the summed scores within 6e-4 (B's own rounding, fixed
+    # for all rows, leaves up to ~2.5e-4 at d = 32; truncation gives >= 1.2e-3)
+    assert abs(x.sum() - ref.sum()) <= 6e-4 * ref.sum()
+
+
+def test_rownorms_tf32_rounds_to_nearest(lsk):
+    """Entries 1 + 3 2^-12 (13 low bits 0x1800) with B = I: the nearest TF32
+    is 1 + 2^-10, the truncated one 1; the scores are 32 (1 + 2^-10)^2."""
+    for sign in (1.0, -1.0):
+        A = np.full((512, 32), sign * (1.0 + 3.0 * 2.0**-12), dtype=np.float32)
+        x = host(lsk.rownorms_prod(dev(A), dev(np.eye(32, dtype=np.float32)), upper_triangular=True,
+                                   prec="tf32")).astype(np.float64)
+        want = 32.0 * (1.0 + 2.0**-10) ** 2
+        assert np.all(np.abs(x - want) <= 1e-6 * want)
+
+
 def test_rownorms_alpha_beta(lsk):
     A = workloads.dense_normal(1000, 20, seed=1)
     B = workloads.dense_normal(20, 7, seed=2)
@@ -386,6 +435,27 @@ def test_leverage_dense_outliers_20000x50(lsk, prec):
                                          oga.PREC_BF16 if prec == "bf16" else oga.PREC_FP32)
     assert np.max(np.abs(ell - ref) / ref) <= 1e-3
     assert set(np.argsort(-ell)[:5]) == set(range(5))
+    colnorm = np.linalg.norm(Ro, axis=0)
+    assert np.all(np.abs(host(R) - Ro) <= 1e-4 * colnorm[None, :])
+
+
+def test_leverage_dense_tf32(lsk):
+    """Config 3's mixed recipe at a smaller size: the BF16 Gaussian stage and
+    the TF32 row norms (checked by profile name), against the oracle's
+    estimates on the same seeds (G rounded to bfloat16 as in the BF16 mode)."""
+    n, d, r, k = 200_000, 64, 8192, 256
+    A = workloads.dense_normal(n, d, seed=11) * (10.0 ** np.linspace(-3, 3, d)).astype(np.float32)
+    ctx = lsk.context()
+    ctx.profile(True)
+    ctx.profile_reset()
+    ell, R = lsk.leverage_scores(dev(A), r, k, 5, "tf32", return_R=True)
+    ctx.sync()
+    names = set(ctx.profile_totals())
+    ctx.profile(False)
+    assert "rownorm_dense_tf32" in names and "rownorm_dense_tc" not in names
+    ell = host(ell).astype(np.float64)
+    ref, Ro = olev.leverage_scores_dense(A.astype(np.float64), r, k, 5, oga.PREC_BF16)
+    assert np.max(np.abs(ell - ref) / ref) <= 1e-3
     colnorm = np.linalg.norm(Ro, axis=0)
     assert np.all(np.abs(host(R) - Ro) <= 1e-4 * colnorm[None, :])
 
