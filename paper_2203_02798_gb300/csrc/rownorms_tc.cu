@@ -634,39 +634,6 @@ struct TmaShape {
 constexpr uint32_t kChunkBytes = kRows * kKC * 4;              // one FP32 chunk = one stage
 static_assert(kChunkBytes == kStageBytes, "a landed FP32 chunk becomes its own hi / lo stage");
 
-// Lane l splits row l / 4 of the block, K-elements 8 (l % 4) .. +7: two
-// 16-byte reads of the FP32 rows (chunk c of row r at 128 r + 16 (c ^ r) under
-// the 128-byte swizzle), one 16-byte write each to the hi and lo atoms (chunk
-// kc of row r at 64 r + 16 (kc ^ (r / 2)) under the 64-byte swizzle).  All
-// reads of the warp's blocks precede the warp barrier, all writes follow it.
-template <int NB>
-__device__ __forceinline__ void split_blocks_in_place(uint8_t* first_block, int lane) {
-    const uint32_t r = (uint32_t)lane >> 2, kc = (uint32_t)lane & 3u;
-    const uint32_t rd0 = 128u * r + 16u * ((2u * kc) ^ r), rd1 = 128u * r + 16u * ((2u * kc + 1u) ^ r);
-    const uint32_t wr = 64u * r + 16u * ((kc ^ (r >> 1)) & 3u);
-    constexpr int kPass = NB < 4 ? NB : 4;   // blocks held in registers at once
-#pragma unroll
-    for (int b0 = 0; b0 < NB; b0 += kPass) {
-        uint4 hi[kPass], lo[kPass];
-#pragma unroll
-        for (int b = 0; b < kPass; ++b) {
-            const uint8_t* blk = first_block + (b0 + b) * 1024;
-            const float4 v0 = *reinterpret_cast<const float4*>(blk + rd0);
-            const float4 v1 = *reinterpret_cast<const float4*>(blk + rd1);
-            tc::split_bf16x2(v0.x, v0.y, hi[b].x, lo[b].x);
-            tc::split_bf16x2(v0.z, v0.w, hi[b].y, lo[b].y);
-            tc::split_bf16x2(v1.x, v1.y, hi[b].z, lo[b].z);
-            tc::split_bf16x2(v1.z, v1.w, hi[b].w, lo[b].w);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < kPass; ++b) {
-            uint8_t* blk = first_block + (b0 + b) * 1024;
-            *reinterpret_cast<uint4*>(blk + wr) = hi[b];
-            *reinterpret_cast<uint4*>(blk + 512 + wr) = lo[b];
-        }
-    }
-}
 
 // TF32 = false: the BF16x3 products of the converters' hi / lo split.
 // TF32 = true: one kind::tf32 product per K-step straight from the landed
@@ -860,7 +827,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(T::kThreads, 1)
             static_assert(T::kBlocks * T::kWarps * 8 == kRows, "the converter warps cover the chunk's rows");
             if constexpr (!TF32) {
                 tc::mbar_try_wait(landed + s, u & 1u);   // every lane acquires the landed bytes
-                split_blocks_in_place<T::kBlocks>(sA + s * kStageBytes + wi * T::kBlocks * 1024, lane);
+                tc::split_blocks_in_place<T::kBlocks>(sA + s * kStageBytes + wi * T::kBlocks * 1024, lane);
                 tc::fence_proxy_async_smem();
             }
             __syncwarp();
@@ -1005,35 +972,16 @@ const TmaVariant* tf32_variant(int stages2) {
     return nullptr;
 }
 
-// cuTensorMapEncodeTiled from the driver (looked up once; null if absent)
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled() {
-    static EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return reinterpret_cast<EncodeTiledFn>(f);
-    }();
-    return fn;
-}
-
 // The TMA-fed pair form reads A through a tensor map of boxes 32 columns x
 // 128 rows: rows must start on 16-byte boundaries, and the row count must
 // fit the map's 32-bit coordinates.
 bool tma_ok(const lsk_mat* A) {
     return A->d >= kKC && A->n >= 2 * kRows && A->n < ((int64_t)1 << 31) - 4 * kRows && A->ld % 4 == 0 &&
-           ((uintptr_t)A->values & 15) == 0 && encode_tiled() != nullptr;
+           ((uintptr_t)A->values & 15) == 0 && tc::encode_tiled() != nullptr;
 }
 
 bool make_tmap(const RnParams& p, CUtensorMap* m) {
-    const EncodeTiledFn fn = encode_tiled();
+    const tc::EncodeTiledFn fn = tc::encode_tiled();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)p.d, (cuuint64_t)p.n};
     const cuuint64_t strides[1] = {(cuuint64_t)p.lda * 4};

@@ -8,6 +8,8 @@
 #pragma once
 #include "lsk_internal.cuh"
 
+#include <cuda.h>
+
 namespace tc {
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s per wait
@@ -362,6 +364,66 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uin
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(b - hb), "f"(a - ha));
     hi = h;
     lo = l;
+}
+
+// ---- in-place bf16 split of a landed FP32 tile -------------------------------
+// A 1 KB block of 8 rows x 32 FP32 words, as a 128-byte-swizzled TMA copy
+// leaves it, becomes the 512-byte 64-byte-swizzled atom of its bf16 hi parts
+// (at +0) and that of its lo parts (at +512): 8 rows x 32 bf16 each.  The
+// rows are K for a K-major operand and K for an MN-major one alike (the
+// descriptor says which); the bytes are the same.
+// Lane l splits row l / 4 of the block, K-elements 8 (l % 4) .. +7: two
+// 16-byte reads of the FP32 rows (chunk c of row r at 128 r + 16 (c ^ r) under
+// the 128-byte swizzle), one 16-byte write each to the hi and lo atoms (chunk
+// kc of row r at 64 r + 16 (kc ^ (r / 2)) under the 64-byte swizzle).  All
+// reads of the warp's blocks precede the warp barrier, all writes follow it.
+template <int NB>
+__device__ __forceinline__ void split_blocks_in_place(uint8_t* first_block, int lane) {
+    const uint32_t r = (uint32_t)lane >> 2, kc = (uint32_t)lane & 3u;
+    const uint32_t rd0 = 128u * r + 16u * ((2u * kc) ^ r), rd1 = 128u * r + 16u * ((2u * kc + 1u) ^ r);
+    const uint32_t wr = 64u * r + 16u * ((kc ^ (r >> 1)) & 3u);
+    constexpr int kPass = NB % 4 == 0 ? 4 : NB % 2 == 0 ? 2 : 1;   // blocks held in registers at once
+#pragma unroll
+    for (int b0 = 0; b0 < NB; b0 += kPass) {
+        uint4 hi[kPass], lo[kPass];
+#pragma unroll
+        for (int b = 0; b < kPass; ++b) {
+            const uint8_t* blk = first_block + (b0 + b) * 1024;
+            const float4 v0 = *reinterpret_cast<const float4*>(blk + rd0);
+            const float4 v1 = *reinterpret_cast<const float4*>(blk + rd1);
+            split_bf16x2(v0.x, v0.y, hi[b].x, lo[b].x);
+            split_bf16x2(v0.z, v0.w, hi[b].y, lo[b].y);
+            split_bf16x2(v1.x, v1.y, hi[b].z, lo[b].z);
+            split_bf16x2(v1.z, v1.w, hi[b].w, lo[b].w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < kPass; ++b) {
+            uint8_t* blk = first_block + (b0 + b) * 1024;
+            *reinterpret_cast<uint4*>(blk + wr) = hi[b];
+            *reinterpret_cast<uint4*>(blk + 512 + wr) = lo[b];
+        }
+    }
+}
+
+// ---- tensor maps ------------------------------------------------------------
+// cuTensorMapEncodeTiled from the driver (looked up once; null if absent)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
 }
 
 }  // namespace tc
