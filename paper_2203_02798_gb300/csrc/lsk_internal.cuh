@@ -331,14 +331,15 @@ struct QrJob {
     int d, nchunks, ntiles;
     double* part;            // Gram partials
     double* C;               // FP64 Gram
-    double *Ct, *Rt, *X, *W, *M, *Y, *sc;
-    float *Ct32, *Lpk;
-    int* e;
+    float2* Cp;              // the Gram as FP32 pairs (hi + lo)
+    float2 *X, *W, *M, *Y;   // pair matrices of the correction step
+    float* Lpk;              // packed FP32 Cholesky factor
+    int* e;                  // equilibration exponents
     double* Rinv;            // nullable
     float* Rinv32;
     int* flag;
 };
-enum QrShape { QS_GRAM, QS_GRAMRED, QS_ONE, QS_EW, QS_TRINV, QS_TRI, QS_N };
+enum QrShape { QS_GRAM, QS_GRAMRED, QS_ONE, QS_TRINV, QS_TRI, QS_N };
 struct QrGroup {
     size_t jobs_off, off_off[QS_N];
     int count, blocks[QS_N], dmax;

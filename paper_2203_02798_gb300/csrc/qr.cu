@@ -158,7 +158,7 @@ __global__ void sketch_gram64_reduce_grouped_kernel(const QrJob* __restrict__ jo
     const int g = group_of(off, count, blockIdx.x);
     const QrJob& j = jobs[g];
     const int b0 = __ldg(off + g);
-    sketch_gram64_reduce_body(j.part, j.nchunks, j.d, j.C, (int)blockIdx.x - b0, __ldg(off + g + 1) - b0);
+    sketch_gram64_reduce_body(j.part, j.nchunks, j.d, j.C, (int)blockIdx.x - b0, __ldg(off + g + 1) - b0, j.Cp);
 }
 
 // Factor the diagonal block K of C (lower part) in shared memory.  Every

@@ -1,69 +1,36 @@
-// qr_mixed.cu -- R of the sketch with FP32 factorisation and one FP64 correction.
+// qr_mixed.cu -- R of the sketch (d <= 256) with an FP32 factorisation and
+// one correction step in FP32-pair arithmetic.
 //
-// FP64 on this part is slow and, worse, has long dependent-operation
-// latency, so the serial chain of a Cholesky factorisation is run in FP32
-// and FP64 is used only in parallel matrix products:
-//   1. C = B^T B in FP64 (qr.cu), equilibrated by powers of two:
-//      Ct = D^-1 C D^-1, D_j = 2^round(log2 sqrt(C_jj))            (exact)
-//   2. Ct ~ Rt^T Rt by FP32 Cholesky (one CTA, packed lower triangle in
-//      shared memory), X = Rt^-1 by FP32 back substitution
-//   3. one correction step with FP64-accurate products of triangular matrices
-//      (FP32-pair arithmetic on the FP32 units, FP64 inputs and outputs):
+// FP64 on this part runs at 1/64 of the FP32 rate and has long dependent-
+// operation latency, so no step below computes in FP64; the matrices are
+// FP32 pairs (x = hi + lo, ~48 bits) and FP64 appears only where R and R^-1
+// are written:
+//   1. Cp = B^T B as pairs (qr.cu), equilibrated by powers of two:
+//      Ct = D^-1 C D^-1, D_j = 2^floor(log2 sqrt(C_jj))           (exact)
+//   2. Ct ~ Rt^T Rt by FP32 Cholesky (one CTA, the lower triangle in shared
+//      memory), X = Rt^-1 by FP32 back substitution
+//   3. one correction step with pair-accurate products of triangular matrices:
 //        M = X^T Ct X = I + E,  U = strict_upper(E) + diag(E)/2
 //        Y = X (I - U)                         (= (R D^-1)^-1 to O(|E|^2))
-//        Z = Rt + Rt (I - Y Rt)                (Newton step for Y^-1)
+//        Z = Rt + Rt (I - Y Rt)                (Newton step for Y^-1, when R is wanted)
 //   4. R = Z D, R^-1 = D^-1 Y
+// One sketch runs the chain as five to seven launches; a batch runs the same
+// kernels grouped (one grid per step over all sketches, R not formed).
 // In exact arithmetic R is the Cholesky factor of C, i.e. the sign-normalised
 // Householder R of B.  Rank deficiency is reported when an FP32 pivot is not
-// positive, when the FP32 factor needs a correction larger than 1/4 (the
-// equilibrated sketch is numerically singular at FP32 precision), or when
-// the equilibrated diag(R) spans more than 2^20.
+// positive, when the equilibrated FP32 factor's diagonal spans more than 2^20,
+// or when the FP32 factor needs a correction larger than 1/4 (the
+// equilibrated sketch is numerically singular at FP32 precision).
 #include "lsk_internal.cuh"
 
 #include <algorithm>
 
 namespace {
 
-constexpr int TT = 16;   // tile edge of the FP64 triangular products (one output per thread)
+constexpr int TT = 16;   // tile edge of the triangular pair products (16 x 16 outputs a block)
 
-// e_j = floor(log2 sqrt(C_jj)) and the exact scale 2^-e_j.
-__device__ __forceinline__ void equil_exponents_body(const double* __restrict__ C, int d, int* __restrict__ e,
-                                       double* __restrict__ sc, int* flag, const int blk, const int nblk) {
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        const double c = C[(int64_t)j * d + j];
-        int ex = 0;
-        if (c > 0.0 && isfinite(c)) {
-            int b2;
-            frexp(c, &b2);                  // c = m 2^b2, m in [0.5, 1)
-            ex = (b2 - 1) >> 1;
-        } else {
-            set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
-        }
-        e[j] = ex;
-        sc[j] = ldexp(1.0, -ex);
-    }
-}
-
-// Ct64 = C 2^{-e_i-e_j} (two exact multiplications), Ct32 = float(Ct64).
-__device__ __forceinline__ void equil_scale_body(const double* __restrict__ C, int d, const double* __restrict__ sc,
-                                   double* __restrict__ Ct64, float* __restrict__ Ct32, const int blk, const int nblk) {
-    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
-        const double v = C[t] * sc[t / d] * sc[t % d];
-        Ct64[t] = v;
-        Ct32[t] = (float)v;
-    }
-}
-
-// FP32 Cholesky of Ct (d <= 256) in one CTA, blocked by 32: the lower
-// triangle lives in shared memory as 32 x 33 (padded) tiles T(I, J), I >= J.
-// Per block column K: warp 0 factors T(K, K) with its rows in registers,
-// one thread per row solves the panel T(I, K) L_KK^-T, and the rank-32
-// trailing update T(I, J) -= L_IK L_JK^T runs one tile per warp with each
-// lane's column of L_JK in registers.  Dimensions beyond d are padded with
-// the identity.  Writes Rt = L^T (FP64 values, d x d, zeros below) and the
-// packed rows of L (row l at offset l(l+1)/2) for the inverse.
+// FP32 Cholesky pieces: 32 x 32 tiles (CB) of the lower triangle.
 constexpr int CB = 32;
-constexpr int CP = CB + 1;
 
 // Unblocked Cholesky of one 32 x 32 tile by one warp, row `lane` in a[]:
 // compile-time recursion over (j, k) keeps every index static, so a[] stays
@@ -99,116 +66,6 @@ template <>
 struct DiagStep<CB> {
     static __device__ __forceinline__ void run(float (&)[CB], int, int*) {}
 };
-__device__ __forceinline__ float* ctile(float* S, int I, int J) { return S + (I * (I + 1) / 2 + J) * (CB * CP); }
-
-__device__ __forceinline__ void chol32_body(const float* __restrict__ Ct32, int d, double* __restrict__ Rt,
-                                                      float* __restrict__ Lpk, int* flag, const int blk, const int nblk) {
-    extern __shared__ float S[];
-    __shared__ float rdiag[CB];
-    const int nt = (d + CB - 1) / CB;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    {   // all tiles at once: flat index over (tile, element), tile -> (I, J) from a
-        // small table, eight independent loads in flight per thread
-        __shared__ unsigned char tI[36], tJ[36];   // nt <= 8
-        const int ntl = nt * (nt + 1) / 2;
-        if (threadIdx.x < ntl) {
-            int I = 0, t = threadIdx.x;
-            while (t > I) t -= ++I;
-            tI[threadIdx.x] = (unsigned char)I;
-            tJ[threadIdx.x] = (unsigned char)t;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int t = threadIdx.x; t < ntl * CB * CB; t += blockDim.x) {
-            const int tl = t >> 10, e = t & 1023;
-            const int r = e >> 5, c = e & 31, i = tI[tl] * CB + r, j = tJ[tl] * CB + c;
-            S[tl * (CB * CP) + r * CP + c] = (i < d && j < d) ? __ldg(Ct32 + i * d + j) : (i == j ? 1.f : 0.f);
-        }
-    }
-    __syncthreads();
-    for (int K = 0; K < nt; ++K) {
-        float* D = ctile(S, K, K);
-        if (w == 0) {   // (1) diagonal tile: row `lane` in registers (fully unrolled)
-            float a[CB];
-#pragma unroll
-            for (int k = 0; k < CB; ++k) a[k] = D[lane * CP + k];
-            DiagStep<0>::run(a, lane, flag);
-#pragma unroll
-            for (int k = 0; k < CB; ++k) D[lane * CP + k] = a[k];
-            __syncwarp();
-            rdiag[lane] = 1.f / D[lane * CP + lane];
-            __syncwarp();
-        }
-        __syncthreads();
-        // (2) panel: thread per row of T(I, K), I > K
-        {
-            const int rows = (nt - K - 1) * CB;
-            for (int t = threadIdx.x; t < rows; t += blockDim.x) {
-                const int I = K + 1 + t / CB, r = t % CB;
-                float* T = ctile(S, I, K);
-                float x[CB];
-#pragma unroll
-                for (int j = 0; j < CB; ++j) {
-                    float v = T[r * CP + j];
-#pragma unroll
-                    for (int l = 0; l < j; ++l) v -= x[l] * D[j * CP + l];
-                    x[j] = v * rdiag[j];
-                }
-#pragma unroll
-                for (int j = 0; j < CB; ++j) T[r * CP + j] = x[j];
-            }
-        }
-        __syncthreads();
-        // (3) trailing update, one tile (I, J), K < J <= I, per warp
-        {
-            const int T0 = nt - K - 1;
-            const int ntile = T0 * (T0 + 1) / 2;
-            for (int t = w; t < ntile; t += nw) {
-                int I = 0, tt = t;
-                while (tt > I) {   // lower pairs (J <= I) over the trailing blocks
-                    tt -= I + 1;
-                    ++I;
-                }
-                const int J = tt;
-                I += K + 1;
-                const int Jg = J + K + 1;
-                const float* LI = ctile(S, I, K);
-                const float* LJ = ctile(S, Jg, K);
-                float* T = ctile(S, I, Jg);
-                float lj[CB];
-#pragma unroll
-                for (int k = 0; k < CB; ++k) lj[k] = LJ[lane * CP + k];   // column `lane` of L_JK^T
-                for (int a = 0; a < CB; a += 4) {   // four independent chains
-                    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < CB; ++k) {
-                        acc0 = fmaf(LI[a * CP + k], lj[k], acc0);
-                        acc1 = fmaf(LI[(a + 1) * CP + k], lj[k], acc1);
-                        acc2 = fmaf(LI[(a + 2) * CP + k], lj[k], acc2);
-                        acc3 = fmaf(LI[(a + 3) * CP + k], lj[k], acc3);
-                    }
-                    T[a * CP + lane] -= acc0;
-                    T[(a + 1) * CP + lane] -= acc1;
-                    T[(a + 2) * CP + lane] -= acc2;
-                    T[(a + 3) * CP + lane] -= acc3;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // Rt[i][j] = L[j][i] for j >= i (only when the caller forms R), then the
-    // packed rows of L (row l at l(l+1)/2): warp per row, lanes along it
-    if (Rt) {
-        for (int i = w; i < d; i += nw)
-            for (int j = lane; j < d; j += 32)
-                Rt[(int64_t)i * d + j] = (j >= i) ? (double)ctile(S, j >> 5, i >> 5)[(j & 31) * CP + (i & 31)] : 0.0;
-    }
-    for (int l = w; l < d; l += nw) {
-        float* dst = Lpk + l * (l + 1) / 2;
-        for (int i = lane; i <= l; i += 32) dst[i] = ctile(S, l >> 5, i >> 5)[(l & 31) * CP + (i & 31)];
-    }
-}
-
 // Back substitution steps l = min(j, 32 SL + 31) .. 32 SL of column j: the
 // rows of block SL hold the pivot; rows i < l of blocks <= SL are updated.
 template <int SL>
@@ -232,7 +89,6 @@ __device__ __forceinline__ void trinv_block(float (&xr)[8], const float* P, cons
 // The packed factor (row l of L = column l of Rt at offset l(l+1)/2) is
 // staged in shared memory (once per block of 4 or 16 columns) so the
 // back-substitution chain sees shared-memory latency.
-__device__ __forceinline__ void store_x(double* X, int64_t at, float v) { X[at] = (double)v; }
 __device__ __forceinline__ void store_x(float2* X, int64_t at, float v) { X[at] = make_float2(v, 0.f); }
 template <class T>
 __device__ __forceinline__ void trinv32_body(const float* __restrict__ Lpk, int d, T* __restrict__ X, const int blk, const int nblk) {
@@ -276,32 +132,10 @@ __global__ void __launch_bounds__(512) trinv32_pair_kernel(const float* __restri
     trinv32_body(Lpk, d, X, blockIdx.x, gridDim.x);
 }
 
-// Out = alpha * op(A) * B + beta * Cin + diag_add * I on the upper triangle
-// (tiles I <= J).  op(A) = A or A^T.  The reduction index is limited to
-// where both factors can be non-zero: a_upper (op(A) upper: k >= i),
-// a_lower (op(A) lower: k <= i), b_upper (B upper: k <= j).  Entries below
-// the diagonal of Out are written as zero.
-//
-// Arithmetic: the FP64 inputs are split into FP32 pairs (x = hi + lo, ~48
-// bits), each product is formed as hi*hi exactly (one FMA gives its rounding
-// error) plus the cross terms, and the sum is kept as an FP32 pair (TwoSum),
-// renormalised every 16 terms: about 2^-46 relative per product and d 2^-47
-// of max |term| in the sum -- far inside what the correction step needs --
-// on the FP32 units (FP64 runs at 1/64 of that rate on this part).  alpha,
-// beta and the final combination are FP64.
-struct TriGemm {
-    const double* A;
-    const double* B;
-    const double* Cin;
-    double* Out;
-    int d, transA, a_upper, a_lower, b_upper;
-    double alpha, beta, diag_add;
-};
-
-__device__ __forceinline__ float2 split_pair(double x) {
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
-}
+// Pair arithmetic for the triangular products (FP32 throughout, x = hi + lo
+// ~48 bits): each product is formed as hi*hi exactly (one FMA gives its
+// rounding error) plus the cross terms, and the sum is kept as an FP32 pair
+// (TwoSum), renormalised every 16 terms.
 // (s, c) += a * b with a, b FP32 pairs
 __device__ __forceinline__ void pair_mac(float2 a, float2 b, float& s, float& c) {
     const float p = __fmul_rn(a.x, b.x);
@@ -318,172 +152,6 @@ __device__ __forceinline__ void pair_renorm(float& s, float& c) {
     const float z = __fsub_rn(t, s);
     c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
     s = t;
-}
-
-__device__ __forceinline__ void tri_gemm64_body(const TriGemm g, const int blk, const int nblk) {
-    const int nt = (g.d + TT - 1) / TT;
-    int t = blk, I = 0;
-    while (t >= nt - I) {   // upper tile pairs (I <= J)
-        t -= nt - I;
-        ++I;
-    }
-    const int J = I + t;
-    __shared__ float2 As[TT][TT + 1], Bs[TT][TT + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // output (ty, tx)
-    const int i0 = I * TT, j0 = J * TT;
-    int klo = 0, khi = g.d;
-    if (g.a_upper) klo = i0;
-    if (g.a_lower) khi = min(khi, i0 + TT);
-    if (g.b_upper) khi = min(khi, j0 + TT);
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;   // two chains for latency
-    for (int k0 = klo - (klo % TT); k0 < khi; k0 += TT) {
-        {
-            const int r = threadIdx.x / TT, c = threadIdx.x % TT;
-            const int ia = i0 + r, ka = k0 + c;
-            double a = 0.0;
-            if (ia < g.d && ka < g.d) a = g.transA ? g.A[(int64_t)ka * g.d + ia] : g.A[(int64_t)ia * g.d + ka];
-            As[r][c] = split_pair(a);
-            const int kb = k0 + r, jb = j0 + c;
-            Bs[r][c] = split_pair((kb < g.d && jb < g.d) ? g.B[(int64_t)kb * g.d + jb] : 0.0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < TT; kk += 2) {
-            pair_mac(As[ty][kk], Bs[kk][tx], s0, c0);
-            pair_mac(As[ty][kk + 1], Bs[kk + 1][tx], s1, c1);
-        }
-        pair_renorm(s0, c0);
-        pair_renorm(s1, c1);
-        __syncthreads();
-    }
-    const int i = i0 + ty, j = j0 + tx;
-    if (i >= g.d || j >= g.d) return;
-    double r = 0.0;
-    if (j >= i) {
-        r = g.alpha * (((double)s0 + (double)s1) + ((double)c0 + (double)c1));
-        if (g.beta != 0.0) r += g.beta * g.Cin[(int64_t)i * g.d + j];
-        if (i == j) r += g.diag_add;
-    }
-    g.Out[(int64_t)i * g.d + j] = r;
-}
-
-// U = strict_upper(M - I) + diag(M - I) / 2, in place.  |M - I| > 1/4
-// anywhere means the FP32 factor was too far off for one correction: the
-// equilibrated sketch is numerically rank deficient at FP32 precision.
-__device__ __forceinline__ void correction_body(double* __restrict__ M, int d, int* flag, const int blk, const int nblk) {
-    bool big = false;
-    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
-        const int i = t / d, j = t % d;
-        if (i <= j) {
-            const double e = M[t] - (i == j ? 1.0 : 0.0);
-            if (!(fabs(e) <= 0.25)) big = true;
-            M[t] = (i == j) ? 0.5 * e : e;
-        } else {
-            M[t] = 0.0;
-        }
-    }
-    if (big) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
-}
-
-// R = Z D, R^-1 = D^-1 Y (exact power-of-two scalings); FP32 copy of R^-1.
-__device__ __forceinline__ void unscale_body(const double* __restrict__ Z, const double* __restrict__ Y, const int* __restrict__ e,
-                               int d, double* __restrict__ R, double* __restrict__ Rinv, float* __restrict__ Rinv32, const int blk, const int nblk) {
-    for (int t = blk * blockDim.x + threadIdx.x; t < d * d; t += nblk * blockDim.x) {
-        const int i = t / d, j = t % d;
-        const bool up = j >= i;
-        const double r = (up && Z) ? ldexp(Z[t], e[j]) : 0.0;
-        const double ri = up ? ldexp(Y[t], -e[i]) : 0.0;
-        if (R) R[t] = r;
-        if (Rinv) Rinv[t] = ri;
-        if (Rinv32) Rinv32[t] = (float)ri;
-    }
-}
-
-// min_j Rt_jj <= 2^-20 max_j Rt_jj on the equilibrated factor, with
-// Rt_jj = 1 / Y_jj: beyond that conditioning a factor of the Gram cannot
-// resolve the sketch in FP64.
-__device__ __forceinline__ void rank_check_r_body(const double* __restrict__ Y, int d, int* flag, const int blk, const int nblk) {
-    double mn = INFINITY, mx = 0.0;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        const double v = 1.0 / Y[(int64_t)j * d + j];
-        mn = fmin(mn, v);
-        mx = fmax(mx, v);
-    }
-    for (int o = 16; o; o >>= 1) {
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    __shared__ double smn[32], smx[32];
-    if ((threadIdx.x & 31) == 0) {
-        smn[threadIdx.x >> 5] = mn;
-        smx[threadIdx.x >> 5] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            mn = fmin(mn, smn[w]);
-            mx = fmax(mx, smx[w]);
-        }
-        if (!(mn > 9.5367431640625e-07 * mx) || !isfinite(mx)) set_flag(flag, LSK_FLAG_RANK_DEFICIENT);
-    }
-}
-
-// ---- grouped: one grid per stage over many sketches (QrJob table) --------
-__device__ __forceinline__ const QrJob& job_of(const QrJob* jobs, const int* off, int count, int& blk, int& nblk) {
-    const int g = group_of(off, count, blockIdx.x);
-    const int b0 = __ldg(off + g);
-    blk = (int)blockIdx.x - b0;
-    nblk = __ldg(off + g + 1) - b0;
-    return jobs[g];
-}
-
-__global__ void equil_exponents_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    equil_exponents_body(j.C, j.d, j.e, j.sc, j.flag, blk, nblk);
-}
-__global__ void equil_scale_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    equil_scale_body(j.C, j.d, j.sc, j.Ct, j.Ct32, blk, nblk);
-}
-__global__ void __launch_bounds__(512) chol32_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
-                                                             int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    chol32_body(j.Ct32, j.d, nullptr, j.Lpk, j.flag, blk, nblk);   // R is not formed in a group
-}
-__global__ void __launch_bounds__(512) trinv32_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
-                                                              int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    trinv32_body(j.Lpk, j.d, j.X, blk, nblk);
-}
-// which: 0 W = Ct X, 1 M = X^T W, 2 Y = X - X U (the products of qr_mixed_launch without the Newton step)
-__global__ void __launch_bounds__(256) tri_gemm64_grouped_kernel(const QrJob* __restrict__ jobs,
-                                                                 const int* __restrict__ off, int count, int which) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    TriGemm g;
-    if (which == 0) g = TriGemm{j.Ct, j.X, nullptr, j.W, j.d, 0, 0, 0, 1, 1.0, 0.0, 0.0};
-    else if (which == 1) g = TriGemm{j.X, j.W, nullptr, j.M, j.d, 1, 0, 1, 1, 1.0, 0.0, 0.0};
-    else g = TriGemm{j.X, j.M, j.X, j.Y, j.d, 0, 1, 0, 1, -1.0, 1.0, 0.0};
-    tri_gemm64_body(g, blk, nblk);
-}
-__global__ void correction_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    correction_body(j.M, j.d, j.flag, blk, nblk);
-}
-__global__ void unscale_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    unscale_body(nullptr, j.Y, j.e, j.d, nullptr, j.Rinv, j.Rinv32, blk, nblk);
-}
-__global__ void rank_check_r_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off, int count) {
-    int blk, nblk;
-    const QrJob& j = job_of(jobs, off, count, blk, nblk);
-    rank_check_r_body(j.Y, j.d, j.flag, blk, nblk);
 }
 
 // ---- single-sketch path: fewer launches, no FP64 arithmetic -----------------
@@ -560,8 +228,8 @@ __device__ __forceinline__ void chol_tile_update(float* S, int I, int J, int K, 
     }
 }
 
-__global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__ Cp, int d, int* __restrict__ e_out,
-                                                      float2* __restrict__ Rt, float* __restrict__ Lpk, int* flag) {
+__device__ __forceinline__ void chol_eq_body(const float2* __restrict__ Cp, int d, int* __restrict__ e_out,
+                                             float2* __restrict__ Rt, float* __restrict__ Lpk, int* flag) {
     extern __shared__ __align__(16) float S[];
     __shared__ float rdiag[CB];
     __shared__ float scf[256];
@@ -707,6 +375,11 @@ __global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(512) chol_eq_kernel(const float2* __restrict__ Cp, int d, int* __restrict__ e_out,
+                                                      float2* __restrict__ Rt, float* __restrict__ Lpk, int* flag) {
+    chol_eq_body(Cp, d, e_out, Rt, Lpk, flag);
+}
+
 // Out = alpha op(A) B + beta Cin + diag_add I on the upper triangle (the
 // TriGemm operation on pair matrices), with the whole reduction range of a
 // 16 x 16 output tile staged in shared memory at once and split between two
@@ -740,11 +413,11 @@ size_t tri_gemm_pair_smem(int d) {
     return (size_t)TT * (kmax + 1) * 8 + (size_t)kmax * (TT + 1) * 8 + (size_t)TT * TT * 4 * 4;
 }
 
-__global__ void __launch_bounds__(kTgThreads) tri_gemm_pair_kernel(const TriGemmP g) {
+__device__ __forceinline__ void tri_gemm_pair_body(const TriGemmP& g, const int tile) {
     extern __shared__ __align__(16) float2 smp[];
     const int nt = (g.d + TT - 1) / TT;
     const int kmax = nt * TT;
-    int t = blockIdx.x, I = 0;
+    int t = tile, I = 0;
     while (t >= nt - I) {
         t -= nt - I;
         ++I;
@@ -848,6 +521,46 @@ __global__ void __launch_bounds__(kTgThreads) tri_gemm_pair_kernel(const TriGemm
     }
 }
 
+__global__ void __launch_bounds__(kTgThreads) tri_gemm_pair_kernel(const TriGemmP g) { tri_gemm_pair_body(g, blockIdx.x); }
+
+// ---- grouped: one grid per stage over many sketches (QrJob table), the
+// same pair chain as one sketch's (R is not formed in a group) -------------
+__device__ __forceinline__ const QrJob& job_of(const QrJob* jobs, const int* off, int count, int& blk, int& nblk) {
+    const int g = group_of(off, count, blockIdx.x);
+    const int b0 = __ldg(off + g);
+    blk = (int)blockIdx.x - b0;
+    nblk = __ldg(off + g + 1) - b0;
+    return jobs[g];
+}
+__global__ void __launch_bounds__(512) chol_eq_grouped_kernel(const QrJob* __restrict__ jobs, const int* __restrict__ off,
+                                                              int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    chol_eq_body(j.Cp, j.d, j.e, nullptr, j.Lpk, j.flag);
+}
+__global__ void __launch_bounds__(512) trinv32_pair_grouped_kernel(const QrJob* __restrict__ jobs,
+                                                                   const int* __restrict__ off, int count) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    trinv32_body(j.Lpk, j.d, j.X, blk, nblk);
+}
+// which: 0 W = Ct X, 1 M = X^T W (epilogue U), 2 Y = X - X U (epilogue R^-1)
+__global__ void __launch_bounds__(kTgThreads) tri_gemm_pair_grouped_kernel(const QrJob* __restrict__ jobs,
+                                                                           const int* __restrict__ off, int count,
+                                                                           int which) {
+    int blk, nblk;
+    const QrJob& j = job_of(jobs, off, count, blk, nblk);
+    TriGemmP g;
+    if (which == 0)
+        g = TriGemmP{j.Cp, j.X, nullptr, j.W, j.e, j.d, 0, 0, 0, 1, kPlain, 1.f, 0, 0, nullptr, nullptr, nullptr, j.flag};
+    else if (which == 1)
+        g = TriGemmP{j.X, j.W, nullptr, j.M, nullptr, j.d, 1, 0, 1, 1, kCorrect, 1.f, 0, 0, nullptr, nullptr, nullptr,
+                     j.flag};
+    else
+        g = TriGemmP{j.X, j.M, j.X, j.Y, nullptr, j.d, 0, 1, 0, 1, kInverse, -1.f, 1, 0, j.e, j.Rinv, j.Rinv32, j.flag};
+    tri_gemm_pair_body(g, blk);
+}
+
 // C (FP64, d x d) -> FP32 pairs, for callers that start from an FP64 Gram
 __global__ void to_pair_kernel(const double* __restrict__ C, int64_t len, float2* __restrict__ Cp) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
@@ -857,10 +570,6 @@ __global__ void to_pair_kernel(const double* __restrict__ C, int64_t len, float2
     }
 }
 
-size_t chol32_smem(int d) {
-    const int nt = (d + CB - 1) / CB;
-    return (size_t)nt * (nt + 1) / 2 * CB * CP * 4;
-}
 
 
 }  // namespace
@@ -872,23 +581,19 @@ size_t qr_mixed_workspace_bytes(int64_t d) {
 
 void qr_mixed_carve(QrJob& j, void* ws) {
     const size_t d = (size_t)j.d;
-    WsCarver wc{(char*)ws, 0};   // the same layout as qr_mixed_launch
-    j.Ct = wc.take<double>(d * d);
-    j.Ct32 = wc.take<float>(d * d);
+    WsCarver wc{(char*)ws, 0};   // within qr_mixed_workspace_bytes(d)
+    j.Cp = wc.take<float2>(d * d);
     j.Lpk = wc.take<float>(d * (d + 1) / 2);
-    j.Rt = wc.take<double>(d * d);
-    j.X = wc.take<double>(d * d);
-    j.W = wc.take<double>(d * d);
-    j.M = wc.take<double>(d * d);
-    j.Y = wc.take<double>(d * d);
+    j.X = wc.take<float2>(d * d);
+    j.W = wc.take<float2>(d * d);
+    j.M = wc.take<float2>(d * d);
+    j.Y = wc.take<float2>(d * d);
     j.e = wc.take<int>(d);
-    j.sc = wc.take<double>(d);
 }
 
 int qr_mixed_blocks(int d, int shape) {
     switch (shape) {
         case QS_ONE: return 1;
-        case QS_EW: return std::min((d * d + 255) / 256, 64);
         case QS_TRINV: return (d * 32 + 511) / 512;
         case QS_TRI: {
             const int nt = (d + TT - 1) / TT;
@@ -901,26 +606,21 @@ int qr_mixed_blocks(int d, int shape) {
 cudaError_t qr_mixed_group_launch(const QrGroup& g, const unsigned char* table, cudaStream_t st) {
     const QrJob* jobs = reinterpret_cast<const QrJob*>(table + g.jobs_off);
     const int* one = reinterpret_cast<const int*>(table + g.off_off[QS_ONE]);
-    const int* ew = reinterpret_cast<const int*>(table + g.off_off[QS_EW]);
     const int* tinv = reinterpret_cast<const int*>(table + g.off_off[QS_TRINV]);
     const int* tri = reinterpret_cast<const int*>(table + g.off_off[QS_TRI]);
     const int n = g.count;
-    LSK_PROF("qr_equil", st) equil_exponents_grouped_kernel<<<g.blocks[QS_ONE], 256, 0, st>>>(jobs, one, n);
-    LSK_PROF("qr_equil", st) equil_scale_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
-    const size_t tiles = chol32_smem(g.dmax);
-    cudaError_t err = allow_dynamic_smem(chol32_grouped_kernel);
-    if (err != cudaSuccess) return err;
-    LSK_PROF("qr_chol32", st) chol32_grouped_kernel<<<g.blocks[QS_ONE], 512, tiles, st>>>(jobs, one, n);
+    cudaError_t err;
+    if ((err = allow_dynamic_smem(chol_eq_grouped_kernel)) != cudaSuccess) return err;
+    LSK_PROF("qr_chol32", st) chol_eq_grouped_kernel<<<g.blocks[QS_ONE], 512, chol_eq_smem(g.dmax), st>>>(jobs, one, n);
     const size_t pk = (size_t)g.dmax * (g.dmax + 1) / 2 * 4;
-    err = allow_dynamic_smem(trinv32_grouped_kernel);
-    if (err != cudaSuccess) return err;
-    LSK_PROF("qr_trinv32", st) trinv32_grouped_kernel<<<g.blocks[QS_TRINV], 512, pk, st>>>(jobs, tinv, n);
-    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 0);
-    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 1);
-    LSK_PROF("qr_refine64", st) correction_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
-    LSK_PROF("qr_refine64", st) tri_gemm64_grouped_kernel<<<g.blocks[QS_TRI], 256, 0, st>>>(jobs, tri, n, 2);
-    LSK_PROF("qr_finish", st) unscale_grouped_kernel<<<g.blocks[QS_EW], 256, 0, st>>>(jobs, ew, n);
-    LSK_PROF("qr_finish", st) rank_check_r_grouped_kernel<<<g.blocks[QS_ONE], 256, 0, st>>>(jobs, one, n);
+    if ((err = allow_dynamic_smem(trinv32_pair_grouped_kernel)) != cudaSuccess) return err;
+    LSK_PROF("qr_trinv32", st) trinv32_pair_grouped_kernel<<<g.blocks[QS_TRINV], 512, pk, st>>>(jobs, tinv, n);
+    if ((err = allow_dynamic_smem(tri_gemm_pair_grouped_kernel)) != cudaSuccess) return err;
+    const size_t tsm = tri_gemm_pair_smem(g.dmax);
+    for (int which = 0; which < 3; ++which) {
+        LSK_PROF("qr_refine64", st) tri_gemm_pair_grouped_kernel<<<g.blocks[QS_TRI], kTgThreads, tsm, st>>>(jobs, tri,
+                                                                                                          n, which);
+    }
     return cudaGetLastError();
 }
 
