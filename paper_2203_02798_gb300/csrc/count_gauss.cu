@@ -551,7 +551,7 @@ cudaError_t count_gauss_launch(const lsk_mat* A, int64_t r, int64_t k, uint64_t 
     plan(A, r, k, maxc < half ? maxc : half, p);
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
-    cudaError_t e = cs_prep_launch(A->n, r, seed, ws, sm_count, st, &off, &perm, row0);
+    cudaError_t e = cs_prep_launch(A->n, r, seed, ws, sm_count, st, &off, &perm, row0, flag);
     if (e != cudaSuccess) return e;
     p.A = (const float*)A->values;
     p.lda = A->ld;

@@ -155,53 +155,107 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint3
     return cudaGetLastError();
 }
 
-__global__ void write_total_kernel(uint32_t* off, int64_t r, uint32_t n) { off[r] = n; }
-
-// Exclusive scan of len <= 16384 counts in one block: rounds of 4096
-// (1024 threads x 4 consecutive counts, coalesced), carried across rounds;
-// then off[len] = total.
-__global__ void __launch_bounds__(1024) scan_one_block_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                              int64_t len) {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry_s;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t carry = 0;
-    for (int64_t r0 = 0; r0 < len; r0 += 4096) {
-        const int64_t i0 = r0 + 4 * (int64_t)threadIdx.x;
-        uint32_t v[4];
+// Single-pass exclusive scan of the counters (decoupled look-back): block b
+// takes tile t (the t-th ticket, kScanTile counts), scans it, publishes its
+// aggregate, then adds the published values of the tiles before it, nearest
+// first and 32 at a time (one warp), until one carries its inclusive prefix,
+// and publishes its own.  A
+// tile only waits on tiles whose tickets were taken earlier, i.e. by blocks
+// already running.  Writes off[i] = cursor[i] = the exclusive prefix and
+// off[len] = the total.  state: the ticket, then one word per tile (flag
+// << 32 | value; flag 1 = aggregate, 2 = inclusive prefix), zeroed before
+// the launch.  A wait that runs out sets the TIMEOUT flag.
+constexpr int kLookbackSpins = 1 << 20;
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__global__ void __launch_bounds__(kScanBlock) scan_lookback_kernel(const uint32_t* __restrict__ in,
+                                                                   uint32_t* __restrict__ off,
+                                                                   uint32_t* __restrict__ cursor, int64_t len,
+                                                                   unsigned long long* state, int* flag) {
+    __shared__ uint32_t warp_tot[kScanBlock / 32];
+    __shared__ uint32_t s_tile, s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int*>(state), 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    unsigned long long* tiles = state + 1;
+    const int64_t base = t * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t run = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (i0 + q < len) ? in[i0 + q] : 0u;
-        const uint32_t run = v[0] + v[1] + v[2] + v[3];
-        uint32_t incl = run;
+    for (int q = 0; q < kScanItems; ++q) {
+        const int64_t i = base + q;
+        const uint32_t x = (i < len) ? in[i] : 0u;
+        v[q] = run;
+        run += x;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t w = (lane < kScanBlock / 32) ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
-        if (lane == 31) wsum[w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            const uint32_t x = wsum[lane];
-            uint32_t xi = x;
+        if (lane < kScanBlock / 32) warp_tot[lane] = wi - w;
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, kScanBlock / 32 - 1);   // the tile's sum
+        uint32_t prefix = 0;
+        if (t == 0) {
+            if (lane == 0) st_release_u64(tiles, (2ull << 32) | total);
+        } else {
+            if (lane == 0) st_release_u64(tiles + t, (1ull << 32) | total);
+            // the warp reads 32 tiles at once, nearest first (lane l: tile p0 - l);
+            // before tile 0 counts as an inclusive prefix of 0
+            for (int64_t p0 = t - 1;; p0 -= 32) {
+                const int64_t p = p0 - lane;
+                unsigned long long x = 2ull << 32;
+                if (p >= 0) {
+                    x = ld_acquire_u64(tiles + p);
+                    for (int spin = 0; (x >> 32) == 0 && spin < kLookbackSpins; ++spin) x = ld_acquire_u64(tiles + p);
+                    if ((x >> 32) == 0) {
+                        set_flag(flag, LSK_FLAG_TIMEOUT);
+                        x = 2ull << 32;
+                    }
+                }
+                const unsigned incl_lanes = __ballot_sync(0xffffffffu, (x >> 32) == 2);
+                const int stop = incl_lanes ? __ffs(incl_lanes) - 1 : 31;   // the nearest inclusive prefix
+                uint32_t val = lane <= stop ? (uint32_t)x : 0u;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += y;
+                for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                prefix += val;
+                if (incl_lanes) break;
             }
-            wsum[lane] = xi - x;
-            if (lane == 31) carry_s = xi;
+            if (lane == 0) st_release_u64(tiles + t, (2ull << 32) | (prefix + total));
         }
-        __syncthreads();
-        uint32_t acc = carry + wsum[w] + incl - run;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (i0 + q < len) out[i0 + q] = acc;
-            acc += v[q];
+        if (lane == 0) {
+            s_prefix = prefix;
+            if ((t + 1) * kScanTile >= len) off[len] = prefix + total;   // the last tile: the total
         }
-        carry += carry_s;
-        __syncthreads();   // wsum / carry_s are rewritten next round
     }
-    if (threadIdx.x == 0) out[len] = carry;
+    __syncthreads();
+    const uint32_t excl = s_prefix + warp_tot[wid] + incl - run;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const int64_t i = base + q;
+        if (i < len) {
+            off[i] = v[q] + excl;
+            if (cursor) cursor[i] = v[q] + excl;
+        }
+    }
 }
 
 // ---- dense gather ---------------------------------------------------------
@@ -518,10 +572,32 @@ inline unsigned grid_for(int64_t items, int threads, int sm_count, int per_sm = 
 
 }  // namespace
 
-size_t cs_workspace_bytes(int64_t n, int64_t r) {
-    return ws_round((size_t)(r + 1) * 4) * 4 + ws_round((size_t)(n > 0 ? n : 1) * 4) +
-           ws_round(scan_tmp_words(r) * 4) + 4096;
+// the look-back scan's ticket and tile words
+size_t scan_state_words(int64_t len) { return (size_t)((len + kScanTile - 1) / kScanTile) + 1; }
+
+// The CountSketch workspace, in this order: the counters and the scan's
+// state (zeroed by one memset), the bucket offsets, the cursors, the
+// permutation, the multi-level scan's scratch, the compaction positions.
+struct CsWs {
+    uint32_t *cnt, *off, *cursor, *perm, *tmp, *cpos;
+    unsigned long long* state;
+    size_t bytes;
+};
+CsWs cs_carve(void* ws, int64_t n, int64_t r) {
+    WsCarver wc{(char*)ws, 0};
+    CsWs w{};
+    w.cnt = wc.take<uint32_t>(r + 1);
+    w.state = wc.take<unsigned long long>(scan_state_words(r));
+    w.off = wc.take<uint32_t>(r + 1);
+    w.cursor = wc.take<uint32_t>(r + 1);
+    w.perm = wc.take<uint32_t>(n > 0 ? (size_t)n : 1);
+    w.tmp = wc.take<uint32_t>(scan_tmp_words(r));
+    w.cpos = wc.take<uint32_t>(r + 1);
+    w.bytes = ws_round(wc.off) + 256;
+    return w;
 }
+
+size_t cs_workspace_bytes(int64_t n, int64_t r) { return cs_carve(nullptr, n, r).bytes; }
 
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st) {
@@ -535,31 +611,21 @@ cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket,
 // and *perm_out (n entries, local row indices) point into ws; the launches
 // are queued on st.  Row i is hashed as column row0 + i of S.
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
-                           const uint32_t** off_out, const uint32_t** perm_out, uint64_t row0) {
+                           const uint32_t** off_out, const uint32_t** perm_out, uint64_t row0, int* flag) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    WsCarver wc{(char*)ws, 0};
-    uint32_t* cnt = wc.take<uint32_t>(r + 1);
-    uint32_t* off = wc.take<uint32_t>(r + 1);
-    uint32_t* cursor = wc.take<uint32_t>(r + 1);
-    uint32_t* perm = wc.take<uint32_t>(n > 0 ? n : 1);
-    uint32_t* tmp = wc.take<uint32_t>(scan_tmp_words(r));
-    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)r * 4, st);
+    const CsWs w = cs_carve(ws, n, r);
+    // the counters and the scan's state are contiguous: one memset
+    cudaError_t e =
+        cudaMemsetAsync(w.cnt, 0, (size_t)((char*)(w.state + scan_state_words(r)) - (char*)w.cnt), st);
     if (e != cudaSuccess) return e;
-    if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, cnt);
-    if (r <= 16384) {
-        LSK_PROF("cs_scan", st) scan_one_block_kernel<<<1, 1024, 0, st>>>(cnt, off, r);
-    } else {
-        e = exclusive_scan(cnt, off, r, tmp, st);   // its launches are profiled one by one
-        if (e != cudaSuccess) return e;
-        LSK_PROF("cs_scan", st) write_total_kernel<<<1, 1, 0, st>>>(off, r, (uint32_t)n);
-    }
+    if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, w.cnt);
+    const unsigned tiles = (unsigned)((r + kScanTile - 1) / kScanTile);
+    LSK_PROF("cs_scan", st) scan_lookback_kernel<<<tiles, kScanBlock, 0, st>>>(w.cnt, w.off, w.cursor, r, w.state, flag);
     if (n > 0) {
-        e = cudaMemcpyAsync(cursor, off, (size_t)r * 4, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return e;
-        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, cursor, perm);
+        LSK_PROF("cs_place", st) cs_place_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, w.cursor, w.perm);
     }
-    *off_out = off;
-    *perm_out = perm;
+    *off_out = w.off;
+    *perm_out = w.perm;
     return cudaGetLastError();
 }
 
@@ -569,19 +635,12 @@ cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, voi
     const int64_t n = A->n;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
-    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0);
+    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0, flag);
     if (e != cudaSuccess) return e;
     const bool compact = cidx != nullptr && ccount != nullptr && !accumulate;
     uint32_t* cpos = nullptr;
     if (compact) {
-        // after cs_prep_launch's carve: cnt, off, cursor, perm, scan tmp
-        WsCarver wc{(char*)ws, 0};
-        wc.take<uint32_t>(r + 1);
-        wc.take<uint32_t>(r + 1);
-        wc.take<uint32_t>(r + 1);
-        wc.take<uint32_t>(n > 0 ? n : 1);
-        wc.take<uint32_t>(scan_tmp_words(r));
-        cpos = wc.take<uint32_t>(r + 1);
+        cpos = cs_carve(ws, n, r).cpos;
         LSK_PROF("cs_compact", st) cs_compact_kernel<<<1, 1024, 0, st>>>(off, r, cpos, cidx, ccount);
     }
     return cs_gather_launch(A, r, off, perm, cpos, SA, flag, sm_count, st, accumulate);
