@@ -25,6 +25,9 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblsk.so")
 
+# prec: "fp32" FP32 accuracy; "bf16" tensor cores (bf16 G, split-bf16
+# operands); "tf32" the bf16 mode with the row-norm GEMM A B as one TF32
+# product (A rounded to the nearest TF32 by the copy engine)
 PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2
 _PRECS = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16}
 
@@ -285,9 +288,9 @@ def set_fused_sketch(mode):
 
 def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):
     """alpha A^T A + beta C (d x d float32, C updated in place if given).
-    prec: "fp32" (lsk_gram_prec FP32: CUDA-core FP32), "bf16" (lsk_gram_prec
-    BF16: tensor-core products of a bf16 split), None (lsk_gram: the tensor
-    cores for dense d <= 256, else FP32)."""
+    prec: "fp32" (lsk_gram_prec FP32: CUDA-core FP32), "bf16" or "tf32"
+    (lsk_gram_prec BF16: tensor-core products of a bf16 split), None
+    (lsk_gram: the tensor cores for dense d <= 256, else FP32)."""
     m, n, d = _mat(A)
     ctx = ctx or context(_dev(A).index)
     if C is None:
@@ -301,7 +304,10 @@ def gram(A, alpha=1.0, beta=0.0, C=None, prec="fp32", ctx=None):
 
 
 def rownorms_prod(A, B, alpha=1.0, beta=0.0, x=None, upper_triangular=False, prec="fp32", ctx=None):
-    """lsk_rownorms_prod: alpha ||A_i B||^2 + beta x_i (n float32)."""
+    """lsk_rownorms_prod: alpha ||A_i B||^2 + beta x_i (n float32).  prec:
+    "fp32" CUDA cores; "bf16" BF16x3 on the tensor cores; "tf32" one TF32
+    product on the tensor cores (dense A with 32 <= d <= 256, rows 16-byte
+    aligned, n >= 256; other shapes take the BF16x3 or FP32 form)."""
     m, n, d = _mat(A)
     _check_cuda(B)
     B = B.contiguous()

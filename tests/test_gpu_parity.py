@@ -87,8 +87,12 @@ def test_gaussian_bf16_rounding_agrees(lsk):
 
 # ---------------------------------------------------------------- S * A ----
 @pytest.mark.parametrize("n,d,r", [(20_011, 50, 2500), (9_000, 256, 700), (4_099, 130, 5000),
-                                   (3_000, 3, 1), (1_000, 1, 7), (2_500, 64, 40_000)])
+                                   (3_000, 3, 1), (1_000, 1, 7), (2_500, 64, 40_000),
+                                   (300_000, 4, 81_925), (200_003, 4, 1_000_003)])
 def test_cs_sketch_dense_integer_bit_exact(lsk, n, d, r):
+    """Exact on integer data; the last two cases span 41 and 489 tiles of
+    the bucket-offset scan, so its look-back reads more than one window of 32
+    tiles (r not a multiple of the 2,048-counter tile, r > n)."""
     A = workloads.integer_dense(n, d, seed=n + d)
     SA = host(lsk.cs_sketch(dev(A), r, seed=11))
     ref = ocs.cs_sketch_dense(A, r, 11)
