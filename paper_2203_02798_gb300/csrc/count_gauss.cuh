@@ -10,7 +10,7 @@
 // have run.
 // A bounded wait of the scan that runs out sets LSK_FLAG_TIMEOUT in *flag.
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
-                           const uint32_t** off, const uint32_t** perm, uint64_t row0, int* flag);
+                           const uint32_t** off, const uint32_t** perm, uint64_t row0, int* flag, bool rx = true);
 
 // out[e] = the slice-order compensated sum of part[z * len + e], z < slices.
 cudaError_t gauss_tc_reduce_launch(const float* part, int slices, int64_t len, float* out, int sm_count,

@@ -258,6 +258,200 @@ __global__ void __launch_bounds__(kScanBlock) scan_lookback_kernel(const uint32_
     }
 }
 
+// ---- two-level counting sort of the rows by bucket --------------------------
+// The permutation of count / scan / place with the per-row atomics in shared
+// memory instead of L2, and every write coalesced: bucket b splits into
+// coarse c = b >> shift and fine f = b & (F - 1).  (1) block k hashes its
+// chunk of rows, keeps (bucket | sign) per row and counts its rows per
+// coarse bucket in shared memory; (2) the counts, laid out coarse bucket by
+// coarse bucket and block by block, are scanned in place (the look-back
+// scan): each block's offset inside each coarse bucket; (3) each block sorts
+// its chunk by coarse bucket in shared memory and writes each coarse bucket's
+// run contiguously (row | sign, and f); (4) block c counts coarse bucket c's
+// rows per fine bucket, scans the counts (the offsets of its F buckets),
+// sorts the rows by fine bucket in shared memory and writes them
+// contiguously.  F makes a coarse bucket ~kRxRowsPerCoarse rows on average.
+constexpr int kRxThreads = 512;
+constexpr int64_t kRxMaxFine = 4096;
+constexpr int64_t kRxMaxCoarse = 2048;
+constexpr int64_t kRxRowsPerCoarse = 8192;
+constexpr int64_t kRxChunk = 16384;        // rows a block sorts in shared memory (step 3)
+constexpr int64_t kRxStage = 16384;        // rows of a coarse bucket sorted in shared memory (step 4)
+struct RxPlan {
+    int64_t F, B, chunk;
+    int shift, nct;
+};
+bool rx_plan(int64_t n, int64_t r, RxPlan& q) {
+    if (n <= 0 || n >= ((int64_t)1 << 31) || r < 1) return false;
+    int64_t F = 1;
+    int sh = 0;
+    while (F < kRxMaxFine && n * (F * 2) <= kRxRowsPerCoarse * r) {
+        F *= 2;
+        ++sh;
+    }
+    if (n * F > 2 * kRxRowsPerCoarse * r) return false;   // few buckets for many rows: the atomic form
+    const int64_t B = (r + F - 1) / F;
+    if (B > kRxMaxCoarse) return false;
+    int64_t nct = (n + kRxChunk - 1) / kRxChunk;
+    if (nct < 256) nct = 256;
+    if (B * nct > ((int64_t)1 << 24)) return false;
+    q.F = F;
+    q.B = B;
+    q.shift = sh;
+    q.nct = (int)nct;
+    q.chunk = (n + nct - 1) / nct;
+    return true;
+}
+size_t rx_scatter_smem(const RxPlan& q) { return (size_t)q.B * 12 + 16 + (size_t)q.chunk * 8; }
+size_t rx_fine_smem(const RxPlan& q) { return (size_t)q.F * 4 + (size_t)kRxStage * 4; }
+
+// block-wide exclusive scan of cnt[0 .. len) in shared memory (len <=
+// 8 kRxThreads), in place; `tot` receives the total
+__device__ __forceinline__ void rx_block_scan(uint32_t* cnt, int len, uint32_t* wsum, uint32_t& tot) {
+    const int per = (len + kRxThreads - 1) / kRxThreads;
+    const int lo = (int)threadIdx.x * per, hi = min(len, lo + per);
+    uint32_t run = 0;
+    for (int i = lo; i < hi; ++i) run += cnt[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t x = lane < kRxThreads / 32 ? wsum[lane] : 0u;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < kRxThreads / 32) wsum[lane] = xi - x;
+        if (lane == 31) wsum[kRxThreads / 32] = xi;
+    }
+    __syncthreads();
+    uint32_t acc = wsum[w] + incl - run;
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t c = cnt[i];
+        cnt[i] = acc;
+        acc += c;
+    }
+    tot = wsum[kRxThreads / 32];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kRxThreads) rx_count_kernel(int64_t n, uint64_t row0, uint32_t r, uint32_t k0,
+                                                              uint32_t k1, RxPlan q, uint32_t* __restrict__ bsign,
+                                                              uint32_t* __restrict__ H, unsigned long long* hstate,
+                                                              int hstate_words) {
+    extern __shared__ uint32_t hs[];
+    if (blockIdx.x == 0)   // the scan's state, zeroed for the next launch
+        for (int j = threadIdx.x; j < hstate_words; j += blockDim.x) hstate[j] = 0ull;
+    for (int64_t c = threadIdx.x; c < q.B; c += blockDim.x) hs[c] = 0u;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * q.chunk, i1 = min(n, i0 + q.chunk);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += (int64_t)kPrepRows * kRxThreads) {
+        uint32_t b[kPrepRows], neg[kPrepRows];
+#pragma unroll
+        for (int u = 0; u < kPrepRows; ++u)
+            if (i + u * kRxThreads < i1) cs_hash(row0 + (uint64_t)(i + u * kRxThreads), r, k0, k1, b[u], neg[u]);
+#pragma unroll
+        for (int u = 0; u < kPrepRows; ++u) {
+            if (i + u * kRxThreads < i1) {
+                bsign[i + u * kRxThreads] = b[u] | (neg[u] << 31);
+                atomicAdd(&hs[b[u] >> q.shift], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < q.B; c += blockDim.x) H[c * q.nct + blockIdx.x] = hs[c];
+}
+
+// step 3: shared memory holds the global base and the local offset (then the
+// cursor) of every coarse bucket, and the chunk sorted by coarse bucket as
+// (row | sign, fine | coarse << 16)
+__global__ void __launch_bounds__(kRxThreads) rx_scatter_kernel(int64_t n, RxPlan q,
+                                                                const uint32_t* __restrict__ bsign,
+                                                                const uint32_t* __restrict__ base,
+                                                                uint32_t* __restrict__ T, uint16_t* __restrict__ TF) {
+    extern __shared__ uint32_t sm[];
+    __shared__ uint32_t wsum[kRxThreads / 32 + 1];
+    uint32_t* hb = sm;                 // [B] global start of this block's run in coarse bucket c
+    uint32_t* lo = sm + q.B;           // [B] local start of coarse bucket c in the sorted chunk
+    uint32_t* cur = sm + 2 * q.B;      // [B] cursor
+    uint2* stage = reinterpret_cast<uint2*>(sm + ((3 * q.B + 3) & ~(int64_t)1));
+    for (int64_t c = threadIdx.x; c < q.B; c += blockDim.x) {
+        const int64_t idx = c * q.nct + blockIdx.x;
+        const uint32_t b0 = __ldg(base + idx);
+        hb[c] = b0;
+        lo[c] = __ldg(base + idx + 1) - b0;   // this block's rows in coarse bucket c
+    }
+    __syncthreads();
+    uint32_t tot;
+    rx_block_scan(lo, (int)q.B, wsum, tot);
+    for (int64_t c = threadIdx.x; c < q.B; c += blockDim.x) cur[c] = lo[c];
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * q.chunk, i1 = min(n, i0 + q.chunk);
+    const uint32_t fmask = (uint32_t)q.F - 1u;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kRxThreads) {
+        const uint32_t v = __ldg(bsign + i);
+        const uint32_t b = v & 0x7fffffffu, c = b >> q.shift;
+        const uint32_t p = atomicAdd(&cur[c], 1u);
+        stage[p] = make_uint2((uint32_t)i | (v & 0x80000000u), (b & fmask) | (c << 16));
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < tot; p += kRxThreads) {
+        const uint2 e = stage[p];
+        const uint32_t c = e.y >> 16;
+        const uint32_t g = hb[c] + (p - lo[c]);
+        T[g] = e.x;
+        TF[g] = (uint16_t)(e.y & 0xffffu);
+    }
+}
+
+// step 4: block c, rows [s, e) of coarse bucket c
+__global__ void __launch_bounds__(kRxThreads) rx_fine_kernel(int64_t n, int64_t r, RxPlan q,
+                                                             const uint32_t* __restrict__ base,
+                                                             const uint32_t* __restrict__ T,
+                                                             const uint16_t* __restrict__ TF,
+                                                             uint32_t* __restrict__ perm, uint32_t* __restrict__ off) {
+    extern __shared__ uint32_t fc[];   // [F] counts, then starts; then the staged rows
+    __shared__ uint32_t wsum[kRxThreads / 32 + 1];
+    uint32_t* stage = fc + q.F;
+    const int64_t c = blockIdx.x;
+    const uint32_t s = __ldg(base + c * q.nct);
+    const uint32_t e = (c + 1 < q.B) ? __ldg(base + (c + 1) * q.nct) : (uint32_t)n;
+    for (int f = threadIdx.x; f < (int)q.F; f += kRxThreads) fc[f] = 0u;
+    __syncthreads();
+    for (uint32_t i = s + threadIdx.x; i < e; i += kRxThreads) atomicAdd(&fc[__ldg(TF + i)], 1u);
+    __syncthreads();
+    uint32_t tot;
+    rx_block_scan(fc, (int)q.F, wsum, tot);
+    for (int f = threadIdx.x; f < (int)q.F; f += kRxThreads) {
+        const int64_t b = c * q.F + f;
+        if (b < r) off[b] = s + fc[f];
+    }
+    if (c == q.B - 1 && threadIdx.x == 0) off[r] = (uint32_t)n;
+    __syncthreads();
+    if (e - s <= (uint32_t)kRxStage) {
+        // sorted in shared memory, then written contiguously
+        for (uint32_t i = s + threadIdx.x; i < e; i += kRxThreads) {
+            const uint32_t p = atomicAdd(&fc[__ldg(TF + i)], 1u);
+            stage[p] = __ldg(T + i);
+        }
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < e - s; p += kRxThreads) perm[s + p] = stage[p];
+    } else {
+        for (uint32_t i = s + threadIdx.x; i < e; i += kRxThreads) {
+            const uint32_t p = atomicAdd(&fc[__ldg(TF + i)], 1u);
+            perm[s + p] = __ldg(T + i);
+        }
+    }
+}
+
 // ---- dense gather ---------------------------------------------------------
 // One warp per bucket part.  Lanes own VEC consecutive columns in each of U
 // column groups of 32*VEC; the rows are fetched kBatch at a time so that
@@ -577,27 +771,47 @@ size_t scan_state_words(int64_t len) { return (size_t)((len + kScanTile - 1) / k
 
 // The CountSketch workspace, in this order: the counters and the scan's
 // state (zeroed by one memset), the bucket offsets, the cursors, the
-// permutation, the multi-level scan's scratch, the compaction positions.
+// permutation, the multi-level scan's scratch, the compaction positions;
+// then, for the two-level sort, the per-row (bucket | sign), the rows
+// grouped by coarse bucket with their fine indices, the per-block counts
+// (scanned in place) and their scan state.
 struct CsWs {
     uint32_t *cnt, *off, *cursor, *perm, *tmp, *cpos;
     unsigned long long* state;
+    uint32_t *bsign, *T, *H;
+    uint16_t* TF;
+    unsigned long long* hstate;
+    int hstate_words;
     size_t bytes;
 };
-CsWs cs_carve(void* ws, int64_t n, int64_t r) {
+CsWs cs_carve(void* ws, int64_t n, int64_t r, const RxPlan* q) {
     WsCarver wc{(char*)ws, 0};
     CsWs w{};
+    const size_t nn = n > 0 ? (size_t)n : 1;
     w.cnt = wc.take<uint32_t>(r + 1);
     w.state = wc.take<unsigned long long>(scan_state_words(r));
     w.off = wc.take<uint32_t>(r + 1);
     w.cursor = wc.take<uint32_t>(r + 1);
-    w.perm = wc.take<uint32_t>(n > 0 ? (size_t)n : 1);
+    w.perm = wc.take<uint32_t>(nn);
     w.tmp = wc.take<uint32_t>(scan_tmp_words(r));
     w.cpos = wc.take<uint32_t>(r + 1);
+    if (q) {
+        w.bsign = wc.take<uint32_t>(nn);
+        w.T = wc.take<uint32_t>(nn);
+        w.TF = wc.take<uint16_t>(nn);
+        w.H = wc.take<uint32_t>((size_t)q->B * q->nct + 1);
+        w.hstate_words = (int)scan_state_words(q->B * q->nct);
+        w.hstate = wc.take<unsigned long long>((size_t)w.hstate_words);
+    }
     w.bytes = ws_round(wc.off) + 256;
     return w;
 }
 
-size_t cs_workspace_bytes(int64_t n, int64_t r) { return cs_carve(nullptr, n, r).bytes; }
+size_t cs_workspace_bytes(int64_t n, int64_t r) {
+    RxPlan q;
+    return cs_carve(nullptr, n, r, rx_plan(n, r, q) ? &q : nullptr).bytes;
+}
+size_t cs_workspace_bytes_atomic(int64_t n, int64_t r) { return cs_carve(nullptr, n, r, nullptr).bytes; }
 
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st) {
@@ -609,14 +823,34 @@ cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket,
 
 // Steps 1-3 (count, scan, place): on return *off_out (r + 1 entries, off[r] = n)
 // and *perm_out (n entries, local row indices) point into ws; the launches
-// are queued on st.  Row i is hashed as column row0 + i of S.
+// are queued on st.  Row i is hashed as column row0 + i of S.  rx: ws holds
+// cs_workspace_bytes (the two-level sort where its plan applies), else
+// cs_workspace_bytes_atomic (count / scan / place with L2 atomics).
 cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm_count, cudaStream_t st,
-                           const uint32_t** off_out, const uint32_t** perm_out, uint64_t row0, int* flag) {
+                           const uint32_t** off_out, const uint32_t** perm_out, uint64_t row0, int* flag, bool rx) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const CsWs w = cs_carve(ws, n, r);
+    RxPlan q;
+    const bool two_level = rx && rx_plan(n, r, q);
+    const CsWs w = cs_carve(ws, n, r, two_level ? &q : nullptr);
+    cudaError_t e;
+    if (two_level) {
+        if ((e = allow_dynamic_smem(rx_scatter_kernel)) != cudaSuccess) return e;
+        if ((e = allow_dynamic_smem(rx_fine_kernel)) != cudaSuccess) return e;
+        LSK_PROF("cs_count", st) rx_count_kernel<<<q.nct, kRxThreads, (size_t)q.B * 4, st>>>(
+            n, row0, (uint32_t)r, k0, k1, q, w.bsign, w.H, w.hstate, w.hstate_words);
+        const int64_t len = q.B * q.nct;
+        LSK_PROF("cs_scan", st) scan_lookback_kernel<<<(unsigned)((len + kScanTile - 1) / kScanTile), kScanBlock, 0,
+                                                       st>>>(w.H, w.H, nullptr, len, w.hstate, flag);
+        LSK_PROF("cs_place", st) rx_scatter_kernel<<<q.nct, kRxThreads, rx_scatter_smem(q), st>>>(n, q, w.bsign, w.H,
+                                                                                                  w.T, w.TF);
+        LSK_PROF("cs_fine", st) rx_fine_kernel<<<(unsigned)q.B, kRxThreads, rx_fine_smem(q), st>>>(n, r, q, w.H, w.T,
+                                                                                                   w.TF, w.perm, w.off);
+        *off_out = w.off;
+        *perm_out = w.perm;
+        return cudaGetLastError();
+    }
     // the counters and the scan's state are contiguous: one memset
-    cudaError_t e =
-        cudaMemsetAsync(w.cnt, 0, (size_t)((char*)(w.state + scan_state_words(r)) - (char*)w.cnt), st);
+    e = cudaMemsetAsync(w.cnt, 0, (size_t)((char*)(w.state + scan_state_words(r)) - (char*)w.cnt), st);
     if (e != cudaSuccess) return e;
     if (n > 0) LSK_PROF("cs_count", st) cs_count_kernel<<<grid_for(n, 256, sm_count), 256, 0, st>>>(n, row0, (uint32_t)r, k0, k1, w.cnt);
     const unsigned tiles = (unsigned)((r + kScanTile - 1) / kScanTile);
@@ -631,16 +865,16 @@ cudaError_t cs_prep_launch(int64_t n, int64_t r, uint64_t seed, void* ws, int sm
 
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws, int* flag,
                       int sm_count, cudaStream_t st, uint64_t row0, bool accumulate, uint32_t* cidx,
-                      uint32_t* ccount) {
+                      uint32_t* ccount, bool rx) {
     const int64_t n = A->n;
     const uint32_t* off = nullptr;
     const uint32_t* perm = nullptr;
-    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0, flag);
+    cudaError_t e = cs_prep_launch(n, r, seed, ws, sm_count, st, &off, &perm, row0, flag, rx);
     if (e != cudaSuccess) return e;
     const bool compact = cidx != nullptr && ccount != nullptr && !accumulate;
     uint32_t* cpos = nullptr;
     if (compact) {
-        cpos = cs_carve(ws, n, r).cpos;
+        cpos = cs_carve(ws, n, r, nullptr).cpos;   // the same place in either form
         LSK_PROF("cs_compact", st) cs_compact_kernel<<<1, 1024, 0, st>>>(off, r, cpos, cidx, ccount);
     }
     return cs_gather_launch(A, r, off, perm, cpos, SA, flag, sm_count, st, accumulate);

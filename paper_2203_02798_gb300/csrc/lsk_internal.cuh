@@ -177,7 +177,8 @@ __device__ __forceinline__ void set_flag(int* flag, int bit) {
 // internal launchers (all asynchronous on `st`)
 // ---------------------------------------------------------------------------
 // countsketch.cu
-size_t cs_workspace_bytes(int64_t n, int64_t r);
+size_t cs_workspace_bytes(int64_t n, int64_t r);          // with the two-level sort's scratch
+size_t cs_workspace_bytes_atomic(int64_t n, int64_t r);   // count / scan / place with L2 atomics only
 // row0: global index of A's first row (A is a block of rows of a larger matrix);
 // accumulate: SA += S A (SA holds a previous block's sketch) instead of SA = S A
 // cidx / ccount (both or neither): compact SA to the non-empty buckets in
@@ -185,7 +186,7 @@ size_t cs_workspace_bytes(int64_t n, int64_t r);
 // past it are left as they were); not with accumulate
 cudaError_t cs_launch(const lsk_mat* A, int64_t r, uint64_t seed, float* SA, void* ws,
                       int* flag, int sm_count, cudaStream_t st, uint64_t row0 = 0, bool accumulate = false,
-                      uint32_t* cidx = nullptr, uint32_t* ccount = nullptr);
+                      uint32_t* cidx = nullptr, uint32_t* ccount = nullptr, bool rx = true);
 cudaError_t cs_hash_launch(int64_t n, int64_t r, uint64_t seed, int32_t* bucket, int8_t* sign,
                            cudaStream_t st);
 // The gather step alone (S A from a prepared permutation: off[b] .. off[b+1]

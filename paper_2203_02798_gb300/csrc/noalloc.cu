@@ -58,7 +58,7 @@ int check_args(const lsk_mat* A, int64_t r, const float* SA) {
     }
     // the fixed capacity: rows, buckets, and the scratch they need together
     if (A->n > LSK_NOALLOC_MAX_ROWS || r > LSK_NOALLOC_MAX_BUCKETS) return LSK_ERR_UNSUPPORTED;
-    if (cs_workspace_bytes(A->n, r) > kNoallocScratchBytes) return LSK_ERR_UNSUPPORTED;
+    if (cs_workspace_bytes_atomic(A->n, r) > kNoallocScratchBytes) return LSK_ERR_UNSUPPORTED;
     return LSK_OK;
 }
 
@@ -103,7 +103,9 @@ extern "C" int lsk_cs_sketch_noalloc(const lsk_mat* A, int64_t r, uint64_t seed,
     if (rc) return rc;
     // CSR entries out of range are skipped by the kernels; with no context
     // there is no flag to report them through (flag = NULL).
-    cudaError_t e = cs_launch(A, r, seed, SA, slot->scratch, nullptr, slot->sm_count, (cudaStream_t)stream);
+    // the atomic form, whose scratch the fixed capacity is sized for
+    cudaError_t e = cs_launch(A, r, seed, SA, slot->scratch, nullptr, slot->sm_count, (cudaStream_t)stream, 0, false,
+                              nullptr, nullptr, false);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LSK_OK : LSK_ERR_CUDA;
 }
